@@ -1,0 +1,498 @@
+/*
+ * lst_oracle.c -- plain, slow, single-threaded CPU reference of the LST hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. It shares no code, header or constant with
+ * the CUDA library; both receive the same detector, module map, hits, cut parameters
+ * and network weights as inputs.
+ *
+ * What it computes (arXiv 2403.13166, Section 1, Table 1 steps 1-4, and Section 2-3 for
+ * the T5-DNN):
+ *   step 1  mini-doublets (MD): two hits in one pT-module (one per sensor) that pass the
+ *           MD cuts (the pT > 0.8 GeV requirement and the luminous-region road);
+ *   step 2  line segments (LS): two MDs in modules linked by the module map
+ *           ("nearby modules that fulfill some geometric criteria") with consistent pT;
+ *   step 3  triplets (T3): two LSs sharing the common MD (outer MD of the first is the
+ *           inner MD of the second);
+ *   step 4  quintuplets (T5): two T3s sharing the common MD (last MD of the first is the
+ *           first MD of the second); the middle three MDs form the "bridge" T3;
+ *   score   38 input features -> Linear(38,32)+ReLU -> [Linear(32,32)+ReLU]* ->
+ *           Linear(32,1) -> sigmoid, binary-cross-entropy classifier (Section 2);
+ *           selected iff score >= working point (Section 3).
+ * The paper prints no cut formula; the cuts below are the project's specification of
+ * "consistency with a continuous, helical trajectory" (Section 1). Every cut is FP32,
+ * written with the parentheses of that specification and evaluated in that order; build
+ * with -ffp-contract=off so that no multiply-add is fused. Features and the network are
+ * FP64.
+ *
+ * Loops run in the plainest order: modules, then hit pairs; modules, then map targets,
+ * then MD pairs; LS pairs by common MD; T3 pairs by common MD. A brute-force mode drops
+ * the module indexing (all hit pairs of a module's two sensors from the raw hit list,
+ * all MD pairs in layer-adjacent modules, all LS/T3 pairs tested for the shared MD).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NFEAT 38
+#define NHID 32
+
+typedef struct {
+    float kappa_max, z_lum, hit_err, sensor_gap, t3_kappa_factor, t3_rz_tol, t5_kappa_rel,
+        t5_kappa_abs, t5_rz_tol, t5_chi2_max, hit_sigma, k_field, wp;
+} ocuts;
+
+typedef struct {
+    int32_t n_mod;
+    const int32_t *layer, *subdet, *side;
+    const int32_t *map_off, *map_tgt;
+} ogeom;
+
+typedef struct {
+    int32_t n_hidden;      /* hidden layers, 1..4, width 32 */
+    const double *w;       /* W0(32x38),b0(32),[Wh(32x32),bh(32)]*,Wout(32),bout(1) */
+} omlp;
+
+typedef struct {
+    int64_t n_md, n_ls, n_t3, n_t5;
+    int64_t pairs[4];                     /* candidate pairs tested per step */
+    int32_t *md_lo, *md_up, *md_mod;       /* original hit indices, module */
+    float *md_kappa;                       /* signed curvature estimate (0 for endcap) */
+    int32_t *ls_in, *ls_out;               /* MD indices */
+    float *ls_kappa;
+    int32_t *t3_ls1, *t3_ls2, *t3_md;      /* t3_md: [n][3] */
+    float *t3_kappa;
+    int32_t *t5_t3a, *t5_t3b, *t5_md;      /* t5_md: [n][5] */
+    double *t5_feat, *t5_score;            /* [n][38], [n] */
+    uint8_t *t5_sel;
+} oresult;
+
+/* ------------------------------------------------------------------ growable arrays */
+typedef struct { void *p; int64_t n, cap; size_t es; } vec;
+static void vinit(vec *v, size_t es) { v->p = NULL; v->n = 0; v->cap = 0; v->es = es; }
+static void *vpush(vec *v) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 1024;
+        v->p = realloc(v->p, (size_t)v->cap * v->es);
+    }
+    return (char *)v->p + (size_t)(v->n++) * v->es;
+}
+
+typedef struct { float x, y, z, r; } hit;
+typedef struct { int32_t lo, up, mod; float kappa; double kfeat; } md_t;
+typedef struct { int32_t in, out; float kappa; } ls_t;
+typedef struct { int32_t ls1, ls2, md[3]; float kappa; } t3_t;
+typedef struct { int32_t t3a, t3b, md[5]; } t5_t;
+
+static hit mkhit(const float *x, const float *y, const float *z, int32_t i) {
+    hit h;
+    h.x = x[i]; h.y = y[i]; h.z = z[i];
+    h.r = sqrtf(h.x * h.x + h.y * h.y);
+    return h;
+}
+
+/* ------------------------------------------------------------------ step 1: MD cuts */
+/* Lower hit L, upper hit U of one module. Returns 1 if the pair is a mini-doublet. */
+int oracle_md_cut(const float *Lp, const float *Up, int endcap, const ocuts *c, float *kappa)
+{
+    hit L = {Lp[0], Lp[1], Lp[2], Lp[3]}, U = {Up[0], Up[1], Up[2], Up[3]};
+    float dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
+    float dT = sqrtf(dx * dx + dy * dy);
+    float cr = L.x * dy - L.y * dx;
+    float dt = L.x * dx + L.y * dy;
+    float rL = L.r;
+    if (!endcap) {
+        if (!(dt > 0.0f)) return 0;                                       /* MD-dir */
+        float sa = cr / (rL * dT);
+        if (!(fabsf(sa) <= rL * (0.5f * c->kappa_max) + c->hit_err / c->sensor_gap))
+            return 0;                                                      /* MD-bend */
+        float dr = U.r - L.r;
+        if (!(fabsf(dz - (L.z / rL) * dr) <= (c->z_lum / rL) * dr + c->hit_err))
+            return 0;                                                      /* MD-z */
+        *kappa = 2.0f * sa / rL;
+        return 1;
+    }
+    if (!(dt > 0.0f && dz * L.z > 0.0f)) return 0;                        /* MD-dir */
+    float para = dt / rL, perp = cr / rL;
+    float azl = fabsf(L.z), adz = fabsf(dz);
+    float pe = adz * rL / azl;
+    if (!(fabsf(para - pe) <= adz * rL * c->z_lum / (azl * (azl - c->z_lum)) + c->hit_err))
+        return 0;                                                          /* MD-z */
+    float S = rL * (0.5f * c->kappa_max);
+    float T = S / sqrtf(1.0f - S * S);
+    if (!(fabsf(perp) <= para * T + c->hit_err)) return 0;                /* MD-bend */
+    *kappa = 0.0f;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ step 2: LS cuts */
+/* Anchors A (inner MD) and B (outer MD); kA/kB the MD curvatures, bA/bB barrel flags. */
+int oracle_ls_cut(const float *Ap, const float *Bp, float kA, float kB, int bA, int bB,
+                  const ocuts *c, float *kappa)
+{
+    float xa = Ap[0], ya = Ap[1], za = Ap[2], ra = Ap[3];
+    float xb = Bp[0], yb = Bp[1], zb = Bp[2], rb = Bp[3];
+    float e = c->hit_err;
+    if (!(fabsf(za * (rb - ra) - ra * (zb - za)) <= (c->z_lum + e) * fabsf(rb - ra) + e * ra))
+        return 0;                                                          /* LS-z0 */
+    float dx = xb - xa, dy = yb - ya;
+    float dT = sqrtf(dx * dx + dy * dy);
+    float cr = xa * dy - ya * dx;
+    float dt = xa * dx + ya * dy;
+    if (!(dt > 0.0f)) return 0;                                           /* LS-dir */
+    float sl = cr / (ra * dT);
+    if (!(fabsf(sl) <= rb * (0.5f * c->kappa_max) + e / dT)) return 0;    /* LS-bend */
+    float k = 2.0f * sl / rb;
+    if (bA && !(fabsf(kA - k) <= 2.0f * (e / c->sensor_gap) / ra + 2.0f * (e / dT) / rb))
+        return 0;                                                          /* LS-kappa, inner */
+    if (bB && !(fabsf(kB - k) <= 2.0f * (e / c->sensor_gap) / rb + 2.0f * (e / dT) / rb))
+        return 0;                                                          /* LS-kappa, outer */
+    *kappa = k;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ step 3: T3 cuts */
+int oracle_t3_cut(const float *P0, const float *P1, const float *P2, const ocuts *c,
+                  float *kappa)
+{
+    float x0 = P0[0], y0 = P0[1], z0 = P0[2];
+    float x1 = P1[0], y1 = P1[1], z1 = P1[2];
+    float x2 = P2[0], y2 = P2[1], z2 = P2[2];
+    float d01x = x1 - x0, d01y = y1 - y0;
+    float d12x = x2 - x1, d12y = y2 - y1;
+    float d02x = x2 - x0, d02y = y2 - y0;
+    float a = sqrtf(d01x * d01x + d01y * d01y);
+    float b = sqrtf(d12x * d12x + d12y * d12y);
+    float cc = sqrtf(d02x * d02x + d02y * d02y);
+    float cr = d01x * d02y - d01y * d02x;
+    float k3 = 2.0f * cr / (a * b * cc);
+    if (!(fabsf(k3) <= c->kappa_max * c->t3_kappa_factor)) return 0;      /* T3-pT */
+    float s01 = a * (1.0f + a * a * k3 * k3 / 24.0f);
+    float s12 = b * (1.0f + b * b * k3 * k3 / 24.0f);
+    float zp = z0 + (z2 - z0) * s01 / (s01 + s12);
+    if (!(fabsf(z1 - zp) <= c->t3_rz_tol)) return 0;                      /* T3-rz */
+    *kappa = k3;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ step 4: T5 cuts */
+/* P: the five anchors in chain order; ka/kb the curvatures of T3a=(0,1,2), T3b=(2,3,4). */
+int oracle_t5_cut(const float *P, float ka, float kb, const ocuts *c)
+{
+    if (!(ka * kb > 0.0f)) return 0;                                      /* T5-q */
+    if (!(fabsf(ka - kb) <= c->t5_kappa_rel * 0.5f * (fabsf(ka) + fabsf(kb)) + c->t5_kappa_abs))
+        return 0;                                                          /* T5-kappa */
+    float kbar = 0.5f * (ka + kb);
+    float S[5];
+    S[0] = 0.0f;
+    for (int i = 0; i < 4; i++) {
+        float dx = P[4 * (i + 1)] - P[4 * i], dy = P[4 * (i + 1) + 1] - P[4 * i + 1];
+        float d = sqrtf(dx * dx + dy * dy);
+        float s = d * (1.0f + d * d * kbar * kbar / 24.0f);
+        S[i + 1] = (i == 0) ? s : S[i] + s;
+    }
+    float z0 = P[2], z4 = P[18];
+    for (int j = 1; j <= 3; j++) {
+        float zj = P[4 * j + 2];
+        if (!(fabsf(zj - (z0 + (z4 - z0) * S[j] / S[4])) <= c->t5_rz_tol)) return 0;  /* T5-rz */
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------ features (FP64) */
+/* Signed three-point curvature 2*cross/(a*b*c) of transverse points (Menger curvature). */
+static double curv3(const double *p0, const double *p1, const double *p2)
+{
+    double ax = p1[0] - p0[0], ay = p1[1] - p0[1];
+    double bx = p2[0] - p1[0], by = p2[1] - p1[1];
+    double cx = p2[0] - p0[0], cy = p2[1] - p0[1];
+    double a = sqrt(ax * ax + ay * ay), b = sqrt(bx * bx + by * by), c = sqrt(cx * cx + cy * cy);
+    double cr = ax * cy - ay * cx;
+    return 2.0 * cr / (a * b * c);
+}
+
+/* |kappa| floor: radii above 1e7 cm are treated as 1e7 cm in the log features. */
+static double kabs(double k) { double a = fabs(k); return a < 1e-7 ? 1e-7 : a; }
+
+/* MD curvature estimate of a barrel MD in FP64 (same definition as the MD cut). */
+static double md_kappa_fp64(const double *L, const double *U)
+{
+    double dx = U[0] - L[0], dy = U[1] - L[1];
+    double dT = sqrt(dx * dx + dy * dy);
+    double rL = sqrt(L[0] * L[0] + L[1] * L[1]);
+    double cr = L[0] * dy - L[1] * dx;
+    double sa = cr / (rL * dT);
+    return 2.0 * sa / rL;
+}
+
+/* Section 2: pT and radius of each T3's circle, anchor (r, phi, z, eta, layer) plus the
+ * MD curvature estimate for each of the 5 MDs, T5 pT/eta/phi, bridge-T3 radius. */
+void oracle_t5_features(const double *anc /*[5][3]*/, const int32_t *layer /*[5]*/,
+                        const double *mdk /*[5] FP64 MD curvature, 0 endcap*/, double kf,
+                        double *f /*[38]*/)
+{
+    for (int i = 0; i < 5; i++) {
+        double x = anc[3 * i], y = anc[3 * i + 1], z = anc[3 * i + 2];
+        double r = sqrt(x * x + y * y);
+        f[6 * i + 0] = r / 100.0;
+        f[6 * i + 1] = atan2(y, x) / M_PI;
+        f[6 * i + 2] = z / 100.0;
+        f[6 * i + 3] = asinh(z / r) / 2.5;
+        f[6 * i + 4] = layer[i] / 11.0;
+        f[6 * i + 5] = 100.0 * mdk[i];
+    }
+    double ka = curv3(anc + 0, anc + 3, anc + 6);
+    double kb = curv3(anc + 6, anc + 9, anc + 12);
+    f[30] = log10(kf / kabs(ka));
+    f[31] = log10(1.0 / kabs(ka));
+    f[32] = log10(kf / kabs(kb));
+    f[33] = log10(1.0 / kabs(kb));
+    double k5 = curv3(anc + 0, anc + 6, anc + 12);
+    f[34] = log10(kf / kabs(k5));
+    double kbar = 0.5 * (ka + kb), S4 = 0.0;
+    for (int i = 0; i < 4; i++) {
+        double dx = anc[3 * (i + 1)] - anc[3 * i], dy = anc[3 * (i + 1) + 1] - anc[3 * i + 1];
+        double d = sqrt(dx * dx + dy * dy);
+        S4 += d * (1.0 + d * d * kbar * kbar / 24.0);
+    }
+    f[35] = asinh((anc[14] - anc[2]) / S4) / 2.5;
+    f[36] = atan2(anc[13] - anc[1], anc[12] - anc[0]) / M_PI;
+    double kbr = curv3(anc + 3, anc + 6, anc + 9);
+    f[37] = log10(1.0 / kabs(kbr));
+}
+
+/* Section 2: the T5-DNN forward pass, FP64, nested loops over the weight arrays. */
+double oracle_mlp(const omlp *m, const double *f)
+{
+    double h[NHID], t[NHID];
+    const double *w = m->w;
+    for (int o = 0; o < NHID; o++) {
+        double s = w[NHID * NFEAT + o];
+        for (int i = 0; i < NFEAT; i++) s += w[o * NFEAT + i] * f[i];
+        h[o] = s > 0.0 ? s : 0.0;
+    }
+    w += NHID * NFEAT + NHID;
+    for (int l = 1; l < m->n_hidden; l++) {
+        for (int o = 0; o < NHID; o++) {
+            double s = w[NHID * NHID + o];
+            for (int i = 0; i < NHID; i++) s += w[o * NHID + i] * h[i];
+            t[o] = s > 0.0 ? s : 0.0;
+        }
+        memcpy(h, t, sizeof h);
+        w += NHID * NHID + NHID;
+    }
+    double s = w[NHID];
+    for (int i = 0; i < NHID; i++) s += w[i] * h[i];
+    return 1.0 / (1.0 + exp(-s));
+}
+
+/* ------------------------------------------------------------------ event driver */
+static int layer_adjacent(int la, int sa, int lb, int sb)
+{
+    if (la <= 5 && lb == la + 1) return 1;          /* barrel l -> l+1 */
+    if (la <= 6 && lb == 7) return 1;               /* barrel -> first disk */
+    if (la >= 7 && la <= 10 && lb == la + 1 && sa == sb) return 1;  /* disk d -> d+1 */
+    return 0;
+}
+
+static void fill_md_anchor(const hit *H, float *a) { a[0] = H->x; a[1] = H->y; a[2] = H->z; a[3] = H->r; }
+
+int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
+               const int32_t *sensor, int64_t n_hits, const ocuts *c, const omlp *mlp,
+               int brute, oresult *out)
+{
+    memset(out, 0, sizeof *out);
+    int32_t nm = g->n_mod;
+    for (int64_t i = 0; i < n_hits; i++)
+        if (sensor[i] < 0 || sensor[i] >= 2 * nm || !isfinite(x[i]) || !isfinite(y[i]) || !isfinite(z[i]))
+            return 1;
+    hit *H = malloc(sizeof(hit) * (size_t)(n_hits ? n_hits : 1));
+    for (int64_t i = 0; i < n_hits; i++) H[i] = mkhit(x, y, z, (int32_t)i);
+
+    /* hits of each sensor, ascending original index (stable counting sort) */
+    int64_t ns = 2 * (int64_t)nm;
+    int64_t *soff = calloc((size_t)ns + 1, sizeof(int64_t));
+    int32_t *sidx = malloc(sizeof(int32_t) * (size_t)(n_hits ? n_hits : 1));
+    for (int64_t i = 0; i < n_hits; i++) soff[sensor[i] + 1]++;
+    for (int64_t s = 0; s < ns; s++) soff[s + 1] += soff[s];
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)ns);
+    memcpy(fill, soff, sizeof(int64_t) * (size_t)ns);
+    for (int64_t i = 0; i < n_hits; i++) sidx[fill[sensor[i]]++] = (int32_t)i;
+    free(fill);
+
+    /* ---- step 1: mini-doublets, module by module ---- */
+    vec mds; vinit(&mds, sizeof(md_t));
+    int64_t *mdoff = calloc((size_t)nm + 1, sizeof(int64_t));
+    for (int32_t m = 0; m < nm; m++) {
+        int endcap = g->subdet[m] != 0;
+        if (!brute) {
+            for (int64_t a = soff[2 * m]; a < soff[2 * m + 1]; a++)
+                for (int64_t b = soff[2 * m + 1]; b < soff[2 * m + 2]; b++) {
+                    out->pairs[0]++;
+                    float L[4], U[4], k;
+                    fill_md_anchor(&H[sidx[a]], L);
+                    fill_md_anchor(&H[sidx[b]], U);
+                    if (oracle_md_cut(L, U, endcap, c, &k)) {
+                        md_t *d = vpush(&mds);
+                        d->lo = sidx[a]; d->up = sidx[b]; d->mod = m; d->kappa = k;
+                    }
+                }
+        } else {
+            for (int64_t i = 0; i < n_hits; i++) {
+                if (sensor[i] != 2 * m) continue;
+                for (int64_t j = 0; j < n_hits; j++) {
+                    if (sensor[j] != 2 * m + 1) continue;
+                    out->pairs[0]++;
+                    float L[4], U[4], k;
+                    fill_md_anchor(&H[i], L);
+                    fill_md_anchor(&H[j], U);
+                    if (oracle_md_cut(L, U, endcap, c, &k)) {
+                        md_t *d = vpush(&mds);
+                        d->lo = (int32_t)i; d->up = (int32_t)j; d->mod = m; d->kappa = k;
+                    }
+                }
+            }
+        }
+        mdoff[m + 1] = mds.n;
+    }
+    md_t *MD = mds.p;
+    for (int64_t i = 0; i < mds.n; i++) {
+        if (g->subdet[MD[i].mod] != 0) { MD[i].kfeat = 0.0; continue; }
+        double L[2] = {x[MD[i].lo], y[MD[i].lo]}, U[2] = {x[MD[i].up], y[MD[i].up]};
+        MD[i].kfeat = md_kappa_fp64(L, U);
+    }
+
+    /* ---- step 2: line segments, MD pairs across linked modules ---- */
+    vec lss; vinit(&lss, sizeof(ls_t));
+    for (int32_t m = 0; m < nm; m++) {
+        for (int64_t i = mdoff[m]; i < mdoff[m + 1]; i++) {
+            float A[4]; fill_md_anchor(&H[MD[i].lo], A);
+            int bA = g->subdet[m] == 0;
+            if (!brute) {
+                for (int32_t t = g->map_off[m]; t < g->map_off[m + 1]; t++) {
+                    int32_t mt = g->map_tgt[t];
+                    for (int64_t j = mdoff[mt]; j < mdoff[mt + 1]; j++) {
+                        out->pairs[1]++;
+                        float B[4], k; fill_md_anchor(&H[MD[j].lo], B);
+                        if (oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k)) {
+                            ls_t *s = vpush(&lss); s->in = (int32_t)i; s->out = (int32_t)j; s->kappa = k;
+                        }
+                    }
+                }
+            } else {
+                for (int64_t j = 0; j < mds.n; j++) {
+                    int32_t mt = MD[j].mod;
+                    if (!layer_adjacent(g->layer[m], g->side[m], g->layer[mt], g->side[mt])) continue;
+                    out->pairs[1]++;
+                    float B[4], k; fill_md_anchor(&H[MD[j].lo], B);
+                    if (oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k)) {
+                        ls_t *s = vpush(&lss); s->in = (int32_t)i; s->out = (int32_t)j; s->kappa = k;
+                    }
+                }
+            }
+        }
+    }
+    ls_t *LS = lss.p;
+    /* LS list of every MD as inner MD (LSs are already ordered by inner MD) */
+    int64_t *lsoff = calloc((size_t)mds.n + 1, sizeof(int64_t));
+    for (int64_t s = 0; s < lss.n; s++) lsoff[LS[s].in + 1]++;
+    for (int64_t i = 0; i < mds.n; i++) lsoff[i + 1] += lsoff[i];
+
+    /* ---- step 3: triplets, LS pairs sharing the middle MD ---- */
+    vec t3s; vinit(&t3s, sizeof(t3_t));
+    for (int64_t s1 = 0; s1 < lss.n; s1++) {
+        int64_t lo = brute ? 0 : lsoff[LS[s1].out], hi = brute ? lss.n : lsoff[LS[s1].out + 1];
+        for (int64_t s2 = lo; s2 < hi; s2++) {
+            if (LS[s2].in != LS[s1].out) continue;
+            out->pairs[2]++;
+            float P0[4], P1[4], P2[4], k;
+            fill_md_anchor(&H[MD[LS[s1].in].lo], P0);
+            fill_md_anchor(&H[MD[LS[s1].out].lo], P1);
+            fill_md_anchor(&H[MD[LS[s2].out].lo], P2);
+            if (oracle_t3_cut(P0, P1, P2, c, &k)) {
+                t3_t *t = vpush(&t3s);
+                t->ls1 = (int32_t)s1; t->ls2 = (int32_t)s2;
+                t->md[0] = LS[s1].in; t->md[1] = LS[s1].out; t->md[2] = LS[s2].out;
+                t->kappa = k;
+            }
+        }
+    }
+    t3_t *T3 = t3s.p;
+    /* T3 list of every MD as first MD (T3s are ordered by their first LS, hence first MD) */
+    int64_t *t3off = calloc((size_t)mds.n + 1, sizeof(int64_t));
+    for (int64_t t = 0; t < t3s.n; t++) t3off[T3[t].md[0] + 1]++;
+    for (int64_t i = 0; i < mds.n; i++) t3off[i + 1] += t3off[i];
+
+    /* ---- step 4: quintuplets, T3 pairs sharing the joint MD, then the score ---- */
+    vec t5s; vinit(&t5s, sizeof(t5_t));
+    for (int64_t a = 0; a < t3s.n; a++) {
+        int64_t lo = brute ? 0 : t3off[T3[a].md[2]], hi = brute ? t3s.n : t3off[T3[a].md[2] + 1];
+        for (int64_t b = lo; b < hi; b++) {
+            if (T3[b].md[0] != T3[a].md[2]) continue;
+            out->pairs[3]++;
+            int32_t md5[5] = {T3[a].md[0], T3[a].md[1], T3[a].md[2], T3[b].md[1], T3[b].md[2]};
+            float P[20];
+            for (int i = 0; i < 5; i++) fill_md_anchor(&H[MD[md5[i]].lo], P + 4 * i);
+            if (oracle_t5_cut(P, T3[a].kappa, T3[b].kappa, c)) {
+                t5_t *q = vpush(&t5s);
+                q->t3a = (int32_t)a; q->t3b = (int32_t)b;
+                memcpy(q->md, md5, sizeof md5);
+            }
+        }
+    }
+    t5_t *T5 = t5s.p;
+
+    /* ---- outputs ---- */
+    out->n_md = mds.n; out->n_ls = lss.n; out->n_t3 = t3s.n; out->n_t5 = t5s.n;
+    size_t nmd = (size_t)(mds.n ? mds.n : 1), nls = (size_t)(lss.n ? lss.n : 1);
+    size_t nt3 = (size_t)(t3s.n ? t3s.n : 1), nt5 = (size_t)(t5s.n ? t5s.n : 1);
+    out->md_lo = malloc(4 * nmd); out->md_up = malloc(4 * nmd); out->md_mod = malloc(4 * nmd);
+    out->md_kappa = malloc(4 * nmd);
+    for (int64_t i = 0; i < mds.n; i++) {
+        out->md_lo[i] = MD[i].lo; out->md_up[i] = MD[i].up; out->md_mod[i] = MD[i].mod;
+        out->md_kappa[i] = MD[i].kappa;
+    }
+    out->ls_in = malloc(4 * nls); out->ls_out = malloc(4 * nls); out->ls_kappa = malloc(4 * nls);
+    for (int64_t i = 0; i < lss.n; i++) {
+        out->ls_in[i] = LS[i].in; out->ls_out[i] = LS[i].out; out->ls_kappa[i] = LS[i].kappa;
+    }
+    out->t3_ls1 = malloc(4 * nt3); out->t3_ls2 = malloc(4 * nt3); out->t3_md = malloc(12 * nt3);
+    out->t3_kappa = malloc(4 * nt3);
+    for (int64_t i = 0; i < t3s.n; i++) {
+        out->t3_ls1[i] = T3[i].ls1; out->t3_ls2[i] = T3[i].ls2;
+        memcpy(out->t3_md + 3 * i, T3[i].md, 12); out->t3_kappa[i] = T3[i].kappa;
+    }
+    out->t5_t3a = malloc(4 * nt5); out->t5_t3b = malloc(4 * nt5); out->t5_md = malloc(20 * nt5);
+    out->t5_feat = malloc(sizeof(double) * NFEAT * nt5); out->t5_score = malloc(sizeof(double) * nt5);
+    out->t5_sel = malloc(nt5);
+    for (int64_t i = 0; i < t5s.n; i++) {
+        out->t5_t3a[i] = T5[i].t3a; out->t5_t3b[i] = T5[i].t3b;
+        memcpy(out->t5_md + 5 * i, T5[i].md, 20);
+        double anc[15], mdk[5];
+        int32_t lay[5];
+        for (int j = 0; j < 5; j++) {
+            const md_t *d = &MD[T5[i].md[j]];
+            anc[3 * j] = x[d->lo]; anc[3 * j + 1] = y[d->lo]; anc[3 * j + 2] = z[d->lo];
+            lay[j] = g->layer[d->mod];
+            mdk[j] = d->kfeat;
+        }
+        double *f = out->t5_feat + (size_t)NFEAT * i;
+        oracle_t5_features(anc, lay, mdk, (double)c->k_field, f);
+        double s = mlp ? oracle_mlp(mlp, f) : 0.0;
+        out->t5_score[i] = s;
+        out->t5_sel[i] = s >= (double)c->wp;
+    }
+    free(H); free(soff); free(sidx); free(mdoff); free(lsoff); free(t3off);
+    free(mds.p); free(lss.p); free(t3s.p); free(t5s.p);
+    return 0;
+}
+
+void oracle_free(oresult *r)
+{
+    void *ps[] = {r->md_lo, r->md_up, r->md_mod, r->md_kappa, r->ls_in, r->ls_out, r->ls_kappa,
+                  r->t3_ls1, r->t3_ls2, r->t3_md, r->t3_kappa, r->t5_t3a, r->t5_t3b, r->t5_md,
+                  r->t5_feat, r->t5_score, r->t5_sel};
+    for (size_t i = 0; i < sizeof ps / sizeof ps[0]; i++) free(ps[i]);
+    memset(r, 0, sizeof *r);
+}
