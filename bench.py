@@ -1,0 +1,428 @@
+"""Throughput benchmark of the LST hot path on PU200-like synthetic events.
+
+One step = one batch of B PU200-like events (the workload of a single HL-LHC-like event,
+many of them) through all stages: hit binning, mini-doublets, line segments, triplets,
+quintuplets and the T5-DNN score. The headline `value` is the batched path (one
+persistent launch per stage over the batch, replayed as a CUDA graph); `plain` is the
+same events one launch sequence per event; `e2e` is the batched path through the C-ABI
+with host (pinned) inputs and host outputs, copies inside the timed region.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun): events are independent, every rank takes its own events (no data
+exchange); only a barrier and a max over ranks of the elapsed time are collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PU200-like events/s on 1 GB300, plain vs batched+served; p50/p99 event latency"
+PILEUP = 200
+PER_VERTEX = 96          # particles per vertex: ~19k particles, ~250k hits per event
+L2_BYTES = 129 * 2 ** 20
+
+
+# ------------------------------------------------------------------ host-side workers (spawn)
+def _gen_event(args):
+    index, pileup, per_vertex, config = args
+    from paper_2403_13166_gb300 import synth
+    g = _geom()
+    e = synth.pileup_event(g, index, pileup=pileup, mean_per_vertex=per_vertex, config=config)
+    return index, e.x, e.y, e.z, e.sensor
+
+
+_GEOM = None
+
+
+def _geom():
+    global _GEOM
+    if _GEOM is None:
+        from paper_2403_13166_gb300 import synth
+        _GEOM = synth.build_geometry(True)
+    return _GEOM
+
+
+def _oracle_time(args):
+    """Oracle (as it stands) on one event; returns seconds of oracle time (generation excluded)."""
+    index, pileup, per_vertex, config, weights = args
+    import oracle
+    from paper_2403_13166_gb300 import synth
+    g = _geom()
+    e = synth.pileup_event(g, index, pileup=pileup, mean_per_vertex=per_vertex, config=config)
+    cuts = synth.default_cuts()
+    t0 = time.perf_counter()
+    r = oracle.run_event(g, e, cuts, weights, 2)
+    dt = time.perf_counter() - t0
+    return dt, r.counts["t5"]
+
+
+def _weights():
+    from paper_2403_13166_gb300 import synth, model_store
+    w = model_store.load_trained()
+    if w is not None:
+        return w["flat"], w["n_hidden"], w.get("wp"), "trained"
+    return synth.mlp_flat(synth.xavier_mlp()), 2, None, "xavier-seed2403"
+
+
+def cpu_baseline(pool, n_cores, events_per_core=2, config=2):
+    """Bounded sample: every core runs `events_per_core` oracle events (~1 s each)."""
+    flat, nh, _, _ = _weights()
+    jobs = [(10_000 + i, PILEUP, PER_VERTEX, config, flat) for i in range(n_cores * events_per_core)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_time, jobs, chunksize=events_per_core)
+    wall = time.perf_counter() - t0
+    times = [r[0] for r in res]
+    # per-core sums -> throughput with all cores busy, excluding the generator's time
+    per_core = [sum(times[i::n_cores]) for i in range(n_cores)]
+    value = len(times) / max(per_core)
+    return {"value": round(value, 3), "unit": "events/s", "cores": n_cores, "kind": "oracle",
+            "sample": f"{len(times)} PU200-like events ({events_per_core} per core, oracle time only, "
+                      f"{sum(times):.1f} s CPU, generation excluded)",
+            "value_1core": round(1.0 / statistics.mean(times), 3), "wall_s": round(wall, 2)}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.15)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def nvsmi_index(torch, dev, local_rank) -> str:
+    """nvidia-smi index of the torch device (matched by UUID), else the visible index."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid).lower()
+        out = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            i, uu = [x.strip() for x in line.split(",")]
+            if u and u in uu.lower():
+                return i
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[local_rank].strip().isdigit():
+        return vis.split(",")[local_rank].strip()
+    return str(local_rank)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank, pool):
+    import torch
+    from paper_2403_13166_gb300 import lst, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B = args.batch
+    # events of this rank (distinct seeds per rank)
+    idx = [rank * 100_000 + i for i in range(B)]
+    evs = pool.map(_gen_event, [(i, PILEUP, PER_VERTEX, 2) for i in idx])
+    n_hits = np.array([len(e[1]) for e in evs])
+    g = _geom()
+    flat, nh, wp, wname = _weights()
+    cuts = synth.default_cuts()
+    if wp is not None:
+        cuts["wp"] = np.float32(wp)
+    precision = lst.LST_BF16 if args.precision == "bf16" else lst.LST_FP32
+    ctx = lst.Context(local_rank, max_events=2 * B, precision=precision, use_graphs=1)
+    ctx.load_geometry(g, cuts, flat, nh)
+    if args.tune:
+        from paper_2403_13166_gb300 import autotune
+        autotune.apply_cached(ctx, g)
+    d_in = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in e[1:]] for e in evs]
+    stream = torch.cuda.current_stream(dev)
+
+    def sync_all():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def batched_step(inputs, prev):
+        hs = ctx.run_batch(inputs, stream)
+        if prev is not None:
+            for h in prev:
+                c = h.counts()
+                if c["status"] != lst.LST_OK:
+                    raise RuntimeError(f"event status {c['status']}")
+                h.release()
+        return hs
+
+    def drain(prev):
+        out = []
+        for h in prev or []:
+            out.append(h.counts())
+            h.release()
+        return out
+
+    # ---------------- batched (graph) path; warm-up captures the same (timed) graph
+    ctx.set_timing(True)
+    prev = None
+    for _ in range(args.warmup):
+        prev = batched_step(d_in, prev)
+    counts = drain(prev)
+    prev = None
+    ctx.set_timing(True)   # resets the stage statistics
+    gpu_id = nvsmi_index(torch, dev, local_rank)
+    sync_all()
+    with ClockSampler(gpu_id) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            prev = batched_step(d_in, prev)
+        drain(prev)
+        e1.record(stream)
+        sync_all()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, n_launch = ctx.stage_times()
+    ctx.set_timing(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    events_total = B * args.steps * world
+    value = events_total / (ms_total / 1000.0)
+
+    # ---------------- plain path: one launch sequence per event
+    plain = None
+    if not args.skip_plain:
+        n_plain = min(B, args.plain_events)
+        for i in range(min(3, n_plain)):
+            ctx.run_event(*d_in[i], stream=stream).release()
+        sync_all()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for i in range(n_plain):
+            ctx.run_event(*d_in[i], stream=stream).release()
+        p1.record(stream)
+        sync_all()
+        pms = p0.elapsed_time(p1)
+        plain = {"value": round(n_plain / (pms / 1000.0), 2), "unit": "events/s",
+                 "ms_per_event": round(pms / n_plain, 4), "events": n_plain,
+                 "gpu_launches_per_event": 10}
+
+    # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
+    h2d = int(sum(16 * n for n in n_hits))
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    for _ in range(2):
+        for h in ctx.run_batch(pinned, stream):
+            h.candidates(lst.LST_T5)
+            h.release()
+    sync_all()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hs = ctx.run_batch(pinned, stream)
+        for h in hs:
+            c = h.counts()
+            hits, score, sel = h.candidates(lst.LST_T5)
+            d2h += hits.nbytes + score.nbytes + sel.nbytes + 96
+            h.release()
+    sync_all()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(B * e2e_steps * world / e2e_s, 2), "unit": "events/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "steps": e2e_steps}
+
+    # ---------------- roofline of the dominant kernel
+    c0 = counts[0] if counts else {}
+    mean_counts = {k: float(np.mean([c[k] for c in counts])) for k in ("md", "ls", "t3", "t5")}
+    pairs = np.mean(np.array([c["pairs"] for c in counts], np.float64), axis=0)
+    names = ["bin", "md", "ls", "t3", "t5", "score"]
+    dom = int(np.argmax(stage_ms))
+    roofline = roofline_entry(names[dom], float(stage_ms[dom]), B, mean_counts, pairs, float(np.mean(n_hits)),
+                              clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
+    roofline["stage_ms_per_launch"] = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
+    roofline["launches_timed"] = int(n_launch)
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == lst.LST_FP32 else "f32+bf16",
+        "data": "synthetic",
+        "config": {"workload": "pu200_like_batched", "events_per_step": B, "pileup": PILEUP,
+                   "particles_per_vertex": PER_VERTEX, "hits_per_event_mean": int(np.mean(n_hits)),
+                   "modules": g.n_mod, "score_precision": args.precision, "weights": wname,
+                   "graphs": True, "l2": f"inputs larger than L2 ({int(h2d / 2**20)} MiB of hits per step)",
+                   "objects_per_event_mean": {k: int(v) for k, v in mean_counts.items()}},
+        "plain": plain,
+        "e2e": e2e,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "gpu_launches": 10 * args.steps,
+    }
+    ctx.close()
+    return line
+
+
+# algorithmic work per unit ("Roofline accounting")
+FP32_OPS_PER_PAIR = {"md": 6, "ls": 12, "t3": 16, "t5": 6}
+FP32_OPS_PER_OBJECT = {"md": 30, "ls": 35, "t3": 30, "t5": 40}
+
+
+def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if stage in ("md", "ls", "t3", "t5"):
+        k = ["md", "ls", "t3", "t5"].index(stage)
+        ops = B * (pairs[k] * FP32_OPS_PER_PAIR[stage] + counts[stage] * FP32_OPS_PER_OBJECT[stage])
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+        achieved = ops / (ms / 1000.0) / 1e12
+        return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": f"k_{stage}",
+                "peak_note": f"FP32 lanes x SM clock: {n_sm} SMs x 128 x {sm_mhz:.0f} MHz (non-FMA ops)"}
+    # score / bin: HBM bound
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if stage == "score":
+        by = B * counts["t5"] * (32 + 5 * (16 + 8 + 4) + 5)
+    else:
+        by = B * hits * (16 + 20 + 20)
+    achieved = by / (ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "kernel": f"k_{stage}",
+            "peak_note": "measured" if peaks else "fallback"}
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+def run_reference(args, pool, n_cores):
+    flat, nh, _, _ = _weights()
+    per_step = n_cores          # one event per core per step (~1 s of oracle work each)
+    jobs = lambda s: [(20_000 + s * per_step + i, PILEUP, PER_VERTEX, 2, flat) for i in range(per_step)]
+    for s in range(args.warmup):
+        pool.map(_oracle_time, jobs(s), chunksize=1)
+    busy = []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        res = pool.map(_oracle_time, jobs(args.warmup + s), chunksize=1)
+        busy.append(max(r[0] for r in res))
+    wall = time.perf_counter() - t0
+    oracle_s = sum(busy)
+    value = per_step * args.steps / oracle_s
+    return {"metric": METRIC, "value": round(value, 3), "unit": "events/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * oracle_s / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "pu200_like_batched", "events_per_step": per_step, "pileup": PILEUP,
+                       "particles_per_vertex": PER_VERTEX},
+            "cpu_baseline": {"value": round(value, 3), "unit": "events/s", "cores": n_cores, "kind": "oracle",
+                             "sample": f"{per_step} PU200-like events per step, one per core, oracle time "
+                                       f"only (generation excluded); wall {wall:.1f} s"},
+            "e2e": {"value": round(value, 3), "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lst", choices=["lst", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--plain-events", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    n_cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    # the process pool starts with `spawn` before any GPU call
+    ctx_mp = mp.get_context("spawn")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        with ctx_mp.Pool(n_cores) as pool:
+            print(json.dumps(run_reference(args, pool, n_cores)), flush=True)
+        return
+    with ctx_mp.Pool(min(n_cores, 16)) as pool:
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(pool, min(n_cores, 16))
+        if world > 1:
+            import torch.distributed as dist
+            import torch
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        line = run_gpu(args, rank, world, local_rank, pool)
+        line["cpu_baseline"] = cpu
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * lst.h -- C-ABI of the GB300 line-segment-tracking (LST) library (liblst.so).
+ *
+ * The library builds, per collision event, the LST track segments of arXiv 2403.13166
+ * (Section 1, Table 1, steps 1-4) on the GPU and scores every quintuplet with the
+ * T5-DNN (Sections 2-3):
+ *   step 1  mini-doublets (MD): one hit in each sensor of a pT-module, pT > 0.8 GeV;
+ *   step 2  line segments (LS): two MDs in modules linked by the module map;
+ *   step 3  triplets (T3): two LSs sharing their common MD;
+ *   step 4  quintuplets (T5): two T3s sharing their common MD;
+ *   score   38 features -> 32 -> 32 -> 1 (ReLU, sigmoid), selected iff score >= wp.
+ *
+ * Conventions for every call:
+ *   - Every function returns an lst_status (0 = LST_OK). No call aborts, exits or traps;
+ *     device-side failures are reported through status words that the host reads.
+ *   - Pointers documented as DEVICE must be CUDA device (or managed) memory of the
+ *     context's device; HOST pointers are ordinary host memory (pinned or not).
+ *   - `cuda_stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   - Input buffers stay owned by the caller and must stay valid until the call's work
+ *     on the stream has finished. Everything the library allocates is owned by the
+ *     context (geometry, weights, per-event object buffers) and freed by lst_destroy.
+ *   - Output hit indices always refer to the caller's original hit order.
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef LST_H
+#define LST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lst_status {
+    LST_OK = 0,
+    LST_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad enum) */
+    LST_ERR_CAPACITY = 2,   /* an object buffer or caller buffer was too small; sizes reported */
+    LST_ERR_CUDA = 3,       /* a CUDA runtime call failed (message in lst_last_error) */
+    LST_ERR_TIMEOUT = 4,    /* a bounded device-side wait ran out */
+    LST_ERR_NOT_READY = 5,  /* no geometry loaded / no free event slot / work still running */
+    LST_ERR_INPUT = 6,      /* a hit had a sensor id out of range or a non-finite coordinate */
+    LST_ERR_NOMEM = 7       /* device allocation failed */
+} lst_status;
+
+typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3 } lst_kind;
+typedef enum lst_precision { LST_FP32 = 0, LST_BF16 = 1 } lst_precision;
+
+/* One pT-module (Section 1: two sensors a few mm apart). Sensor ids of module m are
+ * 2*m (lower sensor, nearer the interaction point; its hit is the MD anchor, Section 2)
+ * and 2*m+1 (upper sensor). */
+typedef struct lst_module {
+    int32_t layer;    /* 1..6 barrel layers, 7..11 endcap disks (T5-DNN "layer" input) */
+    int32_t subdet;   /* 0 = barrel (flat module parallel to z), 1 = endcap (disk module) */
+    int32_t side;     /* 0 barrel, -1 / +1 endcap side */
+    int32_t ps;       /* 1 = PS module (macro-pixel + strip), 0 = 2S (two strips) */
+} lst_module;
+
+/* Cut parameters of the MD/LS/T3/T5 selections (Section 1: "consistency with a
+ * continuous, helical trajectory"). All FP32; units cm, GeV, 1/cm. */
+typedef struct lst_cuts {
+    float kappa_max;        /* curvature of a 0.8 GeV track: k_field / 0.8 */
+    float z_lum;            /* luminous-region half length for the z0 road */
+    float hit_err;          /* 3-sigma error of a two-hit difference */
+    float sensor_gap;       /* distance between the two sensors of a module */
+    float t3_kappa_factor;  /* T3 curvature bound = kappa_max * factor */
+    float t3_rz_tol;        /* T3 z residual of the middle anchor */
+    float t5_kappa_rel;     /* T5 curvature agreement, relative part */
+    float t5_kappa_abs;     /* T5 curvature agreement, absolute part */
+    float t5_rz_tol;        /* T5 z residual of the inner anchors */
+    float t5_chi2_max;      /* reserved: circle-fit selection of the pre-DNN mode */
+    float hit_sigma;        /* single-hit resolution */
+    float k_field;          /* pT [GeV] = k_field * R [cm] */
+    float wp;               /* T5-DNN working point: selected iff score >= wp */
+} lst_cuts;
+
+/* T5-DNN weights (Section 2), FP32, PyTorch Linear layout W[out][in], flattened as
+ * W0(32x38), b0(32), { Wh(32x32), bh(32) } x (n_hidden-1), Wout(32), bout(1). */
+typedef struct lst_mlp {
+    int32_t n_hidden;       /* hidden layers of width 32: 1..4 (Section 2 compares 1-4) */
+    const float *w;         /* HOST pointer, copied by lst_load_geometry */
+} lst_mlp;
+
+typedef struct lst_config {
+    int32_t precision;          /* lst_precision of the fused T5 score inside lst_run_event */
+    int32_t max_events;         /* event slots (events resident at once), >= 1 */
+    int32_t use_graphs;         /* 1: batched runs replay a captured CUDA graph */
+    int32_t reserved;
+    float md_per_hit;           /* initial capacity ratios of the per-event object buffers; */
+    float ls_per_md;            /* they grow automatically after an overflow */
+    float t3_per_md;
+    float t5_per_md;
+} lst_config;
+
+typedef struct lst_ctx_s *lst_ctx;
+typedef struct lst_event_s *lst_event;
+
+/* Per-event counters after a run. */
+typedef struct lst_counts {
+    int64_t n_hits, n_md, n_ls, n_t3, n_t5, n_selected;
+    int64_t pairs[4];           /* candidate pairs tested by steps 1-4 (MD, LS, T3, T5) */
+    int32_t status;             /* lst_status of the event */
+    int32_t overflow_mask;      /* bit k set: buffer of kind k overflowed */
+} lst_counts;
+
+/* Fills `cfg` with defaults (FP32 score, 1 slot, graphs on, ratios sized for PU200). */
+lst_status lst_default_config(lst_config *cfg);
+
+/* Creates a context on CUDA device `cuda_device`. cfg may be NULL (defaults). */
+lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out);
+
+/* Uploads the detector and model once; they stay resident across events.
+ *   mods     HOST [n_mod] module table;
+ *   map_off  HOST [n_mod+1], map_tgt HOST [map_off[n_mod]]: module map in CSR form
+ *            (Section 1: LSs only across adjacent modules passing geometric criteria);
+ *   cuts     HOST cut parameters; weights HOST network (may be NULL: scores = 0.5).
+ * Everything is copied; the caller keeps ownership. Errors: LST_ERR_ARG for a malformed
+ * table (layer/subdet out of range, map not monotonic, target out of range). */
+lst_status lst_load_geometry(lst_ctx ctx, const lst_module *mods, int32_t n_mod,
+                             const int32_t *map_off, const int32_t *map_tgt,
+                             const lst_cuts *cuts, const lst_mlp *weights);
+
+/* Runs steps 1-4 and the T5-DNN score on one event, one launch sequence per event.
+ *   x, y, z  DEVICE float32 [n_hits] global hit coordinates (cm);
+ *   sensor   DEVICE int32 [n_hits] sensor id (2*module + 0/1).
+ * The work is enqueued on `cuda_stream`; the call then waits for the event's counters
+ * (one synchronisation per event) and, if an object buffer overflowed, grows it and
+ * re-runs the event, so a successful return always carries complete results.
+ * Errors: LST_ERR_INPUT for an invalid hit (no results), LST_ERR_NOT_READY without
+ * geometry or a free slot, LST_ERR_ARG for n_hits < 0 or null pointers with n_hits > 0. */
+lst_status lst_run_event(lst_ctx ctx, const float *x, const float *y, const float *z,
+                         const int32_t *sensor, int64_t n_hits, void *cuda_stream,
+                         lst_event *out);
+
+/* Batched form: n_events events (each with its own DEVICE arrays, pointer tables on the
+ * HOST) go through one persistent launch per stage; with cfg.use_graphs the launch
+ * sequence is a CUDA graph captured once. Asynchronous: returns once the work is
+ * enqueued. lst_event_counts / lst_get_candidates wait for it. An event whose buffers
+ * overflowed reports LST_ERR_CAPACITY (and grows its slot for the next run). */
+lst_status lst_run_batch(lst_ctx ctx, int32_t n_events, const float *const *x,
+                         const float *const *y, const float *const *z,
+                         const int32_t *const *sensor, const int64_t *n_hits,
+                         void *cuda_stream, lst_event *out);
+
+/* Waits for the event and returns its counters. */
+lst_status lst_event_counts(lst_event ev, lst_counts *out);
+
+/* Copies the objects of one kind as hit-index tuples:
+ *   hit_idx   [n][2|4|6|10] int32 (MD: lower,upper; LS: 2 MDs; T3: 3 MDs; T5: 5 MDs, each
+ *             MD as lower,upper), chain order, original hit indices;
+ *   score     [n] float T5-DNN score (T5 only, may be NULL);
+ *   selected  [n] uint8 score >= wp (T5 only, may be NULL).
+ * Buffers may be HOST or DEVICE memory (detected). *n_out is always set; if
+ * capacity < n the call copies nothing and returns LST_ERR_CAPACITY. Objects come in the
+ * library's order; compare as sets. */
+lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score,
+                              uint8_t *selected, int64_t capacity, int64_t *n_out);
+
+/* Copies the 38 T5-DNN input features of every T5 (Section 2 list) as float [n][38]
+ * (HOST or DEVICE); same size protocol as lst_get_candidates. */
+lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out);
+
+/* Scores precomputed features with the loaded network (Section 2):
+ *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores)
+ *   or LST_BF16 (tensor cores, FP32 accumulation). Asynchronous on cuda_stream. */
+lst_status lst_score_t5(lst_ctx ctx, const float *feat, int64_t n, int32_t precision,
+                        float *score_out, void *cuda_stream);
+
+/* Returns the event's slot to the context. */
+lst_status lst_event_release(lst_event ev);
+
+/* Frees everything the context owns (waits for its work first). */
+lst_status lst_destroy(lst_ctx ctx);
+
+/* Static text of a status code; never NULL. */
+const char *lst_status_str(int32_t status);
+
+/* Last error message of the calling thread (CUDA error string, argument check). */
+const char *lst_last_error(void);
+
+/* Launch shapes of the stage kernels (threads per CTA, shared-memory list and staging
+ * sizes). lst_set_launch validates (threads a multiple of 32 in 32..256, sizes >= 1, the
+ * shared memory within the device limit) and recomputes the persistent grid sizes; the
+ * results never depend on these values, only the speed does. */
+typedef struct lst_launch {
+    int32_t md_threads, md_buf;              /* step 1: CTA size, per-warp candidate list */
+    int32_t ls_threads, ls_stage, ls_buf;    /* step 2: CTA size, staged target MDs, list */
+    int32_t t3_threads, t3_buf;              /* step 3 */
+    int32_t t5_threads;                      /* step 4 */
+    int32_t sc_threads;                      /* score */
+} lst_launch;
+lst_status lst_get_launch(lst_ctx ctx, lst_launch *out);
+lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);
+
+/* Per-stage device timing. lst_set_timing(ctx, 1) resets the statistics and makes every
+ * later launch (lst_run_event and lst_run_batch, graph launches included) record CUDA
+ * events at the stage boundaries on the launch stream. lst_stage_times returns the mean
+ * device time per launch of each stage in ms (0 bin, 1 md, 2 ls, 3 t3, 4 t5, 5 score) and
+ * the number of launches averaged. */
+lst_status lst_set_timing(lst_ctx ctx, int32_t enable);
+lst_status lst_stage_times(lst_ctx ctx, float *ms6, int64_t *n_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LST_H */

@@ -1,0 +1,859 @@
+// lst_api.cu -- C-ABI and runtime of the GB300 LST library: context, resident geometry and
+// network, per-event device buffers (event slots), the one-launch-per-stage pipeline over
+// a batch of events, a CUDA-graph cache for batched runs, and candidate export.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lst_internal.cuh"
+
+namespace lstk {
+// kernels (lst_kernels.cu, lst_score.cu, lst_mma.cu)
+__global__ void k_reset(const EvDesc *, DevGeom);
+__global__ void k_bin_count(const EvDesc *, DevGeom);
+__global__ void k_bin_scan(const EvDesc *, DevGeom);
+__global__ void k_bin_scatter(const EvDesc *, DevGeom);
+__global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
+__global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, int, int);
+__global__ void k_t3(const EvDesc *, int, lst_cuts, int *, int);
+__global__ void k_t5(const EvDesc *, int, lst_cuts, int *);
+__global__ void k_score_fp32(const EvDesc *, int, DevGeom, lst_cuts, const float *, int);
+__global__ void k_features(const EvDesc *, DevGeom, float, float *, int);
+__global__ void k_score_feat_fp32(const float *, int64_t, const float *, int, float *);
+__global__ void k_gather(const EvDesc *, int, int, int32_t *, float *, uint8_t *);
+__global__ void k_collect(const EvDesc *, int, int *);
+}  // namespace lstk
+
+using namespace lstk;
+
+namespace {
+
+thread_local std::string g_err;
+
+lst_status fail(lst_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      return fail(_e == cudaErrorMemoryAllocation ? LST_ERR_NOMEM : LST_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(_e));                     \
+    }                                                                                     \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Slot {
+  EvDesc d{};
+  void *mem = nullptr;
+  size_t bytes = 0;
+  int64_t hit_cap = 0;
+  int md_cap = 0, ls_cap = 0, t3_cap = 0, t5_cap = 0;
+  void *in_mem = nullptr;          // staging for host inputs
+  int64_t in_cap = 0;
+  bool busy = false;
+  int lane = -1;                   // lane whose last batch holds this slot's counters
+  int lane_pos = -1;
+  uint64_t lane_gen = 0;
+  int32_t cnt[C_NCOUNTERS] = {0};  // harvested counters
+  bool have_cnt = false;
+  int64_t n_hits = 0;
+};
+
+struct Lane {
+  EvDesc *d_desc = nullptr;        // [MAX_EVENTS]
+  EvDesc *h_desc = nullptr;        // pinned
+  int *d_work = nullptr;           // [16]
+  int *d_counts = nullptr;         // [MAX_EVENTS * C_NCOUNTERS]
+  int *h_counts = nullptr;         // pinned
+  int slots[MAX_EVENTS];
+  int n = 0;
+  uint64_t gen = 0;
+  bool inflight = false;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t tev[7] = {};         // stage boundaries of the last launch (when timed)
+  bool timed = false;
+  cudaStream_t cap_stream = nullptr;
+  std::map<long long, cudaGraphExec_t> graphs;
+};
+
+}  // namespace
+
+struct lst_ctx_s {
+  int device = 0;
+  lst_config cfg{};
+  int n_sm = 0;
+  bool have_geom = false;
+  DevGeom g{};
+  int8_t *d_subdet = nullptr, *d_layer = nullptr;
+  int32_t *d_map_off = nullptr, *d_map_tgt = nullptr;
+  lst_cuts cuts{};
+  int n_hidden = 2;
+  float *d_w = nullptr;
+  int n_w = 0;
+  std::vector<Slot> slots;
+  std::vector<Lane> lanes;     // lane 0: lst_run_event; lanes 1..: batches, round robin
+  int next_lane = 1;
+  float r_md, r_ls, r_t3, r_t5;
+  // launch shapes (autotuned)
+  int md_threads = 256, md_buf = 128;
+  int ls_threads = 256, ls_stage = 3072, ls_buf = 256;
+  int t3_threads = 256, t3_buf = 128;
+  int t5_threads = 256;
+  int sc_threads = 256;
+  int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
+  // per-stage device times accumulated over timed launches
+  bool timing = false;
+  double stage_sum[6] = {0};
+  int64_t stage_n = 0;
+  cudaStream_t aux = nullptr;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+struct lst_event_s {
+  lst_ctx ctx;
+  int slot;
+  int status;
+};
+
+namespace {
+
+size_t ls_smem(const lst_ctx_s *c) {
+  return (size_t)c->ls_stage * (16 + 4 + 4) + (2 * MAX_FANOUT + 1) * 4 +
+         (size_t)(c->ls_threads / 32) * c->ls_buf * 8;
+}
+size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * c->md_buf * 12; }
+size_t t3_smem(const lst_ctx_s *c) {
+  return (size_t)(c->t3_threads / 32) * (sizeof(int) * 128) + (size_t)(c->t3_threads / 32) * c->t3_buf * 12;
+}
+size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (sizeof(int) * 128); }
+int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
+
+lst_status compute_grids(lst_ctx_s *c) {
+  // Function attributes are process-wide (shared by every context): allow the device's
+  // opt-in maximum once, so that no context's launch shape limits another's.
+  int optin = 0;
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  auto allow = [&](const void *fn) -> cudaError_t {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  };
+  CU(allow((const void *)k_ls));
+  CU(allow((const void *)k_md));
+  CU(allow((const void *)k_t3));
+  CU(allow((const void *)k_t5));
+  CU(allow((const void *)k_score_fp32));
+  CU(allow((const void *)k_score_feat_fp32));
+  int occ = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ls, c->ls_threads, ls_smem(c)));
+  c->grid_ls = std::max(1, occ) * c->n_sm;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_md, c->md_threads, md_smem(c)));
+  c->grid_md = std::max(1, occ) * c->n_sm;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_t3, c->t3_threads, t3_smem(c)));
+  c->grid_t3 = std::max(1, occ) * c->n_sm;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_t5, c->t5_threads, t5_smem(c)));
+  c->grid_t5 = std::max(1, occ) * c->n_sm;
+  const size_t sw = (size_t)mlp_floats_host(4) * 4;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_fp32, c->sc_threads, sw));
+  c->grid_sc = std::max(1, occ) * c->n_sm;
+  return LST_OK;
+}
+
+// capacities for n hits with the context's current ratios
+void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5) {
+  const double nmd = std::ceil(c->r_md * (double)n) + 256;
+  md = (int)std::min(nmd, 2.0e9);
+  ls = (int)std::min(std::ceil(c->r_ls * nmd) + 1024, 2.0e9);
+  t3 = (int)std::min(std::ceil(c->r_t3 * nmd) + 1024, 2.0e9);
+  t5 = (int)std::min(std::ceil(c->r_t5 * nmd) + 1024, 2.0e9);
+}
+
+lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
+  int md, ls, t3, t5;
+  caps_for(c, n_hits, md, ls, t3, t5);
+  const int64_t hcap = std::max<int64_t>(n_hits, 1024);
+  if (s.mem && s.hit_cap >= n_hits && s.md_cap >= md && s.ls_cap >= ls && s.t3_cap >= t3 && s.t5_cap >= t5)
+    return LST_OK;
+  // grow with headroom
+  const int64_t H = std::max<int64_t>(s.hit_cap, (int64_t)(hcap * 1.1));
+  md = std::max(s.md_cap, md); ls = std::max(s.ls_cap, ls); t3 = std::max(s.t3_cap, t3); t5 = std::max(s.t5_cap, t5);
+  const int nm = c->g.n_mod;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_hit = take(16 * H), o_orig = take(4 * H);
+  const size_t o_scnt = take(4 * (size_t)2 * nm), o_soff = take(4 * ((size_t)2 * nm + 1));
+  const size_t o_manc = take(16 * (size_t)md), o_mk = take(8 * (size_t)md), o_mmod = take(4 * (size_t)md),
+               o_mh = take(8 * (size_t)md), o_mst = take(4 * (size_t)nm), o_mcn = take(4 * (size_t)nm);
+  const size_t o_lin = take(4 * (size_t)ls), o_lout = take(4 * (size_t)ls), o_lk = take(4 * (size_t)ls),
+               o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
+  const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
+               o_t3c = take(4 * (size_t)md);
+  const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
+               o_t5e = take((size_t)t5);
+  const size_t o_cnt = take(4 * C_NCOUNTERS);
+  if (s.mem) {
+    CU(cudaDeviceSynchronize());
+    cudaFree(s.mem);
+    s.mem = nullptr;
+  }
+  CU(cudaMalloc(&s.mem, off));
+  s.bytes = off;
+  char *b = (char *)s.mem;
+  EvDesc &d = s.d;
+  d.hit = (float4 *)(b + o_hit); d.hit_orig = (int32_t *)(b + o_orig);
+  d.sens_cnt = (int32_t *)(b + o_scnt); d.sens_off = (int32_t *)(b + o_soff);
+  d.md_anchor = (float4 *)(b + o_manc); d.md_kappa = (float2 *)(b + o_mk); d.md_mod = (int32_t *)(b + o_mmod);
+  d.md_hits = (int2 *)(b + o_mh); d.md_start = (int32_t *)(b + o_mst); d.md_cnt = (int32_t *)(b + o_mcn);
+  d.ls_in = (int32_t *)(b + o_lin); d.ls_out = (int32_t *)(b + o_lout); d.ls_kappa = (float *)(b + o_lk);
+  d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
+  d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_start = (int32_t *)(b + o_t3s);
+  d.t3_cnt = (int32_t *)(b + o_t3c);
+  d.t5_a = (int4 *)(b + o_t5a); d.t5_b = (int4 *)(b + o_t5b); d.t5_score = (float *)(b + o_t5s);
+  d.t5_sel = (uint8_t *)(b + o_t5e); d.cnt = (int32_t *)(b + o_cnt);
+  s.hit_cap = H; s.md_cap = md; s.ls_cap = ls; s.t3_cap = t3; s.t5_cap = t5;
+  d.md_cap = md; d.ls_cap = ls; d.t3_cap = t3; d.t5_cap = t5;
+  return LST_OK;
+}
+
+// stage host inputs into the slot's own device buffer (copies on `st`)
+lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, const float *z,
+                       const int32_t *sensor, int64_t n, cudaStream_t st) {
+  (void)c;
+  s.d.n_hits = (int32_t)n;
+  s.n_hits = n;
+  const bool dev = n == 0 || is_device_ptr(x);
+  if (dev) {
+    s.d.x = x; s.d.y = y; s.d.z = z; s.d.sensor = sensor;
+    return LST_OK;
+  }
+  if (s.in_cap < n) {
+    if (s.in_mem) { CU(cudaDeviceSynchronize()); cudaFree(s.in_mem); s.in_mem = nullptr; }
+    const int64_t cap = (int64_t)(n * 1.1) + 1024;
+    CU(cudaMalloc(&s.in_mem, (size_t)cap * 16));
+    s.in_cap = cap;
+  }
+  float *b = (float *)s.in_mem;
+  float *dx = b, *dy = b + s.in_cap, *dz = b + 2 * s.in_cap;
+  int32_t *ds = (int32_t *)(b + 3 * s.in_cap);
+  CU(cudaMemcpyAsync(dx, x, 4 * n, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(dy, y, 4 * n, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(dz, z, 4 * n, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ds, sensor, 4 * n, cudaMemcpyHostToDevice, st));
+  s.d.x = dx; s.d.y = dy; s.d.z = dz; s.d.sensor = ds;
+  return LST_OK;
+}
+
+lst_status lane_init(Lane &L) {
+  CU(cudaMalloc(&L.d_desc, sizeof(EvDesc) * MAX_EVENTS));
+  CU(cudaMallocHost(&L.h_desc, sizeof(EvDesc) * MAX_EVENTS));
+  CU(cudaMalloc(&L.d_work, sizeof(int) * 16));
+  CU(cudaMalloc(&L.d_counts, sizeof(int) * MAX_EVENTS * C_NCOUNTERS));
+  CU(cudaMallocHost(&L.h_counts, sizeof(int) * MAX_EVENTS * C_NCOUNTERS));
+  CU(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+  for (auto &e : L.tev) CU(cudaEventCreate(&e));
+  CU(cudaStreamCreateWithFlags(&L.cap_stream, cudaStreamNonBlocking));
+  return LST_OK;
+}
+
+// Wait for the lane's last batch and copy its counters into the slots.
+lst_status lane_harvest(lst_ctx_s *c, Lane &L) {
+  if (!L.inflight) return LST_OK;
+  CU(cudaEventSynchronize(L.done));
+  for (int i = 0; i < L.n; i++) {
+    Slot &s = c->slots[L.slots[i]];
+    if (s.lane_gen == L.gen && s.lane == (int)(&L - c->lanes.data())) {
+      std::memcpy(s.cnt, L.h_counts + i * C_NCOUNTERS, sizeof(s.cnt));
+      s.have_cnt = true;
+    }
+  }
+  if (L.timed) {
+    for (int k = 0; k < 6; k++) {
+      float ms = 0.0f;
+      CU(cudaEventElapsedTime(&ms, L.tev[k], L.tev[k + 1]));
+      c->stage_sum[k] += ms;
+    }
+    c->stage_n++;
+  }
+  L.inflight = false;
+  return LST_OK;
+}
+
+// Enqueue the whole pipeline for the lane's current batch (desc already on device).
+lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool timed, bool capturing) {
+  const DevGeom g = c->g;
+  const int bx = std::max(1, (4 * c->n_sm + n - 1) / n);
+  // stage boundary events; inside a capture they become event-record nodes of the graph
+  auto mark = [&](int i) {
+    if (timed) cudaEventRecordWithFlags(L.tev[i], st, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  };
+  mark(0);
+  k_reset<<<dim3(std::max(1, c->n_sm / n + 1), n), 256, 0, st>>>(L.d_desc, g);
+  k_bin_count<<<dim3(bx, n), 256, 0, st>>>(L.d_desc, g);
+  k_bin_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
+  k_bin_scatter<<<dim3(bx, n), 256, 0, st>>>(L.d_desc, g);
+  CU(cudaMemsetAsync(L.d_work, 0, sizeof(int) * 16, st));
+  mark(1);
+  k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 0, c->md_buf);
+  mark(2);
+  k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->ls_stage, c->ls_buf);
+  mark(3);
+  k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts, L.d_work + 2, c->t3_buf);
+  mark(4);
+  k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts, L.d_work + 3);
+  mark(5);
+  k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
+      L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
+  mark(6);
+  k_collect<<<(n + 127) / 128, 128, 0, st>>>(L.d_desc, n, L.d_counts);
+  CU(cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int) * C_NCOUNTERS * n, cudaMemcpyDeviceToHost, st));
+  CU(cudaGetLastError());
+  return LST_OK;
+}
+
+int find_free_slot(lst_ctx_s *c) {
+  for (size_t i = 0; i < c->slots.size(); i++)
+    if (!c->slots[i].busy) return (int)i;
+  return -1;
+}
+
+void grow_ratios(lst_ctx_s *c, const Slot &s, const int32_t *cnt) {
+  const int f = cnt[C_FLAGS];
+  const double n = std::max<double>(1.0, (double)s.n_hits);
+  const double nmd = std::max<double>(1.0, std::ceil(c->r_md * n) + 256);
+  if (f & F_OVF_MD) c->r_md = std::max(c->r_md, (float)(1.3 * cnt[C_MD] / n));
+  if (f & F_OVF_LS) c->r_ls = std::max(c->r_ls, (float)(1.3 * cnt[C_LS] / nmd));
+  if (f & F_OVF_T3) c->r_t3 = std::max(c->r_t3, (float)(1.3 * cnt[C_T3] / nmd));
+  if (f & F_OVF_T5) c->r_t5 = std::max(c->r_t5, (float)(1.3 * cnt[C_T5] / nmd));
+}
+
+lst_status status_of(const int32_t *cnt) {
+  if (cnt[C_FLAGS] & F_INPUT) return LST_ERR_INPUT;
+  if (cnt[C_FLAGS] & (F_OVF_MD | F_OVF_LS | F_OVF_T3 | F_OVF_T5)) return LST_ERR_CAPACITY;
+  return LST_OK;
+}
+
+lst_status wait_event(lst_event ev) {
+  lst_ctx_s *c = ev->ctx;
+  Slot &s = c->slots[ev->slot];
+  if (!s.have_cnt) {
+    if (s.lane < 0) return fail(LST_ERR_NOT_READY, "event has no pending work");
+    lst_status st = lane_harvest(c, c->lanes[s.lane]);
+    if (st != LST_OK) return st;
+    if (!s.have_cnt) return fail(LST_ERR_NOT_READY, "event counters unavailable");
+  }
+  // the lane may have been harvested through another event of the same batch
+  if (ev->status == LST_ERR_NOT_READY) {
+    ev->status = status_of(s.cnt);
+    if (ev->status == LST_ERR_CAPACITY) grow_ratios(c, s, s.cnt);
+  }
+  return LST_OK;
+}
+
+}  // namespace
+
+namespace lstk {
+__global__ void k_collect(const EvDesc *__restrict__ evs, int n, int *out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n)
+    for (int k = 0; k < C_NCOUNTERS; k++) out[e * C_NCOUNTERS + k] = evs[e].cnt[k];
+}
+}  // namespace lstk
+
+// =========================================================================== C-ABI
+extern "C" {
+
+const char *lst_status_str(int32_t s) {
+  switch (s) {
+    case LST_OK: return "LST_OK";
+    case LST_ERR_ARG: return "LST_ERR_ARG";
+    case LST_ERR_CAPACITY: return "LST_ERR_CAPACITY";
+    case LST_ERR_CUDA: return "LST_ERR_CUDA";
+    case LST_ERR_TIMEOUT: return "LST_ERR_TIMEOUT";
+    case LST_ERR_NOT_READY: return "LST_ERR_NOT_READY";
+    case LST_ERR_INPUT: return "LST_ERR_INPUT";
+    case LST_ERR_NOMEM: return "LST_ERR_NOMEM";
+    default: return "LST_ERR_UNKNOWN";
+  }
+}
+
+const char *lst_last_error(void) { return g_err.c_str(); }
+
+lst_status lst_default_config(lst_config *cfg) {
+  if (!cfg) return fail(LST_ERR_ARG, "cfg is NULL");
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->precision = LST_FP32;
+  cfg->max_events = 1;
+  cfg->use_graphs = 1;
+  cfg->md_per_hit = 0.75f;
+  cfg->ls_per_md = 16.0f;
+  cfg->t3_per_md = 3.0f;
+  cfg->t5_per_md = 2.0f;
+  return LST_OK;
+}
+
+lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out) {
+  if (!out) return fail(LST_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (cuda_device < 0 || cuda_device >= ndev) return fail(LST_ERR_ARG, "bad device index");
+  lst_config d;
+  lst_default_config(&d);
+  const lst_config &c = cfg ? *cfg : d;
+  if (c.max_events < 1 || c.max_events > MAX_EVENTS) return fail(LST_ERR_ARG, "max_events out of range");
+  if (c.precision != LST_FP32 && c.precision != LST_BF16) return fail(LST_ERR_ARG, "bad precision");
+  DeviceGuard gd(cuda_device);
+  lst_ctx_s *x = new lst_ctx_s();
+  x->device = cuda_device;
+  x->cfg = c;
+  x->r_md = c.md_per_hit > 0 ? c.md_per_hit : d.md_per_hit;
+  x->r_ls = c.ls_per_md > 0 ? c.ls_per_md : d.ls_per_md;
+  x->r_t3 = c.t3_per_md > 0 ? c.t3_per_md : d.t3_per_md;
+  x->r_t5 = c.t5_per_md > 0 ? c.t5_per_md : d.t5_per_md;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, cuda_device) != cudaSuccess) { delete x; return fail(LST_ERR_CUDA, "device properties"); }
+  x->n_sm = p.multiProcessorCount;
+  x->slots.resize(c.max_events);
+  x->lanes.resize(1 + 2);
+  for (auto &L : x->lanes) {
+    lst_status s = lane_init(L);
+    if (s != LST_OK) { lst_destroy(x); return s; }
+  }
+  cudaStreamCreateWithFlags(&x->aux, cudaStreamNonBlocking);
+  lst_status s = compute_grids(x);
+  if (s != LST_OK) { lst_destroy(x); return s; }
+  *out = x;
+  return LST_OK;
+}
+
+lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, const int32_t *map_off,
+                             const int32_t *map_tgt, const lst_cuts *cuts, const lst_mlp *weights) {
+  if (!c || !mods || !map_off || !cuts || n_mod <= 0) return fail(LST_ERR_ARG, "null argument or n_mod <= 0");
+  if (map_off[0] != 0) return fail(LST_ERR_ARG, "map_off[0] != 0");
+  for (int32_t m = 0; m < n_mod; m++) {
+    if (mods[m].layer < 1 || mods[m].layer > 11) return fail(LST_ERR_ARG, "module layer out of range");
+    if (mods[m].subdet != 0 && mods[m].subdet != 1) return fail(LST_ERR_ARG, "module subdet out of range");
+    if (map_off[m + 1] < map_off[m]) return fail(LST_ERR_ARG, "map_off not monotonic");
+    if (map_off[m + 1] - map_off[m] > MAX_FANOUT) return fail(LST_ERR_ARG, "module map fan-out above 512");
+  }
+  const int32_t nl = map_off[n_mod];
+  if (nl > 0 && !map_tgt) return fail(LST_ERR_ARG, "map_tgt is NULL");
+  for (int32_t i = 0; i < nl; i++)
+    if (map_tgt[i] < 0 || map_tgt[i] >= n_mod) return fail(LST_ERR_ARG, "map target out of range");
+  int nh = 2;
+  if (weights) {
+    nh = weights->n_hidden;
+    if (nh < 1 || nh > 4 || !weights->w) return fail(LST_ERR_ARG, "n_hidden must be 1..4 with weights");
+  }
+  DeviceGuard gd(c->device);
+  CU(cudaDeviceSynchronize());
+  for (auto &L : c->lanes) {
+    for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+    L.graphs.clear();
+  }
+  cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt); cudaFree(c->d_w);
+  c->d_subdet = nullptr; c->d_layer = nullptr; c->d_map_off = nullptr; c->d_map_tgt = nullptr; c->d_w = nullptr;
+  std::vector<int8_t> sd(n_mod), ly(n_mod);
+  for (int32_t m = 0; m < n_mod; m++) { sd[m] = (int8_t)mods[m].subdet; ly[m] = (int8_t)mods[m].layer; }
+  CU(cudaMalloc(&c->d_subdet, n_mod));
+  CU(cudaMalloc(&c->d_layer, n_mod));
+  CU(cudaMalloc(&c->d_map_off, 4 * ((size_t)n_mod + 1)));
+  CU(cudaMalloc(&c->d_map_tgt, 4 * (size_t)std::max(nl, 1)));
+  CU(cudaMemcpy(c->d_subdet, sd.data(), n_mod, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_layer, ly.data(), n_mod, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_map_off, map_off, 4 * ((size_t)n_mod + 1), cudaMemcpyHostToDevice));
+  if (nl > 0) CU(cudaMemcpy(c->d_map_tgt, map_tgt, 4 * (size_t)nl, cudaMemcpyHostToDevice));
+  c->n_hidden = nh;
+  c->n_w = mlp_floats_host(nh);
+  std::vector<float> w(c->n_w, 0.0f);
+  if (weights) std::memcpy(w.data(), weights->w, 4 * (size_t)c->n_w);
+  CU(cudaMalloc(&c->d_w, 4 * (size_t)c->n_w));
+  CU(cudaMemcpy(c->d_w, w.data(), 4 * (size_t)c->n_w, cudaMemcpyHostToDevice));
+  c->g.n_mod = n_mod;
+  c->g.subdet = c->d_subdet;
+  c->g.layer = c->d_layer;
+  c->g.map_off = c->d_map_off;
+  c->g.map_tgt = c->d_map_tgt;
+  c->cuts = *cuts;
+  // slot buffers depend on n_mod: drop them
+  for (auto &s : c->slots) {
+    if (s.mem) cudaFree(s.mem);
+    s.mem = nullptr; s.hit_cap = 0; s.md_cap = s.ls_cap = s.t3_cap = s.t5_cap = 0;
+    s.busy = false; s.have_cnt = false; s.lane = -1;
+  }
+  c->have_geom = true;
+  return LST_OK;
+}
+
+static lst_status run_lane(lst_ctx c, Lane &L, int n, const int *slot_ids, cudaStream_t st, bool allow_graph,
+                           bool timed) {
+  L.gen++;
+  L.n = n;
+  for (int i = 0; i < n; i++) {
+    L.slots[i] = slot_ids[i];
+    Slot &s = c->slots[slot_ids[i]];
+    s.d.md_cap = s.md_cap; s.d.ls_cap = s.ls_cap; s.d.t3_cap = s.t3_cap; s.d.t5_cap = s.t5_cap;
+    L.h_desc[i] = s.d;
+    s.lane = (int)(&L - c->lanes.data());
+    s.lane_pos = i;
+    s.lane_gen = L.gen;
+    s.have_cnt = false;
+  }
+  CU(cudaMemcpyAsync(L.d_desc, L.h_desc, sizeof(EvDesc) * n, cudaMemcpyHostToDevice, st));
+  if (allow_graph && c->cfg.use_graphs) {
+    const long long key = (long long)n * 16 + c->cfg.precision * 2 + (timed ? 1 : 0);
+    auto it = L.graphs.find(key);
+    if (it == L.graphs.end()) {
+      cudaGraph_t graph;
+      CU(cudaStreamBeginCapture(L.cap_stream, cudaStreamCaptureModeThreadLocal));
+      lst_status s = enqueue_pipeline(c, L, n, L.cap_stream, timed, true);
+      cudaError_t e = cudaStreamEndCapture(L.cap_stream, &graph);
+      if (s != LST_OK) return s;
+      if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      cudaGraphExec_t exec;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      it = L.graphs.emplace(key, exec).first;
+    }
+    CU(cudaGraphLaunch(it->second, st));
+  } else {
+    lst_status s = enqueue_pipeline(c, L, n, st, timed, false);
+    if (s != LST_OK) return s;
+  }
+  L.timed = timed;
+  CU(cudaEventRecord(L.done, st));
+  L.inflight = true;
+  return LST_OK;
+}
+
+lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float *z, const int32_t *sensor,
+                         int64_t n_hits, void *cuda_stream, lst_event *out) {
+  if (!c || !out) return fail(LST_ERR_ARG, "null ctx/out");
+  *out = nullptr;
+  if (n_hits < 0 || n_hits > (int64_t)1 << 30) return fail(LST_ERR_ARG, "n_hits out of range");
+  if (n_hits > 0 && (!x || !y || !z || !sensor)) return fail(LST_ERR_ARG, "null hit array");
+  if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no geometry loaded");
+  DeviceGuard gd(c->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Lane &L = c->lanes[0];
+  lst_status s = lane_harvest(c, L);
+  if (s != LST_OK) return s;
+  const int si = find_free_slot(c);
+  if (si < 0) return fail(LST_ERR_NOT_READY, "no free event slot (release events)");
+  Slot &S = c->slots[si];
+  for (int attempt = 0; attempt < 6; attempt++) {
+    s = slot_alloc(c, S, n_hits);
+    if (s != LST_OK) return s;
+    s = slot_inputs(c, S, x, y, z, sensor, n_hits, st);
+    if (s != LST_OK) return s;
+    s = run_lane(c, L, 1, &si, st, false, c->timing);
+    if (s != LST_OK) return s;
+    s = lane_harvest(c, L);
+    if (s != LST_OK) return s;
+    const lst_status es = status_of(S.cnt);
+    if (es == LST_ERR_CAPACITY) { grow_ratios(c, S, S.cnt); continue; }
+    S.busy = true;
+    lst_event ev = new lst_event_s{c, si, es};
+    *out = ev;
+    if (es != LST_OK) return fail(es, "invalid hit in input (sensor id or coordinate)");
+    return LST_OK;
+  }
+  return fail(LST_ERR_CAPACITY, "object buffers kept overflowing");
+}
+
+lst_status lst_run_batch(lst_ctx c, int32_t n, const float *const *x, const float *const *y,
+                         const float *const *z, const int32_t *const *sensor, const int64_t *n_hits,
+                         void *cuda_stream, lst_event *out) {
+  if (!c || !out || !x || !y || !z || !sensor || !n_hits) return fail(LST_ERR_ARG, "null argument");
+  if (n < 1 || n > (int32_t)c->slots.size()) return fail(LST_ERR_ARG, "batch size outside 1..max_events");
+  if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no geometry loaded");
+  for (int i = 0; i < n; i++) {
+    if (n_hits[i] < 0 || n_hits[i] > (int64_t)1 << 30) return fail(LST_ERR_ARG, "n_hits out of range");
+    if (n_hits[i] > 0 && (!x[i] || !y[i] || !z[i] || !sensor[i])) return fail(LST_ERR_ARG, "null hit array");
+  }
+  DeviceGuard gd(c->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int li = c->next_lane;
+  c->next_lane = 1 + (c->next_lane % ((int)c->lanes.size() - 1));
+  Lane &L = c->lanes[li];
+  lst_status s = lane_harvest(c, L);
+  if (s != LST_OK) return s;
+  std::vector<int> ids;
+  for (size_t i = 0; i < c->slots.size() && (int)ids.size() < n; i++)
+    if (!c->slots[i].busy) ids.push_back((int)i);
+  if ((int)ids.size() < n) return fail(LST_ERR_NOT_READY, "not enough free event slots");
+  for (int i = 0; i < n; i++) {
+    Slot &S = c->slots[ids[i]];
+    if (S.lane >= 0 && S.lane != li) { s = lane_harvest(c, c->lanes[S.lane]); if (s != LST_OK) return s; }
+    s = slot_alloc(c, S, n_hits[i]);
+    if (s != LST_OK) return s;
+    s = slot_inputs(c, S, x[i], y[i], z[i], sensor[i], n_hits[i], st);
+    if (s != LST_OK) return s;
+  }
+  s = run_lane(c, L, n, ids.data(), st, true, c->timing);
+  if (s != LST_OK) return s;
+  for (int i = 0; i < n; i++) {
+    c->slots[ids[i]].busy = true;
+    out[i] = new lst_event_s{c, ids[i], LST_ERR_NOT_READY};
+  }
+  return LST_OK;
+}
+
+lst_status lst_event_counts(lst_event ev, lst_counts *out) {
+  if (!ev || !out) return fail(LST_ERR_ARG, "null argument");
+  DeviceGuard gd(ev->ctx->device);
+  lst_status s = wait_event(ev);
+  if (s != LST_OK) return s;
+  const Slot &S = ev->ctx->slots[ev->slot];
+  out->n_hits = S.n_hits;
+  out->n_md = S.cnt[C_MD];
+  out->n_ls = S.cnt[C_LS];
+  out->n_t3 = S.cnt[C_T3];
+  out->n_t5 = S.cnt[C_T5];
+  out->n_selected = S.cnt[C_NSEL];
+  out->pairs[0] = (uint32_t)S.cnt[C_PMD];
+  out->pairs[1] = (uint32_t)S.cnt[C_PLS];
+  out->pairs[2] = (uint32_t)S.cnt[C_PT3];
+  out->pairs[3] = (uint32_t)S.cnt[C_PT5];
+  out->status = status_of(S.cnt);
+  int mask = 0;
+  const int f = S.cnt[C_FLAGS];
+  if (f & F_OVF_MD) mask |= 1 << LST_MD;
+  if (f & F_OVF_LS) mask |= 1 << LST_LS;
+  if (f & F_OVF_T3) mask |= 1 << LST_T3;
+  if (f & F_OVF_T5) mask |= 1 << LST_T5;
+  out->overflow_mask = mask;
+  return LST_OK;
+}
+
+static lst_status slot_desc_device(lst_ctx c, int si, EvDesc **dptr) {
+  // one device copy of the slot descriptor in the context scratch
+  const size_t need = sizeof(EvDesc);
+  if (c->scratch_bytes < need) {
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    CU(cudaMalloc(&c->scratch, 4096));
+    c->scratch_bytes = 4096;
+  }
+  EvDesc d = c->slots[si].d;
+  CU(cudaMemcpyAsync(c->scratch, &d, sizeof d, cudaMemcpyHostToDevice, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  *dptr = (EvDesc *)c->scratch;
+  return LST_OK;
+}
+
+lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score, uint8_t *selected,
+                              int64_t capacity, int64_t *n_out) {
+  if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
+  if (kind < LST_MD || kind > LST_T5) return fail(LST_ERR_ARG, "bad kind");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  lst_status s = wait_event(ev);
+  if (s != LST_OK) return s;
+  const Slot &S = c->slots[ev->slot];
+  const int cs[4] = {C_MD, C_LS, C_T3, C_T5};
+  const int64_t n = S.cnt[cs[kind]];
+  *n_out = n;
+  if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
+  if (capacity < n) return fail(LST_ERR_CAPACITY, "output capacity below object count");
+  if (n == 0) return LST_OK;
+  if (!hit_idx) return fail(LST_ERR_ARG, "hit_idx is NULL");
+  const int width = kind == LST_MD ? 2 : kind == LST_LS ? 4 : kind == LST_T3 ? 6 : 10;
+  EvDesc *dd;
+  s = slot_desc_device(c, ev->slot, &dd);
+  if (s != LST_OK) return s;
+  const bool dev_out = is_device_ptr(hit_idx);
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * c->n_sm);
+  if (dev_out) {
+    k_gather<<<grid, 256, 0, c->aux>>>(dd, kind, (int)n, hit_idx, kind == LST_T5 ? score : nullptr,
+                                       kind == LST_T5 ? selected : nullptr);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->aux));
+    return LST_OK;
+  }
+  const size_t bytes = (size_t)n * width * 4 + (size_t)n * 4 + (size_t)n + 1024;
+  void *tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, bytes, c->aux));
+  int32_t *d_idx = (int32_t *)tmp;
+  float *d_sc = (float *)(d_idx + (size_t)n * width);
+  uint8_t *d_sel = (uint8_t *)(d_sc + n);
+  k_gather<<<grid, 256, 0, c->aux>>>(dd, kind, (int)n, d_idx, d_sc, d_sel);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(hit_idx, d_idx, (size_t)n * width * 4, cudaMemcpyDeviceToHost, c->aux));
+  if (kind == LST_T5 && score) CU(cudaMemcpyAsync(score, d_sc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->aux));
+  if (kind == LST_T5 && selected) CU(cudaMemcpyAsync(selected, d_sel, (size_t)n, cudaMemcpyDeviceToHost, c->aux));
+  CU(cudaFreeAsync(tmp, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+
+lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out) {
+  if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  lst_status s = wait_event(ev);
+  if (s != LST_OK) return s;
+  const int64_t n = c->slots[ev->slot].cnt[C_T5];
+  *n_out = n;
+  if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
+  if (capacity < n) return fail(LST_ERR_CAPACITY, "output capacity below object count");
+  if (n == 0) return LST_OK;
+  if (!feat) return fail(LST_ERR_ARG, "feat is NULL");
+  EvDesc *dd;
+  s = slot_desc_device(c, ev->slot, &dd);
+  if (s != LST_OK) return s;
+  const int grid = (int)std::min<int64_t>((n + 127) / 128, 4 * c->n_sm);
+  if (is_device_ptr(feat)) {
+    k_features<<<grid, 128, 0, c->aux>>>(dd, c->g, c->cuts.k_field, feat, (int)n);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->aux));
+    return LST_OK;
+  }
+  void *tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, (size_t)n * NFEAT * 4, c->aux));
+  k_features<<<grid, 128, 0, c->aux>>>(dd, c->g, c->cuts.k_field, (float *)tmp, (int)n);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(feat, tmp, (size_t)n * NFEAT * 4, cudaMemcpyDeviceToHost, c->aux));
+  CU(cudaFreeAsync(tmp, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+
+lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precision, float *score_out,
+                        void *cuda_stream) {
+  if (!c) return fail(LST_ERR_ARG, "null ctx");
+  if (n < 0) return fail(LST_ERR_ARG, "n < 0");
+  if (precision != LST_FP32 && precision != LST_BF16) return fail(LST_ERR_ARG, "bad precision");
+  if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no network loaded");
+  if (n == 0) return LST_OK;
+  if (!feat || !score_out) return fail(LST_ERR_ARG, "null buffer");
+  DeviceGuard gd(c->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->grid_sc);
+  k_score_feat_fp32<<<grid, 256, (size_t)c->n_w * 4, st>>>(feat, n, c->d_w, c->n_hidden, score_out);
+  CU(cudaGetLastError());
+  return LST_OK;
+}
+
+lst_status lst_event_release(lst_event ev) {
+  if (!ev) return fail(LST_ERR_ARG, "null event");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  Slot &S = c->slots[ev->slot];
+  if (!S.have_cnt && S.lane >= 0) lane_harvest(c, c->lanes[S.lane]);
+  S.busy = false;
+  delete ev;
+  return LST_OK;
+}
+
+lst_status lst_destroy(lst_ctx c) {
+  if (!c) return fail(LST_ERR_ARG, "null ctx");
+  {
+    DeviceGuard gd(c->device);
+    cudaDeviceSynchronize();
+    for (auto &L : c->lanes) {
+      for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+      cudaFree(L.d_desc); cudaFreeHost(L.h_desc); cudaFree(L.d_work); cudaFree(L.d_counts);
+      cudaFreeHost(L.h_counts);
+      if (L.done) cudaEventDestroy(L.done);
+      for (auto &e : L.tev) if (e) cudaEventDestroy(e);
+      if (L.cap_stream) cudaStreamDestroy(L.cap_stream);
+    }
+    for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); }
+    cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt);
+    cudaFree(c->d_w); cudaFree(c->scratch);
+    if (c->aux) cudaStreamDestroy(c->aux);
+  }
+  delete c;
+  return LST_OK;
+}
+
+lst_status lst_get_launch(lst_ctx c, lst_launch *o) {
+  if (!c || !o) return fail(LST_ERR_ARG, "null argument");
+  *o = lst_launch{c->md_threads, c->md_buf, c->ls_threads, c->ls_stage, c->ls_buf,
+                  c->t3_threads, c->t3_buf, c->t5_threads, c->sc_threads};
+  return LST_OK;
+}
+
+lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
+  if (!c || !p) return fail(LST_ERR_ARG, "null argument");
+  const int th[5] = {p->md_threads, p->ls_threads, p->t3_threads, p->t5_threads, p->sc_threads};
+  for (int t : th)
+    if (t < 32 || t > 256 || t % 32) return fail(LST_ERR_ARG, "threads must be a multiple of 32 in 32..256");
+  if (p->md_buf < 1 || p->ls_stage < 1 || p->ls_buf < 1 || p->t3_buf < 1) return fail(LST_ERR_ARG, "sizes must be >= 1");
+  DeviceGuard gd(c->device);
+  CU(cudaDeviceSynchronize());
+  lst_ctx_s old = *c;
+  c->md_threads = p->md_threads; c->md_buf = p->md_buf;
+  c->ls_threads = p->ls_threads; c->ls_stage = p->ls_stage; c->ls_buf = p->ls_buf;
+  c->t3_threads = p->t3_threads; c->t3_buf = p->t3_buf; c->t5_threads = p->t5_threads;
+  c->sc_threads = p->sc_threads;
+  int dev_smem = 0;
+  CU(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  if (ls_smem(c) > (size_t)dev_smem - 2048 || md_smem(c) > (size_t)dev_smem || t3_smem(c) > (size_t)dev_smem - 4096) {
+    c->md_threads = old.md_threads; c->md_buf = old.md_buf; c->ls_threads = old.ls_threads;
+    c->ls_stage = old.ls_stage; c->ls_buf = old.ls_buf; c->t3_threads = old.t3_threads;
+    c->t3_buf = old.t3_buf; c->t5_threads = old.t5_threads; c->sc_threads = old.sc_threads;
+    return fail(LST_ERR_ARG, "shared memory of the launch shape exceeds the device limit");
+  }
+  lst_status s = compute_grids(c);
+  if (s != LST_OK) return s;
+  for (auto &L : c->lanes) {
+    for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+    L.graphs.clear();
+  }
+  return LST_OK;
+}
+
+lst_status lst_set_timing(lst_ctx c, int32_t enable) {
+  if (!c) return fail(LST_ERR_ARG, "null ctx");
+  c->timing = enable != 0;
+  for (double &v : c->stage_sum) v = 0.0;
+  c->stage_n = 0;
+  return LST_OK;
+}
+
+lst_status lst_stage_times(lst_ctx c, float *ms6, int64_t *n_launches) {
+  if (!c || !ms6) return fail(LST_ERR_ARG, "null argument");
+  for (int k = 0; k < 6; k++) ms6[k] = c->stage_n ? (float)(c->stage_sum[k] / c->stage_n) : 0.0f;
+  if (n_launches) *n_launches = c->stage_n;
+  return LST_OK;
+}
+
+}  // extern "C"

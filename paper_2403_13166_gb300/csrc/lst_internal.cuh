@@ -1,0 +1,257 @@
+// lst_internal.cuh -- device data layout, cut arithmetic and small warp/block helpers of
+// the GB300 LST library. Cut code is compiled with -fmad=false and IEEE division and
+// square root so that every FP32 cut value is the correctly rounded result of the
+// expression tree written below (no fused multiply-add, no fast-math).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lst.h"
+
+namespace lstk {
+
+constexpr int NFEAT = 38;
+constexpr int NHID = 32;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_EVENTS = 512;       // event slots per context (batch size limit)
+constexpr int MAX_FANOUT = 512;       // module-map targets of one module
+
+// per-event counter words (int32 each)
+enum CounterSlot {
+  C_MD = 0, C_LS = 1, C_T3 = 2, C_T5 = 3, C_FLAGS = 4, C_NSEL = 5,
+  C_PMD = 6, C_PLS = 7, C_PT3 = 8, C_PT5 = 9,   // candidate pairs tested per step
+  C_NCOUNTERS = 12
+};
+enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16 };
+
+struct DevGeom {
+  int32_t n_mod;
+  int32_t pad;
+  const int8_t *subdet;    // [n_mod] 0 barrel, 1 endcap
+  const int8_t *layer;     // [n_mod] 1..11
+  const int32_t *map_off;  // [n_mod+1]
+  const int32_t *map_tgt;  // [n_links]
+};
+
+// Device buffers of one event slot. Object indices (MD, LS, T3, T5) are event-local.
+struct EvDesc {
+  const float *x, *y, *z;      // caller's input (device)
+  const int32_t *sensor;
+  int32_t n_hits;
+  int32_t md_cap, ls_cap, t3_cap, t5_cap;
+  int32_t pad;
+  float4 *hit;                 // [n_hits] hits grouped by sensor: x, y, z, r
+  int32_t *hit_orig;           // [n_hits] original index of each grouped hit
+  int32_t *sens_cnt;           // [2 n_mod] histogram, then scatter cursor
+  int32_t *sens_off;           // [2 n_mod + 1]
+  float4 *md_anchor;           // [md_cap] lower-sensor hit (anchor): x, y, z, r
+  float2 *md_kappa;            // [md_cap] (cut curvature, feature curvature); 0 for endcap
+  int32_t *md_mod;             // [md_cap] module
+  int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
+  int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
+  int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD
+  float *ls_kappa;             // [ls_cap]
+  int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
+  int4 *t3_md;                 // [t3_cap] (md0, md1, md2, -)
+  float *t3_kappa;             // [t3_cap]
+  int32_t *t3_start, *t3_cnt;  // [md_cap] T3s of each first MD: contiguous range
+  int4 *t5_a;                  // [t5_cap] (md0, md1, md2, md3)
+  int4 *t5_b;                  // [t5_cap] (md4, t3a, t3b, -)
+  float *t5_score;             // [t5_cap]
+  uint8_t *t5_sel;             // [t5_cap]
+  int32_t *cnt;                // [C_NCOUNTERS]
+};
+
+// ------------------------------------------------------------------ FP32 cut arithmetic
+// Step 1 (Section 1, Table 1): two hits of one pT-module, pT above 0.8 GeV and inside the
+// luminous-region road. L = lower-sensor hit, U = upper-sensor hit, both (x, y, z, r).
+__device__ __forceinline__ bool md_cut(const float4 L, const float4 U, bool endcap,
+                                       const lst_cuts &c, float &kappa) {
+  const float dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
+  const float dt = L.x * dx + L.y * dy;
+  const float rL = L.w;
+  if (!endcap) {
+    if (!(dt > 0.0f)) return false;                                    // direction
+    const float dT = sqrtf(dx * dx + dy * dy);
+    const float cr = L.x * dy - L.y * dx;
+    const float sa = cr / (rL * dT);
+    if (!(fabsf(sa) <= rL * (0.5f * c.kappa_max) + c.hit_err / c.sensor_gap)) return false;  // bend
+    const float dr = U.w - L.w;
+    if (!(fabsf(dz - (L.z / rL) * dr) <= (c.z_lum / rL) * dr + c.hit_err)) return false;    // z road
+    kappa = 2.0f * sa / rL;
+    return true;
+  }
+  if (!(dt > 0.0f && dz * L.z > 0.0f)) return false;                   // direction
+  const float para = dt / rL;
+  const float azl = fabsf(L.z), adz = fabsf(dz);
+  const float pe = adz * rL / azl;
+  if (!(fabsf(para - pe) <= adz * rL * c.z_lum / (azl * (azl - c.z_lum)) + c.hit_err)) return false;
+  const float cr = L.x * dy - L.y * dx;
+  const float perp = cr / rL;
+  const float S = rL * (0.5f * c.kappa_max);
+  const float T = S / sqrtf(1.0f - S * S);
+  if (!(fabsf(perp) <= para * T + c.hit_err)) return false;           // bend
+  kappa = 0.0f;
+  return true;
+}
+
+// Step 2: MD anchors A (inner) and B (outer) in linked modules; kA/kB the MD curvature
+// estimates (cut values), bA/bB barrel flags. Cheapest test first (the set is the same).
+__device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA, float kB,
+                                       bool bA, bool bB, const lst_cuts &c, float &kappa) {
+  const float e = c.hit_err;
+  const float drr = B.w - A.w;
+  if (!(fabsf(A.z * drr - A.w * (B.z - A.z)) <= (c.z_lum + e) * fabsf(drr) + e * A.w)) return false;  // z0
+  const float dx = B.x - A.x, dy = B.y - A.y;
+  const float dt = A.x * dx + A.y * dy;
+  if (!(dt > 0.0f)) return false;                                      // direction
+  const float dT = sqrtf(dx * dx + dy * dy);
+  const float cr = A.x * dy - A.y * dx;
+  const float sl = cr / (A.w * dT);
+  if (!(fabsf(sl) <= B.w * (0.5f * c.kappa_max) + e / dT)) return false;  // bend
+  const float k = 2.0f * sl / B.w;
+  if (bA && !(fabsf(kA - k) <= 2.0f * (e / c.sensor_gap) / A.w + 2.0f * (e / dT) / B.w)) return false;
+  if (bB && !(fabsf(kB - k) <= 2.0f * (e / c.sensor_gap) / B.w + 2.0f * (e / dT) / B.w)) return false;
+  kappa = k;
+  return true;
+}
+
+// Step 3: anchors of md0, md1, md2 along the chain (LS1.out == LS2.in).
+__device__ __forceinline__ bool t3_cut(const float4 P0, const float4 P1, const float4 P2,
+                                       const lst_cuts &c, float &kappa) {
+  const float ax = P1.x - P0.x, ay = P1.y - P0.y;
+  const float bx = P2.x - P1.x, by = P2.y - P1.y;
+  const float cx = P2.x - P0.x, cy = P2.y - P0.y;
+  const float a = sqrtf(ax * ax + ay * ay);
+  const float b = sqrtf(bx * bx + by * by);
+  const float cc = sqrtf(cx * cx + cy * cy);
+  const float cr = ax * cy - ay * cx;
+  const float k3 = 2.0f * cr / (a * b * cc);
+  if (!(fabsf(k3) <= c.kappa_max * c.t3_kappa_factor)) return false;     // pT
+  const float s01 = a * (1.0f + a * a * k3 * k3 / 24.0f);
+  const float s12 = b * (1.0f + b * b * k3 * k3 / 24.0f);
+  const float zp = P0.z + (P2.z - P0.z) * s01 / (s01 + s12);
+  if (!(fabsf(P1.z - zp) <= c.t3_rz_tol)) return false;                 // rz
+  kappa = k3;
+  return true;
+}
+
+// Step 4: five anchors in chain order; ka, kb the curvatures of T3a = (0,1,2), T3b = (2,3,4).
+__device__ __forceinline__ bool t5_cut(const float4 *P, float ka, float kb, const lst_cuts &c) {
+  if (!(ka * kb > 0.0f)) return false;                                   // same charge
+  if (!(fabsf(ka - kb) <= c.t5_kappa_rel * 0.5f * (fabsf(ka) + fabsf(kb)) + c.t5_kappa_abs)) return false;
+  const float kbar = 0.5f * (ka + kb);
+  float S[5];
+  S[0] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const float dx = P[i + 1].x - P[i].x, dy = P[i + 1].y - P[i].y;
+    const float d = sqrtf(dx * dx + dy * dy);
+    const float s = d * (1.0f + d * d * kbar * kbar / 24.0f);
+    S[i + 1] = (i == 0) ? s : S[i] + s;
+  }
+  const float z0 = P[0].z, z4 = P[4].z;
+#pragma unroll
+  for (int j = 1; j <= 3; j++)
+    if (!(fabsf(P[j].z - (z0 + (z4 - z0) * S[j] / S[4])) <= c.t5_rz_tol)) return false;  // rz
+  return true;
+}
+
+// ------------------------------------------------------------------ accurate FP32 helpers
+// (features only; cut values above never use them)
+struct ff { float hi, lo; };
+// a - b = hi + lo exactly (Knuth's two-sum on a + (-b))
+__device__ __forceinline__ ff two_diff(float a, float b) {
+  const float nb = -b;
+  const float s = a + nb;
+  const float bb = s - a;
+  const float err = (a - (s - bb)) + (nb - bb);
+  return {s, err};
+}
+// a*d - b*c with an FMA-compensated product (Kahan): error within 1.5 ulp of the result
+__device__ __forceinline__ float diff_of_products(float a, float d, float b, float c) {
+  const float w = b * c;
+  const float e = __fmaf_rn(-b, c, w);
+  const float f = __fmaf_rn(a, d, -w);
+  return f + e;
+}
+// cross product u x v of two exact differences u = (ux.hi+ux.lo, ...), v likewise
+__device__ __forceinline__ float cross_acc(ff ux, ff uy, ff vx, ff vy) {
+  const float main = diff_of_products(ux.hi, vy.hi, uy.hi, vx.hi);
+  const float corr = (ux.hi * vy.lo + ux.lo * vy.hi) - (uy.hi * vx.lo + uy.lo * vx.hi);
+  return main + corr;
+}
+// signed three-point curvature 2 (P1-P0)x(P2-P0) / (|P1-P0| |P2-P1| |P2-P0|), accurate
+__device__ __forceinline__ float curv3_acc(const float4 P0, const float4 P1, const float4 P2) {
+  const ff ax = two_diff(P1.x, P0.x), ay = two_diff(P1.y, P0.y);
+  const ff cx = two_diff(P2.x, P0.x), cy = two_diff(P2.y, P0.y);
+  const ff bx = two_diff(P2.x, P1.x), by = two_diff(P2.y, P1.y);
+  const float cr = cross_acc(ax, ay, cx, cy);
+  const float a = sqrtf(ax.hi * ax.hi + ay.hi * ay.hi);
+  const float b = sqrtf(bx.hi * bx.hi + by.hi * by.hi);
+  const float c = sqrtf(cx.hi * cx.hi + cy.hi * cy.hi);
+  return 2.0f * cr / (a * b * c);
+}
+// MD curvature estimate 2 sin(angle(L, U-L)) / rL of a barrel MD, accurate
+__device__ __forceinline__ float md_kappa_acc(const float4 L, const float4 U) {
+  const ff dx = two_diff(U.x, L.x), dy = two_diff(U.y, L.y);
+  const ff lx = {L.x, 0.0f}, ly = {L.y, 0.0f};
+  const float cr = cross_acc(lx, ly, dx, dy);
+  const float dT = sqrtf(dx.hi * dx.hi + dy.hi * dy.hi);
+  return 2.0f * (cr / (L.w * dT)) / L.w;
+}
+
+// ------------------------------------------------------------------ warp / block helpers
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive prefix over events of a per-event unit count, built in shared memory by
+// the whole block: pref[e] = sum_{f<e} count(f), pref[n] = total. n <= MAX_EVENTS.
+template <typename F>
+__device__ void block_event_prefix(int n, F count, int *pref) {
+  __shared__ int s_part[MAX_EVENTS / 32 + 1];
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int e = base + threadIdx.x;
+    if (e < n) pref[e + 1] = count(e);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int e = base + threadIdx.x;
+      int v = (e < n) ? pref[e + 1] : 0;
+      const int inc = warp_incl_scan(v);
+      if (e < n) pref[e + 1] = carry + inc;
+      carry += __shfl_sync(FULL, inc, 31);
+    }
+    if (threadIdx.x == 0) pref[0] = 0;
+  }
+  (void)s_part;
+  __syncthreads();
+}
+
+// index e with pref[e] <= u < pref[e+1]
+__device__ __forceinline__ int find_event(const int *pref, int n, int u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int clamp_count(int n, int cap) { return n < cap ? n : cap; }
+
+}  // namespace lstk

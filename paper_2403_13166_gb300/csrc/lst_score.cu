@@ -1,0 +1,207 @@
+// lst_score.cu -- T5-DNN (arXiv 2403.13166, Sections 2-3): the 38 input features of each
+// quintuplet and the 38 -> 32 -> ... -> 1 network (ReLU hidden layers, sigmoid output),
+// FP32 on the CUDA cores. Output candidates are exported as hit-index tuples here too.
+//
+// Features are FP32. Quantities that suffer cancellation in FP32 (three-point curvatures,
+// MD curvature estimates) use exact two-sum differences and FMA-compensated cross
+// products, so that every feature is within a few ulp of its exact value given the
+// FP32 hit coordinates; the network then keeps the score within 1e-6 of an FP64
+// evaluation.
+#include "lst_internal.cuh"
+
+namespace lstk {
+
+constexpr float KAPPA_FLOOR = 1e-7f;   // radii above 1e7 cm count as 1e7 cm in the log features
+constexpr float INV_PI = 0.318309886183790672f;
+
+// Section 2: for each of the 5 MDs the anchor hit's r, phi, z, eta, layer (+ the MD's
+// curvature estimate), the pT and radius of each T3's circle, the T5's pT, eta and phi,
+// and the radius of the bridge T3 (middle three MDs).
+__device__ void t5_features(const EvDesc &ev, const DevGeom &g, int t, float k_field, float *f) {
+  const int4 a = ev.t5_a[t], b = ev.t5_b[t];
+  const int md[5] = {a.x, a.y, a.z, a.w, b.x};
+  float4 P[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    P[i] = ev.md_anchor[md[i]];
+    const float r = P[i].w;
+    f[6 * i + 0] = r * 0.01f;
+    f[6 * i + 1] = atan2f(P[i].y, P[i].x) * INV_PI;
+    f[6 * i + 2] = P[i].z * 0.01f;
+    f[6 * i + 3] = asinhf(P[i].z / r) * 0.4f;
+    f[6 * i + 4] = (float)g.layer[ev.md_mod[md[i]]] / 11.0f;
+    f[6 * i + 5] = 100.0f * ev.md_kappa[md[i]].y;
+  }
+  const float ka = curv3_acc(P[0], P[1], P[2]);
+  const float kb = curv3_acc(P[2], P[3], P[4]);
+  const float la = log10f(fmaxf(fabsf(ka), KAPPA_FLOOR));
+  const float lb = log10f(fmaxf(fabsf(kb), KAPPA_FLOOR));
+  const float lk = log10f(k_field);
+  f[30] = lk - la;
+  f[31] = -la;
+  f[32] = lk - lb;
+  f[33] = -lb;
+  const float k5 = curv3_acc(P[0], P[2], P[4]);
+  f[34] = lk - log10f(fmaxf(fabsf(k5), KAPPA_FLOOR));
+  const float kbar = 0.5f * (ka + kb);
+  float S4 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const ff dx = two_diff(P[i + 1].x, P[i].x), dy = two_diff(P[i + 1].y, P[i].y);
+    const float d = sqrtf(dx.hi * dx.hi + dy.hi * dy.hi);
+    S4 += d * (1.0f + d * d * kbar * kbar * (1.0f / 24.0f));
+  }
+  const ff dz = two_diff(P[4].z, P[0].z);
+  f[35] = asinhf(dz.hi / S4) * 0.4f;
+  const ff ex = two_diff(P[4].x, P[0].x), ey = two_diff(P[4].y, P[0].y);
+  f[36] = atan2f(ey.hi, ex.hi) * INV_PI;
+  const float kbr = curv3_acc(P[1], P[2], P[3]);
+  f[37] = -log10f(fmaxf(fabsf(kbr), KAPPA_FLOOR));
+}
+
+// FP32 network with the weights in shared memory (flat layout of lst_mlp).
+__device__ __forceinline__ float mlp_fp32(const float *__restrict__ w, int n_hidden, const float *f) {
+  float h[NHID], t[NHID];
+#pragma unroll 4
+  for (int o = 0; o < NHID; o++) {
+    float s = w[NHID * NFEAT + o];
+#pragma unroll
+    for (int i = 0; i < NFEAT; i++) s = __fmaf_rn(w[o * NFEAT + i], f[i], s);
+    h[o] = fmaxf(s, 0.0f);
+  }
+  const float *p = w + NHID * NFEAT + NHID;
+  for (int l = 1; l < n_hidden; l++) {
+#pragma unroll 4
+    for (int o = 0; o < NHID; o++) {
+      float s = p[NHID * NHID + o];
+#pragma unroll
+      for (int i = 0; i < NHID; i++) s = __fmaf_rn(p[o * NHID + i], h[i], s);
+      t[o] = fmaxf(s, 0.0f);
+    }
+#pragma unroll
+    for (int o = 0; o < NHID; o++) h[o] = t[o];
+    p += NHID * NHID + NHID;
+  }
+  float s = p[NHID];
+#pragma unroll
+  for (int i = 0; i < NHID; i++) s = __fmaf_rn(p[i], h[i], s);
+  return 1.0f / (1.0f + expf(-s));
+}
+
+__host__ __device__ constexpr int mlp_floats(int n_hidden) {
+  return NHID * NFEAT + NHID + (n_hidden - 1) * (NHID * NHID + NHID) + NHID + 1;
+}
+
+// Fused features + FP32 network over every T5 of every event of the batch.
+__global__ void __launch_bounds__(256) k_score_fp32(const EvDesc *__restrict__ evs, int n_events,
+                                                   DevGeom g, lst_cuts c, const float *__restrict__ wts,
+                                                   int n_hidden) {
+  extern __shared__ __align__(16) float s_w[];
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  const int nw = mlp_floats(n_hidden);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) s_w[i] = wts[i];
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return clamp_count(ev.cnt[C_T5], ev.t5_cap);
+  }, s_pref);
+  const int total = s_pref[n_events];
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count so that the ballot below sees the full warp
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    const int u = base + lane;
+    bool sel = false;
+    int e = 0;
+    if (u < total) {
+      e = find_event(s_pref, n_events, u);
+      const EvDesc &ev = evs[e];
+      const int t = u - s_pref[e];
+      float f[NFEAT];
+      t5_features(ev, g, t, c.k_field, f);
+      const float s = mlp_fp32(s_w, n_hidden, f);
+      sel = s >= c.wp;
+      ev.t5_score[t] = s;
+      ev.t5_sel[t] = sel ? 1 : 0;
+    }
+    // count selected per event: lanes of one warp may straddle events
+    const unsigned act = __ballot_sync(FULL, u < total);
+    if (u < total) {
+      const unsigned same = __match_any_sync(act, e);
+      const unsigned sb = __ballot_sync(act, sel) & same;
+      if ((same & lanemask_lt()) == 0 && sb) atomicAdd(evs[e].cnt + C_NSEL, __popc(sb));
+    }
+  }
+}
+
+// Feature export [n][38] of one event (lst_get_t5_features).
+__global__ void k_features(const EvDesc *__restrict__ ev_p, DevGeom g, float k_field, float *out, int n) {
+  const EvDesc &ev = *ev_p;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    float f[NFEAT];
+    t5_features(ev, g, t, k_field, f);
+#pragma unroll
+    for (int i = 0; i < NFEAT; i++) out[(size_t)t * NFEAT + i] = f[i];
+  }
+}
+
+// Standalone scoring of precomputed features (lst_score_t5), FP32.
+__global__ void __launch_bounds__(256) k_score_feat_fp32(const float *__restrict__ feat, int64_t n,
+                                                        const float *__restrict__ wts, int n_hidden,
+                                                        float *__restrict__ out) {
+  extern __shared__ __align__(16) float s_w[];
+  const int nw = mlp_floats(n_hidden);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) s_w[i] = wts[i];
+  __syncthreads();
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    float f[NFEAT];
+#pragma unroll
+    for (int i = 0; i < NFEAT; i++) f[i] = feat[t * NFEAT + i];
+    out[t] = mlp_fp32(s_w, n_hidden, f);
+  }
+}
+
+// Hit-index tuples of one object kind of one event.
+__global__ void k_gather(const EvDesc *__restrict__ ev_p, int kind, int n, int32_t *out, float *score,
+                         uint8_t *sel) {
+  const EvDesc &ev = *ev_p;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    if (kind == LST_MD) {
+      const int2 h = ev.md_hits[t];
+      out[2 * (size_t)t] = h.x;
+      out[2 * (size_t)t + 1] = h.y;
+    } else if (kind == LST_LS) {
+      const int2 a = ev.md_hits[ev.ls_in[t]], b = ev.md_hits[ev.ls_out[t]];
+      int32_t *o = out + 4 * (size_t)t;
+      o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    } else if (kind == LST_T3) {
+      const int4 m = ev.t3_md[t];
+      const int2 a = ev.md_hits[m.x], b = ev.md_hits[m.y], c = ev.md_hits[m.z];
+      int32_t *o = out + 6 * (size_t)t;
+      o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y;
+    } else {
+      const int4 a = ev.t5_a[t], b = ev.t5_b[t];
+      const int md[5] = {a.x, a.y, a.z, a.w, b.x};
+      int32_t *o = out + 10 * (size_t)t;
+#pragma unroll
+      for (int i = 0; i < 5; i++) {
+        const int2 h = ev.md_hits[md[i]];
+        o[2 * i] = h.x;
+        o[2 * i + 1] = h.y;
+      }
+      if (score) score[t] = ev.t5_score[t];
+      if (sel) sel[t] = ev.t5_sel[t];
+    }
+  }
+}
+
+// Zero the per-event counters, sensor histogram and the per-MD range counts (units whose
+// MD range was dropped after an overflow must read as empty).
+__global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  if (tid < C_NCOUNTERS) ev.cnt[tid] = 0;
+  for (int i = tid; i < 2 * g.n_mod; i += st) ev.sens_cnt[i] = 0;
+  for (int i = tid; i < ev.md_cap; i += st) { ev.ls_cnt[i] = 0; ev.t3_cnt[i] = 0; }
+}
+
+}  // namespace lstk

@@ -1,0 +1,351 @@
+"""Thin Python binding of liblst.so (include/lst.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels. Device buffers and streams
+come from PyTorch (``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``);
+host numpy arrays are accepted where the C-ABI accepts host memory. There is no CPU
+fallback: if the library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblst.so")
+
+LST_OK, LST_ERR_ARG, LST_ERR_CAPACITY, LST_ERR_CUDA, LST_ERR_TIMEOUT, LST_ERR_NOT_READY, \
+    LST_ERR_INPUT, LST_ERR_NOMEM = range(8)
+LST_MD, LST_LS, LST_T3, LST_T5 = range(4)
+LST_FP32, LST_BF16 = 0, 1
+WIDTH = {LST_MD: 2, LST_LS: 4, LST_T3: 6, LST_T5: 10}
+NFEAT = 38
+
+
+class LstError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {_status_str(status)} ({msg})")
+        self.status = status
+
+
+class lst_module(C.Structure):
+    _fields_ = [("layer", C.c_int32), ("subdet", C.c_int32), ("side", C.c_int32), ("ps", C.c_int32)]
+
+
+class lst_cuts(C.Structure):
+    _fields_ = [(f, C.c_float) for f in synth.CUT_FIELDS]
+
+
+class lst_mlp(C.Structure):
+    _fields_ = [("n_hidden", C.c_int32), ("w", C.c_void_p)]
+
+
+class lst_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_events", C.c_int32), ("use_graphs", C.c_int32),
+                ("reserved", C.c_int32), ("md_per_hit", C.c_float), ("ls_per_md", C.c_float),
+                ("t3_per_md", C.c_float), ("t5_per_md", C.c_float)]
+
+
+class lst_launch(C.Structure):
+    _fields_ = [(f, C.c_int32) for f in ("md_threads", "md_buf", "ls_threads", "ls_stage", "ls_buf",
+                                          "t3_threads", "t3_buf", "t5_threads", "sc_threads")]
+
+
+class lst_counts(C.Structure):
+    _fields_ = [("n_hits", C.c_int64), ("n_md", C.c_int64), ("n_ls", C.c_int64), ("n_t3", C.c_int64),
+                ("n_t5", C.c_int64), ("n_selected", C.c_int64), ("pairs", C.c_int64 * 4),
+                ("status", C.c_int32), ("overflow_mask", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); every function returns lst_status unless stated
+_SIGS = {
+    "lst_default_config": [C.POINTER(lst_config)],
+    "lst_create": [C.c_int, C.POINTER(lst_config), C.POINTER(C.c_void_p)],
+    "lst_load_geometry": [C.c_void_p, C.POINTER(lst_module), C.c_int32, C.c_void_p, C.c_void_p,
+                          C.POINTER(lst_cuts), C.POINTER(lst_mlp)],
+    "lst_run_event": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                      C.POINTER(C.c_void_p)],
+    "lst_run_batch": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                      C.c_void_p, C.c_void_p],
+    "lst_event_counts": [C.c_void_p, C.POINTER(lst_counts)],
+    "lst_get_candidates": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                           C.POINTER(C.c_int64)],
+    "lst_get_t5_features": [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)],
+    "lst_score_t5": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p],
+    "lst_event_release": [C.c_void_p],
+    "lst_destroy": [C.c_void_p],
+    "lst_set_timing": [C.c_void_p, C.c_int32],
+    "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
+    "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
+    "lst_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p],
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblst.so; raises if it is missing (build it with paper_2403_13166_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"liblst.so not built ({path}); run __graft_entry__.build()")
+            lib = C.CDLL(path)
+            for name, argt in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = C.c_int
+                f.argtypes = argt
+            lib.lst_status_str.restype = C.c_char_p
+            lib.lst_status_str.argtypes = [C.c_int32]
+            lib.lst_last_error.restype = C.c_char_p
+            lib.lst_last_error.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _status_str(s):
+    try:
+        return load_library().lst_status_str(int(s)).decode()
+    except Exception:  # pragma: no cover - only for messages
+        return str(s)
+
+
+def _check(status, where, ok=(LST_OK,)):
+    if status not in ok:
+        raise LstError(status, where, load_library().lst_last_error().decode())
+    return status
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(type(a))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def default_config(**kw) -> lst_config:
+    cfg = lst_config()
+    _check(load_library().lst_default_config(C.byref(cfg)), "lst_default_config")
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def cuts_struct(cuts: dict) -> lst_cuts:
+    return lst_cuts(*[float(np.float32(cuts[f])) for f in synth.CUT_FIELDS])
+
+
+class Event:
+    """Handle of one event's results (lst_event)."""
+
+    def __init__(self, ctx, handle, status=LST_OK):
+        self.ctx = ctx
+        self.h = handle
+        self.status = status
+
+    def counts(self) -> dict:
+        c = lst_counts()
+        _check(load_library().lst_event_counts(self.h, C.byref(c)), "lst_event_counts")
+        return dict(n_hits=c.n_hits, md=c.n_md, ls=c.n_ls, t3=c.n_t3, t5=c.n_t5, selected=c.n_selected,
+                    pairs=list(c.pairs), status=c.status, overflow_mask=c.overflow_mask)
+
+    def candidates(self, kind: int, out=None, score=None, selected=None):
+        """Hit tuples [n][2|4|6|10] (+ T5 score and selection). Host numpy by default; pass
+        torch CUDA tensors to receive device copies."""
+        lib = load_library()
+        n = C.c_int64(0)
+        st = lib.lst_get_candidates(self.h, kind, None, None, None, 0, C.byref(n))
+        _check(st, "lst_get_candidates", ok=(LST_OK, LST_ERR_CAPACITY))
+        cnt = n.value
+        w = WIDTH[kind]
+        if out is None:
+            out = np.zeros((cnt, w), np.int32)
+            if kind == LST_T5:
+                score = np.zeros(cnt, np.float32)
+                selected = np.zeros(cnt, np.uint8)
+        if cnt:
+            _check(lib.lst_get_candidates(self.h, kind, _ptr(out), _ptr(score), _ptr(selected), cnt,
+                                          C.byref(n)), "lst_get_candidates")
+        if kind == LST_T5:
+            return out, score, selected
+        return out
+
+    def features(self):
+        lib = load_library()
+        n = C.c_int64(0)
+        _check(lib.lst_get_t5_features(self.h, None, 0, C.byref(n)), "lst_get_t5_features",
+               ok=(LST_OK, LST_ERR_CAPACITY))
+        f = np.zeros((n.value, NFEAT), np.float32)
+        if n.value:
+            _check(lib.lst_get_t5_features(self.h, _ptr(f), n.value, C.byref(n)), "lst_get_t5_features")
+        return f
+
+    def release(self):
+        if self.h:
+            load_library().lst_event_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Context:
+    """lst_ctx: device-resident detector, module map, cut parameters and T5-DNN."""
+
+    def __init__(self, device: int = 0, **cfg):
+        lib = load_library()
+        self._cfg = default_config(**cfg)
+        h = C.c_void_p()
+        _check(lib.lst_create(device, C.byref(self._cfg), C.byref(h)), "lst_create")
+        self.h = h
+        self.device = device
+
+    def load_geometry(self, geom, cuts: dict, mlp_flat=None, n_hidden: int = 2):
+        lib = load_library()
+        n = geom.n_mod
+        mods = (lst_module * n)()
+        for i in range(n):
+            mods[i] = lst_module(int(geom.layer[i]), int(geom.subdet[i]), int(geom.side[i]), int(geom.ps[i]))
+        off = np.ascontiguousarray(geom.map_off, np.int32)
+        tgt = np.ascontiguousarray(geom.map_tgt, np.int32)
+        cs = cuts_struct(cuts)
+        mp = None
+        self._w = None
+        if mlp_flat is not None:
+            self._w = np.ascontiguousarray(mlp_flat, np.float32)
+            mp = C.byref(lst_mlp(int(n_hidden), self._w.ctypes.data))
+        _check(lib.lst_load_geometry(self.h, mods, n, _ptr(off), _ptr(tgt), C.byref(cs), mp),
+               "lst_load_geometry")
+        self.cuts = dict(cuts)
+
+    def run_event(self, x, y, z, sensor, stream=None) -> Event:
+        lib = load_library()
+        n = int(x.shape[0])
+        ev = C.c_void_p()
+        st = lib.lst_run_event(self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(sensor), n, _stream_handle(stream),
+                               C.byref(ev))
+        _check(st, "lst_run_event", ok=(LST_OK, LST_ERR_INPUT))
+        return Event(self, ev, st)
+
+    def run_batch(self, events, stream=None):
+        """events: list of (x, y, z, sensor) device tensors or host arrays."""
+        lib = load_library()
+        n = len(events)
+        P = C.c_void_p * n
+        xs, ys, zs, ss = P(), P(), P(), P()
+        nh = (C.c_int64 * n)()
+        for i, (x, y, z, s) in enumerate(events):
+            xs[i], ys[i], zs[i], ss[i] = _ptr(x), _ptr(y), _ptr(z), _ptr(s)
+            nh[i] = int(x.shape[0])
+        out = (C.c_void_p * n)()
+        _check(lib.lst_run_batch(self.h, n, xs, ys, zs, ss, nh, _stream_handle(stream), out),
+               "lst_run_batch")
+        return [Event(self, C.c_void_p(out[i]), LST_ERR_NOT_READY) for i in range(n)]
+
+    def score_t5(self, feat, out, precision=LST_FP32, stream=None):
+        lib = load_library()
+        _check(lib.lst_score_t5(self.h, _ptr(feat), int(feat.shape[0]), precision, _ptr(out),
+                                _stream_handle(stream)), "lst_score_t5")
+
+    def get_launch(self) -> dict:
+        p = lst_launch()
+        _check(load_library().lst_get_launch(self.h, C.byref(p)), "lst_get_launch")
+        return {f: getattr(p, f) for f, _ in lst_launch._fields_}
+
+    def set_launch(self, **kw):
+        cur = self.get_launch()
+        cur.update(kw)
+        p = lst_launch(**cur)
+        _check(load_library().lst_set_launch(self.h, C.byref(p)), "lst_set_launch")
+
+    def set_timing(self, on=True):
+        _check(load_library().lst_set_timing(self.h, int(on)), "lst_set_timing")
+
+    def stage_times(self):
+        """Mean device ms per launch of (bin, md, ls, t3, t5, score), and the launch count."""
+        a = np.zeros(6, np.float32)
+        n = C.c_int64(0)
+        _check(load_library().lst_stage_times(self.h, _ptr(a), C.byref(n)), "lst_stage_times")
+        return a, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().lst_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# C-ABI names, for callers that prefer the flat interface
+def lst_create(device=0, **cfg):
+    return Context(device, **cfg)
+
+
+def lst_load_geometry(ctx, geom, cuts, mlp_flat=None, n_hidden=2):
+    ctx.load_geometry(geom, cuts, mlp_flat, n_hidden)
+
+
+def lst_run_event(ctx, x, y, z, sensor, stream=None):
+    return ctx.run_event(x, y, z, sensor, stream)
+
+
+def lst_run_batch(ctx, events, stream=None):
+    return ctx.run_batch(events, stream)
+
+
+def lst_get_candidates(ev, kind):
+    return ev.candidates(kind)
+
+
+def lst_get_t5_features(ev):
+    return ev.features()
+
+
+def lst_score_t5(ctx, feat, out, precision=LST_FP32, stream=None):
+    ctx.score_t5(feat, out, precision, stream)
+
+
+def lst_event_release(ev):
+    ev.release()
+
+
+def lst_destroy(ctx):
+    ctx.close()
+
+
+def header_symbols(header_path: str):
+    """Entry points declared in include/lst.h."""
+    import re
+    src = open(header_path).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(lst_\w+)\s*\(", src, re.M)))

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/lst.h
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2403_13166_gb300 import build
+    return build.build()
+
+
+def test_header_symbols_exported(libpath):
+    from paper_2403_13166_gb300 import lst
+    syms = lst.header_symbols(os.path.join(ROOT, "include", "lst.h"))
+    for must in ("lst_load_geometry", "lst_run_event", "lst_get_candidates", "lst_score_t5",
+                 "lst_create", "lst_destroy", "lst_run_batch"):
+        assert must in syms
+    lib = ctypes.CDLL(libpath)
+    for s in syms:
+        assert hasattr(lib, s), s
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(syms) <= exported
+
+
+def test_binding_loads_and_reports_status(libpath):
+    from paper_2403_13166_gb300 import lst
+    lib = lst.load_library()
+    assert lib.lst_status_str(lst.LST_ERR_CAPACITY).decode() == "LST_ERR_CAPACITY"
+    assert lib.lst_status_str(99).decode() == "LST_ERR_UNKNOWN"
+    cfg = lst.default_config()
+    assert cfg.max_events >= 1 and cfg.precision == lst.LST_FP32
+    # argument checks need no device
+    h = ctypes.c_void_p()
+    assert lib.lst_create(0, None, None) == lst.LST_ERR_ARG
+    assert lib.lst_run_event(None, None, None, None, None, 0, None, ctypes.byref(h)) == lst.LST_ERR_ARG
+
+
+def test_binding_names_match_abi(libpath):
+    from paper_2403_13166_gb300 import lst
+    for name in ("lst_create", "lst_load_geometry", "lst_run_event", "lst_run_batch", "lst_get_candidates",
+                 "lst_get_t5_features", "lst_score_t5", "lst_event_release", "lst_destroy"):
+        assert callable(getattr(lst, name))
+
+
+def test_structs_match_header_layout(libpath):
+    from paper_2403_13166_gb300 import lst
+    assert ctypes.sizeof(lst.lst_cuts) == 13 * 4
+    assert ctypes.sizeof(lst.lst_module) == 16
+    assert ctypes.sizeof(lst.lst_config) == 32
+    assert ctypes.sizeof(lst.lst_counts) == 10 * 8 + 8
+    assert ctypes.sizeof(lst.lst_launch) == 9 * 4

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA library (through the C-ABI) against the CPU oracle.
+
+Bar: MD/LS/T3/T5 candidate sets bit-identical after canonical sorting (FP32 cut
+arithmetic is the same expression tree on both sides); T5-DNN scores within 1e-6 of the
+FP64 oracle; selection flags equal except where the oracle score lies within 1e-5 of the
+working point."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_13166_gb300 import lst, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SCORE_TOL = 1e-6
+WP_BAND = 1e-5
+KINDS = ((lst.LST_MD, "md_hits"), (lst.LST_LS, "ls_hits"), (lst.LST_T3, "t3_hits"), (lst.LST_T5, "t5_hits"))
+
+
+def canon_order(a):
+    return np.lexsort(a.T[::-1]) if len(a) else np.zeros(0, np.int64)
+
+
+def dev(e):
+    d = torch.device("cuda:0")
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(d) for a in (e.x, e.y, e.z, e.sensor)]
+
+
+def compare(ev, ref, wp, check_features=False):
+    for kind, name in KINDS:
+        got = ev.candidates(kind)
+        if kind == lst.LST_T5:
+            got, score, sel = got
+        exp = getattr(ref, name)()
+        assert got.shape == exp.shape, (name, got.shape, exp.shape)
+        og, oe = canon_order(got), canon_order(exp)
+        assert np.array_equal(got[og], exp[oe]), name
+    c = ev.counts()
+    assert list(c["pairs"]) == list(ref.pairs), (c["pairs"], ref.pairs)
+    if len(exp):
+        s_ref = ref.t5_score[oe]
+        s_got = score[og].astype(np.float64)
+        err = np.max(np.abs(s_got - s_ref))
+        assert err <= SCORE_TOL, err
+        far = np.abs(s_ref - wp) >= WP_BAND
+        assert np.array_equal(sel[og][far].astype(bool), (s_ref >= wp)[far])
+        if check_features:
+            f = ev.features()[og].astype(np.float64)
+            df = np.abs(f - ref.t5_feat[oe])
+            assert np.max(df) <= 4e-6, (np.max(df), np.unravel_index(np.argmax(df), df.shape))
+    return c
+
+
+@pytest.fixture(scope="module")
+def model():
+    return synth.mlp_flat(synth.xavier_mlp()), 2
+
+
+@pytest.fixture(scope="module")
+def ctx_toy(geom_toy, cuts, model):
+    c = lst.Context(0, max_events=8)
+    c.load_geometry(geom_toy, cuts, *model)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_full(geom_full, cuts, model):
+    c = lst.Context(0, max_events=16)
+    c.load_geometry(geom_full, cuts, *model)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("index", [0, 1, 2])
+def test_toy_parity(ctx_toy, geom_toy, cuts, model, index):
+    e = synth.toy_event(geom_toy, index)
+    ref = oracle.run_event(geom_toy, e, cuts, *model)
+    ev = ctx_toy.run_event(*dev(e))
+    c = compare(ev, ref, float(cuts["wp"]), check_features=True)
+    assert c["t5"] == ref.counts["t5"] > 0
+    ev.release()
+
+
+@pytest.mark.parametrize("pileup,index", [(20, 0), (60, 1)])
+def test_pileup_slice_parity(ctx_full, geom_full, cuts, model, pileup, index):
+    e = synth.pileup_event(geom_full, index, pileup=pileup, mean_per_vertex=96)
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = ctx_full.run_event(*dev(e))
+    compare(ev, ref, float(cuts["wp"]), check_features=True)
+    ev.release()
+
+
+def test_pu200_full_parity(ctx_full, geom_full, cuts, model):
+    e = synth.pileup_event(geom_full, 0, pileup=200, mean_per_vertex=96)
+    assert e.n_hits > 200_000
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = ctx_full.run_event(*dev(e))
+    c = compare(ev, ref, float(cuts["wp"]), check_features=True)
+    assert c["ls"] > 500_000
+    ev.release()
+
+
+def test_empty_and_degenerate_events(ctx_full, geom_full, cuts, model):
+    empty = synth.Event(x=np.zeros(0, np.float32), y=np.zeros(0, np.float32), z=np.zeros(0, np.float32),
+                        sensor=np.zeros(0, np.int32), pid=np.zeros(0, np.int32), particles={})
+    ev = ctx_full.run_event(*dev(empty))
+    c = ev.counts()
+    assert c["md"] == c["ls"] == c["t3"] == c["t5"] == 0 and c["status"] == lst.LST_OK
+    ev.release()
+    # a single track whose hits are all in lower sensors: no MD at all
+    e = synth.muon_event(geom_full, [2.0], [0.3], [0.1], [1.0], sigma=0.0)
+    keep = e.sensor % 2 == 0
+    lo = synth.Event(x=e.x[keep], y=e.y[keep], z=e.z[keep], sensor=e.sensor[keep], pid=e.pid[keep], particles={})
+    ev = ctx_full.run_event(*dev(lo))
+    assert ev.counts()["md"] == 0
+    ev.release()
+    # one noiseless track
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = ctx_full.run_event(*dev(e))
+    compare(ev, ref, float(cuts["wp"]))
+    ev.release()
+
+
+def test_invalid_hits_report_input_error(ctx_full, geom_full, cuts, model):
+    e = synth.pileup_event(geom_full, 3, pileup=5, mean_per_vertex=96)
+    for mutate in ("sensor", "nan"):
+        x, s = e.x.copy(), e.sensor.copy()
+        if mutate == "sensor":
+            s[7] = geom_full.n_sensor + 3
+        else:
+            x[11] = np.nan
+        bad = synth.Event(x=x, y=e.y, z=e.z, sensor=s, pid=e.pid, particles={})
+        ev = ctx_full.run_event(*dev(bad))
+        assert ev.status == lst.LST_ERR_INPUT
+        ev.release()
+    # the context stays usable
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = ctx_full.run_event(*dev(e))
+    compare(ev, ref, float(cuts["wp"]))
+    ev.release()
+
+
+def test_overflow_regrows_to_exact_result(geom_full, cuts, model):
+    c = lst.Context(0, max_events=2, md_per_hit=0.001, ls_per_md=0.01, t3_per_md=0.01, t5_per_md=0.01)
+    c.load_geometry(geom_full, cuts, *model)
+    e = synth.pileup_event(geom_full, 4, pileup=30, mean_per_vertex=96)
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = c.run_event(*dev(e))
+    compare(ev, ref, float(cuts["wp"]))
+    ev.release()
+    c.close()
+
+
+def test_list_overflow_and_unstaged_paths(geom_full, cuts, model):
+    """Tiny per-warp lists and staging buffers force the re-evaluation and global-memory
+    paths of every stage; results must not change."""
+    c = lst.Context(0, max_events=2)
+    c.load_geometry(geom_full, cuts, *model)
+    c.set_launch(md_buf=1, ls_buf=2, ls_stage=16, t3_buf=1, md_threads=64, ls_threads=128, t3_threads=96)
+    e = synth.pileup_event(geom_full, 5, pileup=40, mean_per_vertex=96)
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = c.run_event(*dev(e))
+    compare(ev, ref, float(cuts["wp"]))
+    ev.release()
+    c.close()
+
+
+def test_batch_equals_single_and_graph_replay(ctx_full, geom_full, cuts, model):
+    evs = [synth.pileup_event(geom_full, i, pileup=pu, mean_per_vertex=96, config=4)
+           for i, pu in enumerate((50, 250, 120, 7, 180, 90))]
+    inputs = [dev(e) for e in evs]
+    singles = []
+    for t in inputs:
+        ev = ctx_full.run_event(*t)
+        singles.append({k: np.sort(ev.candidates(k)[0] if k == lst.LST_T5 else ev.candidates(k), axis=0)
+                        for k, _ in KINDS})
+        ev.release()
+    for rep in range(3):   # first run captures the graph, later runs replay it
+        handles = ctx_full.run_batch(inputs)
+        for h, s, e in zip(handles, singles, evs):
+            assert h.counts()["status"] == lst.LST_OK
+            for k, _ in KINDS:
+                got = h.candidates(k)
+                got = got[0] if k == lst.LST_T5 else got
+                assert np.array_equal(np.sort(got, axis=0), s[k])
+            h.release()
+    # one batched event also against the oracle
+    ref = oracle.run_event(geom_full, evs[1], cuts, *model)
+    h = ctx_full.run_batch(inputs[1:2])[0]
+    compare(h, ref, float(cuts["wp"]))
+    h.release()
+
+
+def test_host_inputs_match_device_inputs(ctx_full, geom_full, cuts, model):
+    e = synth.pileup_event(geom_full, 6, pileup=25, mean_per_vertex=96)
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = ctx_full.run_event(e.x, e.y, e.z, e.sensor)
+    compare(ev, ref, float(cuts["wp"]))
+    ev.release()
+
+
+def test_score_t5_standalone_fp32(ctx_full, model):
+    rng = np.random.default_rng(11)
+    f = rng.normal(0, 1, (5000, 38)).astype(np.float32)
+    d = torch.from_numpy(f).cuda()
+    out = torch.empty(5000, dtype=torch.float32, device="cuda")
+    ctx_full.score_t5(d, out, lst.LST_FP32)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    exp = np.array([oracle.mlp_forward(model[0], 2, f[i].astype(np.float64)) for i in range(0, 5000, 7)])
+    assert np.max(np.abs(got[::7] - exp)) <= SCORE_TOL
