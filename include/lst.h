@@ -199,6 +199,43 @@ lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);
 lst_status lst_set_timing(lst_ctx ctx, int32_t enable);
 lst_status lst_stage_times(lst_ctx ctx, float *ms6, int64_t *n_launches);
 
+/* ---------------------------------------------------------------------------------
+ * Mini-doublet finder that allocates nothing (the paper has no counterpart; it is a
+ * deployment aid of this library).
+ *
+ * For callers that cannot call cudaMalloc/cudaFree while they run: a host framework
+ * that owns all device memory through its own caching allocator (a foreign cudaFree
+ * synchronises the device), trigger or real-time loops whose latency budget cannot
+ * absorb that synchronisation, or code that enqueues work while a global-mode stream
+ * capture is active elsewhere in the process (allocation is prohibited then).
+ *
+ * Does steps 0-1 (hit grouping by sensor, then every mini-doublet of the event, with
+ * the same FP32 cuts as lst_run_event) using only a fixed scratch array compiled into
+ * the library: LST_NOALLOC_SCRATCH_BYTES (about 10.3 MiB) of device memory that every
+ * GPU loading the library holds until the process exits. Limits: n_hits <=
+ * LST_NOALLOC_MAX_HITS and 2 * n_mod <= LST_NOALLOC_MAX_SENSORS; larger requests return
+ * LST_ERR_ARG before any GPU work (lst_last_error says which limit).
+ *   ctx       a context with geometry loaded (lst_load_geometry);
+ *   x,y,z,sensor  DEVICE hit arrays as in lst_run_event;
+ *   md_hits   DEVICE int32 [capacity][2] (lower, upper) original hit indices, caller-owned;
+ *   md_kappa  DEVICE float [capacity] MD curvature estimate (0 for endcap), may be NULL;
+ *   md_count  DEVICE int64 [1]: number of MDs found (may exceed capacity: then only
+ *             `capacity` of them, in unspecified order, were written), or -1 if a hit had
+ *             an invalid sensor id or a non-finite coordinate.
+ * Asynchronous on cuda_stream; MDs come in no particular order (compare as sets).
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture. Every call reuses the same scratch and clears what must start at
+ * zero; calls that overlap on the GPU (other streams, other threads) race on it and
+ * must be serialised by the caller. */
+#define LST_NOALLOC_MAX_HITS 524288
+#define LST_NOALLOC_MAX_SENSORS 32768
+#define LST_NOALLOC_SCRATCH_BYTES 10748416
+lst_status lst_find_minidoublets_noalloc(lst_ctx ctx, const float *x, const float *y, const float *z,
+                                         const int32_t *sensor, int64_t n_hits, int32_t *md_hits,
+                                         float *md_kappa, int64_t capacity, int64_t *md_count,
+                                         void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -857,3 +857,17 @@ lst_status lst_stage_times(lst_ctx c, float *ms6, int64_t *n_launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- internal accessors
+namespace lstk {
+// Geometry, cuts and device of a context (false while no geometry is loaded).
+bool ctx_geometry(lst_ctx ctx, DevGeom *g, lst_cuts *c, int *device) {
+  if (!ctx || !ctx->have_geom) return false;
+  *g = ctx->g;
+  *c = ctx->cuts;
+  *device = ctx->device;
+  return true;
+}
+// Sets the calling thread's lst_last_error text.
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace lstk

@@ -85,7 +85,14 @@ _SIGS = {
     "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "lst_find_minidoublets_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                      C.c_void_p],
 }
+
+#: limits of lst_find_minidoublets_noalloc's fixed scratch array (include/lst.h)
+NOALLOC_MAX_HITS = 524288
+NOALLOC_MAX_SENSORS = 32768
 
 
 def load_library(path: str = LIB_PATH):
@@ -273,6 +280,18 @@ class Context:
         lib = load_library()
         _check(lib.lst_score_t5(self.h, _ptr(feat), int(feat.shape[0]), precision, _ptr(out),
                                 _stream_handle(stream)), "lst_score_t5")
+
+    def find_minidoublets_noalloc(self, x, y, z, sensor, md_hits, md_kappa, md_count, stream=None) -> int:
+        """Steps 0-1 without any device allocation by the library (for callers that cannot
+        allocate while they run, e.g. inside a framework that owns all device memory). All
+        buffers are the caller's device tensors: md_hits int32 [cap, 2], md_kappa float32
+        [cap] or None, md_count int64 [1] (count found, or -1 for an invalid hit).
+        Returns the lst_status; raises on errors other than success."""
+        cap = int(md_hits.shape[0]) if md_hits is not None else 0
+        st = load_library().lst_find_minidoublets_noalloc(
+            self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(sensor), int(x.shape[0]), _ptr(md_hits), _ptr(md_kappa),
+            cap, _ptr(md_count), _stream_handle(stream))
+        return _check(st, "lst_find_minidoublets_noalloc")
 
     def get_launch(self) -> dict:
         p = lst_launch()
