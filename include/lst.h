@@ -182,11 +182,12 @@ const char *lst_last_error(void);
  * shared memory within the device limit) and recomputes the persistent grid sizes; the
  * results never depend on these values, only the speed does. */
 typedef struct lst_launch {
-    int32_t md_threads, md_buf;              /* step 1: CTA size, per-warp candidate list */
-    int32_t ls_threads, ls_stage, ls_buf;    /* step 2: CTA size, staged target MDs, list */
-    int32_t t3_threads, t3_buf;              /* step 3 */
-    int32_t t5_threads;                      /* step 4 */
-    int32_t sc_threads;                      /* score */
+    int32_t md_threads, md_buf;    /* step 1: CTA size, per-warp candidate list entries */
+    int32_t ls_threads, ls_list;   /* step 2: CTA size, shared candidate list entries per tile */
+    int32_t t3_threads;            /* step 3: CTA size */
+    int32_t t5_threads;            /* step 4: CTA size */
+    int32_t sc_threads;            /* score: CTA size */
+    int32_t reserved;
 } lst_launch;
 lst_status lst_get_launch(lst_ctx ctx, lst_launch *out);
 lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);

@@ -20,9 +20,11 @@ __global__ void k_bin_count(const EvDesc *, DevGeom);
 __global__ void k_bin_scan(const EvDesc *, DevGeom);
 __global__ void k_bin_scatter(const EvDesc *, DevGeom);
 __global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
-__global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, int, int);
-__global__ void k_t3(const EvDesc *, int, lst_cuts, int *, int);
-__global__ void k_t5(const EvDesc *, int, lst_cuts, int *);
+__global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
+__global__ void k_t3(const EvDesc *, int, lst_cuts);
+__global__ void k_t3_scan(const EvDesc *);
+__global__ void k_t3_scatter(const EvDesc *, int);
+__global__ void k_t5(const EvDesc *, int, lst_cuts);
 __global__ void k_score_fp32(const EvDesc *, int, DevGeom, lst_cuts, const float *, int);
 __global__ void k_features(const EvDesc *, DevGeom, float, float *, int);
 __global__ void k_score_feat_fp32(const float *, int64_t, const float *, int, float *);
@@ -129,8 +131,8 @@ struct lst_ctx_s {
   float r_md, r_ls, r_t3, r_t5;
   // launch shapes (autotuned)
   int md_threads = 256, md_buf = 128;
-  int ls_threads = 256, ls_stage = 3072, ls_buf = 256;
-  int t3_threads = 256, t3_buf = 128;
+  int ls_threads = 128, ls_list = 1024;
+  int t3_threads = 256;
   int t5_threads = 256;
   int sc_threads = 256;
   int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
@@ -151,15 +153,13 @@ struct lst_event_s {
 
 namespace {
 
+constexpr int LS_IN_CHUNK_HOST = 64;   // k_ls inner-MD tile (LS_IN_CHUNK)
 size_t ls_smem(const lst_ctx_s *c) {
-  return (size_t)c->ls_stage * (16 + 4 + 4) + (2 * MAX_FANOUT + 1) * 4 +
-         (size_t)(c->ls_threads / 32) * c->ls_buf * 8;
+  return (size_t)LS_IN_CHUNK_HOST * (16 + 4 + 4 + 4) + (3 * MAX_FANOUT + 1) * 4 + (size_t)c->ls_list * 12;
 }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * c->md_buf * 12; }
-size_t t3_smem(const lst_ctx_s *c) {
-  return (size_t)(c->t3_threads / 32) * (sizeof(int) * 128) + (size_t)(c->t3_threads / 32) * c->t3_buf * 12;
-}
-size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (sizeof(int) * 128); }
+size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * (4 * 128 + 2 * 512); }
+size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
 int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
 
 lst_status compute_grids(lst_ctx_s *c) {
@@ -222,7 +222,7 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   const size_t o_lin = take(4 * (size_t)ls), o_lout = take(4 * (size_t)ls), o_lk = take(4 * (size_t)ls),
                o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
   const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
-               o_t3c = take(4 * (size_t)md);
+               o_t3c = take(4 * (size_t)md), o_t3u = take(16 * (size_t)t3), o_t3uk = take(4 * (size_t)t3);
   const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
                o_t5e = take((size_t)t5);
   const size_t o_cnt = take(4 * C_NCOUNTERS);
@@ -241,8 +241,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   d.md_hits = (int2 *)(b + o_mh); d.md_start = (int32_t *)(b + o_mst); d.md_cnt = (int32_t *)(b + o_mcn);
   d.ls_in = (int32_t *)(b + o_lin); d.ls_out = (int32_t *)(b + o_lout); d.ls_kappa = (float *)(b + o_lk);
   d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
-  d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_start = (int32_t *)(b + o_t3s);
-  d.t3_cnt = (int32_t *)(b + o_t3c);
+  d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_pos = (int32_t *)(b + o_t3s);
+  d.t3_cnt = (int32_t *)(b + o_t3c); d.t3u_md = (int4 *)(b + o_t3u); d.t3u_kappa = (float *)(b + o_t3uk);
   d.t5_a = (int4 *)(b + o_t5a); d.t5_b = (int4 *)(b + o_t5b); d.t5_score = (float *)(b + o_t5s);
   d.t5_sel = (uint8_t *)(b + o_t5e); d.cnt = (int32_t *)(b + o_cnt);
   s.hit_cap = H; s.md_cap = md; s.ls_cap = ls; s.t3_cap = t3; s.t5_cap = t5;
@@ -330,11 +330,13 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   mark(1);
   k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 0, c->md_buf);
   mark(2);
-  k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->ls_stage, c->ls_buf);
+  k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->ls_list);
   mark(3);
-  k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts, L.d_work + 2, c->t3_buf);
+  k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts);
+  k_t3_scan<<<n, 1024, 0, st>>>(L.d_desc);
+  k_t3_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
   mark(4);
-  k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts, L.d_work + 3);
+  k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
   mark(5);
   k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
       L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
@@ -362,6 +364,7 @@ void grow_ratios(lst_ctx_s *c, const Slot &s, const int32_t *cnt) {
 }
 
 lst_status status_of(const int32_t *cnt) {
+  if (cnt[C_FLAGS] & F_CHECK) return LST_ERR_CUDA;   // failed device bounds check (LST_CHECK builds)
   if (cnt[C_FLAGS] & F_INPUT) return LST_ERR_INPUT;
   if (cnt[C_FLAGS] & (F_OVF_MD | F_OVF_LS | F_OVF_T3 | F_OVF_T5)) return LST_ERR_CAPACITY;
   return LST_OK;
@@ -588,6 +591,12 @@ lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float 
     if (s != LST_OK) return s;
     const lst_status es = status_of(S.cnt);
     if (es == LST_ERR_CAPACITY) { grow_ratios(c, S, S.cnt); continue; }
+    if (S.cnt[C_FLAGS] & F_CHECK) {
+      char msg[128];
+      std::snprintf(msg, sizeof msg, "device bounds check failed at site %d, index %d", S.cnt[C_DBG_SITE],
+                    S.cnt[C_DBG_VAL]);
+      return fail(LST_ERR_CUDA, msg);
+    }
     S.busy = true;
     lst_event ev = new lst_event_s{c, si, es};
     *out = ev;
@@ -806,8 +815,8 @@ lst_status lst_destroy(lst_ctx c) {
 
 lst_status lst_get_launch(lst_ctx c, lst_launch *o) {
   if (!c || !o) return fail(LST_ERR_ARG, "null argument");
-  *o = lst_launch{c->md_threads, c->md_buf, c->ls_threads, c->ls_stage, c->ls_buf,
-                  c->t3_threads, c->t3_buf, c->t5_threads, c->sc_threads};
+  *o = lst_launch{c->md_threads, c->md_buf, c->ls_threads, c->ls_list, c->t3_threads, c->t5_threads,
+                  c->sc_threads, 0};
   return LST_OK;
 }
 
@@ -816,20 +825,20 @@ lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
   const int th[5] = {p->md_threads, p->ls_threads, p->t3_threads, p->t5_threads, p->sc_threads};
   for (int t : th)
     if (t < 32 || t > 256 || t % 32) return fail(LST_ERR_ARG, "threads must be a multiple of 32 in 32..256");
-  if (p->md_buf < 1 || p->ls_stage < 1 || p->ls_buf < 1 || p->t3_buf < 1) return fail(LST_ERR_ARG, "sizes must be >= 1");
+  if (p->md_buf < 1 || p->ls_list < 1) return fail(LST_ERR_ARG, "sizes must be >= 1");
   DeviceGuard gd(c->device);
   CU(cudaDeviceSynchronize());
   lst_ctx_s old = *c;
   c->md_threads = p->md_threads; c->md_buf = p->md_buf;
-  c->ls_threads = p->ls_threads; c->ls_stage = p->ls_stage; c->ls_buf = p->ls_buf;
-  c->t3_threads = p->t3_threads; c->t3_buf = p->t3_buf; c->t5_threads = p->t5_threads;
+  c->ls_threads = p->ls_threads; c->ls_list = p->ls_list;
+  c->t3_threads = p->t3_threads; c->t5_threads = p->t5_threads;
   c->sc_threads = p->sc_threads;
   int dev_smem = 0;
   CU(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   if (ls_smem(c) > (size_t)dev_smem - 2048 || md_smem(c) > (size_t)dev_smem || t3_smem(c) > (size_t)dev_smem - 4096) {
     c->md_threads = old.md_threads; c->md_buf = old.md_buf; c->ls_threads = old.ls_threads;
-    c->ls_stage = old.ls_stage; c->ls_buf = old.ls_buf; c->t3_threads = old.t3_threads;
-    c->t3_buf = old.t3_buf; c->t5_threads = old.t5_threads; c->sc_threads = old.sc_threads;
+    c->ls_list = old.ls_list; c->t3_threads = old.t3_threads;
+    c->t5_threads = old.t5_threads; c->sc_threads = old.sc_threads;
     return fail(LST_ERR_ARG, "shared memory of the launch shape exceeds the device limit");
   }
   lst_status s = compute_grids(c);

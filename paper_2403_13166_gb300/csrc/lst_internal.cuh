@@ -20,9 +20,10 @@ constexpr int MAX_FANOUT = 512;       // module-map targets of one module
 enum CounterSlot {
   C_MD = 0, C_LS = 1, C_T3 = 2, C_T5 = 3, C_FLAGS = 4, C_NSEL = 5,
   C_PMD = 6, C_PLS = 7, C_PT3 = 8, C_PT5 = 9,   // candidate pairs tested per step
+  C_DBG_SITE = 10, C_DBG_VAL = 11,              // first failed bounds check (LST_CHECK builds)
   C_NCOUNTERS = 12
 };
-enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16 };
+enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16, F_CHECK = 32 };
 
 struct DevGeom {
   int32_t n_mod;
@@ -52,9 +53,12 @@ struct EvDesc {
   int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD
   float *ls_kappa;             // [ls_cap]
   int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
-  int4 *t3_md;                 // [t3_cap] (md0, md1, md2, -)
+  int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, -), any order
+  float *t3u_kappa;            // [t3_cap]
+  int4 *t3_md;                 // [t3_cap] T3s grouped by first MD
   float *t3_kappa;             // [t3_cap]
-  int32_t *t3_start, *t3_cnt;  // [md_cap] T3s of each first MD: contiguous range
+  int32_t *t3_pos, *t3_cnt;    // [md_cap] per first MD: start of its range (end after the
+                               // grouping scatter) and count
   int4 *t5_a;                  // [t5_cap] (md0, md1, md2, md3)
   int4 *t5_b;                  // [t5_cap] (md4, t3a, t3b, -)
   float *t5_score;             // [t5_cap]
@@ -253,5 +257,25 @@ __device__ __forceinline__ int find_event(const int *pref, int n, int u) {
 }
 
 __device__ __forceinline__ int clamp_count(int n, int cap) { return n < cap ? n : cap; }
+
+// An event whose input was invalid or whose buffers overflowed is skipped by every later
+// stage (its results are void and the host re-runs it with larger buffers).
+__device__ __forceinline__ bool ev_void(const EvDesc &ev) {
+  return (ev.cnt[C_FLAGS] & (F_INPUT | F_OVF_MD | F_OVF_LS | F_OVF_T3 | F_OVF_T5 | F_CHECK)) != 0;
+}
+
+// Bounds check of a data-derived index (debug builds, -DLST_CHECK): an index outside
+// [0, cap) is not used; the first failing site and index are recorded in the event's
+// counters and the event is voided, so the host reports it instead of the GPU faulting.
+#ifdef LST_CHECK
+static __device__ __noinline__ bool chk(const EvDesc &ev, long long i, long long cap, int site) {
+  if (i >= 0 && i < cap) return true;
+  if (atomicCAS(ev.cnt + C_DBG_SITE, 0, site) == 0) ev.cnt[C_DBG_VAL] = (int)i;
+  atomicOr(ev.cnt + C_FLAGS, F_CHECK);
+  return false;
+}
+#else
+__device__ __forceinline__ bool chk(const EvDesc &, long long, long long, int) { return true; }
+#endif
 
 }  // namespace lstk

@@ -82,15 +82,8 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, DevGeom g) {
 }
 
 // ===================================================================== shared machinery
-// Fetch the next unit for a warp from a global work counter.
-__device__ __forceinline__ int warp_next(int *work) {
-  int u = 0;
-  if ((threadIdx.x & 31) == 0) u = atomicAdd(work, 1);
-  return __shfl_sync(FULL, u, 0);
-}
-
-// Reserve n output slots for a unit: one atomicAdd per warp. Returns the base or -1 if the
-// buffer would overflow (then the flag is set; the counter still records the demand).
+// Reserve n output slots: one atomicAdd per warp. Returns the base or -1 if the buffer
+// would overflow (then the flag is set; the counter still records the demand).
 __device__ __forceinline__ int warp_reserve(int *counter, int *flags, int flag, int n, int cap) {
   int base = 0;
   if ((threadIdx.x & 31) == 0 && n > 0) {
@@ -104,9 +97,11 @@ __device__ __forceinline__ int warp_reserve(int *counter, int *flags, int flag, 
 }
 
 // ===================================================================== step 1: mini-doublets
-// One warp per (event, module): all (lower, upper) hit pairs of the module.
+// One warp per (event, module): all (lower, upper) hit pairs of the module. Warps take
+// MD_CHUNK consecutive modules per atomic fetch.
 // smem per warp: buf_cap entries of (pair index, cut kappa, feature kappa).
 struct MdBuf { int p; float kc, kf; };
+constexpr int MD_CHUNK = 4;
 
 __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
                                            lst_cuts c, int *work, int buf_cap) {
@@ -115,396 +110,471 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
   const int lane = threadIdx.x & 31;
   const int total = n_events * g.n_mod;
   for (;;) {
-    const int u = warp_next(work);
-    if (u >= total) break;
-    const int e = u / g.n_mod, m = u - e * g.n_mod;
-    const EvDesc &ev = evs[e];
-    const int flags = ev.cnt[C_FLAGS];
-    const int lo0 = ev.sens_off[2 * m], lo1 = ev.sens_off[2 * m + 1], up1 = ev.sens_off[2 * m + 2];
-    const int nlo = lo1 - lo0, nup = up1 - lo1;
-    const long long np64 = (long long)nlo * nup;
-    if (np64 > (1ll << 30)) {   // more hit pairs in one module than an int index can address
-      if (lane == 0) { atomicOr(ev.cnt + C_FLAGS, F_INPUT); ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
-      continue;
-    }
-    const int np = (flags & F_INPUT) ? 0 : (int)np64;
-    const bool endcap = g.subdet[m] != 0;
-    if (lane == 0 && np) atomicAdd(ev.cnt + C_PMD, np);
-    // pass 1: evaluate, compact into the warp's list
-    int nsel = 0;
-    for (int b = 0; b < np; b += 32) {
-      const int p = b + lane;
-      bool pass = false;
-      float kc = 0.0f, kf = 0.0f;
-      int i = 0, j = 0;
-      if (p < np) {
-        i = p / nup;
-        j = p - i * nup;
-        const float4 L = ev.hit[lo0 + i], U = ev.hit[lo1 + j];
-        pass = md_cut(L, U, endcap, c, kc);
-        if (pass && !endcap) kf = md_kappa_acc(L, U);
+    int u0 = 0;
+    if (lane == 0) u0 = atomicAdd(work, MD_CHUNK);
+    u0 = __shfl_sync(FULL, u0, 0);
+    if (u0 >= total) break;
+    for (int u = u0; u < min(u0 + MD_CHUNK, total); u++) {
+      const int e = u / g.n_mod, m = u - e * g.n_mod;
+      const EvDesc &ev = evs[e];
+      // one read per warp: other warps may set a flag concurrently, all lanes must agree
+      const int flags = __shfl_sync(FULL, lane == 0 ? ev.cnt[C_FLAGS] : 0, 0);
+      const int lo0 = ev.sens_off[2 * m], lo1 = ev.sens_off[2 * m + 1], up1 = ev.sens_off[2 * m + 2];
+      const int nlo = lo1 - lo0, nup = up1 - lo1;
+      const long long np64 = (long long)nlo * nup;
+      if (np64 > (1ll << 30)) {   // more hit pairs in one module than an int index can address
+        if (lane == 0) { atomicOr(ev.cnt + C_FLAGS, F_INPUT); ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
+        continue;
       }
-      const unsigned bal = __ballot_sync(FULL, pass);
-      const int slot = nsel + __popc(bal & lanemask_lt());
-      if (pass && slot < buf_cap) buf[slot] = {p, kc, kf};
-      nsel += __popc(bal);
-    }
-    __syncwarp();
-    const int base = warp_reserve(ev.cnt + C_MD, ev.cnt + C_FLAGS, F_OVF_MD, nsel, ev.md_cap);
-    if (base < 0 || nsel == 0) {
-      if (lane == 0) { ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
-      continue;
-    }
-    if (nsel <= buf_cap) {
-      for (int k = lane; k < nsel; k += 32) {
-        const MdBuf r = buf[k];
-        const int i = r.p / nup, j = r.p - (r.p / nup) * nup;
-        ev.md_anchor[base + k] = ev.hit[lo0 + i];
-        ev.md_kappa[base + k] = make_float2(r.kc, r.kf);
-        ev.md_mod[base + k] = m;
-        ev.md_hits[base + k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
-      }
-    } else {
-      // list overflow: evaluate again and write in place (same pair order)
-      int w = 0;
+      const int np = (flags & F_INPUT) ? 0 : (int)np64;
+      const bool endcap = g.subdet[m] != 0;
+      if (lane == 0 && np) atomicAdd(ev.cnt + C_PMD, np);
+      // pass 1: evaluate, compact into the warp's list
+      int nsel = 0;
       for (int b = 0; b < np; b += 32) {
         const int p = b + lane;
         bool pass = false;
         float kc = 0.0f, kf = 0.0f;
-        int i = 0, j = 0;
-        float4 L, U;
         if (p < np) {
-          i = p / nup;
-          j = p - i * nup;
-          L = ev.hit[lo0 + i];
-          U = ev.hit[lo1 + j];
-          pass = md_cut(L, U, endcap, c, kc);
-          if (pass && !endcap) kf = md_kappa_acc(L, U);
+          const int i = p / nup, j = p - (p / nup) * nup;
+          if (chk(ev, lo0 + i, ev.n_hits, 12) && chk(ev, lo1 + j, ev.n_hits, 13)) {
+            const float4 L = ev.hit[lo0 + i], U = ev.hit[lo1 + j];
+            pass = md_cut(L, U, endcap, c, kc);
+            if (pass && !endcap) kf = md_kappa_acc(L, U);
+          }
         }
         const unsigned bal = __ballot_sync(FULL, pass);
-        if (pass) {
-          const int k = base + w + __popc(bal & lanemask_lt());
-          ev.md_anchor[k] = L;
-          ev.md_kappa[k] = make_float2(kc, kf);
-          ev.md_mod[k] = m;
-          ev.md_hits[k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
-        }
-        w += __popc(bal);
+        const int slot = nsel + __popc(bal & lanemask_lt());
+        if (pass && slot < buf_cap) buf[slot] = {p, kc, kf};
+        nsel += __popc(bal);
       }
+      __syncwarp();
+      const int base = warp_reserve(ev.cnt + C_MD, ev.cnt + C_FLAGS, F_OVF_MD, nsel, ev.md_cap);
+      if (base < 0 || nsel == 0) {
+        if (lane == 0) { ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
+        continue;
+      }
+      if (nsel <= buf_cap) {
+        for (int k = lane; k < nsel; k += 32) {
+          const MdBuf r = buf[k];
+          const int i = r.p / nup, j = r.p - (r.p / nup) * nup;
+          if (!chk(ev, base + k, ev.md_cap, 11)) continue;
+          ev.md_anchor[base + k] = ev.hit[lo0 + i];
+          ev.md_kappa[base + k] = make_float2(r.kc, r.kf);
+          ev.md_mod[base + k] = m;
+          ev.md_hits[base + k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
+        }
+      } else {
+        // list overflow: evaluate again and write in place (same pair order)
+        int w = 0;
+        for (int b = 0; b < np; b += 32) {
+          const int p = b + lane;
+          bool pass = false;
+          float kc = 0.0f, kf = 0.0f;
+          int i = 0, j = 0;
+          float4 L, U;
+          if (p < np) {
+            i = p / nup;
+            j = p - i * nup;
+            L = ev.hit[lo0 + i];
+            U = ev.hit[lo1 + j];
+            pass = md_cut(L, U, endcap, c, kc);
+            if (pass && !endcap) kf = md_kappa_acc(L, U);
+          }
+          const unsigned bal = __ballot_sync(FULL, pass);
+          if (pass) {
+            const int k = base + w + __popc(bal & lanemask_lt());
+            ev.md_anchor[k] = L;
+            ev.md_kappa[k] = make_float2(kc, kf);
+            ev.md_mod[k] = m;
+            ev.md_hits[k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
+          }
+          w += __popc(bal);
+        }
+      }
+      if (lane == 0) { ev.md_start[m] = base; ev.md_cnt[m] = nsel; }
+      __syncwarp();
     }
-    if (lane == 0) { ev.md_start[m] = base; ev.md_cnt[m] = nsel; }
-    __syncwarp();
   }
 }
 
 // ===================================================================== step 2: line segments
-// One CTA per (event, module m). The MDs of every module linked to m by the module map are
-// staged once in shared memory (anchor, cut curvature, barrel flag, MD index); each warp
-// then takes one inner MD of m and tests it against all staged MDs, lanes across targets.
-struct LsBuf { int j; float k; };
+// One CTA per (event, module m). The target MDs (all MDs of the modules linked to m by
+// the module map, concatenated) are spread over the lanes: every lane holds one target MD
+// in registers and loops over the inner MDs of m, which sit in shared memory and are read
+// as broadcasts. A tile of 32 targets x IN_CHUNK inner MDs therefore costs one shared-memory
+// broadcast per pair and the FP32 cut. Passing pairs go to a shared list with per-inner-MD
+// counts; after the tile the CTA reserves one output range (one atomicAdd) and scatters
+// the list so that the LSs of each inner MD are contiguous.
+constexpr int LS_IN_CHUNK = 64;
+struct LsEntry { int i; int md; float k; };
 
 __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
-                                           lst_cuts c, int *work, int stage_cap, int buf_cap) {
+                                           lst_cuts c, int *work, int list_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_anc = reinterpret_cast<float4 *>(smem_raw);                 // [stage_cap]
-  float *s_k = reinterpret_cast<float *>(s_anc + stage_cap);            // [stage_cap]
-  int *s_idx = reinterpret_cast<int *>(s_k + stage_cap);                // [stage_cap] MD index, sign = barrel
-  int *s_tpref = s_idx + stage_cap;                                     // [MAX_FANOUT + 1]
-  int *s_tstart = s_tpref + MAX_FANOUT + 1;                             // [MAX_FANOUT]
-  LsBuf *s_buf = reinterpret_cast<LsBuf *>(s_tstart + MAX_FANOUT);      // [warps][buf_cap]
-  __shared__ int s_unit;
+  float4 *s_in = reinterpret_cast<float4 *>(smem_raw);                   // [LS_IN_CHUNK]
+  float *s_ink = reinterpret_cast<float *>(s_in + LS_IN_CHUNK);          // [LS_IN_CHUNK]
+  int *s_cnt = reinterpret_cast<int *>(s_ink + LS_IN_CHUNK);             // [LS_IN_CHUNK]
+  int *s_off = s_cnt + LS_IN_CHUNK;                                      // [LS_IN_CHUNK]
+  int *s_tpref = s_off + LS_IN_CHUNK;                                    // [MAX_FANOUT + 1]
+  int *s_tstart = s_tpref + MAX_FANOUT + 1;                              // [MAX_FANOUT]
+  int *s_tbar = s_tstart + MAX_FANOUT;                                   // [MAX_FANOUT]
+  LsEntry *s_list = reinterpret_cast<LsEntry *>(s_tbar + MAX_FANOUT);    // [list_cap]
+  __shared__ int s_unit, s_nin, s_nlist, s_base;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  LsBuf *buf = s_buf + wid * buf_cap;
   const int total = n_events * g.n_mod;
   for (;;) {
-    if (threadIdx.x == 0) s_unit = atomicAdd(work, 1);
+    // One thread fetches the unit and reads the event's state; the whole CTA then uses
+    // that one copy (the overflow flag may change under other CTAs at any time, and every
+    // thread must take the same path through the barriers below).
+    if (threadIdx.x == 0) {
+      const int uu = atomicAdd(work, 1);
+      int nin = 0;
+      if (uu < total) {
+        const int ee = uu / g.n_mod;
+        const EvDesc &evv = evs[ee];
+        nin = ev_void(evv) ? 0 : evv.md_cnt[uu - ee * g.n_mod];
+      }
+      s_unit = uu;
+      s_nin = nin;
+    }
     __syncthreads();
     const int u = s_unit;
-    __syncthreads();
     if (u >= total) break;
     const int e = u / g.n_mod, m = u - e * g.n_mod;
     const EvDesc &ev = evs[e];
-    const int n_in = ev.md_cnt[m];
-    if (n_in == 0) continue;
+    const int n_in = s_nin;
+    if (n_in == 0) { __syncthreads(); continue; }
     const int in0 = ev.md_start[m];
-    // target list with prefix of MD counts
+    const bool bA = g.subdet[m] == 0;
+    // target list: prefix of MD counts over the module map of m
     const int t0 = g.map_off[m], nt = min(g.map_off[m + 1] - t0, MAX_FANOUT);
     if (wid == 0) {
       int carry = 0;
       for (int b = 0; b < nt; b += 32) {
         const int t = b + lane;
-        int cnt = 0, st = 0;
+        int cnt = 0, st = 0, bar = 0;
         if (t < nt) {
           const int mt = g.map_tgt[t0 + t];
           cnt = ev.md_cnt[mt];
           st = ev.md_start[mt];
+          bar = g.subdet[mt] == 0;
         }
         const int inc = warp_incl_scan(cnt);
-        if (t < nt) { s_tpref[t + 1] = carry + inc; s_tstart[t] = st; }
+        if (t < nt) { s_tpref[t + 1] = carry + inc; s_tstart[t] = st; s_tbar[t] = bar; }
         carry += __shfl_sync(FULL, inc, 31);
       }
       if (lane == 0) s_tpref[0] = 0;
     }
     __syncthreads();
     const int S = s_tpref[nt];
-    const bool staged = S <= stage_cap;
     if (threadIdx.x == 0 && S) atomicAdd(ev.cnt + C_PLS, n_in * S);
-    if (staged) {
-      for (int q = threadIdx.x; q < S; q += blockDim.x) {
-        const int t = find_event(s_tpref, nt + 1, q);
-        const int md = s_tstart[t] + (q - s_tpref[t]);
-        s_anc[q] = ev.md_anchor[md];
-        s_k[q] = ev.md_kappa[md].x;
-        const bool barrel = g.subdet[ev.md_mod[md]] == 0;
-        s_idx[q] = barrel ? md : ~md;
+    for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
+      const int nc = min(LS_IN_CHUNK, n_in - c0);
+      for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        s_in[t] = ev.md_anchor[in0 + c0 + t];
+        s_ink[t] = ev.md_kappa[in0 + c0 + t].x;
+        s_cnt[t] = 0;
       }
+      if (threadIdx.x == 0) s_nlist = 0;
+      __syncthreads();
+      // ---- tile: lanes over targets, loop over inner MDs
+      for (int pass_no = 0; pass_no < 2; pass_no++) {
+        const bool writing = pass_no == 1;   // second sweep only after a list overflow
+        for (int j0 = wid * 32; j0 < S; j0 += nwarps * 32) {
+          const int j = j0 + lane;
+          bool valid = j < S;
+          float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+          float kB = 0.0f;
+          bool bB = false;
+          int md = 0;
+          if (valid) {
+            const int t = find_event(s_tpref, nt + 1, j);
+            md = s_tstart[t] + (j - s_tpref[t]);
+            if (chk(ev, md, ev.md_cap, 21)) {
+              B = ev.md_anchor[md];
+              kB = ev.md_kappa[md].x;
+              bB = s_tbar[t] != 0;
+            } else {
+              valid = false;
+            }
+          }
+          for (int i = 0; i < nc; i++) {
+            float k = 0.0f;
+            const bool pass = valid && ls_cut(s_in[i], B, s_ink[i], kB, bA, bB, c, k);
+            const unsigned bal = __ballot_sync(FULL, pass);
+            if (bal == 0) continue;
+            if (!writing) {
+              int pos = 0;
+              if (lane == 0) {
+                pos = atomicAdd(&s_nlist, __popc(bal));
+                atomicAdd(&s_cnt[i], __popc(bal));
+              }
+              pos = __shfl_sync(FULL, pos, 0);
+              const int q = pos + __popc(bal & lanemask_lt());
+              if (pass && q < list_cap) s_list[q] = {i, md, k};
+            } else if (pass) {
+              const int o = s_base + s_off[i] + atomicAdd(&s_cnt[i], 1);
+              if (!chk(ev, o, ev.ls_cap, 23)) continue;
+              ev.ls_in[o] = in0 + c0 + i;
+              ev.ls_out[o] = md;
+              ev.ls_kappa[o] = k;
+            }
+          }
+        }
+        __syncthreads();
+        if (writing) break;
+        // ---- per-inner-MD offsets, one reservation for the tile
+        if (wid == 0) {
+          int carry = 0;
+          for (int b = 0; b < nc; b += 32) {
+            const int t = b + lane;
+            const int v = t < nc ? s_cnt[t] : 0;
+            const int inc = warp_incl_scan(v);
+            if (t < nc) s_off[t] = carry + inc - v;
+            carry += __shfl_sync(FULL, inc, 31);
+          }
+          int base = 0;
+          if (lane == 0 && carry > 0) {
+            base = atomicAdd(ev.cnt + C_LS, carry);
+            if (base + carry > ev.ls_cap) { atomicOr(ev.cnt + C_FLAGS, F_OVF_LS); base = -1; }
+          }
+          if (lane == 0) s_base = carry > 0 ? base : -1;
+        }
+        __syncthreads();
+        const int base = s_base;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+          ev.ls_start[in0 + c0 + t] = base >= 0 ? base + s_off[t] : 0;
+          ev.ls_cnt[in0 + c0 + t] = base >= 0 ? s_cnt[t] : 0;
+        }
+        __syncthreads();
+        const int nlist = s_nlist;
+        if (base < 0) break;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) s_cnt[t] = 0;   // cursors
+        __syncthreads();
+        if (nlist <= list_cap) {
+          for (int q = threadIdx.x; q < nlist; q += blockDim.x) {
+            const LsEntry r = s_list[q];
+            const int o = base + s_off[r.i] + atomicAdd(&s_cnt[r.i], 1);
+            ev.ls_in[o] = in0 + c0 + r.i;
+            ev.ls_out[o] = r.md;
+            ev.ls_kappa[o] = r.k;
+          }
+          __syncthreads();
+          break;
+        }
+        // list overflow: sweep the tile again, writing in place
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const bool bA = g.subdet[m] == 0;
-    for (int ii = wid; ii < n_in; ii += nwarps) {
-      const int i = in0 + ii;
-      const float4 A = ev.md_anchor[i];
-      const float kA = ev.md_kappa[i].x;
-      int nsel = 0;
-      for (int b = 0; b < S; b += 32) {
-        const int q = b + lane;
-        bool pass = false;
-        float k = 0.0f;
-        int jm = 0;
-        if (q < S) {
-          float4 B;
-          float kB;
-          int code;
-          if (staged) {
-            B = s_anc[q]; kB = s_k[q]; code = s_idx[q];
-          } else {
-            const int t = find_event(s_tpref, nt + 1, q);
-            const int md = s_tstart[t] + (q - s_tpref[t]);
-            B = ev.md_anchor[md]; kB = ev.md_kappa[md].x;
-            code = g.subdet[ev.md_mod[md]] == 0 ? md : ~md;
-          }
-          const bool bB = code >= 0;
-          jm = bB ? code : ~code;
-          pass = ls_cut(A, B, kA, kB, bA, bB, c, k);
-        }
-        const unsigned bal = __ballot_sync(FULL, pass);
-        const int slot = nsel + __popc(bal & lanemask_lt());
-        if (pass && slot < buf_cap) buf[slot] = {jm, k};
-        nsel += __popc(bal);
-      }
-      __syncwarp();
-      const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, nsel, ev.ls_cap);
-      if (base < 0 || nsel == 0) {
-        if (lane == 0) { ev.ls_start[i] = 0; ev.ls_cnt[i] = 0; }
-        __syncwarp();
-        continue;
-      }
-      if (nsel <= buf_cap) {
-        for (int k = lane; k < nsel; k += 32) {
-          const LsBuf r = buf[k];
-          ev.ls_in[base + k] = i;
-          ev.ls_out[base + k] = r.j;
-          ev.ls_kappa[base + k] = r.k;
-        }
-      } else {
-        int w = 0;
-        for (int b = 0; b < S; b += 32) {
-          const int q = b + lane;
-          bool pass = false;
-          float k = 0.0f;
-          int jm = 0;
-          if (q < S) {
-            const int t = find_event(s_tpref, nt + 1, q);
-            const int md = s_tstart[t] + (q - s_tpref[t]);
-            const float4 B = ev.md_anchor[md];
-            const bool bB = g.subdet[ev.md_mod[md]] == 0;
-            jm = md;
-            pass = ls_cut(A, B, kA, ev.md_kappa[md].x, bA, bB, c, k);
-          }
-          const unsigned bal = __ballot_sync(FULL, pass);
-          if (pass) {
-            const int o = base + w + __popc(bal & lanemask_lt());
-            ev.ls_in[o] = i; ev.ls_out[o] = jm; ev.ls_kappa[o] = k;
-          }
-          w += __popc(bal);
-        }
-      }
-      if (lane == 0) { ev.ls_start[i] = base; ev.ls_cnt[i] = nsel; }
-      __syncwarp();
-    }
-    __syncthreads();
   }
 }
 
 // ===================================================================== steps 3 and 4
-// Both enumerate, for one first MD (md0), all pairs (X1, X2) with X1 in out(md0) and X2 in
-// out(mid(X1)) where out() is a contiguous range per MD. A warp flattens the pairs: lanes
-// hold up to 32 X1 with their out-degree, an inclusive warp scan of the degrees maps each
-// flat pair index to (X1, X2) by binary search in the warp's shared copy of the scan.
-struct PairWarp {
-  int incl[32];
-  int mid[32];     // middle MD of X1
-  int st2[32];     // start of out(mid)
-  int x1[32];      // X1 index
+// Both enumerate pairs (X1, X2) where X2 ranges over a contiguous list attached to the
+// middle MD of X1. A warp takes 32 consecutive X1 (one per lane, with its list length);
+// an inclusive warp scan of the lengths maps each flat pair index to (X1, X2) by a binary
+// search in the warp's shared copy of the scan. Work is spread by static striding over
+// chunks of 32 X1 of all events (no atomics); pair counts are summed per warp and flushed
+// once per event.
+struct T3Warp {
+  int incl[32], st2[32], md0[32], md1[32];
+  float4 P0[32], P1[32];
 };
-struct T3Buf { int md1, md2; float k; };
 
-__global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c,
-                                           int *work, int buf_cap) {
+__global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_pref[MAX_EVENTS + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  PairWarp *pw = reinterpret_cast<PairWarp *>(smem_raw) + wid;
-  T3Buf *buf = reinterpret_cast<T3Buf *>(reinterpret_cast<PairWarp *>(smem_raw) + nwarps) + wid * buf_cap;
+  T3Warp &w = reinterpret_cast<T3Warp *>(smem_raw)[wid];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return (ev.cnt[C_FLAGS] & F_INPUT) ? 0 : clamp_count(ev.cnt[C_MD], ev.md_cap);
+    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 31) / 32;
   }, s_pref);
   const int total = s_pref[n_events];
-  for (;;) {
-    const int u = warp_next(work);
-    if (u >= total) break;
+  const int W = gridDim.x * nwarps;
+  int cur = -1, acc = 0;
+  for (int u = blockIdx.x * nwarps + wid; u < total; u += W) {
     const int e = find_event(s_pref, n_events, u);
+    if (e != cur) {
+      if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT3, acc);
+      acc = 0;
+      cur = e;
+    }
     const EvDesc &ev = evs[e];
-    const int md0 = u - s_pref[e];
-    const int n1 = ev.ls_cnt[md0], s1 = ev.ls_start[md0];
-    const float4 P0 = ev.md_anchor[md0];
-    // count pass (with list), possibly a write pass if the list overflowed
-    int nsel = 0, base = 0;
-    for (int pass_no = 0; pass_no < 2; pass_no++) {
-      int w = 0;
-      for (int k0 = 0; k0 < n1; k0 += 32) {
-        int deg = 0;
-        if (k0 + lane < n1) {
-          const int l1 = s1 + k0 + lane;
-          const int md1 = ev.ls_out[l1];
-          deg = ev.ls_cnt[md1];
-          pw->mid[lane] = md1;
-          pw->st2[lane] = ev.ls_start[md1];
-          pw->x1[lane] = l1;
-        }
-        const int inc = warp_incl_scan(deg);
-        pw->incl[lane] = inc;
-        __syncwarp();
-        const int tot = __shfl_sync(FULL, inc, 31);
-        if (pass_no == 0 && lane == 0 && tot) atomicAdd(ev.cnt + C_PT3, tot);
-        for (int f0 = 0; f0 < tot; f0 += 32) {
-          const int f = f0 + lane;
-          bool pass = false;
-          float k = 0.0f;
-          int md1 = 0, md2 = 0;
-          if (f < tot) {
-            int lo = 0, hi = 31;
-            while (lo < hi) { const int mid = (lo + hi) >> 1; if (pw->incl[mid] > f) hi = mid; else lo = mid + 1; }
-            const int prev = lo ? pw->incl[lo - 1] : 0;
-            md1 = pw->mid[lo];
-            const int l2 = pw->st2[lo] + (f - prev);
-            md2 = ev.ls_out[l2];
-            pass = t3_cut(P0, ev.md_anchor[md1], ev.md_anchor[md2], c, k);
-          }
-          const unsigned bal = __ballot_sync(FULL, pass);
-          const int slot = w + __popc(bal & lanemask_lt());
-          if (pass) {
-            if (pass_no == 0) {
-              if (slot < buf_cap) buf[slot] = {md1, md2, k};
-            } else {
-              ev.t3_md[base + slot] = make_int4(md0, md1, md2, 0);
-              ev.t3_kappa[base + slot] = k;
-            }
-          }
-          w += __popc(bal);
-        }
-        __syncwarp();
+    const int nls = clamp_count(ev.cnt[C_LS], ev.ls_cap);
+    const int l1 = (u - s_pref[e]) * 32 + lane;
+    int deg = 0;
+    if (l1 < nls) {
+      const int md0 = ev.ls_in[l1], md1 = ev.ls_out[l1];
+      deg = ev.ls_cnt[md1];
+      w.st2[lane] = ev.ls_start[md1];
+      w.md0[lane] = md0;
+      w.md1[lane] = md1;
+      w.P0[lane] = ev.md_anchor[md0];
+      w.P1[lane] = ev.md_anchor[md1];
+    }
+    const int inc = warp_incl_scan(deg);
+    w.incl[lane] = inc;
+    __syncwarp();
+    const int tot = __shfl_sync(FULL, inc, 31);
+    acc += tot;
+    for (int f0 = 0; f0 < tot; f0 += 32) {
+      const int f = f0 + lane;
+      bool pass = false;
+      float k = 0.0f;
+      int x = 0, md2 = 0;
+      if (f < tot) {
+        int lo = 0, hi = 31;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
+        x = lo;
+        const int prev = lo ? w.incl[lo - 1] : 0;
+        md2 = ev.ls_out[w.st2[lo] + (f - prev)];
+        pass = t3_cut(w.P0[lo], w.P1[lo], ev.md_anchor[md2], c, k);
       }
-      if (pass_no == 0) {
-        nsel = w;
-        base = warp_reserve(ev.cnt + C_T3, ev.cnt + C_FLAGS, F_OVF_T3, nsel, ev.t3_cap);
-        if (base < 0 || nsel == 0) { nsel = 0; base = 0; break; }
-        if (nsel <= buf_cap) {
-          for (int k = lane; k < nsel; k += 32) {
-            const T3Buf r = buf[k];
-            ev.t3_md[base + k] = make_int4(md0, r.md1, r.md2, 0);
-            ev.t3_kappa[base + k] = r.k;
-          }
-          break;
+      const unsigned bal = __ballot_sync(FULL, pass);
+      if (bal) {
+        const int base = warp_reserve(ev.cnt + C_T3, ev.cnt + C_FLAGS, F_OVF_T3, __popc(bal), ev.t3_cap);
+        if (pass && base >= 0) {
+          const int o = base + __popc(bal & lanemask_lt());
+          ev.t3u_md[o] = make_int4(w.md0[x], w.md1[x], md2, 0);
+          ev.t3u_kappa[o] = k;
+          atomicAdd(ev.t3_cnt + w.md0[x], 1);
         }
       }
     }
-    if (lane == 0) { ev.t3_start[md0] = base; ev.t3_cnt[md0] = nsel; }
     __syncwarp();
+  }
+  if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT3, acc);
+}
+
+// T3s grouped by first MD: exclusive scan of the per-MD counts (one CTA per event) ...
+__global__ void k_t3_scan(const EvDesc *__restrict__ evs) {
+  const EvDesc &ev = evs[blockIdx.x];
+  if (ev_void(ev)) return;
+  const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  int local = 0;
+  for (int k = 0; k < per && b0 + k < n; k++) local += ev.t3_cnt[b0 + k];
+  __shared__ int s_w[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int inc = warp_incl_scan(local);
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    const int v = lane < nw ? s_w[lane] : 0;
+    const int vi = warp_incl_scan(v);
+    if (lane < nw) s_w[lane] = vi - v;
+  }
+  __syncthreads();
+  int run = s_w[wid] + inc - local;
+  for (int k = 0; k < per && b0 + k < n; k++) {
+    ev.t3_pos[b0 + k] = run;
+    run += ev.t3_cnt[b0 + k];
   }
 }
 
-__global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int n_events, lst_cuts c,
-                                           int *work) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// ... then a scatter into that order; afterwards t3_pos[md] holds the END of md's range.
+__global__ void k_t3_scatter(const EvDesc *__restrict__ evs, int n_events) {
   __shared__ int s_pref[MAX_EVENTS + 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  PairWarp *pw = reinterpret_cast<PairWarp *>(smem_raw) + wid;
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return (ev.cnt[C_FLAGS] & F_INPUT) ? 0 : clamp_count(ev.cnt[C_MD], ev.md_cap);
+    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_T3], ev.t3_cap);
   }, s_pref);
   const int total = s_pref[n_events];
-  for (;;) {
-    const int u = warp_next(work);
-    if (u >= total) break;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
     const int e = find_event(s_pref, n_events, u);
     const EvDesc &ev = evs[e];
-    const int md0 = u - s_pref[e];
-    const int n1 = ev.t3_cnt[md0], s1 = ev.t3_start[md0];
-    if (n1 == 0) continue;
-    const float4 P0 = ev.md_anchor[md0];
-    for (int k0 = 0; k0 < n1; k0 += 32) {
-      int deg = 0;
-      if (k0 + lane < n1) {
-        const int ta = s1 + k0 + lane;
-        const int md2 = ev.t3_md[ta].z;
-        deg = ev.t3_cnt[md2];
-        pw->mid[lane] = md2;
-        pw->st2[lane] = ev.t3_start[md2];
-        pw->x1[lane] = ta;
-      }
-      const int inc = warp_incl_scan(deg);
-      pw->incl[lane] = inc;
-      __syncwarp();
-      const int tot = __shfl_sync(FULL, inc, 31);
-      if (lane == 0 && tot) atomicAdd(ev.cnt + C_PT5, tot);
-      for (int f0 = 0; f0 < tot; f0 += 32) {
-        const int f = f0 + lane;
-        bool pass = false;
-        int4 a = make_int4(0, 0, 0, 0), b = make_int4(0, 0, 0, 0);
-        if (f < tot) {
-          int lo = 0, hi = 31;
-          while (lo < hi) { const int mid = (lo + hi) >> 1; if (pw->incl[mid] > f) hi = mid; else lo = mid + 1; }
-          const int prev = lo ? pw->incl[lo - 1] : 0;
-          const int ta = pw->x1[lo];
-          const int tb = pw->st2[lo] + (f - prev);
-          const int4 A3 = ev.t3_md[ta], B3 = ev.t3_md[tb];
-          float4 P[5];
-          P[0] = P0;
-          P[1] = ev.md_anchor[A3.y];
-          P[2] = ev.md_anchor[A3.z];
-          P[3] = ev.md_anchor[B3.y];
-          P[4] = ev.md_anchor[B3.z];
-          pass = t5_cut(P, ev.t3_kappa[ta], ev.t3_kappa[tb], c);
-          a = make_int4(md0, A3.y, A3.z, B3.y);
-          b = make_int4(B3.z, ta, tb, 0);
-        }
-        const unsigned bal = __ballot_sync(FULL, pass);
-        const int n = __popc(bal);
-        if (n) {
-          const int base = warp_reserve(ev.cnt + C_T5, ev.cnt + C_FLAGS, F_OVF_T5, n, ev.t5_cap);
-          if (pass && base >= 0) {
-            const int o = base + __popc(bal & lanemask_lt());
-            ev.t5_a[o] = a;
-            ev.t5_b[o] = b;
-          }
-        }
-      }
-      __syncwarp();
-    }
+    const int o = u - s_pref[e];
+    const int4 t = ev.t3u_md[o];
+    const int pos = atomicAdd(ev.t3_pos + t.x, 1);
+    ev.t3_md[pos] = t;
+    ev.t3_kappa[pos] = ev.t3u_kappa[o];
   }
+}
+
+struct T5Warp {
+  int incl[32], st2[32], ta[32];
+  float ka[32];
+  float4 P0[32], P1[32], P2[32];
+  int md1[32];
+};
+
+__global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  T5Warp &w = reinterpret_cast<T5Warp *>(smem_raw)[wid];
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_T3], ev.t3_cap) + 31) / 32;
+  }, s_pref);
+  const int total = s_pref[n_events];
+  const int W = gridDim.x * nwarps;
+  int cur = -1, acc = 0;
+  for (int u = blockIdx.x * nwarps + wid; u < total; u += W) {
+    const int e = find_event(s_pref, n_events, u);
+    if (e != cur) {
+      if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT5, acc);
+      acc = 0;
+      cur = e;
+    }
+    const EvDesc &ev = evs[e];
+    const int nt3 = clamp_count(ev.cnt[C_T3], ev.t3_cap);
+    const int ta = (u - s_pref[e]) * 32 + lane;
+    int deg = 0;
+    if (ta < nt3) {
+      const int4 A3 = ev.t3_md[ta];
+      deg = ev.t3_cnt[A3.z];
+      w.st2[lane] = ev.t3_pos[A3.z] - deg;
+      w.ta[lane] = ta;
+      w.ka[lane] = ev.t3_kappa[ta];
+      w.md1[lane] = A3.y;
+      w.P0[lane] = ev.md_anchor[A3.x];
+      w.P1[lane] = ev.md_anchor[A3.y];
+      w.P2[lane] = ev.md_anchor[A3.z];
+    }
+    const int inc = warp_incl_scan(deg);
+    w.incl[lane] = inc;
+    __syncwarp();
+    const int tot = __shfl_sync(FULL, inc, 31);
+    acc += tot;
+    for (int f0 = 0; f0 < tot; f0 += 32) {
+      const int f = f0 + lane;
+      bool pass = false;
+      int4 a = make_int4(0, 0, 0, 0), b = make_int4(0, 0, 0, 0);
+      if (f < tot) {
+        int lo = 0, hi = 31;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
+        const int prev = lo ? w.incl[lo - 1] : 0;
+        const int tb = w.st2[lo] + (f - prev);
+        const int4 B3 = ev.t3_md[tb];
+        float4 P[5];
+        P[0] = w.P0[lo];
+        P[1] = w.P1[lo];
+        P[2] = w.P2[lo];
+        P[3] = ev.md_anchor[B3.y];
+        P[4] = ev.md_anchor[B3.z];
+        pass = t5_cut(P, w.ka[lo], ev.t3_kappa[tb], c);
+        const int4 A3 = ev.t3_md[w.ta[lo]];
+        a = make_int4(A3.x, A3.y, A3.z, B3.y);
+        b = make_int4(B3.z, w.ta[lo], tb, 0);
+      }
+      const unsigned bal = __ballot_sync(FULL, pass);
+      if (bal) {
+        const int base = warp_reserve(ev.cnt + C_T5, ev.cnt + C_FLAGS, F_OVF_T5, __popc(bal), ev.t5_cap);
+        if (pass && base >= 0) {
+          const int o = base + __popc(bal & lanemask_lt());
+          ev.t5_a[o] = a;
+          ev.t5_b[o] = b;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT5, acc);
 }
 
 }  // namespace lstk

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_score_fp32(const EvDesc *__restrict__ e
   for (int i = threadIdx.x; i < nw; i += blockDim.x) s_w[i] = wts[i];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return clamp_count(ev.cnt[C_T5], ev.t5_cap);
+    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_T5], ev.t5_cap);
   }, s_pref);
   const int total = s_pref[n_events];
   const int lane = threadIdx.x & 31;

@@ -51,8 +51,8 @@ class lst_config(C.Structure):
 
 
 class lst_launch(C.Structure):
-    _fields_ = [(f, C.c_int32) for f in ("md_threads", "md_buf", "ls_threads", "ls_stage", "ls_buf",
-                                          "t3_threads", "t3_buf", "t5_threads", "sc_threads")]
+    _fields_ = [(f, C.c_int32) for f in ("md_threads", "md_buf", "ls_threads", "ls_list", "t3_threads",
+                                          "t5_threads", "sc_threads", "reserved")]
 
 
 class lst_counts(C.Structure):

@@ -153,12 +153,12 @@ def test_overflow_regrows_to_exact_result(geom_full, cuts, model):
     c.close()
 
 
-def test_list_overflow_and_unstaged_paths(geom_full, cuts, model):
-    """Tiny per-warp lists and staging buffers force the re-evaluation and global-memory
-    paths of every stage; results must not change."""
+def test_list_overflow_paths(geom_full, cuts, model):
+    """Tiny candidate lists force the re-evaluation paths of the MD and LS kernels, odd CTA
+    sizes change every work decomposition; results must not change."""
     c = lst.Context(0, max_events=2)
     c.load_geometry(geom_full, cuts, *model)
-    c.set_launch(md_buf=1, ls_buf=2, ls_stage=16, t3_buf=1, md_threads=64, ls_threads=128, t3_threads=96)
+    c.set_launch(md_buf=1, ls_list=2, md_threads=64, ls_threads=64, t3_threads=96, t5_threads=160)
     e = synth.pileup_event(geom_full, 5, pileup=40, mean_per_vertex=96)
     ref = oracle.run_event(geom_full, e, cuts, *model)
     ev = c.run_event(*dev(e))
