@@ -182,7 +182,7 @@ const char *lst_last_error(void);
  * shared memory within the device limit) and recomputes the persistent grid sizes; the
  * results never depend on these values, only the speed does. */
 typedef struct lst_launch {
-    int32_t md_threads, md_buf;    /* step 1: CTA size, per-warp candidate list entries */
+    int32_t md_threads, md_buf;    /* step 1: CTA size; md_buf is unused (kept for layout) */
     int32_t ls_threads, ls_list;   /* step 2: CTA size, shared candidate list entries per tile */
     int32_t t3_threads;            /* step 3: CTA size */
     int32_t t5_threads;            /* step 4: CTA size */

@@ -19,7 +19,9 @@ __global__ void k_reset(const EvDesc *, DevGeom);
 __global__ void k_bin_count(const EvDesc *, DevGeom);
 __global__ void k_bin_scan(const EvDesc *, DevGeom);
 __global__ void k_bin_scatter(const EvDesc *, DevGeom);
-__global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
+__global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts);
+__global__ void k_md_scan(const EvDesc *, DevGeom);
+__global__ void k_md_scatter(const EvDesc *, int);
 __global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
 __global__ void k_t3(const EvDesc *, int, lst_cuts);
 __global__ void k_t3_scan(const EvDesc *);
@@ -157,8 +159,8 @@ constexpr int LS_IN_CHUNK_HOST = 64;   // k_ls inner-MD tile (LS_IN_CHUNK)
 size_t ls_smem(const lst_ctx_s *c) {
   return (size_t)LS_IN_CHUNK_HOST * (16 + 4 + 4 + 4) + (3 * MAX_FANOUT + 1) * 4 + (size_t)c->ls_list * 12;
 }
-size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * c->md_buf * 12; }
-size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * (4 * 128 + 2 * 512); }
+size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
+size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * (2 * 512 + 4 * 128 + 2 * 256); }
 size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
 int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
 
@@ -215,10 +217,12 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   const int nm = c->g.n_mod;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  const size_t o_hit = take(16 * H), o_orig = take(4 * H);
+  const size_t o_hit = take(16 * H), o_orig = take(4 * H), o_hmod = take(4 * H);
   const size_t o_scnt = take(4 * (size_t)2 * nm), o_soff = take(4 * ((size_t)2 * nm + 1));
   const size_t o_manc = take(16 * (size_t)md), o_mk = take(8 * (size_t)md), o_mmod = take(4 * (size_t)md),
-               o_mh = take(8 * (size_t)md), o_mst = take(4 * (size_t)nm), o_mcn = take(4 * (size_t)nm);
+               o_mh = take(8 * (size_t)md), o_mst = take(4 * (size_t)nm), o_mcn = take(4 * (size_t)nm),
+               o_mcur = take(4 * (size_t)nm), o_uanc = take(16 * (size_t)md), o_uk = take(8 * (size_t)md),
+               o_umod = take(4 * (size_t)md), o_uh = take(8 * (size_t)md);
   const size_t o_lin = take(4 * (size_t)ls), o_lout = take(4 * (size_t)ls), o_lk = take(4 * (size_t)ls),
                o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
   const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
@@ -235,10 +239,12 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   s.bytes = off;
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
-  d.hit = (float4 *)(b + o_hit); d.hit_orig = (int32_t *)(b + o_orig);
+  d.hit = (float4 *)(b + o_hit); d.hit_orig = (int32_t *)(b + o_orig); d.hit_mod = (int32_t *)(b + o_hmod);
   d.sens_cnt = (int32_t *)(b + o_scnt); d.sens_off = (int32_t *)(b + o_soff);
   d.md_anchor = (float4 *)(b + o_manc); d.md_kappa = (float2 *)(b + o_mk); d.md_mod = (int32_t *)(b + o_mmod);
   d.md_hits = (int2 *)(b + o_mh); d.md_start = (int32_t *)(b + o_mst); d.md_cnt = (int32_t *)(b + o_mcn);
+  d.md_cur = (int32_t *)(b + o_mcur); d.mdu_anchor = (float4 *)(b + o_uanc); d.mdu_kappa = (float2 *)(b + o_uk);
+  d.mdu_mod = (int32_t *)(b + o_umod); d.mdu_hits = (int2 *)(b + o_uh);
   d.ls_in = (int32_t *)(b + o_lin); d.ls_out = (int32_t *)(b + o_lout); d.ls_kappa = (float *)(b + o_lk);
   d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
   d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_pos = (int32_t *)(b + o_t3s);
@@ -328,7 +334,9 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   k_bin_scatter<<<dim3(bx, n), 256, 0, st>>>(L.d_desc, g);
   CU(cudaMemsetAsync(L.d_work, 0, sizeof(int) * 16, st));
   mark(1);
-  k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 0, c->md_buf);
+  k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts);
+  k_md_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
+  k_md_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
   mark(2);
   k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->ls_list);
   mark(3);

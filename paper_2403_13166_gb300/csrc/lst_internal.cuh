@@ -43,13 +43,20 @@ struct EvDesc {
   int32_t pad;
   float4 *hit;                 // [n_hits] hits grouped by sensor: x, y, z, r
   int32_t *hit_orig;           // [n_hits] original index of each grouped hit
-  int32_t *sens_cnt;           // [2 n_mod] histogram, then scatter cursor
-  int32_t *sens_off;           // [2 n_mod + 1]
-  float4 *md_anchor;           // [md_cap] lower-sensor hit (anchor): x, y, z, r
+  int32_t *hit_mod;            // [n_hits] module of each grouped hit
+  int32_t *sens_cnt;           // [2 n_mod] histogram by key, then scatter cursor
+  int32_t *sens_off;           // [2 n_mod + 1] key k < n_mod: lower sensor of module k,
+                               // key n_mod + k: upper sensor of module k
+  float4 *mdu_anchor;          // [md_cap] MDs as found, any order (same fields as below)
+  float2 *mdu_kappa;
+  int32_t *mdu_mod;
+  int2 *mdu_hits;
+  float4 *md_anchor;           // [md_cap] MDs grouped by module: lower-sensor hit (anchor) x, y, z, r
   float2 *md_kappa;            // [md_cap] (cut curvature, feature curvature); 0 for endcap
   int32_t *md_mod;             // [md_cap] module
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
+  int32_t *md_cur;             // [n_mod] scatter cursor of the grouping
   int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD
   float *ls_kappa;             // [ls_cap]
   int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
@@ -120,6 +127,25 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
   return true;
 }
 
+// Necessary condition of md_cut without division or square root (barrel), or the exact
+// direction test (endcap). hb2r2 = (rL * hb)^2 with hb = rL*(kappa_max/2) + e/g, the bend
+// bound of md_cut, precomputed per lower hit. Bend: |cr| <= rL dT hb. z road, multiplied
+// by rL > 0: |dz rL - zL dr| <= Zl dr + e rL. The slack (1e-3 relative) covers FP32
+// rounding, so a pair rejected here always fails md_cut too.
+__device__ __forceinline__ bool md_prefilter(const float4 L, const float4 U, bool endcap, float hb2r2,
+                                             const lst_cuts &c) {
+  const float dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
+  const float dt = L.x * dx + L.y * dy;
+  if (endcap) return (dt > 0.0f) & (dz * L.z > 0.0f);
+  const float cr = L.x * dy - L.y * dx;
+  const float dT2 = dx * dx + dy * dy;
+  const bool bend = cr * cr <= hb2r2 * dT2 * 1.001f + 1e-9f;
+  const float dr = U.w - L.w;
+  const float a = dz * L.w, b = L.z * dr, rhs = c.z_lum * dr + c.hit_err * L.w;
+  const bool zr = fabsf(a - b) <= rhs + 1e-3f * (fabsf(a) + fabsf(b) + fabsf(rhs)) + 1e-6f;
+  return (dt > 0.0f) & bend & zr;
+}
+
 // Step 3: anchors of md0, md1, md2 along the chain (LS1.out == LS2.in).
 __device__ __forceinline__ bool t3_cut(const float4 P0, const float4 P1, const float4 P2,
                                        const lst_cuts &c, float &kappa) {
@@ -138,6 +164,30 @@ __device__ __forceinline__ bool t3_cut(const float4 P0, const float4 P1, const f
   if (!(fabsf(P1.z - zp) <= c.t3_rz_tol)) return false;                 // rz
   kappa = k3;
   return true;
+}
+
+// Necessary condition of t3_cut without division or IEEE square root. pT: |2 cr| <=
+// K a b c  <=>  4 cr^2 <= K^2 a^2 b^2 c^2 (K = kappa_max * factor). rz: the same residual
+// multiplied by (s01 + s12) > 0, with a, b from the approximate rsqrt (relative error
+// ~1e-7) and kappa^2 from the squares; the slack (1e-3 relative, 1e-4 cm absolute) is far
+// above the approximation and rounding errors, so a rejected triplet always fails t3_cut.
+__device__ __forceinline__ bool t3_prefilter(const float4 P0, const float4 P1, const float4 P2,
+                                             const lst_cuts &c) {
+  const float ax = P1.x - P0.x, ay = P1.y - P0.y;
+  const float bx = P2.x - P1.x, by = P2.y - P1.y;
+  const float cx = P2.x - P0.x, cy = P2.y - P0.y;
+  const float a2 = ax * ax + ay * ay, b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+  const float cr = ax * cy - ay * cx;
+  const float K = c.kappa_max * c.t3_kappa_factor;
+  const float abc2 = a2 * b2 * c2;
+  const bool pt = 4.0f * cr * cr <= K * K * abc2 * 1.001f + 1e-12f;
+  const float k2 = __fdividef(4.0f * cr * cr, fmaxf(abc2, 1e-30f));   // kappa^2, approximate
+  const float a = a2 * rsqrtf(fmaxf(a2, 1e-30f)), b = b2 * rsqrtf(fmaxf(b2, 1e-30f));
+  const float s01 = a * (1.0f + a2 * k2 * (1.0f / 24.0f));
+  const float s12 = b * (1.0f + b2 * k2 * (1.0f / 24.0f));
+  const float lhs = fabsf((P1.z - P0.z) * (s01 + s12) - (P2.z - P0.z) * s01);
+  const bool rz = lhs <= (c.t3_rz_tol * 1.001f + 1e-4f) * (s01 + s12);
+  return pt & rz;
 }
 
 // Step 4: five anchors in chain order; ka, kb the curvatures of T3a = (0,1,2), T3b = (2,3,4).

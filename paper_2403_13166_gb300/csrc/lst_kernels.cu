@@ -16,7 +16,9 @@
 namespace lstk {
 
 // ===================================================================== step 0: hit binning
-// Count hits per sensor (validating sensor ids and coordinates).
+// Count hits per sensor (validating sensor ids and coordinates). Sensors are keyed as
+// (sensor & 1) * n_mod + module, so that all lower-sensor hits come first in the grouped
+// order: key k < n_mod is the lower sensor of module k, key n_mod + k its upper sensor.
 __global__ void k_bin_count(const EvDesc *__restrict__ evs, DevGeom g) {
   const EvDesc &ev = evs[blockIdx.y];
   const int n = ev.n_hits, ns = 2 * g.n_mod;
@@ -27,7 +29,7 @@ __global__ void k_bin_count(const EvDesc *__restrict__ evs, DevGeom g) {
       atomicOr(ev.cnt + C_FLAGS, F_INPUT);
       continue;
     }
-    atomicAdd(ev.sens_cnt + s, 1);
+    atomicAdd(ev.sens_cnt + (s & 1) * g.n_mod + (s >> 1), 1);
   }
 }
 
@@ -75,9 +77,11 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, DevGeom g) {
     const int s = __ldg(ev.sensor + i);
     const float x = __ldg(ev.x + i), y = __ldg(ev.y + i), z = __ldg(ev.z + i);
     if (s < 0 || s >= ns || !isfinite(x) || !isfinite(y) || !isfinite(z)) continue;
-    const int pos = ev.sens_off[s] + atomicAdd(ev.sens_cnt + s, 1);
+    const int key = (s & 1) * g.n_mod + (s >> 1);
+    const int pos = ev.sens_off[key] + atomicAdd(ev.sens_cnt + key, 1);
     ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
     ev.hit_orig[pos] = i;
+    ev.hit_mod[pos] = s >> 1;
   }
 }
 
@@ -97,104 +101,169 @@ __device__ __forceinline__ int warp_reserve(int *counter, int *flags, int flag, 
 }
 
 // ===================================================================== step 1: mini-doublets
-// One warp per (event, module): all (lower, upper) hit pairs of the module. Warps take
-// MD_CHUNK consecutive modules per atomic fetch.
-// smem per warp: buf_cap entries of (pair index, cut kappa, feature kappa).
-struct MdBuf { int p; float kc, kf; };
-constexpr int MD_CHUNK = 4;
+// One lane per lower-sensor hit. Binning puts the lower-sensor hits of all modules first,
+// so warps take 32 consecutive lower hits (static striding over all events) and the pairs
+// of a dense module spread over many warps. Each lane loops over the upper-sensor hits of
+// its own module; pairs that pass md_prefilter are queued per warp and the exact cut runs
+// on full warps of queued pairs. MDs are appended in any order (one atomicAdd per warp and
+// ballot) and counted per module; a counting sort (k_md_scan, k_md_scatter) then groups
+// them by module.
+struct MdWarp {
+  float4 L[32];
+  int lo[32], mod[32], endc[32];
+  int qx[64], qu[64];   // queue of (lane, upper hit) pairs that passed md_prefilter
+};
 
 __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
-                                           lst_cuts c, int *work, int buf_cap) {
-  extern __shared__ unsigned char smem_raw[];
-  MdBuf *buf = reinterpret_cast<MdBuf *>(smem_raw) + (threadIdx.x >> 5) * buf_cap;
-  const int lane = threadIdx.x & 31;
-  const int total = n_events * g.n_mod;
-  for (;;) {
-    int u0 = 0;
-    if (lane == 0) u0 = atomicAdd(work, MD_CHUNK);
-    u0 = __shfl_sync(FULL, u0, 0);
-    if (u0 >= total) break;
-    for (int u = u0; u < min(u0 + MD_CHUNK, total); u++) {
-      const int e = u / g.n_mod, m = u - e * g.n_mod;
-      const EvDesc &ev = evs[e];
-      // one read per warp: other warps may set a flag concurrently, all lanes must agree
-      const int flags = __shfl_sync(FULL, lane == 0 ? ev.cnt[C_FLAGS] : 0, 0);
-      const int lo0 = ev.sens_off[2 * m], lo1 = ev.sens_off[2 * m + 1], up1 = ev.sens_off[2 * m + 2];
-      const int nlo = lo1 - lo0, nup = up1 - lo1;
-      const long long np64 = (long long)nlo * nup;
-      if (np64 > (1ll << 30)) {   // more hit pairs in one module than an int index can address
-        if (lane == 0) { atomicOr(ev.cnt + C_FLAGS, F_INPUT); ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
-        continue;
-      }
-      const int np = (flags & F_INPUT) ? 0 : (int)np64;
-      const bool endcap = g.subdet[m] != 0;
-      if (lane == 0 && np) atomicAdd(ev.cnt + C_PMD, np);
-      // pass 1: evaluate, compact into the warp's list
-      int nsel = 0;
-      for (int b = 0; b < np; b += 32) {
-        const int p = b + lane;
-        bool pass = false;
-        float kc = 0.0f, kf = 0.0f;
-        if (p < np) {
-          const int i = p / nup, j = p - (p / nup) * nup;
-          if (chk(ev, lo0 + i, ev.n_hits, 12) && chk(ev, lo1 + j, ev.n_hits, 13)) {
-            const float4 L = ev.hit[lo0 + i], U = ev.hit[lo1 + j];
-            pass = md_cut(L, U, endcap, c, kc);
-            if (pass && !endcap) kf = md_kappa_acc(L, U);
-          }
-        }
-        const unsigned bal = __ballot_sync(FULL, pass);
-        const int slot = nsel + __popc(bal & lanemask_lt());
-        if (pass && slot < buf_cap) buf[slot] = {p, kc, kf};
-        nsel += __popc(bal);
-      }
-      __syncwarp();
-      const int base = warp_reserve(ev.cnt + C_MD, ev.cnt + C_FLAGS, F_OVF_MD, nsel, ev.md_cap);
-      if (base < 0 || nsel == 0) {
-        if (lane == 0) { ev.md_start[m] = 0; ev.md_cnt[m] = 0; }
-        continue;
-      }
-      if (nsel <= buf_cap) {
-        for (int k = lane; k < nsel; k += 32) {
-          const MdBuf r = buf[k];
-          const int i = r.p / nup, j = r.p - (r.p / nup) * nup;
-          if (!chk(ev, base + k, ev.md_cap, 11)) continue;
-          ev.md_anchor[base + k] = ev.hit[lo0 + i];
-          ev.md_kappa[base + k] = make_float2(r.kc, r.kf);
-          ev.md_mod[base + k] = m;
-          ev.md_hits[base + k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
-        }
-      } else {
-        // list overflow: evaluate again and write in place (same pair order)
-        int w = 0;
-        for (int b = 0; b < np; b += 32) {
-          const int p = b + lane;
-          bool pass = false;
-          float kc = 0.0f, kf = 0.0f;
-          int i = 0, j = 0;
-          float4 L, U;
-          if (p < np) {
-            i = p / nup;
-            j = p - i * nup;
-            L = ev.hit[lo0 + i];
-            U = ev.hit[lo1 + j];
-            pass = md_cut(L, U, endcap, c, kc);
-            if (pass && !endcap) kf = md_kappa_acc(L, U);
-          }
-          const unsigned bal = __ballot_sync(FULL, pass);
-          if (pass) {
-            const int k = base + w + __popc(bal & lanemask_lt());
-            ev.md_anchor[k] = L;
-            ev.md_kappa[k] = make_float2(kc, kf);
-            ev.md_mod[k] = m;
-            ev.md_hits[k] = make_int2(ev.hit_orig[lo0 + i], ev.hit_orig[lo1 + j]);
-          }
-          w += __popc(bal);
-        }
-      }
-      if (lane == 0) { ev.md_start[m] = base; ev.md_cnt[m] = nsel; }
-      __syncwarp();
+                                           lst_cuts c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  MdWarp &w = reinterpret_cast<MdWarp *>(smem_raw)[wid];
+  const int nm = g.n_mod;
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return (ev.cnt[C_FLAGS] & F_INPUT) ? 0 : (ev.sens_off[nm] + 31) / 32;
+  }, s_pref);
+  const int total = s_pref[n_events];
+  const int W = gridDim.x * nwarps;
+  int cur = -1, acc = 0;
+  for (int u = blockIdx.x * nwarps + wid; u < total; u += W) {
+    const int e = find_event(s_pref, n_events, u);
+    if (e != cur) {
+      if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PMD, acc);
+      acc = 0;
+      cur = e;
     }
+    const EvDesc &ev = evs[e];
+    const int h = (u - s_pref[e]) * 32 + lane;
+    int nup = 0, up0 = 0;
+    bool endcap = false;
+    float4 L = make_float4(0.f, 0.f, 0.f, 1.f);
+    float hb2r2 = 0.0f;
+    if (h < ev.sens_off[nm]) {
+      const int m = ev.hit_mod[h];
+      up0 = ev.sens_off[nm + m];
+      nup = ev.sens_off[nm + m + 1] - up0;
+      endcap = g.subdet[m] != 0;
+      L = ev.hit[h];
+      const float hb = L.w * (0.5f * c.kappa_max) + c.hit_err / c.sensor_gap;
+      hb2r2 = (L.w * hb) * (L.w * hb);
+      w.L[lane] = L;
+      w.lo[lane] = h;
+      w.mod[lane] = m;
+      w.endc[lane] = endcap;
+    }
+    int mx = nup, sum = nup;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+      sum += __shfl_xor_sync(FULL, sum, o);
+    }
+    acc += sum;
+    // exact cut on queued pairs [q0, q0 + n)
+    auto run_queue = [&](int q0, int n) {
+      bool pass = false;
+      float kc = 0.0f, kf = 0.0f;
+      int x = 0, uh = 0;
+      if (lane < n) {
+        x = w.qx[q0 + lane];
+        uh = w.qu[q0 + lane];
+        const float4 LL = w.L[x], U = ev.hit[uh];
+        const bool ec = w.endc[x] != 0;
+        pass = md_cut(LL, U, ec, c, kc);
+        if (pass && !ec) kf = md_kappa_acc(LL, U);
+      }
+      const unsigned bal = __ballot_sync(FULL, pass);
+      if (bal) {
+        const int base = warp_reserve(ev.cnt + C_MD, ev.cnt + C_FLAGS, F_OVF_MD, __popc(bal), ev.md_cap);
+        if (pass && base >= 0) {
+          const int o = base + __popc(bal & lanemask_lt());
+          if (chk(ev, o, ev.md_cap, 11)) {
+            ev.mdu_anchor[o] = w.L[x];
+            ev.mdu_kappa[o] = make_float2(kc, kf);
+            ev.mdu_mod[o] = w.mod[x];
+            ev.mdu_hits[o] = make_int2(ev.hit_orig[w.lo[x]], ev.hit_orig[uh]);
+            atomicAdd(ev.md_cnt + w.mod[x], 1);
+          }
+        }
+      }
+    };
+    __syncwarp();
+    int qlen = 0;
+    for (int j = 0; j < mx; j++) {
+      bool pre = false;
+      if (j < nup) pre = md_prefilter(L, ev.hit[up0 + j], endcap, hb2r2, c);
+      const unsigned bal = __ballot_sync(FULL, pre);
+      if (bal == 0) continue;
+      if (pre) {
+        const int q = qlen + __popc(bal & lanemask_lt());
+        w.qx[q] = lane;
+        w.qu[q] = up0 + j;
+      }
+      qlen += __popc(bal);
+      if (qlen >= 32) {
+        __syncwarp();
+        run_queue(qlen - 32, 32);
+        qlen -= 32;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    if (qlen > 0) run_queue(0, qlen);
+    __syncwarp();
+  }
+  if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PMD, acc);
+}
+
+// MDs grouped by module: exclusive scan of the per-module counts (one CTA per event) ...
+__global__ void k_md_scan(const EvDesc *__restrict__ evs, DevGeom g) {
+  const EvDesc &ev = evs[blockIdx.x];
+  if (ev_void(ev)) return;
+  const int n = g.n_mod;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  int local = 0;
+  for (int k = 0; k < per && b0 + k < n; k++) local += ev.md_cnt[b0 + k];
+  __shared__ int s_w[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int inc = warp_incl_scan(local);
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    const int v = lane < nw ? s_w[lane] : 0;
+    const int vi = warp_incl_scan(v);
+    if (lane < nw) s_w[lane] = vi - v;
+  }
+  __syncthreads();
+  int run = s_w[wid] + inc - local;
+  for (int k = 0; k < per && b0 + k < n; k++) {
+    ev.md_start[b0 + k] = run;
+    ev.md_cur[b0 + k] = run;
+    run += ev.md_cnt[b0 + k];
+  }
+}
+
+// ... then a scatter into module order.
+__global__ void k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_MD], ev.md_cap);
+  }, s_pref);
+  const int total = s_pref[n_events];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    const int e = find_event(s_pref, n_events, u);
+    const EvDesc &ev = evs[e];
+    const int o = u - s_pref[e];
+    const int m = ev.mdu_mod[o];
+    const int pos = atomicAdd(ev.md_cur + m, 1);
+    if (!chk(ev, pos, ev.md_cap, 14)) continue;
+    ev.md_anchor[pos] = ev.mdu_anchor[o];
+    ev.md_kappa[pos] = ev.mdu_kappa[o];
+    ev.md_mod[pos] = m;
+    ev.md_hits[pos] = ev.mdu_hits[o];
   }
 }
 
@@ -378,8 +447,9 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
 // chunks of 32 X1 of all events (no atomics); pair counts are summed per warp and flushed
 // once per event.
 struct T3Warp {
-  int incl[32], st2[32], md0[32], md1[32];
   float4 P0[32], P1[32];
+  int incl[32], st2[32], md0[32], md1[32];
+  int qx[64], qmd[64];   // queue of pairs that passed t3_prefilter
 };
 
 __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
@@ -419,18 +489,15 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     __syncwarp();
     const int tot = __shfl_sync(FULL, inc, 31);
     acc += tot;
-    for (int f0 = 0; f0 < tot; f0 += 32) {
-      const int f = f0 + lane;
+    // exact cut on queued pairs [q0, q0 + n): (LS1 lane, outer MD)
+    auto run_queue = [&](int q0, int n) {
       bool pass = false;
       float k = 0.0f;
       int x = 0, md2 = 0;
-      if (f < tot) {
-        int lo = 0, hi = 31;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
-        x = lo;
-        const int prev = lo ? w.incl[lo - 1] : 0;
-        md2 = ev.ls_out[w.st2[lo] + (f - prev)];
-        pass = t3_cut(w.P0[lo], w.P1[lo], ev.md_anchor[md2], c, k);
+      if (lane < n) {
+        x = w.qx[q0 + lane];
+        md2 = w.qmd[q0 + lane];
+        pass = t3_cut(w.P0[x], w.P1[x], ev.md_anchor[md2], c, k);
       }
       const unsigned bal = __ballot_sync(FULL, pass);
       if (bal) {
@@ -442,7 +509,37 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
           atomicAdd(ev.t3_cnt + w.md0[x], 1);
         }
       }
+    };
+    int qlen = 0;
+    for (int f0 = 0; f0 < tot; f0 += 32) {
+      const int f = f0 + lane;
+      bool pre = false;
+      int x = 0, md2 = 0;
+      if (f < tot) {
+        int lo = 0, hi = 31;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
+        x = lo;
+        const int prev = lo ? w.incl[lo - 1] : 0;
+        md2 = ev.ls_out[w.st2[lo] + (f - prev)];
+        pre = t3_prefilter(w.P0[lo], w.P1[lo], ev.md_anchor[md2], c);
+      }
+      const unsigned bal = __ballot_sync(FULL, pre);
+      if (bal == 0) continue;
+      if (pre) {
+        const int q = qlen + __popc(bal & lanemask_lt());
+        w.qx[q] = x;
+        w.qmd[q] = md2;
+      }
+      qlen += __popc(bal);
+      if (qlen >= 32) {
+        __syncwarp();
+        run_queue(qlen - 32, 32);
+        qlen -= 32;
+        __syncwarp();
+      }
     }
+    __syncwarp();
+    if (qlen > 0) run_queue(0, qlen);
     __syncwarp();
   }
   if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT3, acc);

@@ -202,6 +202,7 @@ __global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {
   if (tid < C_NCOUNTERS) ev.cnt[tid] = 0;
   for (int i = tid; i < 2 * g.n_mod; i += st) ev.sens_cnt[i] = 0;
   for (int i = tid; i < ev.md_cap; i += st) { ev.ls_cnt[i] = 0; ev.t3_cnt[i] = 0; }
+  for (int i = tid; i < g.n_mod; i += st) ev.md_cnt[i] = 0;
 }
 
 }  // namespace lstk
