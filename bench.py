@@ -182,6 +182,9 @@ def run_gpu(args, rank, world, local_rank, pool):
     precision = lst.LST_BF16 if args.precision == "bf16" else lst.LST_FP32
     ctx = lst.Context(local_rank, max_events=2 * B, precision=precision, use_graphs=1)
     ctx.load_geometry(g, cuts, flat, nh)
+    # the plain form: one launch sequence per event, FP32 score
+    ctx_p = lst.Context(local_rank, max_events=2, precision=lst.LST_FP32, use_graphs=0)
+    ctx_p.load_geometry(g, cuts, flat, nh)
     if args.tune:
         from paper_2403_13166_gb300 import autotune
         autotune.apply_cached(ctx, g)
@@ -245,18 +248,18 @@ def run_gpu(args, rank, world, local_rank, pool):
     if not args.skip_plain:
         n_plain = min(B, args.plain_events)
         for i in range(min(3, n_plain)):
-            ctx.run_event(*d_in[i], stream=stream).release()
+            ctx_p.run_event(*d_in[i], stream=stream).release()
         sync_all()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for i in range(n_plain):
-            ctx.run_event(*d_in[i], stream=stream).release()
+            ctx_p.run_event(*d_in[i], stream=stream).release()
         p1.record(stream)
         sync_all()
         pms = p0.elapsed_time(p1)
         plain = {"value": round(n_plain / (pms / 1000.0), 2), "unit": "events/s",
-                 "ms_per_event": round(pms / n_plain, 4), "events": n_plain,
-                 "gpu_launches_per_event": 10}
+                 "ms_per_event": round(pms / n_plain, 4), "events": n_plain, "score_precision": "fp32",
+                 "gpu_launches_per_event": 14, "form": "one launch sequence per event, no graph"}
 
     # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
@@ -313,9 +316,10 @@ def run_gpu(args, rank, world, local_rank, pool):
         "e2e": e2e,
         "roofline": roofline,
         "clocks": clk.summary(),
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": 14 * args.steps,
     }
     ctx.close()
+    ctx_p.close()
     return line
 
 
@@ -386,7 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lst", choices=["lst", "reference"])
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--plain-events", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")

@@ -161,9 +161,19 @@ lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int6
 
 /* Scores precomputed features with the loaded network (Section 2):
  *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores)
- *   or LST_BF16 (tensor cores, FP32 accumulation). Asynchronous on cuda_stream. */
+ *   or LST_BF16 (tensor cores: BF16 operands, FP32 accumulation). Asynchronous on
+ *   cuda_stream; a tensor-core wait that ran out is reported by lst_device_errors. */
 lst_status lst_score_t5(lst_ctx ctx, const float *feat, int64_t n, int32_t precision,
                         float *score_out, void *cuda_stream);
+
+/* Waits for the device and returns LST_ERR_TIMEOUT if a bounded device-side wait (the
+ * tensor-core score kernels wait for their MMAs with an iteration limit) ran out since the
+ * last call, else LST_OK; clears the condition. Events of a batch whose score wait ran out
+ * report LST_ERR_TIMEOUT themselves. */
+lst_status lst_device_errors(lst_ctx ctx);
+
+/* Iteration limit of those device-side waits (default 2^26 polls). */
+lst_status lst_set_wait_limit(lst_ctx ctx, int64_t iterations);
 
 /* Returns the event's slot to the context. */
 lst_status lst_event_release(lst_event ev);

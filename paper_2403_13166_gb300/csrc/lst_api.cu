@@ -32,6 +32,12 @@ __global__ void k_features(const EvDesc *, DevGeom, float, float *, int);
 __global__ void k_score_feat_fp32(const float *, int64_t, const float *, int, float *);
 __global__ void k_gather(const EvDesc *, int, int, int32_t *, float *, uint8_t *);
 __global__ void k_collect(const EvDesc *, int, int *);
+cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
+                                     const float *, int, int *, long long);
+cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
+                                       const float *, int64_t, float *, int *, long long);
+int score_bf16_blocks_per_sm();
+void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
 }  // namespace lstk
 
 using namespace lstk;
@@ -127,6 +133,10 @@ struct lst_ctx_s {
   int n_hidden = 2;
   float *d_w = nullptr;
   int n_w = 0;
+  uint16_t *d_wpack = nullptr;   // BF16 weights in the tensor-core operand layout
+  int *d_err = nullptr;          // device error word (bounded waits of the tensor-core kernel)
+  long long wait_limit = 1ll << 26;
+  int grid_bf = 0;
   std::vector<Slot> slots;
   std::vector<Lane> lanes;     // lane 0: lst_run_event; lanes 1..: batches, round robin
   int next_lane = 1;
@@ -193,6 +203,7 @@ lst_status compute_grids(lst_ctx_s *c) {
   const size_t sw = (size_t)mlp_floats_host(4) * 4;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_fp32, c->sc_threads, sw));
   c->grid_sc = std::max(1, occ) * c->n_sm;
+  c->grid_bf = score_bf16_blocks_per_sm() * c->n_sm;
   return LST_OK;
 }
 
@@ -346,8 +357,12 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   mark(4);
   k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
   mark(5);
-  k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
-      L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
+  if (c->cfg.precision == LST_BF16)
+    CU(launch_score_bf16_events(c->grid_bf, st, L.d_desc, n, g, c->cuts, c->d_wpack, c->d_w, c->n_hidden, c->d_err,
+                                c->wait_limit));
+  else
+    k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
+        L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
   mark(6);
   k_collect<<<(n + 127) / 128, 128, 0, st>>>(L.d_desc, n, L.d_counts);
   CU(cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int) * C_NCOUNTERS * n, cudaMemcpyDeviceToHost, st));
@@ -373,6 +388,7 @@ void grow_ratios(lst_ctx_s *c, const Slot &s, const int32_t *cnt) {
 
 lst_status status_of(const int32_t *cnt) {
   if (cnt[C_FLAGS] & F_CHECK) return LST_ERR_CUDA;   // failed device bounds check (LST_CHECK builds)
+  if (cnt[C_FLAGS] & F_TIMEOUT) return LST_ERR_TIMEOUT;
   if (cnt[C_FLAGS] & F_INPUT) return LST_ERR_INPUT;
   if (cnt[C_FLAGS] & (F_OVF_MD | F_OVF_LS | F_OVF_T3 | F_OVF_T5)) return LST_ERR_CAPACITY;
   return LST_OK;
@@ -466,6 +482,10 @@ lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out) {
     if (s != LST_OK) { lst_destroy(x); return s; }
   }
   cudaStreamCreateWithFlags(&x->aux, cudaStreamNonBlocking);
+  if (cudaMalloc(&x->d_err, sizeof(int)) != cudaSuccess || cudaMemset(x->d_err, 0, sizeof(int)) != cudaSuccess) {
+    lst_destroy(x);
+    return fail(LST_ERR_NOMEM, "device error word");
+  }
   lst_status s = compute_grids(x);
   if (s != LST_OK) { lst_destroy(x); return s; }
   *out = x;
@@ -515,6 +535,14 @@ lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, c
   if (weights) std::memcpy(w.data(), weights->w, 4 * (size_t)c->n_w);
   CU(cudaMalloc(&c->d_w, 4 * (size_t)c->n_w));
   CU(cudaMemcpy(c->d_w, w.data(), 4 * (size_t)c->n_w, cudaMemcpyHostToDevice));
+  {
+    std::vector<uint16_t> pk(32 * 48 + 3 * 32 * 32, 0);
+    pack_weights_bf16(w.data(), nh, pk.data());
+    cudaFree(c->d_wpack);
+    c->d_wpack = nullptr;
+    CU(cudaMalloc(&c->d_wpack, pk.size() * 2));
+    CU(cudaMemcpy(c->d_wpack, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice));
+  }
   c->g.n_mod = n_mod;
   c->g.subdet = c->d_subdet;
   c->g.layer = c->d_layer;
@@ -782,8 +810,14 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
   if (!feat || !score_out) return fail(LST_ERR_ARG, "null buffer");
   DeviceGuard gd(c->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->grid_sc);
-  k_score_feat_fp32<<<grid, 256, (size_t)c->n_w * 4, st>>>(feat, n, c->d_w, c->n_hidden, score_out);
+  if (precision == LST_BF16) {
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->grid_bf);
+    CU(launch_score_bf16_features(grid, st, c->g, c->cuts, c->d_wpack, c->d_w, c->n_hidden, feat, n, score_out,
+                                  c->d_err, c->wait_limit));
+  } else {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->grid_sc);
+    k_score_feat_fp32<<<grid, 256, (size_t)c->n_w * 4, st>>>(feat, n, c->d_w, c->n_hidden, score_out);
+  }
   CU(cudaGetLastError());
   return LST_OK;
 }
@@ -814,7 +848,7 @@ lst_status lst_destroy(lst_ctx c) {
     }
     for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); }
     cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt);
-    cudaFree(c->d_w); cudaFree(c->scratch);
+    cudaFree(c->d_w); cudaFree(c->scratch); cudaFree(c->d_wpack); cudaFree(c->d_err);
     if (c->aux) cudaStreamDestroy(c->aux);
   }
   delete c;
@@ -851,6 +885,27 @@ lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
   }
   lst_status s = compute_grids(c);
   if (s != LST_OK) return s;
+  for (auto &L : c->lanes) {
+    for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+    L.graphs.clear();
+  }
+  return LST_OK;
+}
+
+lst_status lst_device_errors(lst_ctx c) {
+  if (!c) return fail(LST_ERR_ARG, "null ctx");
+  DeviceGuard gd(c->device);
+  int e = 0;
+  CU(cudaDeviceSynchronize());
+  CU(cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+  CU(cudaMemset(c->d_err, 0, sizeof e));
+  if (e) return fail((lst_status)e, "a bounded device wait ran out (tensor-core score)");
+  return LST_OK;
+}
+
+lst_status lst_set_wait_limit(lst_ctx c, int64_t iterations) {
+  if (!c || iterations < 1) return fail(LST_ERR_ARG, "null ctx or limit < 1");
+  c->wait_limit = iterations;
   for (auto &L : c->lanes) {
     for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
     L.graphs.clear();

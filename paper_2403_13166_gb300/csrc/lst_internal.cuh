@@ -23,7 +23,7 @@ enum CounterSlot {
   C_DBG_SITE = 10, C_DBG_VAL = 11,              // first failed bounds check (LST_CHECK builds)
   C_NCOUNTERS = 12
 };
-enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16, F_CHECK = 32 };
+enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16, F_CHECK = 32, F_TIMEOUT = 64 };
 
 struct DevGeom {
   int32_t n_mod;

@@ -1,0 +1,298 @@
+// lst_mma.cu -- T5-DNN on the sm_103a tensor cores (BF16 operands, FP32 accumulation).
+//
+// The network of Section 2 (38 inputs -> 32 -> 32 -> 1) is evaluated as GEMMs over tiles of
+// 128 quintuplets: features (FP32, same code as the FP32 path) are rounded to BF16 into a
+// shared-memory tile A[128 x 48] (K padded 38 -> 48 with zeros); one elected thread issues
+// tcgen05.mma (M=128, N=32, K=16 per instruction) against the BF16 weight tile W1[32 x 48];
+// the FP32 accumulator lives in tensor memory (TMEM) and each warp reads its 32 rows back
+// with tcgen05.ld. Bias + ReLU are applied in registers, the hidden activations go back to
+// shared memory as BF16 for the next layer (K = 32), and the 32 -> 1 output layer plus the
+// sigmoid run on the CUDA cores. Operands use the canonical K-major layout without swizzle:
+// 8 x 16-byte core matrices, LBO = 128 B between K-adjacent core matrices, SBO = (K/8)*128 B
+// between 8-row groups.
+//
+// Completion of each MMA group is tracked by an mbarrier (tcgen05.commit). Every wait is
+// bounded: when it runs out, the kernel records LST_ERR_TIMEOUT in the error word, skips
+// the rest of its work, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "lst_features.cuh"
+
+namespace lstk {
+
+namespace {
+
+constexpr int TILE_M = 128;
+constexpr int K1 = 48;                 // 38 features padded to a multiple of 16
+constexpr int TMEM_COLS = 32;          // one 128 x 32 FP32 accumulator, reused by every layer
+                                       // (16 CTAs per SM x 32 columns fit the 512 columns)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, no swizzle, descriptor version 1
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; i++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// 32 lanes x 32 columns (this warp's quarter of TMEM) into 32 registers, waiting for them
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle tile with K columns
+__device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
+  return (uint32_t)((row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// write one row of K values (K a multiple of 8) as BF16 with 16-byte stores
+template <int K>
+__device__ __forceinline__ void store_row_bf16(unsigned char *tile, int row, const float *v) {
+#pragma unroll
+  for (int k8 = 0; k8 < K / 8; k8++) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) h[j] = __float2bfloat16_rn(v[k8 * 8 + j]);
+    *reinterpret_cast<uint4 *>(tile + core_off(row, k8 * 8, K)) = *reinterpret_cast<const uint4 *>(h);
+  }
+}
+
+}  // namespace
+
+// wpack: BF16 weights already in the core-matrix layout: W0 [32 x 48], then W1..W_{nh-1}
+// [32 x 32]. wflat: the FP32 flat network (biases, output layer). FROM_EVENTS: features of
+// the T5s of the batch; otherwise rows of feat_in [n][38].
+template <bool FROM_EVENTS>
+__global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
+                                                   lst_cuts c, const uint16_t *__restrict__ wpack,
+                                                   const float *__restrict__ wflat, int n_hidden,
+                                                   const float *__restrict__ feat_in, int64_t n_rows,
+                                                   float *__restrict__ score_out, int *err,
+                                                   long long wait_limit) {
+  __shared__ __align__(1024) unsigned char sA[TILE_M * K1 * 2];          // 12 KB
+  __shared__ __align__(1024) unsigned char sW[(32 * K1 + 3 * 32 * 32) * 2];  // 9 KB
+  __shared__ float sBias[4 * 32], sOut[33];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // weights -> shared memory
+  const int wbytes = (32 * K1 + (n_hidden - 1) * 32 * 32) * 2;
+  for (int i = tid; i < wbytes / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(wpack)[i];
+  {
+    const float *p = wflat + NHID * NFEAT;            // b0
+    if (tid < 32) sBias[tid] = p[tid];
+    p += NHID;
+    for (int l = 1; l < n_hidden; l++) {
+      if (tid < 32) sBias[32 * l + tid] = p[NHID * NHID + tid];
+      p += NHID * NHID + NHID;
+    }
+    if (tid < 33) sOut[tid] = p[tid];                 // w_out[32], b_out
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  int64_t total;
+  if (FROM_EVENTS) {
+    block_event_prefix(n_events, [&](int e) {
+      const EvDesc &ev = evs[e];
+      return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_T5], ev.t5_cap);
+    }, s_pref);
+    total = s_pref[n_events];
+  } else {
+    __syncthreads();
+    total = n_rows;
+  }
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t aA = smem_u32(sA), aW = smem_u32(sW);
+  uint32_t phase = 0;
+  const uint32_t idesc = make_idesc(TILE_M, 32);
+
+  for (int64_t base = (int64_t)blockIdx.x * TILE_M; base < total; base += (int64_t)gridDim.x * TILE_M) {
+    const int64_t row = base + tid;
+    const bool valid = row < total;
+    int e = 0, t = 0;
+    float f[NFEAT];
+    if (valid) {
+      if (FROM_EVENTS) {
+        e = find_event(s_pref, n_events, (int)row);
+        t = (int)row - s_pref[e];
+        t5_features(evs[e], g, t, c.k_field, f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NFEAT; i++) f[i] = feat_in[row * NFEAT + i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NFEAT; i++) f[i] = 0.0f;
+    }
+    {
+      float v[K1];
+#pragma unroll
+      for (int i = 0; i < K1; i++) v[i] = i < NFEAT ? f[i] : 0.0f;
+      store_row_bf16<K1>(sA, tid, v);
+    }
+    float h[32];
+    for (int l = 0; l < n_hidden; l++) {
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      const int K = l == 0 ? K1 : 32;
+      const uint32_t wofs = l == 0 ? 0 : (uint32_t)(32 * K1 * 2 + (l - 1) * 32 * 32 * 2);
+      const uint32_t dcol = tmem;
+      if (tid == 0 && !s_abort) {
+        fence_after();
+        for (int k = 0; k < K / 16; k++) {
+          const uint64_t da = make_desc(aA + k * 256, 128, (K / 8) * 128);
+          const uint64_t db = make_desc(aW + wofs + k * 256, 128, (K / 8) * 128);
+          mma_bf16(dcol, da, db, idesc, k > 0 ? 1u : 0u);
+        }
+        mma_commit(mb);
+      }
+      if (!s_abort && !mbar_wait(mb, phase, wait_limit)) {
+        atomicExch(err, LST_ERR_TIMEOUT);
+        s_abort = 1;
+      }
+      phase ^= 1;
+      __syncthreads();
+      if (s_abort) break;
+      fence_after();
+      float acc[32];
+      tmem_ld32(dcol + ((uint32_t)(warp * 32) << 16), acc);
+#pragma unroll
+      for (int j = 0; j < 32; j++) h[j] = fmaxf(acc[j] + sBias[32 * l + j], 0.0f);
+      if (l + 1 < n_hidden) store_row_bf16<32>(sA, tid, h);
+    }
+    if (s_abort) {
+      // the accumulator never arrived: void every event of the batch (host reports a timeout)
+      if (FROM_EVENTS && tid == 0)
+        for (int ee = 0; ee < n_events; ee++) atomicOr(evs[ee].cnt + C_FLAGS, F_TIMEOUT);
+      break;
+    }
+    float s = sOut[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) s = __fmaf_rn(sOut[j], h[j], s);
+    const float score = 1.0f / (1.0f + expf(-s));
+    if (valid) {
+      if (FROM_EVENTS) {
+        const EvDesc &ev = evs[e];
+        const bool sel = score >= c.wp;
+        ev.t5_score[t] = score;
+        ev.t5_sel[t] = sel ? 1 : 0;
+        if (sel) atomicAdd(ev.cnt + C_NSEL, 1);
+      } else {
+        score_out[row] = score;
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Host-side launchers (kernel template instances stay in this translation unit).
+cudaError_t launch_score_bf16_events(int grid, cudaStream_t st, const EvDesc *evs, int n_events, DevGeom g,
+                                     lst_cuts c, const uint16_t *wpack, const float *wflat, int n_hidden, int *err,
+                                     long long wait_limit) {
+  k_score_bf16<true><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr, err,
+                                           wait_limit);
+  return cudaGetLastError();
+}
+cudaError_t launch_score_bf16_features(int grid, cudaStream_t st, DevGeom g, lst_cuts c, const uint16_t *wpack,
+                                       const float *wflat, int n_hidden, const float *feat, int64_t n, float *out,
+                                       int *err, long long wait_limit) {
+  k_score_bf16<false><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err, wait_limit);
+  return cudaGetLastError();
+}
+int score_bf16_blocks_per_sm() {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true>, 128, 0) != cudaSuccess) return 1;
+  return occ > 0 ? occ : 1;
+}
+
+// BF16 weights in the core-matrix layout expected above, built on the host (see the layout
+// comment at the top): element (n, k) of an N=32 x K matrix at byte offset
+// (n/8)*(K/8)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2.
+void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out) {
+  auto put = [&](const float *W, int K_in, int K, uint16_t *dst) {
+    for (int n = 0; n < 32; n++)
+      for (int k = 0; k < K; k++) {
+        const float v = k < K_in ? W[n * K_in + k] : 0.0f;
+        const size_t off = (size_t)(n / 8) * (K / 8) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        dst[off / 2] = *reinterpret_cast<const uint16_t *>(&b);
+      }
+  };
+  put(wflat, NFEAT, K1, out);
+  const float *p = wflat + NHID * NFEAT + NHID;
+  for (int l = 1; l < n_hidden; l++) {
+    put(p, NHID, 32, out + 32 * K1 + (l - 1) * 32 * 32);
+    p += NHID * NHID + NHID;
+  }
+}
+
+}  // namespace lstk

@@ -211,3 +211,52 @@ def test_score_t5_standalone_fp32(ctx_full, model):
     got = out.cpu().numpy().astype(np.float64)
     exp = np.array([oracle.mlp_forward(model[0], 2, f[i].astype(np.float64)) for i in range(0, 5000, 7)])
     assert np.max(np.abs(got[::7] - exp)) <= SCORE_TOL
+
+
+# --------------------------------------------------------------------------- BF16 tensor cores
+BF16_TOL = 2e-2   # stated bound of the BF16 score (BF16 operands, FP32 accumulation) vs FP64
+
+
+def test_score_t5_standalone_bf16(ctx_full, model):
+    rng = np.random.default_rng(12)
+    f = rng.normal(0, 1, (4099, 38)).astype(np.float32)   # ragged last tile of 128 rows
+    d = torch.from_numpy(f).cuda()
+    out32 = torch.empty(4099, dtype=torch.float32, device="cuda")
+    out16 = torch.empty(4099, dtype=torch.float32, device="cuda")
+    ctx_full.score_t5(d, out32, lst.LST_FP32)
+    ctx_full.score_t5(d, out16, lst.LST_BF16)
+    torch.cuda.synchronize()
+    assert lst.load_library().lst_device_errors(ctx_full.h) == lst.LST_OK
+    a, b = out32.cpu().numpy().astype(np.float64), out16.cpu().numpy().astype(np.float64)
+    exp = np.array([oracle.mlp_forward(model[0], 2, f[i].astype(np.float64)) for i in range(0, 4099, 5)])
+    err = np.max(np.abs(b[::5] - exp))
+    print(f"bf16 standalone max|dscore| vs fp64 = {err:.3e}")
+    assert err <= BF16_TOL
+    assert np.max(np.abs(a[::5] - exp)) <= SCORE_TOL
+
+
+def test_bf16_event_path(geom_full, cuts, model):
+    c = lst.Context(0, max_events=4, precision=lst.LST_BF16)
+    c.load_geometry(geom_full, cuts, *model)
+    e = synth.pileup_event(geom_full, 9, pileup=120, mean_per_vertex=96)
+    ref = oracle.run_event(geom_full, e, cuts, *model)
+    ev = c.run_event(*dev(e))
+    hits, score, sel = ev.candidates(lst.LST_T5)
+    exp = ref.t5_hits()
+    og, oe = canon_order(hits), canon_order(exp)
+    assert np.array_equal(hits[og], exp[oe])          # the cuts are FP32 in both precisions
+    err = np.max(np.abs(score[og].astype(np.float64) - ref.t5_score[oe]))
+    flips = int(np.sum(sel[og].astype(bool) != (ref.t5_score[oe] >= float(cuts["wp"]))))
+    print(f"bf16 event path: {len(hits)} T5, max|dscore| = {err:.3e}, selection flips = {flips}")
+    assert err <= BF16_TOL
+    # a flip needs the FP64 score within the error of the working point
+    near = np.abs(ref.t5_score[oe] - float(cuts["wp"])) <= err
+    assert np.all((sel[og].astype(bool) == (ref.t5_score[oe] >= float(cuts["wp"]))) | near)
+    ev.release()
+    # batched BF16 (graph) path gives the same scores as the single-event BF16 path
+    h = c.run_batch([dev(e)])[0]
+    hb, sb, _ = h.candidates(lst.LST_T5)
+    ob = canon_order(hb)
+    assert np.array_equal(hb[ob], hits[og]) and np.array_equal(sb[ob], score[og])
+    h.release()
+    c.close()
