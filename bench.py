@@ -290,6 +290,11 @@ def run_gpu(args, rank, world, local_rank, pool):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h / e2e_steps),
            "steps": e2e_steps}
 
+    # ---------------- served: Poisson arrivals, continuous batching, BF16 score
+    served = None
+    if not args.skip_served and world == 1:
+        served = run_served(args, pool, g, cuts, flat, nh, local_rank)
+
     # ---------------- roofline of the dominant kernel
     c0 = counts[0] if counts else {}
     mean_counts = {k: float(np.mean([c[k] for c in counts])) for k in ("md", "ls", "t3", "t5")}
@@ -313,6 +318,7 @@ def run_gpu(args, rank, world, local_rank, pool):
                    "graphs": True, "l2": f"inputs larger than L2 ({int(h2d / 2**20)} MiB of hits per step)",
                    "objects_per_event_mean": {k: int(v) for k, v in mean_counts.items()}},
         "plain": plain,
+        "served": served,
         "e2e": e2e,
         "roofline": roofline,
         "clocks": clk.summary(),
@@ -323,7 +329,61 @@ def run_gpu(args, rank, world, local_rank, pool):
     return line
 
 
-# algorithmic work per unit ("Roofline accounting")
+def run_served(args, pool, g, cuts, flat, nh, local_rank):
+    """Requests arrive one at a time (Poisson) and are served by the library's continuous-
+    batching worker; latency = completion of the event (results on the host) - arrival."""
+    import torch
+    from paper_2403_13166_gb300 import lst
+    rng = np.random.default_rng(5)
+    pus = rng.integers(140, 201, args.served_pool)
+    evs = pool.map(_gen_event, [(500_000 + i, int(pu), PER_VERTEX, 5) for i, pu in enumerate(pus)])
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in e[1:]] for e in evs]
+    ctx = lst.Context(local_rank, max_events=2 * args.batch, precision=lst.LST_BF16, use_graphs=1)
+    ctx.load_geometry(g, cuts, flat, nh)
+    out = {"workload": "pu140_200_poisson", "pool_events": int(args.served_pool), "max_batch": args.batch,
+           "lanes": 2, "score_precision": "bf16", "rates": []}
+    srv = lst.Server(ctx, max_batch=args.batch, lanes=2, mem_budget_bytes=int(args.served_mem_gb * 2**30),
+                     copy_t5=True)
+    # warm-up: one burst (captures the graphs for the batch sizes seen first)
+    for k in range(2 * args.batch):
+        e = pinned[k % len(pinned)]
+        srv.submit(*e, tag=k)
+    got = 0
+    while got < 2 * args.batch:
+        got += len(srv.poll(wait_ms=100))
+    tag = 10**6
+    for rate in args.served_rates:
+        n = max(50, int(rate * args.served_seconds))
+        gaps = rng.exponential(1.0 / rate, n)
+        t0 = lst.clock() + 0.01
+        arr = t0 + np.cumsum(gaps)
+        res = []
+        for k in range(n):
+            while True:
+                now = lst.clock()
+                if now >= arr[k]:
+                    break
+                if arr[k] - now > 0.002:
+                    time.sleep(0.0005)
+                res.extend(srv.poll())
+            e = pinned[k % len(pinned)]
+            srv.submit(*e, tag=tag + k, t_arrival=float(arr[k]))
+        while len(res) < n:
+            res.extend(srv.poll(wait_ms=100))
+        tag += n
+        lat = np.array([r["t_done"] - r["t_arrival"] for r in res]) * 1000.0
+        ok = all(r["status"] == lst.LST_OK for r in res)
+        span = max(r["t_done"] for r in res) - arr[0]
+        out["rates"].append({"offered_per_s": rate, "events": n, "achieved_per_s": round(n / span, 1),
+                             "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3), "all_ok": ok})
+    srv.stop()
+    ctx.close()
+    return out
+
+
+# Algorithmic work for the roofline: FP32 operations of the cut expressions per candidate
+# pair tested (the cheapest test every pair needs) and per accepted object (the rest).
 FP32_OPS_PER_PAIR = {"md": 6, "ls": 12, "t3": 16, "t5": 6}
 FP32_OPS_PER_OBJECT = {"md": 30, "ls": 35, "t3": 30, "t5": 40}
 
@@ -396,6 +456,11 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--skip-served", action="store_true")
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000])
+    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-pool", type=int, default=48)
+    ap.add_argument("--served-mem-gb", type=float, default=16.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -211,6 +211,54 @@ lst_status lst_set_timing(lst_ctx ctx, int32_t enable);
 lst_status lst_stage_times(lst_ctx ctx, float *ms6, int64_t *n_launches);
 
 /* ---------------------------------------------------------------------------------
+ * Serving: continuous batching of events that arrive one by one (Section 3 runs events
+ * concurrently on CUDA streams; here events share batched launches instead).
+ * A worker thread owns the context while the server runs (make no other call on it).
+ * Requests are admitted in arrival order when an event slot is free and the estimated
+ * object-buffer memory of all admitted events stays within mem_budget_bytes (a single
+ * event is always admitted when nothing else is). Admitted events go to the GPU in
+ * batches of up to max_batch (one launch per stage, CUDA graph) on `lanes` streams, so a
+ * new batch starts while the previous one is still running.
+ *   submit: x, y, z, sensor are HOST arrays that must stay valid until the request's
+ *           result has been polled; t_arrival is the request time on lst_clock() (<= 0:
+ *           now); the latency of a request is t_done - t_arrival.
+ *   poll:   returns up to `max` finished requests (waiting up to wait_ms for the first);
+ *           each result owns host copies of its T5 tuples when copy_t5 is set
+ *           (lst_serve_free_result frees them).
+ *   stop:   finishes every submitted request, then joins the worker. */
+typedef struct lst_serve_config {
+    int32_t max_batch;          /* events per batched launch, 1..max_events */
+    int32_t lanes;              /* batches in flight: 1 or 2 */
+    int64_t mem_budget_bytes;   /* admission budget (estimated device bytes of admitted events) */
+    int32_t copy_t5;            /* 1: results carry the T5 hit tuples, scores, selection */
+    int32_t reserved;
+} lst_serve_config;
+
+typedef struct lst_serve_result {
+    uint64_t tag;               /* the caller's tag */
+    int32_t status;             /* lst_status of the event */
+    int32_t reserved;
+    lst_counts counts;
+    double t_arrival, t_admit, t_launch, t_done;   /* lst_clock() seconds */
+    int64_t n_t5;
+    int32_t *t5_hits;           /* HOST [n_t5][10] */
+    float *t5_score;            /* HOST [n_t5] */
+    uint8_t *t5_sel;            /* HOST [n_t5] */
+} lst_serve_result;
+
+typedef struct lst_server_s *lst_server;
+
+/* Monotonic clock of the library, seconds. */
+double lst_clock(void);
+lst_status lst_serve_start(lst_ctx ctx, const lst_serve_config *cfg, lst_server *out);
+lst_status lst_serve_submit(lst_server s, const float *x, const float *y, const float *z,
+                            const int32_t *sensor, int64_t n_hits, uint64_t tag, double t_arrival);
+lst_status lst_serve_poll(lst_server s, lst_serve_result *out, int32_t max, int32_t *n_out,
+                          int32_t wait_ms);
+lst_status lst_serve_free_result(lst_serve_result *r);
+lst_status lst_serve_stop(lst_server s);
+
+/* ---------------------------------------------------------------------------------
  * Mini-doublet finder that allocates nothing (the paper has no counterpart; it is a
  * deployment aid of this library).
  *

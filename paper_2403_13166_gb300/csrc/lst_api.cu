@@ -943,3 +943,280 @@ bool ctx_geometry(lst_ctx ctx, DevGeom *g, lst_cuts *c, int *device) {
 // Sets the calling thread's lst_last_error text.
 void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 }  // namespace lstk
+
+// ================================================================ serving (continuous batching)
+// A worker thread owns the context while the server runs. Requests (host hit arrays) are
+// admitted in arrival order while an event slot is free and the estimated object-buffer
+// memory of the admitted events stays within the budget; admitted events go out in
+// batches (one launch per stage over the batch, CUDA graph) on two lanes with their own
+// streams, so a batch can start while the previous one is still on the device. Requests
+// that arrive meanwhile wait only for a slot and memory, not for the running batch.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServeReq {
+  uint64_t tag = 0;
+  const float *x = nullptr, *y = nullptr, *z = nullptr;
+  const int32_t *sensor = nullptr;
+  int64_t n = 0;
+  double t_arrival = 0, t_admit = 0, t_launch = 0;
+  int slot = -1;
+  size_t est = 0;
+  int retries = 0;
+};
+
+// estimated device bytes of one event's object buffers (the slot layout of slot_alloc)
+size_t est_bytes(const lst_ctx_s *c, int64_t n) {
+  int md, ls, t3, t5;
+  caps_for(c, n, md, ls, t3, t5);
+  const size_t nm = (size_t)c->g.n_mod;
+  return (size_t)n * 24 + nm * 8 * 4 + (size_t)md * (16 + 8 + 4 + 8 + 8 + 16 + 8 + 4 + 8) +
+         (size_t)ls * 12 + (size_t)t3 * 40 + (size_t)t5 * 37 + (size_t)n * 16;
+}
+
+}  // namespace
+
+struct lst_server_s {
+  lst_ctx c = nullptr;
+  lst_serve_config cfg{};
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<ServeReq> submitted;       // guarded by mu
+  std::deque<lst_serve_result> done;    // guarded by mu
+  bool stop = false;                    // guarded by mu
+  std::string error;                    // guarded by mu
+  // worker-only state
+  std::deque<ServeReq> waiting;         // not yet given a slot
+  std::deque<ServeReq> ready;           // holds a slot, not launched
+  std::vector<ServeReq> inflight[2];
+  cudaStream_t st[2] = {nullptr, nullptr};
+  size_t mem_in_use = 0;
+};
+
+namespace {
+
+void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t *cnt) {
+  lst_ctx_s *c = S->c;
+  lst_serve_result res;
+  std::memset(&res, 0, sizeof res);
+  res.tag = r.tag;
+  res.status = status;
+  res.counts.n_hits = r.n;
+  if (cnt) {
+    res.counts.n_md = cnt[C_MD]; res.counts.n_ls = cnt[C_LS]; res.counts.n_t3 = cnt[C_T3];
+    res.counts.n_t5 = cnt[C_T5]; res.counts.n_selected = cnt[C_NSEL];
+    res.counts.pairs[0] = (uint32_t)cnt[C_PMD]; res.counts.pairs[1] = (uint32_t)cnt[C_PLS];
+    res.counts.pairs[2] = (uint32_t)cnt[C_PT3]; res.counts.pairs[3] = (uint32_t)cnt[C_PT5];
+  }
+  res.counts.status = status;
+  res.t_arrival = r.t_arrival;
+  res.t_admit = r.t_admit;
+  res.t_launch = r.t_launch;
+  if (status == LST_OK && S->cfg.copy_t5 && cnt && cnt[C_T5] > 0) {
+    const int64_t n5 = cnt[C_T5];
+    res.t5_hits = (int32_t *)std::malloc((size_t)n5 * 10 * 4);
+    res.t5_score = (float *)std::malloc((size_t)n5 * 4);
+    res.t5_sel = (uint8_t *)std::malloc((size_t)n5);
+    lst_event_s ev{c, r.slot, LST_OK};
+    int64_t got = 0;
+    if (!res.t5_hits || !res.t5_score || !res.t5_sel ||
+        lst_get_candidates(&ev, LST_T5, res.t5_hits, res.t5_score, res.t5_sel, n5, &got) != LST_OK) {
+      res.status = LST_ERR_CUDA;
+    }
+    res.n_t5 = got;
+  }
+  res.t_done = now_s();
+  c->slots[r.slot].busy = false;
+  S->mem_in_use -= std::min(S->mem_in_use, r.est);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->done.push_back(res);
+  S->cv.notify_all();
+}
+
+void serve_loop(lst_server_s *S) {
+  lst_ctx_s *c = S->c;
+  cudaSetDevice(c->device);
+  const int nl = std::max(1, std::min(2, S->cfg.lanes));
+  for (;;) {
+    bool progress = false;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (!S->submitted.empty()) {
+        S->waiting.push_back(S->submitted.front());
+        S->submitted.pop_front();
+        progress = true;
+      }
+      const bool idle = S->waiting.empty() && S->ready.empty() && S->inflight[0].empty() && S->inflight[1].empty();
+      if (S->stop && idle) break;
+      if (idle) {
+        S->cv.wait_for(lk, std::chrono::microseconds(200));
+        continue;
+      }
+    }
+    // admission: a free slot and room in the memory budget, in arrival order
+    while (!S->waiting.empty()) {
+      ServeReq &r = S->waiting.front();
+      const size_t est = est_bytes(c, r.n);
+      const bool fits = S->mem_in_use == 0 || S->mem_in_use + est <= (size_t)S->cfg.mem_budget_bytes;
+      const int si = fits ? find_free_slot(c) : -1;
+      if (si < 0) break;
+      c->slots[si].busy = true;
+      r.slot = si;
+      r.est = est;
+      r.t_admit = now_s();
+      S->mem_in_use += est;
+      S->ready.push_back(r);
+      S->waiting.pop_front();
+      progress = true;
+    }
+    // launch: every free lane takes up to max_batch ready events
+    for (int li = 0; li < nl && !S->ready.empty(); li++) {
+      if (!S->inflight[li].empty()) continue;
+      Lane &L = c->lanes[1 + li];
+      std::vector<int> ids;
+      std::vector<ServeReq> batch;
+      while (!S->ready.empty() && (int)batch.size() < S->cfg.max_batch) {
+        batch.push_back(S->ready.front());
+        S->ready.pop_front();
+      }
+      lst_status st = LST_OK;
+      for (auto &r : batch) {
+        Slot &sl = c->slots[r.slot];
+        if (st == LST_OK) st = slot_alloc(c, sl, r.n);
+        if (st == LST_OK) st = slot_inputs(c, sl, r.x, r.y, r.z, r.sensor, r.n, S->st[li]);
+        ids.push_back(r.slot);
+      }
+      const double tl = now_s();
+      for (auto &r : batch) r.t_launch = tl;
+      if (st == LST_OK) st = run_lane(c, L, (int)batch.size(), ids.data(), S->st[li], true, false);
+      if (st != LST_OK) {
+        for (auto &r : batch) serve_finish(S, r, st, nullptr);
+        continue;
+      }
+      S->inflight[li] = std::move(batch);
+      progress = true;
+    }
+    // completion
+    for (int li = 0; li < nl; li++) {
+      if (S->inflight[li].empty()) continue;
+      Lane &L = c->lanes[1 + li];
+      const cudaError_t q = cudaEventQuery(L.done);
+      if (q == cudaErrorNotReady) continue;
+      lst_status st = q == cudaSuccess ? lane_harvest(c, L) : LST_ERR_CUDA;
+      for (auto &r : S->inflight[li]) {
+        Slot &sl = c->slots[r.slot];
+        const lst_status es = st != LST_OK ? st : status_of(sl.cnt);
+        if (es == LST_ERR_CAPACITY && r.retries < 4) {
+          grow_ratios(c, sl, sl.cnt);       // run again with larger buffers
+          r.retries++;
+          S->ready.push_front(r);
+          continue;
+        }
+        serve_finish(S, r, es, st == LST_OK ? sl.cnt : nullptr);
+      }
+      S->inflight[li].clear();
+      progress = true;
+    }
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+double lst_clock(void) { return now_s(); }
+
+lst_status lst_serve_start(lst_ctx c, const lst_serve_config *cfg, lst_server *out) {
+  if (!c || !cfg || !out) return fail(LST_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no geometry loaded");
+  if (cfg->max_batch < 1 || cfg->max_batch > (int)c->slots.size())
+    return fail(LST_ERR_ARG, "max_batch outside 1..max_events");
+  if (cfg->mem_budget_bytes <= 0) return fail(LST_ERR_ARG, "mem_budget_bytes <= 0");
+  DeviceGuard gd(c->device);
+  for (auto &L : c->lanes) {
+    lst_status s = lane_harvest(c, L);
+    if (s != LST_OK) return s;
+  }
+  for (auto &sl : c->slots)
+    if (sl.busy) return fail(LST_ERR_NOT_READY, "release every event before serving");
+  lst_server_s *S = new lst_server_s();
+  S->c = c;
+  S->cfg = *cfg;
+  for (auto &s : S->st) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete S;
+      return fail(LST_ERR_CUDA, "stream creation");
+    }
+  }
+  S->th = std::thread(serve_loop, S);
+  *out = S;
+  return LST_OK;
+}
+
+lst_status lst_serve_submit(lst_server S, const float *x, const float *y, const float *z, const int32_t *sensor,
+                            int64_t n_hits, uint64_t tag, double t_arrival) {
+  if (!S) return fail(LST_ERR_ARG, "null server");
+  if (n_hits < 0 || n_hits > (int64_t)1 << 30) return fail(LST_ERR_ARG, "n_hits out of range");
+  if (n_hits > 0 && (!x || !y || !z || !sensor)) return fail(LST_ERR_ARG, "null hit array");
+  ServeReq r;
+  r.tag = tag;
+  r.x = x; r.y = y; r.z = z; r.sensor = sensor;
+  r.n = n_hits;
+  r.t_arrival = t_arrival > 0 ? t_arrival : now_s();
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return fail(LST_ERR_NOT_READY, "server is stopping");
+  S->submitted.push_back(r);
+  S->cv.notify_all();
+  return LST_OK;
+}
+
+lst_status lst_serve_poll(lst_server S, lst_serve_result *out, int32_t max, int32_t *n_out, int32_t wait_ms) {
+  if (!S || !n_out || (max > 0 && !out)) return fail(LST_ERR_ARG, "null argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (S->done.empty() && wait_ms > 0)
+    S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+  int n = 0;
+  while (n < max && !S->done.empty()) {
+    out[n++] = S->done.front();
+    S->done.pop_front();
+  }
+  *n_out = n;
+  return LST_OK;
+}
+
+lst_status lst_serve_free_result(lst_serve_result *r) {
+  if (!r) return fail(LST_ERR_ARG, "null result");
+  std::free(r->t5_hits);
+  std::free(r->t5_score);
+  std::free(r->t5_sel);
+  r->t5_hits = nullptr; r->t5_score = nullptr; r->t5_sel = nullptr;
+  return LST_OK;
+}
+
+lst_status lst_serve_stop(lst_server S) {
+  if (!S) return fail(LST_ERR_ARG, "null server");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  for (auto &r : S->done) lst_serve_free_result(&r);
+  for (auto &s : S->st) if (s) cudaStreamDestroy(s);
+  delete S;
+  return LST_OK;
+}
+
+}  // extern "C"

@@ -368,3 +368,90 @@ def header_symbols(header_path: str):
     import re
     src = open(header_path).read()
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(lst_\w+)\s*\(", src, re.M)))
+
+
+# ------------------------------------------------------------------ serving
+class lst_serve_config(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("lanes", C.c_int32), ("mem_budget_bytes", C.c_int64),
+                ("copy_t5", C.c_int32), ("reserved", C.c_int32)]
+
+
+class lst_serve_result(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32), ("counts", lst_counts),
+                ("t_arrival", C.c_double), ("t_admit", C.c_double), ("t_launch", C.c_double),
+                ("t_done", C.c_double), ("n_t5", C.c_int64), ("t5_hits", C.c_void_p),
+                ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p)]
+
+
+def _serve_sigs(lib):
+    lib.lst_clock.restype = C.c_double
+    lib.lst_clock.argtypes = []
+    for name, argt in {
+        "lst_serve_start": [C.c_void_p, C.POINTER(lst_serve_config), C.POINTER(C.c_void_p)],
+        "lst_serve_submit": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                             C.c_uint64, C.c_double],
+        "lst_serve_poll": [C.c_void_p, C.POINTER(lst_serve_result), C.c_int32, C.POINTER(C.c_int32), C.c_int32],
+        "lst_serve_free_result": [C.POINTER(lst_serve_result)],
+        "lst_serve_stop": [C.c_void_p],
+    }.items():
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        f.argtypes = argt
+    return lib
+
+
+def clock() -> float:
+    """lst_clock(): the library's monotonic clock in seconds."""
+    return _serve_sigs(load_library()).lst_clock()
+
+
+class Server:
+    """lst_serve_*: continuous batching of events submitted one at a time (host arrays)."""
+
+    def __init__(self, ctx: Context, max_batch=32, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True):
+        lib = _serve_sigs(load_library())
+        cfg = lst_serve_config(int(max_batch), int(lanes), int(mem_budget_bytes), int(bool(copy_t5)), 0)
+        h = C.c_void_p()
+        _check(lib.lst_serve_start(ctx.h, C.byref(cfg), C.byref(h)), "lst_serve_start")
+        self.h = h
+        self.ctx = ctx
+        self._keep = {}
+        self._buf = (lst_serve_result * 256)()
+
+    def submit(self, x, y, z, sensor, tag: int, t_arrival: float = 0.0):
+        arrs = [np.ascontiguousarray(a) for a in (x, y, z, sensor)]
+        self._keep[int(tag)] = arrs
+        _check(load_library().lst_serve_submit(self.h, *[_ptr(a) for a in arrs], int(arrs[0].shape[0]), int(tag),
+                                               float(t_arrival)), "lst_serve_submit")
+
+    def poll(self, wait_ms: int = 0, max_results: int = 256):
+        lib = load_library()
+        n = C.c_int32(0)
+        _check(lib.lst_serve_poll(self.h, self._buf, min(max_results, 256), C.byref(n), int(wait_ms)),
+               "lst_serve_poll")
+        out = []
+        for i in range(n.value):
+            r = self._buf[i]
+            d = dict(tag=r.tag, status=r.status, t_arrival=r.t_arrival, t_admit=r.t_admit, t_launch=r.t_launch,
+                     t_done=r.t_done, n_t5=r.n_t5, t5=r.counts.n_t5, md=r.counts.n_md, ls=r.counts.n_ls,
+                     t3=r.counts.n_t3, selected=r.counts.n_selected)
+            if r.t5_hits and r.n_t5:
+                n5 = r.n_t5
+                d["t5_hits"] = np.ctypeslib.as_array((C.c_int32 * (n5 * 10)).from_address(r.t5_hits)).reshape(n5, 10).copy()
+                d["t5_score"] = np.ctypeslib.as_array((C.c_float * n5).from_address(r.t5_score)).copy()
+                d["t5_sel"] = np.ctypeslib.as_array((C.c_uint8 * n5).from_address(r.t5_sel)).copy()
+            lib.lst_serve_free_result(C.byref(r))
+            self._keep.pop(int(r.tag), None)
+            out.append(d)
+        return out
+
+    def stop(self):
+        if getattr(self, "h", None):
+            load_library().lst_serve_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
