@@ -162,6 +162,26 @@ def nvsmi_index(torch, dev, local_rank) -> str:
     return str(local_rank)
 
 
+# ------------------------------------------------------------------ multi-rank host logic
+def rank_event_indices(rank: int, batch: int):
+    """Event seeds of one rank: disjoint across ranks (events are independent units)."""
+    return [rank * 100_000 + i for i in range(batch)]
+
+
+def max_over_ranks(x: float, device) -> float:
+    """Slowest rank's elapsed time: the only collective of the benchmark."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(events_per_rank: int, world: int, seconds_max: float) -> float:
+    """Events of all ranks divided by the slowest rank's time."""
+    return events_per_rank * world / seconds_max
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world, local_rank, pool):
     import torch
@@ -171,7 +191,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     dev = torch.device("cuda", local_rank)
     B = args.batch
     # events of this rank (distinct seeds per rank)
-    idx = [rank * 100_000 + i for i in range(B)]
+    idx = rank_event_indices(rank, B)
     evs = pool.map(_gen_event, [(i, PILEUP, PER_VERTEX, 2) for i in idx])
     n_hits = np.array([len(e[1]) for e in evs])
     g = _geom()
@@ -237,11 +257,8 @@ def run_gpu(args, rank, world, local_rank, pool):
     ctx.set_timing(False)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    events_total = B * args.steps * world
-    value = events_total / (ms_total / 1000.0)
+        ms_total = max_over_ranks(ms_total, dev)
+    value = whole_job_rate(B * args.steps, world, ms_total / 1000.0)
 
     # ---------------- plain path: one launch sequence per event
     plain = None
@@ -283,9 +300,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     e2e_s = time.perf_counter() - t0
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dev)
     e2e = {"value": round(B * e2e_steps * world / e2e_s, 2), "unit": "events/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h / e2e_steps),
            "steps": e2e_steps}
@@ -388,6 +403,17 @@ FP32_OPS_PER_PAIR = {"md": 6, "ls": 12, "t3": 16, "t5": 6}
 FP32_OPS_PER_OBJECT = {"md": 30, "ls": 35, "t3": 30, "t5": 40}
 
 
+# DRAM bytes (read + write) per event of a kernel, from one ncu capture of a 16-event
+# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 230.6 MB for
+# k_ls); the traffic is the per-event output plus MD reads, so it scales with the events.
+TRAFFIC_PER_EVENT = {"ls": 230.6e6 / 16}
+
+
+def traffic_per_launch(stage, events):
+    b = TRAFFIC_PER_EVENT.get(stage)
+    return None if b is None else int(b * events)
+
+
 def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
     peaks = {}
     try:
@@ -401,7 +427,7 @@ def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
         peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
         achieved = ops / (ms / 1000.0) / 1e12
         return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": f"k_{stage}",
+                "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(stage, B), "kernel": f"k_{stage}",
                 "peak_note": f"FP32 lanes x SM clock: {n_sm} SMs x 128 x {sm_mhz:.0f} MHz (non-FMA ops)"}
     # score / bin: HBM bound
     hbm = peaks.get("hbm_gbs", 6800.0)
