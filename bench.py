@@ -56,16 +56,27 @@ def _geom():
 
 def _oracle_time(args):
     """Oracle (as it stands) on one event; returns seconds of oracle time (generation excluded)."""
-    index, pileup, per_vertex, config, weights = args
+    index, pileup, per_vertex, config, weights, n_hidden, cut_set = args
     import oracle
     from paper_2403_13166_gb300 import synth
     g = _geom()
     e = synth.pileup_event(g, index, pileup=pileup, mean_per_vertex=per_vertex, config=config)
-    cuts = synth.default_cuts()
+    cuts = _cut_set(cut_set)
     t0 = time.perf_counter()
-    r = oracle.run_event(g, e, cuts, weights, 2)
+    r = oracle.run_event(g, e, cuts, weights, n_hidden)
     dt = time.perf_counter() - t0
     return dt, r.counts["t5"]
+
+
+# score arithmetic of the batched and served forms (the plain form is always FP32)
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+
+
+def _cut_set(name):
+    """'standard': the default cut parameters; 'open': the fit-quality tolerances of steps
+    3-4 opened (the sample the T5-DNN is trained on, where it removes the fakes)."""
+    from paper_2403_13166_gb300 import synth
+    return synth.open_cuts() if name == "open" else synth.default_cuts()
 
 
 def _weights():
@@ -76,10 +87,10 @@ def _weights():
     return synth.mlp_flat(synth.xavier_mlp()), 2, None, "xavier-seed2403"
 
 
-def cpu_baseline(pool, n_cores, events_per_core=2, config=2):
+def cpu_baseline(pool, n_cores, cut_set, events_per_core=2, config=2):
     """Bounded sample: every core runs `events_per_core` oracle events (~1 s each)."""
     flat, nh, _, _ = _weights()
-    jobs = [(10_000 + i, PILEUP, PER_VERTEX, config, flat) for i in range(n_cores * events_per_core)]
+    jobs = [(10_000 + i, PILEUP, PER_VERTEX, config, flat, nh, cut_set) for i in range(n_cores * events_per_core)]
     t0 = time.perf_counter()
     res = pool.map(_oracle_time, jobs, chunksize=events_per_core)
     wall = time.perf_counter() - t0
@@ -196,10 +207,10 @@ def run_gpu(args, rank, world, local_rank, pool):
     n_hits = np.array([len(e[1]) for e in evs])
     g = _geom()
     flat, nh, wp, wname = _weights()
-    cuts = synth.default_cuts()
+    cuts = _cut_set(args.cuts)
     if wp is not None:
         cuts["wp"] = np.float32(wp)
-    precision = lst.LST_BF16 if args.precision == "bf16" else lst.LST_FP32
+    precision = PRECISIONS[args.precision]
     ctx = lst.Context(local_rank, max_events=2 * B, precision=precision, use_graphs=1)
     ctx.load_geometry(g, cuts, flat, nh)
     # the plain form: one launch sequence per event, FP32 score
@@ -305,7 +316,7 @@ def run_gpu(args, rank, world, local_rank, pool):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h / e2e_steps),
            "steps": e2e_steps}
 
-    # ---------------- served: Poisson arrivals, continuous batching, BF16 score
+    # ---------------- served: Poisson arrivals, continuous batching, tensor-core score
     served = None
     if not args.skip_served and world == 1:
         served = run_served(args, pool, g, cuts, flat, nh, local_rank)
@@ -329,7 +340,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         "data": "synthetic",
         "config": {"workload": "pu200_like_batched", "events_per_step": B, "pileup": PILEUP,
                    "particles_per_vertex": PER_VERTEX, "hits_per_event_mean": int(np.mean(n_hits)),
-                   "modules": g.n_mod, "score_precision": args.precision, "weights": wname,
+                   "modules": g.n_mod, "score_precision": args.precision, "weights": wname, "cuts": args.cuts,
                    "graphs": True, "l2": f"inputs larger than L2 ({int(h2d / 2**20)} MiB of hits per step)",
                    "objects_per_event_mean": {k: int(v) for k, v in mean_counts.items()}},
         "plain": plain,
@@ -353,10 +364,10 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
     pus = rng.integers(140, 201, args.served_pool)
     evs = pool.map(_gen_event, [(500_000 + i, int(pu), PER_VERTEX, 5) for i, pu in enumerate(pus)])
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in e[1:]] for e in evs]
-    ctx = lst.Context(local_rank, max_events=2 * args.batch, precision=lst.LST_BF16, use_graphs=1)
+    ctx = lst.Context(local_rank, max_events=2 * args.batch, precision=PRECISIONS[args.precision], use_graphs=1)
     ctx.load_geometry(g, cuts, flat, nh)
     out = {"workload": "pu140_200_poisson", "pool_events": int(args.served_pool), "max_batch": args.batch,
-           "lanes": 2, "score_precision": "bf16", "rates": []}
+           "lanes": 2, "score_precision": args.precision, "rates": []}
     srv = lst.Server(ctx, max_batch=args.batch, lanes=2, mem_budget_bytes=int(args.served_mem_gb * 2**30),
                      copy_t5=True)
     # warm-up: one burst (captures the graphs for the batch sizes seen first)
@@ -445,7 +456,8 @@ def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
 def run_reference(args, pool, n_cores):
     flat, nh, _, _ = _weights()
     per_step = n_cores          # one event per core per step (~1 s of oracle work each)
-    jobs = lambda s: [(20_000 + s * per_step + i, PILEUP, PER_VERTEX, 2, flat) for i in range(per_step)]
+    jobs = lambda s: [(20_000 + s * per_step + i, PILEUP, PER_VERTEX, 2, flat, nh, args.cuts)
+                      for i in range(per_step)]
     for s in range(args.warmup):
         pool.map(_oracle_time, jobs(s), chunksize=1)
     busy = []
@@ -461,7 +473,7 @@ def run_reference(args, pool, n_cores):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "pu200_like_batched", "events_per_step": per_step, "pileup": PILEUP,
-                       "particles_per_vertex": PER_VERTEX},
+                       "particles_per_vertex": PER_VERTEX, "cuts": args.cuts},
             "cpu_baseline": {"value": round(value, 3), "unit": "events/s", "cores": n_cores, "kind": "oracle",
                              "sample": f"{per_step} PU200-like events per step, one per core, oracle time "
                                        f"only (generation excluded); wall {wall:.1f} s"},
@@ -476,7 +488,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lst", choices=["lst", "reference"])
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16x3", choices=list(PRECISIONS))
     ap.add_argument("--plain-events", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
@@ -487,6 +499,7 @@ def main():
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--served-pool", type=int, default=48)
     ap.add_argument("--served-mem-gb", type=float, default=16.0)
+    ap.add_argument("--cuts", default="standard", choices=["standard", "open"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -505,7 +518,7 @@ def main():
     with ctx_mp.Pool(min(n_cores, 16)) as pool:
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(pool, min(n_cores, 16))
+            cpu = cpu_baseline(pool, min(n_cores, 16), args.cuts)
         if world > 1:
             import torch.distributed as dist
             import torch

@@ -43,7 +43,12 @@ typedef enum lst_status {
 } lst_status;
 
 typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3 } lst_kind;
-typedef enum lst_precision { LST_FP32 = 0, LST_BF16 = 1 } lst_precision;
+/* Arithmetic of the T5-DNN score (Section 2 network). LST_FP32: CUDA cores. LST_BF16:
+ * tensor cores, BF16 operands, FP32 accumulation. LST_BF16X3: tensor cores, each operand
+ * split into BF16 hi + lo parts and hi*hi + lo*hi + hi*lo accumulated in FP32 (about 16
+ * significant bits per operand; for networks whose score is sensitive to small input
+ * differences). Not in the paper, whose network runs in FP32. */
+typedef enum lst_precision { LST_FP32 = 0, LST_BF16 = 1, LST_BF16X3 = 2 } lst_precision;
 
 /* One pT-module (Section 1: two sensors a few mm apart). Sensor ids of module m are
  * 2*m (lower sensor, nearer the interaction point; its hit is the MD anchor, Section 2)
@@ -160,8 +165,8 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
 lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out);
 
 /* Scores precomputed features with the loaded network (Section 2):
- *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores)
- *   or LST_BF16 (tensor cores: BF16 operands, FP32 accumulation). Asynchronous on
+ *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores),
+ *   LST_BF16 or LST_BF16X3 (tensor cores, see lst_precision). Asynchronous on
  *   cuda_stream; a tensor-core wait that ran out is reported by lst_device_errors. */
 lst_status lst_score_t5(lst_ctx ctx, const float *feat, int64_t n, int32_t precision,
                         float *score_out, void *cuda_stream);

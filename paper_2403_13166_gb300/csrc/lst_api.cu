@@ -33,10 +33,10 @@ __global__ void k_score_feat_fp32(const float *, int64_t, const float *, int, fl
 __global__ void k_gather(const EvDesc *, int, int, int32_t *, float *, uint8_t *);
 __global__ void k_collect(const EvDesc *, int, int *);
 cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
-                                     const float *, int, int *, long long);
+                                     const float *, int, int *, long long, bool split);
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
-                                       const float *, int64_t, float *, int *, long long);
-int score_bf16_blocks_per_sm();
+                                       const float *, int64_t, float *, int *, long long, bool split);
+int score_bf16_blocks_per_sm(bool split);
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
 }  // namespace lstk
 
@@ -136,7 +136,7 @@ struct lst_ctx_s {
   uint16_t *d_wpack = nullptr;   // BF16 weights in the tensor-core operand layout
   int *d_err = nullptr;          // device error word (bounded waits of the tensor-core kernel)
   long long wait_limit = 1ll << 26;
-  int grid_bf = 0;
+  int grid_bf[2] = {0, 0};   // tensor-core score grid: plain BF16, split BF16
   std::vector<Slot> slots;
   std::vector<Lane> lanes;     // lane 0: lst_run_event; lanes 1..: batches, round robin
   int next_lane = 1;
@@ -203,7 +203,8 @@ lst_status compute_grids(lst_ctx_s *c) {
   const size_t sw = (size_t)mlp_floats_host(4) * 4;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_fp32, c->sc_threads, sw));
   c->grid_sc = std::max(1, occ) * c->n_sm;
-  c->grid_bf = score_bf16_blocks_per_sm() * c->n_sm;
+  c->grid_bf[0] = score_bf16_blocks_per_sm(false) * c->n_sm;
+  c->grid_bf[1] = score_bf16_blocks_per_sm(true) * c->n_sm;
   return LST_OK;
 }
 
@@ -357,9 +358,9 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   mark(4);
   k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
   mark(5);
-  if (c->cfg.precision == LST_BF16)
-    CU(launch_score_bf16_events(c->grid_bf, st, L.d_desc, n, g, c->cuts, c->d_wpack, c->d_w, c->n_hidden, c->d_err,
-                                c->wait_limit));
+  if (c->cfg.precision != LST_FP32)
+    CU(launch_score_bf16_events(c->grid_bf[c->cfg.precision == LST_BF16X3], st, L.d_desc, n, g, c->cuts, c->d_wpack,
+                                c->d_w, c->n_hidden, c->d_err, c->wait_limit, c->cfg.precision == LST_BF16X3));
   else
     k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
         L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
@@ -463,7 +464,8 @@ lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out) {
   lst_default_config(&d);
   const lst_config &c = cfg ? *cfg : d;
   if (c.max_events < 1 || c.max_events > MAX_EVENTS) return fail(LST_ERR_ARG, "max_events out of range");
-  if (c.precision != LST_FP32 && c.precision != LST_BF16) return fail(LST_ERR_ARG, "bad precision");
+  if (c.precision != LST_FP32 && c.precision != LST_BF16 && c.precision != LST_BF16X3)
+    return fail(LST_ERR_ARG, "bad precision");
   DeviceGuard gd(cuda_device);
   lst_ctx_s *x = new lst_ctx_s();
   x->device = cuda_device;
@@ -536,7 +538,7 @@ lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, c
   CU(cudaMalloc(&c->d_w, 4 * (size_t)c->n_w));
   CU(cudaMemcpy(c->d_w, w.data(), 4 * (size_t)c->n_w, cudaMemcpyHostToDevice));
   {
-    std::vector<uint16_t> pk(32 * 48 + 3 * 32 * 32, 0);
+    std::vector<uint16_t> pk(2 * (32 * 48 + 3 * 32 * 32), 0);   // hi parts, then lo parts
     pack_weights_bf16(w.data(), nh, pk.data());
     cudaFree(c->d_wpack);
     c->d_wpack = nullptr;
@@ -804,16 +806,18 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
                         void *cuda_stream) {
   if (!c) return fail(LST_ERR_ARG, "null ctx");
   if (n < 0) return fail(LST_ERR_ARG, "n < 0");
-  if (precision != LST_FP32 && precision != LST_BF16) return fail(LST_ERR_ARG, "bad precision");
+  if (precision != LST_FP32 && precision != LST_BF16 && precision != LST_BF16X3)
+    return fail(LST_ERR_ARG, "bad precision");
   if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no network loaded");
   if (n == 0) return LST_OK;
   if (!feat || !score_out) return fail(LST_ERR_ARG, "null buffer");
   DeviceGuard gd(c->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  if (precision == LST_BF16) {
-    const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->grid_bf);
+  if (precision != LST_FP32) {
+    const bool split = precision == LST_BF16X3;
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->grid_bf[split]);
     CU(launch_score_bf16_features(grid, st, c->g, c->cuts, c->d_wpack, c->d_w, c->n_hidden, feat, n, score_out,
-                                  c->d_err, c->wait_limit));
+                                  c->d_err, c->wait_limit, split));
   } else {
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->grid_sc);
     k_score_feat_fp32<<<grid, 256, (size_t)c->n_w * 4, st>>>(feat, n, c->d_w, c->n_hidden, score_out);

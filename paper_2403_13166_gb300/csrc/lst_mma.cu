@@ -11,6 +11,14 @@
 // 8 x 16-byte core matrices, LBO = 128 B between K-adjacent core matrices, SBO = (K/8)*128 B
 // between 8-row groups.
 //
+// Split mode (LST_BF16X3): every operand x is stored as two BF16 parts, hi = bf16(x) and
+// lo = bf16(x - hi), which together carry about 16 significant bits; each K-step issues
+// hi*hi + lo*hi + hi*lo into the same FP32 accumulator (the lo*lo term is below FP32
+// rounding of the sum and is dropped). The project-trained networks are ill-conditioned in
+// their log-curvature inputs (score sensitivities up to ~200 per unit), so one BF16
+// rounding of the operands moves their score by up to ~0.8 while the split keeps it near
+// 1e-3. The tensor pipe is far from busy in this kernel, so the 3x MMA count is cheap.
+//
 // Completion of each MMA group is tracked by an mbarrier (tcgen05.commit). Every wait is
 // bounded: when it runs out, the kernel records LST_ERR_TIMEOUT in the error word, skips
 // the rest of its work, frees its TMEM and returns.
@@ -26,6 +34,8 @@ constexpr int TILE_M = 128;
 constexpr int K1 = 48;                 // 38 features padded to a multiple of 16
 constexpr int TMEM_COLS = 32;          // one 128 x 32 FP32 accumulator, reused by every layer
                                        // (16 CTAs per SM x 32 columns fit the 512 columns)
+constexpr int A_BYTES = TILE_M * K1 * 2;                 // one BF16 activation tile
+constexpr int W_ELEMS = 32 * K1 + 3 * 32 * 32;           // W0 + up to 3 hidden-to-hidden layers
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -92,32 +102,41 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// write one row of K values (K a multiple of 8) as BF16 with 16-byte stores
-template <int K>
+// write one row of K values (K a multiple of 8) as BF16 with 16-byte stores; with SPLIT
+// also the remainder x - hi (exact in FP32) rounded to BF16 into the second tile
+template <int K, bool SPLIT>
 __device__ __forceinline__ void store_row_bf16(unsigned char *tile, int row, const float *v) {
 #pragma unroll
   for (int k8 = 0; k8 < K / 8; k8++) {
     __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __nv_bfloat16 lo[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) h[j] = __float2bfloat16_rn(v[k8 * 8 + j]);
+    for (int j = 0; j < 8; j++) {
+      h[j] = __float2bfloat16_rn(v[k8 * 8 + j]);
+      if (SPLIT) lo[j] = __float2bfloat16_rn(v[k8 * 8 + j] - __bfloat162float(h[j]));
+    }
     *reinterpret_cast<uint4 *>(tile + core_off(row, k8 * 8, K)) = *reinterpret_cast<const uint4 *>(h);
+    if (SPLIT)
+      *reinterpret_cast<uint4 *>(tile + A_BYTES + core_off(row, k8 * 8, K)) = *reinterpret_cast<const uint4 *>(lo);
   }
 }
 
 }  // namespace
 
 // wpack: BF16 weights already in the core-matrix layout: W0 [32 x 48], then W1..W_{nh-1}
-// [32 x 32]. wflat: the FP32 flat network (biases, output layer). FROM_EVENTS: features of
-// the T5s of the batch; otherwise rows of feat_in [n][38].
-template <bool FROM_EVENTS>
+// [32 x 32] (W_ELEMS values), followed by the same for the lo parts. wflat: the FP32 flat
+// network (biases, output layer). FROM_EVENTS: features of the T5s of the batch; otherwise
+// rows of feat_in [n][38].
+template <bool FROM_EVENTS, bool SPLIT>
 __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
                                                    lst_cuts c, const uint16_t *__restrict__ wpack,
                                                    const float *__restrict__ wflat, int n_hidden,
                                                    const float *__restrict__ feat_in, int64_t n_rows,
                                                    float *__restrict__ score_out, int *err,
                                                    long long wait_limit) {
-  __shared__ __align__(1024) unsigned char sA[TILE_M * K1 * 2];          // 12 KB
-  __shared__ __align__(1024) unsigned char sW[(32 * K1 + 3 * 32 * 32) * 2];  // 9 KB
+  constexpr int NP = SPLIT ? 2 : 1;
+  __shared__ __align__(1024) unsigned char sA[NP * A_BYTES];      // 12 KB per part
+  __shared__ __align__(1024) unsigned char sW[NP * W_ELEMS * 2];  // 9 KB per part
   __shared__ float sBias[4 * 32], sOut[33];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
@@ -127,8 +146,9 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
 
   // weights -> shared memory
   const int wbytes = (32 * K1 + (n_hidden - 1) * 32 * 32) * 2;
-  for (int i = tid; i < wbytes / 16; i += blockDim.x)
-    reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(wpack)[i];
+  for (int p = 0; p < NP; p++)
+    for (int i = tid; i < wbytes / 16; i += blockDim.x)
+      reinterpret_cast<uint4 *>(sW + p * W_ELEMS * 2)[i] = reinterpret_cast<const uint4 *>(wpack + p * W_ELEMS)[i];
   {
     const float *p = wflat + NHID * NFEAT;            // b0
     if (tid < 32) sBias[tid] = p[tid];
@@ -190,7 +210,7 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
       float v[K1];
 #pragma unroll
       for (int i = 0; i < K1; i++) v[i] = i < NFEAT ? f[i] : 0.0f;
-      store_row_bf16<K1>(sA, tid, v);
+      store_row_bf16<K1, SPLIT>(sA, tid, v);
     }
     float h[32];
     for (int l = 0; l < n_hidden; l++) {
@@ -206,6 +226,12 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
           const uint64_t da = make_desc(aA + k * 256, 128, (K / 8) * 128);
           const uint64_t db = make_desc(aW + wofs + k * 256, 128, (K / 8) * 128);
           mma_bf16(dcol, da, db, idesc, k > 0 ? 1u : 0u);
+          if (SPLIT) {
+            const uint64_t dal = make_desc(aA + A_BYTES + k * 256, 128, (K / 8) * 128);
+            const uint64_t dbl = make_desc(aW + W_ELEMS * 2 + wofs + k * 256, 128, (K / 8) * 128);
+            mma_bf16(dcol, dal, db, idesc, 1u);
+            mma_bf16(dcol, da, dbl, idesc, 1u);
+          }
         }
         mma_commit(mb);
       }
@@ -221,7 +247,7 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
       tmem_ld32(dcol + ((uint32_t)(warp * 32) << 16), acc);
 #pragma unroll
       for (int j = 0; j < 32; j++) h[j] = fmaxf(acc[j] + sBias[32 * l + j], 0.0f);
-      if (l + 1 < n_hidden) store_row_bf16<32>(sA, tid, h);
+      if (l + 1 < n_hidden) store_row_bf16<32, SPLIT>(sA, tid, h);
     }
     if (s_abort) {
       // the accumulator never arrived: void every event of the batch (host reports a timeout)
@@ -257,26 +283,39 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
 // Host-side launchers (kernel template instances stay in this translation unit).
 cudaError_t launch_score_bf16_events(int grid, cudaStream_t st, const EvDesc *evs, int n_events, DevGeom g,
                                      lst_cuts c, const uint16_t *wpack, const float *wflat, int n_hidden, int *err,
-                                     long long wait_limit) {
-  k_score_bf16<true><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr, err,
-                                           wait_limit);
+                                     long long wait_limit, bool split) {
+  if (split)
+    k_score_bf16<true, true><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr,
+                                                   err, wait_limit);
+  else
+    k_score_bf16<true, false><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr,
+                                                    err, wait_limit);
   return cudaGetLastError();
 }
 cudaError_t launch_score_bf16_features(int grid, cudaStream_t st, DevGeom g, lst_cuts c, const uint16_t *wpack,
                                        const float *wflat, int n_hidden, const float *feat, int64_t n, float *out,
-                                       int *err, long long wait_limit) {
-  k_score_bf16<false><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err, wait_limit);
+                                       int *err, long long wait_limit, bool split) {
+  if (split)
+    k_score_bf16<false, true><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err,
+                                                    wait_limit);
+  else
+    k_score_bf16<false, false><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err,
+                                                     wait_limit);
   return cudaGetLastError();
 }
-int score_bf16_blocks_per_sm() {
+// resident CTAs per SM, capped at 16 so that 16 x TMEM_COLS fits the 512 TMEM columns
+int score_bf16_blocks_per_sm(bool split) {
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true>, 128, 0) != cudaSuccess) return 1;
-  return occ > 0 ? occ : 1;
+  const cudaError_t e = split ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true, true>, 128, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true, false>, 128, 0);
+  if (e != cudaSuccess || occ < 1) return 1;
+  return occ < 16 ? occ : 16;
 }
 
 // BF16 weights in the core-matrix layout expected above, built on the host (see the layout
 // comment at the top): element (n, k) of an N=32 x K matrix at byte offset
-// (n/8)*(K/8)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2.
+// (n/8)*(K/8)*128 + (k/8)*128 + (n%8)*16 + (k%8)*2. `out` holds 2 * W_ELEMS values: the hi
+// parts, then the lo parts (weight - hi, rounded to BF16).
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out) {
   auto put = [&](const float *W, int K_in, int K, uint16_t *dst) {
     for (int n = 0; n < 32; n++)
@@ -284,7 +323,9 @@ void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out) {
         const float v = k < K_in ? W[n * K_in + k] : 0.0f;
         const size_t off = (size_t)(n / 8) * (K / 8) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(b));
         dst[off / 2] = *reinterpret_cast<const uint16_t *>(&b);
+        dst[W_ELEMS + off / 2] = *reinterpret_cast<const uint16_t *>(&bl);
       }
   };
   put(wflat, NFEAT, K1, out);

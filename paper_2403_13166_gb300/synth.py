@@ -516,6 +516,17 @@ def default_cuts() -> dict:
     )
 
 
+def open_cuts() -> dict:
+    """Cut parameters with the fit-quality tolerances of steps 3-4 opened up (Section 2: the
+    selections correlated with the quality of the r-phi circle fit are removed when the
+    T5-DNN decides instead). Used to build the DNN's training sample: ~95k T5s per
+    PU200-like event, ~64% of them real."""
+    c = default_cuts()
+    c.update(t3_rz_tol=np.float32(0.2), t5_rz_tol=np.float32(2.0), t5_kappa_rel=np.float32(2.0),
+             t5_kappa_abs=np.float32(0.01))
+    return c
+
+
 CUT_FIELDS = ("kappa_max", "z_lum", "hit_err", "sensor_gap", "t3_kappa_factor", "t3_rz_tol",
               "t5_kappa_rel", "t5_kappa_abs", "t5_rz_tol", "t5_chi2_max", "hit_sigma",
               "k_field", "wp")
