@@ -13,9 +13,13 @@ Parity status per function (pins live in tests/test_oracle_*.py):
       noiseless tracks.
   oracle_mlp          pinned: hand-solvable networks (zero weights, single paths,
       asymmetric weights that detect a transposed operand), sigmoid identities.
+  oracle_t5_chi2      pinned: exact circles of any radius give ~0, one displaced anchor gives the
+      linearised least-squares value (leverage from an FP64 hat matrix), invariance under
+      rotation/translation, and the chi-square law with 2 degrees of freedom on
+      single-particle quintuplets of smeared events.
 """
-from .oracle import (OracleResult, build_oracle, md_cut, ls_cut, t3_cut, t5_cut,
+from .oracle import (OracleResult, build_oracle, md_cut, ls_cut, t3_cut, t5_cut, t5_chi2,
                      t5_features, mlp_forward, run_event)
 
-__all__ = ["OracleResult", "build_oracle", "md_cut", "ls_cut", "t3_cut", "t5_cut",
+__all__ = ["OracleResult", "build_oracle", "md_cut", "ls_cut", "t3_cut", "t5_cut", "t5_chi2",
            "t5_features", "mlp_forward", "run_event"]

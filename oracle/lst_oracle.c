@@ -66,6 +66,7 @@ typedef struct {
     int32_t *t5_t3a, *t5_t3b, *t5_md;      /* t5_md: [n][5] */
     double *t5_feat, *t5_score;            /* [n][38], [n] */
     uint8_t *t5_sel;
+    float *t5_chi2;                        /* [n] circle-fit chi2 of the five anchors */
 } oresult;
 
 /* ------------------------------------------------------------------ growable arrays */
@@ -178,6 +179,63 @@ int oracle_t3_cut(const float *P0, const float *P1, const float *P2, const ocuts
 
 /* ------------------------------------------------------------------ step 4: T5 cuts */
 /* P: the five anchors in chain order; ka/kb the curvatures of T3a=(0,1,2), T3b=(2,3,4). */
+/* Circle-fit quality of the five anchors (x, y of P[4*i]), FP32: the selection the T5-DNN
+ * replaces (Section 2), applied in the pre-DNN mode only.
+ *   Coordinates relative to the middle anchor: u = x - x2, v = y - y2; u and v swap when the
+ *   chord P0 -> P4 is longer in y than in x, so v runs across the chord.
+ *   Algebraic circle fit: gamma (u^2 + v^2) + beta u - v + alpha = 0, least squares in the
+ *   residual v - alpha - beta u - gamma (u^2 + v^2); 3x3 normal equations solved by Cramer's
+ *   rule. A straight track is gamma = 0, so the fit stays regular at any radius and every
+ *   term stays at tracker size (no cancellation of radius-sized numbers in FP32).
+ *   Distance of each anchor to that circle: with nu = sqrt(beta^2 + 1 - 4 gamma alpha) the
+ *   normalised residual p = (gamma w + beta u - v + alpha) / nu and A = gamma / nu give the
+ *   signed distance 2 p / (1 + sqrt(1 + 4 A p)) (exact for a circle, no subtraction of
+ *   radii); chi2 = sum of (distance / sigma)^2.
+ * Every sum runs over the anchors in chain order from zero. A degenerate system gives inf
+ * or NaN, which fails any chi2 cut. */
+static float det3f(float a, float b, float c, float d, float e, float f, float g, float h, float i)
+{
+    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+float oracle_t5_chi2(const float *P, float sigma)
+{
+    float u[5], v[5], w[5];
+    int swap = !(fabsf(P[16] - P[0]) >= fabsf(P[17] - P[1]));
+    for (int i = 0; i < 5; i++) {
+        float dx = P[4 * i] - P[8], dy = P[4 * i + 1] - P[9];
+        u[i] = swap ? dy : dx;
+        v[i] = swap ? dx : dy;
+        w[i] = u[i] * u[i] + v[i] * v[i];
+    }
+    float su = 0.0f, sw = 0.0f, suu = 0.0f, suw = 0.0f, sww = 0.0f, sv = 0.0f, suv = 0.0f, swv = 0.0f;
+    for (int i = 0; i < 5; i++) {
+        su = su + u[i];
+        sw = sw + w[i];
+        suu = suu + u[i] * u[i];
+        suw = suw + u[i] * w[i];
+        sww = sww + w[i] * w[i];
+        sv = sv + v[i];
+        suv = suv + u[i] * v[i];
+        swv = swv + w[i] * v[i];
+    }
+    const float n = 5.0f;
+    float det = det3f(n, su, sw, su, suu, suw, sw, suw, sww);
+    float alpha = det3f(sv, su, sw, suv, suu, suw, swv, suw, sww) / det;
+    float beta = det3f(n, sv, sw, su, suv, suw, sw, swv, sww) / det;
+    float gamma = det3f(n, su, sv, su, suu, suv, sw, suw, swv) / det;
+    float nu = sqrtf(beta * beta + 1.0f - 4.0f * gamma * alpha);
+    float A = gamma / nu;
+    float chi2 = 0.0f;
+    for (int i = 0; i < 5; i++) {
+        float p = (gamma * w[i] + beta * u[i] - v[i] + alpha) / nu;
+        float d = 2.0f * p / (1.0f + sqrtf(1.0f + 4.0f * A * p));
+        float t = d / sigma;
+        chi2 = chi2 + t * t;
+    }
+    return chi2;
+}
+
 int oracle_t5_cut(const float *P, float ka, float kb, const ocuts *c)
 {
     if (!(ka * kb > 0.0f)) return 0;                                      /* T5-q */
@@ -197,6 +255,8 @@ int oracle_t5_cut(const float *P, float ka, float kb, const ocuts *c)
         float zj = P[4 * j + 2];
         if (!(fabsf(zj - (z0 + (z4 - z0) * S[j] / S[4])) <= c->t5_rz_tol)) return 0;  /* T5-rz */
     }
+    if (c->t5_chi2_max > 0.0f && !(oracle_t5_chi2(P, c->hit_sigma) <= c->t5_chi2_max))
+        return 0;                                                          /* pre-DNN chi2 */
     return 1;
 }
 
@@ -466,6 +526,7 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
     out->t5_t3a = malloc(4 * nt5); out->t5_t3b = malloc(4 * nt5); out->t5_md = malloc(20 * nt5);
     out->t5_feat = malloc(sizeof(double) * NFEAT * nt5); out->t5_score = malloc(sizeof(double) * nt5);
     out->t5_sel = malloc(nt5);
+    out->t5_chi2 = malloc(4 * nt5);
     for (int64_t i = 0; i < t5s.n; i++) {
         out->t5_t3a[i] = T5[i].t3a; out->t5_t3b[i] = T5[i].t3b;
         memcpy(out->t5_md + 5 * i, T5[i].md, 20);
@@ -477,6 +538,9 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
             lay[j] = g->layer[d->mod];
             mdk[j] = d->kfeat;
         }
+        float P[20];
+        for (int j = 0; j < 5; j++) fill_md_anchor(&H[MD[T5[i].md[j]].lo], P + 4 * j);
+        out->t5_chi2[i] = oracle_t5_chi2(P, c->hit_sigma);
         double *f = out->t5_feat + (size_t)NFEAT * i;
         oracle_t5_features(anc, lay, mdk, (double)c->k_field, f);
         double s = mlp ? oracle_mlp(mlp, f) : 0.0;
@@ -492,7 +556,7 @@ void oracle_free(oresult *r)
 {
     void *ps[] = {r->md_lo, r->md_up, r->md_mod, r->md_kappa, r->ls_in, r->ls_out, r->ls_kappa,
                   r->t3_ls1, r->t3_ls2, r->t3_md, r->t3_kappa, r->t5_t3a, r->t5_t3b, r->t5_md,
-                  r->t5_feat, r->t5_score, r->t5_sel};
+                  r->t5_feat, r->t5_score, r->t5_sel, r->t5_chi2};
     for (size_t i = 0; i < sizeof ps / sizeof ps[0]; i++) free(ps[i]);
     memset(r, 0, sizeof *r);
 }

@@ -44,7 +44,8 @@ class _Result(C.Structure):
                 ("t3_ls1", C.c_void_p), ("t3_ls2", C.c_void_p), ("t3_md", C.c_void_p),
                 ("t3_kappa", C.c_void_p),
                 ("t5_t3a", C.c_void_p), ("t5_t3b", C.c_void_p), ("t5_md", C.c_void_p),
-                ("t5_feat", C.c_void_p), ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p)]
+                ("t5_feat", C.c_void_p), ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p),
+                ("t5_chi2", C.c_void_p)]
 
 
 def build_oracle(force: bool = False) -> str:
@@ -75,6 +76,8 @@ def _load():
             lib.oracle_t3_cut.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Cuts),
                                           C.POINTER(C.c_float)]
             lib.oracle_t5_cut.argtypes = [C.c_void_p, C.c_float, C.c_float, C.POINTER(_Cuts)]
+            lib.oracle_t5_chi2.restype = C.c_float
+            lib.oracle_t5_chi2.argtypes = [C.c_void_p, C.c_float]
             lib.oracle_t5_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                                C.c_void_p]
             lib.oracle_mlp.restype = C.c_double
@@ -126,6 +129,13 @@ def t5_cut(P, ka, kb, cuts):
     return bool(lib.oracle_t5_cut(P.ctypes.data, float(ka), float(kb), C.byref(_cuts(cuts))))
 
 
+def t5_chi2(P, sigma):
+    """Circle-fit chi2 of five anchors P[5][4] = (x, y, z, r) float32 (pre-DNN selection)."""
+    lib = _load()
+    P = _f32(np.asarray(P).ravel(), 20)
+    return np.float32(lib.oracle_t5_chi2(P.ctypes.data, float(np.float32(sigma))))
+
+
 def t5_features(anchors, layers, md_kappa, k_field):
     lib = _load()
     a = np.ascontiguousarray(np.asarray(anchors, np.float64).reshape(15))
@@ -169,6 +179,7 @@ class OracleResult:
     t5_feat: np.ndarray
     t5_score: np.ndarray
     t5_sel: np.ndarray
+    t5_chi2: np.ndarray
 
     @property
     def counts(self):
@@ -235,7 +246,8 @@ def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -
             t5_md=_arr(res.t5_md, n4, np.int32, (5,)), t5_t3a=_arr(res.t5_t3a, n4, np.int32),
             t5_t3b=_arr(res.t5_t3b, n4, np.int32),
             t5_feat=_arr(res.t5_feat, n4, np.float64, (NFEAT,)),
-            t5_score=_arr(res.t5_score, n4, np.float64), t5_sel=_arr(res.t5_sel, n4, np.uint8))
+            t5_score=_arr(res.t5_score, n4, np.float64), t5_sel=_arr(res.t5_sel, n4, np.uint8),
+            t5_chi2=_arr(res.t5_chi2, n4, np.float32))
     finally:
         lib.oracle_free(C.byref(res))
     del keep

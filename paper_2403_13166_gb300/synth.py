@@ -509,7 +509,7 @@ def default_cuts() -> dict:
         t5_kappa_rel=np.float32(0.3),
         t5_kappa_abs=np.float32(0.001),
         t5_rz_tol=np.float32(0.03),
-        t5_chi2_max=np.float32(20.0),
+        t5_chi2_max=np.float32(0.0),       # DNN mode: no circle-fit selection
         hit_sigma=np.float32(HIT_SIGMA),
         k_field=np.float32(K_FIELD),
         wp=np.float32(0.5),
@@ -524,6 +524,14 @@ def open_cuts() -> dict:
     c = default_cuts()
     c.update(t3_rz_tol=np.float32(0.2), t5_rz_tol=np.float32(2.0), t5_kappa_rel=np.float32(2.0),
              t5_kappa_abs=np.float32(0.01))
+    return c
+
+
+def pre_dnn_cuts(chi2_max: float = 20.0) -> dict:
+    """The pre-DNN mode (Section 2): the open-cut quintuplets that also pass a circle-fit
+    chi2 selection (five anchors, sigma = hit_sigma), instead of the T5-DNN score."""
+    c = open_cuts()
+    c["t5_chi2_max"] = np.float32(chi2_max)
     return c
 
 
