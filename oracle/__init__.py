@@ -17,9 +17,12 @@ Parity status per function (pins live in tests/test_oracle_*.py):
       linearised least-squares value (leverage from an FP64 hat matrix), invariance under
       rotation/translation, and the chi-square law with 2 degrees of freedom on
       single-particle quintuplets of smeared events.
+  oracle_tc_select    pinned: hand-built T5 sets (3 shared MDs vs 2, one-pass semantics on
+      a chain of three, ties, NaN chi2, unselected T5s), index == brute force, the kept set
+      holds no duplicates, one track candidate per isolated muon.
 """
 from .oracle import (OracleResult, build_oracle, md_cut, ls_cut, t3_cut, t5_cut, t5_chi2,
-                     t5_features, mlp_forward, run_event)
+                     tc_select, t5_features, mlp_forward, run_event)
 
 __all__ = ["OracleResult", "build_oracle", "md_cut", "ls_cut", "t3_cut", "t5_cut", "t5_chi2",
-           "t5_features", "mlp_forward", "run_event"]
+           "tc_select", "t5_features", "mlp_forward", "run_event"]

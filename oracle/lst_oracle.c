@@ -30,6 +30,7 @@
  * the module indexing (all hit pairs of a module's two sensors from the raw hit list,
  * all MD pairs in layer-adjacent modules, all LS/T3 pairs tested for the shared MD).
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -67,6 +68,7 @@ typedef struct {
     double *t5_feat, *t5_score;            /* [n][38], [n] */
     uint8_t *t5_sel;
     float *t5_chi2;                        /* [n] circle-fit chi2 of the five anchors */
+    uint8_t *t5_tc;                        /* [n] 1: the T5 is a track candidate */
 } oresult;
 
 /* ------------------------------------------------------------------ growable arrays */
@@ -347,6 +349,81 @@ double oracle_mlp(const omlp *m, const double *f)
     return 1.0 / (1.0 + exp(-s));
 }
 
+/* ------------------------------------------------------------------ track candidates */
+/* Table 1 step 6 without pixel seeds (none exist here): the selected T5s, cleaned of
+ * duplicates (Section 2 places duplicate removal downstream of the T5 step). Project
+ * definition:
+ *   two T5s are duplicates when they share at least 3 of their 5 MDs;
+ *   T5 u ranks above T5 t when q_u < q_t, or q_u == q_t and key_u < key_t (lexicographic),
+ *   where q is the circle-fit chi2 (NaN and +inf both count as +inf) and key is the 10
+ *   original hit indices (lower and upper hit of each MD, in chain order);
+ *   a selected T5 is a track candidate iff no selected duplicate ranks above it. This is
+ *   one pass: a T5 that a better duplicate removes still removes the T5s it ranks above.
+ * md [n][5] MD ids below n_md, key [n][10], q [n], sel [n] -> tc [n] (0/1). brute: test
+ * every pair of selected T5s instead of the T5s listed under one of the T5's MDs. */
+#define TC_MIN_SHARED 3
+
+static int shared_mds(const int32_t *a, const int32_t *b)
+{
+    int s = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) s += a[i] == b[j];
+    return s;
+}
+
+static int ranks_above(int64_t u, int64_t t, const int32_t *key, const float *q)
+{
+    float qu = q[u] <= FLT_MAX ? q[u] : INFINITY, qt = q[t] <= FLT_MAX ? q[t] : INFINITY;
+    if (qu < qt) return 1;
+    if (qu > qt) return 0;
+    for (int k = 0; k < 10; k++)
+        if (key[10 * u + k] != key[10 * t + k]) return key[10 * u + k] < key[10 * t + k];
+    return 0;
+}
+
+void oracle_tc_select(int64_t n, const int32_t *md, const int32_t *key, const float *q,
+                      const uint8_t *sel, int64_t n_md, int brute, uint8_t *tc)
+{
+    int64_t *off = NULL, *list = NULL;
+    if (!brute) {                     /* selected T5s listed under each of their MDs */
+        off = calloc((size_t)n_md + 1, sizeof(int64_t));
+        for (int64_t t = 0; t < n; t++)
+            if (sel[t])
+                for (int j = 0; j < 5; j++) off[md[5 * t + j] + 1]++;
+        for (int64_t m = 0; m < n_md; m++) off[m + 1] += off[m];
+        list = malloc(sizeof(int64_t) * (size_t)(off[n_md] ? off[n_md] : 1));
+        int64_t *cur = malloc(sizeof(int64_t) * (size_t)(n_md ? n_md : 1));
+        memcpy(cur, off, sizeof(int64_t) * (size_t)n_md);
+        for (int64_t t = 0; t < n; t++)
+            if (sel[t])
+                for (int j = 0; j < 5; j++) list[cur[md[5 * t + j]]++] = t;
+        free(cur);
+    }
+    for (int64_t t = 0; t < n; t++) {
+        tc[t] = 0;
+        if (!sel[t]) continue;
+        int keep = 1;
+        if (brute) {
+            for (int64_t u = 0; u < n && keep; u++)
+                if (u != t && sel[u] && shared_mds(md + 5 * t, md + 5 * u) >= TC_MIN_SHARED &&
+                    ranks_above(u, t, key, q))
+                    keep = 0;
+        } else {
+            for (int j = 0; j < 5 && keep; j++) {
+                int32_t m = md[5 * t + j];
+                for (int64_t k = off[m]; k < off[m + 1] && keep; k++) {
+                    int64_t u = list[k];
+                    if (u != t && shared_mds(md + 5 * t, md + 5 * u) >= TC_MIN_SHARED && ranks_above(u, t, key, q))
+                        keep = 0;
+                }
+            }
+        }
+        tc[t] = (uint8_t)keep;
+    }
+    free(off);
+    free(list);
+}
+
 /* ------------------------------------------------------------------ event driver */
 static int layer_adjacent(int la, int sa, int lb, int sb)
 {
@@ -545,7 +622,21 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
         oracle_t5_features(anc, lay, mdk, (double)c->k_field, f);
         double s = mlp ? oracle_mlp(mlp, f) : 0.0;
         out->t5_score[i] = s;
-        out->t5_sel[i] = s >= (double)c->wp;
+        /* pre-DNN mode: the chi2 cut already selected the T5; DNN mode: the working point */
+        out->t5_sel[i] = c->t5_chi2_max > 0.0f ? 1 : s >= (double)c->wp;
+    }
+
+    /* ---- track candidates from the selected T5s ---- */
+    out->t5_tc = malloc(nt5);
+    {
+        int32_t *key = malloc(40 * nt5);
+        for (int64_t i = 0; i < t5s.n; i++)
+            for (int j = 0; j < 5; j++) {
+                key[10 * i + 2 * j] = MD[T5[i].md[j]].lo;
+                key[10 * i + 2 * j + 1] = MD[T5[i].md[j]].up;
+            }
+        oracle_tc_select(t5s.n, out->t5_md, key, out->t5_chi2, out->t5_sel, mds.n, brute, out->t5_tc);
+        free(key);
     }
     free(H); free(soff); free(sidx); free(mdoff); free(lsoff); free(t3off);
     free(mds.p); free(lss.p); free(t3s.p); free(t5s.p);
@@ -556,7 +647,7 @@ void oracle_free(oresult *r)
 {
     void *ps[] = {r->md_lo, r->md_up, r->md_mod, r->md_kappa, r->ls_in, r->ls_out, r->ls_kappa,
                   r->t3_ls1, r->t3_ls2, r->t3_md, r->t3_kappa, r->t5_t3a, r->t5_t3b, r->t5_md,
-                  r->t5_feat, r->t5_score, r->t5_sel, r->t5_chi2};
+                  r->t5_feat, r->t5_score, r->t5_sel, r->t5_chi2, r->t5_tc};
     for (size_t i = 0; i < sizeof ps / sizeof ps[0]; i++) free(ps[i]);
     memset(r, 0, sizeof *r);
 }

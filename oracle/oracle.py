@@ -45,7 +45,7 @@ class _Result(C.Structure):
                 ("t3_kappa", C.c_void_p),
                 ("t5_t3a", C.c_void_p), ("t5_t3b", C.c_void_p), ("t5_md", C.c_void_p),
                 ("t5_feat", C.c_void_p), ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p),
-                ("t5_chi2", C.c_void_p)]
+                ("t5_chi2", C.c_void_p), ("t5_tc", C.c_void_p)]
 
 
 def build_oracle(force: bool = False) -> str:
@@ -76,6 +76,8 @@ def _load():
             lib.oracle_t3_cut.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Cuts),
                                           C.POINTER(C.c_float)]
             lib.oracle_t5_cut.argtypes = [C.c_void_p, C.c_float, C.c_float, C.POINTER(_Cuts)]
+            lib.oracle_tc_select.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_int64, C.c_int, C.c_void_p]
             lib.oracle_t5_chi2.restype = C.c_float
             lib.oracle_t5_chi2.argtypes = [C.c_void_p, C.c_float]
             lib.oracle_t5_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
@@ -136,6 +138,21 @@ def t5_chi2(P, sigma):
     return np.float32(lib.oracle_t5_chi2(P.ctypes.data, float(np.float32(sigma))))
 
 
+def tc_select(md, key, q, sel, n_md, brute=False):
+    """Track-candidate flags of T5s given their MD ids [n][5], hit keys [n][10], circle-fit
+    chi2 [n] (float32) and selection flags [n] (duplicate removal by shared MDs)."""
+    lib = _load()
+    md = np.ascontiguousarray(md, np.int32).reshape(-1, 5)
+    n = md.shape[0]
+    key = np.ascontiguousarray(key, np.int32).reshape(n, 10)
+    q = np.ascontiguousarray(q, np.float32).reshape(n)
+    sel = np.ascontiguousarray(sel, np.uint8).reshape(n)
+    tc = np.zeros(max(n, 1), np.uint8)
+    lib.oracle_tc_select(n, md.ctypes.data, key.ctypes.data, q.ctypes.data, sel.ctypes.data, int(n_md),
+                         int(brute), tc.ctypes.data)
+    return tc[:n]
+
+
 def t5_features(anchors, layers, md_kappa, k_field):
     lib = _load()
     a = np.ascontiguousarray(np.asarray(anchors, np.float64).reshape(15))
@@ -180,6 +197,7 @@ class OracleResult:
     t5_score: np.ndarray
     t5_sel: np.ndarray
     t5_chi2: np.ndarray
+    t5_tc: np.ndarray
 
     @property
     def counts(self):
@@ -198,7 +216,12 @@ class OracleResult:
 
     def t5_hits(self):
         mh = self.md_hits()
+        if len(self.t5_md) == 0:
+            return np.zeros((0, 10), np.int32)
         return np.concatenate([mh[self.t5_md[:, i]] for i in range(5)], 1)
+
+    def tc_hits(self):
+        return self.t5_hits()[self.t5_tc.astype(bool)]
 
 
 def _arr(ptr, n, dtype, shape=None):
@@ -247,7 +270,7 @@ def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -
             t5_t3b=_arr(res.t5_t3b, n4, np.int32),
             t5_feat=_arr(res.t5_feat, n4, np.float64, (NFEAT,)),
             t5_score=_arr(res.t5_score, n4, np.float64), t5_sel=_arr(res.t5_sel, n4, np.uint8),
-            t5_chi2=_arr(res.t5_chi2, n4, np.float32))
+            t5_chi2=_arr(res.t5_chi2, n4, np.float32), t5_tc=_arr(res.t5_tc, n4, np.uint8))
     finally:
         lib.oracle_free(C.byref(res))
     del keep
