@@ -68,6 +68,10 @@ def _oracle_time(args):
     return dt, r.counts["t5"]
 
 
+# kernels of one launch sequence: reset, 3 grouping, 3 MD, LS, 3 T3, T5, score, 4 track
+# candidate, counter collection
+KERNELS_PER_LAUNCH = 18
+
 # score arithmetic of the batched and served forms (the plain form is always FP32)
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
@@ -287,7 +291,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         pms = p0.elapsed_time(p1)
         plain = {"value": round(n_plain / (pms / 1000.0), 2), "unit": "events/s",
                  "ms_per_event": round(pms / n_plain, 4), "events": n_plain, "score_precision": "fp32",
-                 "gpu_launches_per_event": 14, "form": "one launch sequence per event, no graph"}
+                 "gpu_launches_per_event": KERNELS_PER_LAUNCH, "form": "one launch sequence per event, no graph"}
 
     # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
@@ -325,7 +329,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     c0 = counts[0] if counts else {}
     mean_counts = {k: float(np.mean([c[k] for c in counts])) for k in ("md", "ls", "t3", "t5")}
     pairs = np.mean(np.array([c["pairs"] for c in counts], np.float64), axis=0)
-    names = ["bin", "md", "ls", "t3", "t5", "score"]
+    names = list(lst.STAGES)
     dom = int(np.argmax(stage_ms))
     roofline = roofline_entry(names[dom], float(stage_ms[dom]), B, mean_counts, pairs, float(np.mean(n_hits)),
                               clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
@@ -348,7 +352,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         "e2e": e2e,
         "roofline": roofline,
         "clocks": clk.summary(),
-        "gpu_launches": 14 * args.steps,
+        "gpu_launches": KERNELS_PER_LAUNCH * args.steps,
     }
     ctx.close()
     ctx_p.close()

@@ -42,7 +42,14 @@ typedef enum lst_status {
     LST_ERR_NOMEM = 7       /* device allocation failed */
 } lst_status;
 
-typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3 } lst_kind;
+/* Object kinds (Table 1): steps 1-4, and the track candidates of step 6 (T5s not matched
+ * to a pixel seed; no pixel seeds exist here), i.e. the selected T5s after duplicate
+ * removal (see lst_get_candidates). */
+typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3, LST_TC = 4 } lst_kind;
+
+/* Timed stages of one launch (lst_stage_times): hit grouping, steps 1-4, score, track
+ * candidates. */
+#define LST_N_STAGES 7
 /* Arithmetic of the T5-DNN score (Section 2 network). LST_FP32: CUDA cores. LST_BF16:
  * tensor cores, BF16 operands, FP32 accumulation. LST_BF16X3: tensor cores, each operand
  * split into BF16 hi + lo parts and hi*hi + lo*hi + hi*lo accumulated in FP32 (about 16
@@ -72,7 +79,9 @@ typedef struct lst_cuts {
     float t5_kappa_rel;     /* T5 curvature agreement, relative part */
     float t5_kappa_abs;     /* T5 curvature agreement, absolute part */
     float t5_rz_tol;        /* T5 z residual of the inner anchors */
-    float t5_chi2_max;      /* reserved: circle-fit selection of the pre-DNN mode */
+    float t5_chi2_max;      /* > 0: pre-DNN mode, T5s also need the chi2 of an algebraic
+                               circle fit to their five anchors (sigma = hit_sigma) <= this;
+                               <= 0: DNN mode, no fit selection (Section 2) */
     float hit_sigma;        /* single-hit resolution */
     float k_field;          /* pT [GeV] = k_field * R [cm] */
     float wp;               /* T5-DNN working point: selected iff score >= wp */
@@ -105,6 +114,7 @@ typedef struct lst_counts {
     int64_t pairs[4];           /* candidate pairs tested by steps 1-4 (MD, LS, T3, T5) */
     int32_t status;             /* lst_status of the event */
     int32_t overflow_mask;      /* bit k set: buffer of kind k overflowed */
+    int64_t n_tc;               /* track candidates (selected T5s after duplicate removal) */
 } lst_counts;
 
 /* Fills `cfg` with defaults (FP32 score, 1 slot, graphs on, ratios sized for PU200). */
@@ -150,10 +160,15 @@ lst_status lst_run_batch(lst_ctx ctx, int32_t n_events, const float *const *x,
 lst_status lst_event_counts(lst_event ev, lst_counts *out);
 
 /* Copies the objects of one kind as hit-index tuples:
- *   hit_idx   [n][2|4|6|10] int32 (MD: lower,upper; LS: 2 MDs; T3: 3 MDs; T5: 5 MDs, each
- *             MD as lower,upper), chain order, original hit indices;
- *   score     [n] float T5-DNN score (T5 only, may be NULL);
- *   selected  [n] uint8 score >= wp (T5 only, may be NULL).
+ *   hit_idx   [n][2|4|6|10] int32 (MD: lower,upper; LS: 2 MDs; T3: 3 MDs; T5 and TC: 5
+ *             MDs, each MD as lower,upper), chain order, original hit indices;
+ *   score     [n] float T5-DNN score (T5 and TC only, may be NULL);
+ *   selected  [n] uint8 (T5 and TC only, may be NULL): DNN mode score >= wp; pre-DNN mode
+ *             (cuts.t5_chi2_max > 0) 1 for every T5, the chi2 cut having selected them.
+ * Track candidates (LST_TC): the selected T5s without duplicates. Two selected T5s are
+ * duplicates when they share >= 3 of their 5 MDs; the one with the smaller circle-fit chi2
+ * (NaN as +inf), then the lexicographically smaller hit tuple, ranks above; a selected
+ * T5 is a track candidate iff no selected duplicate ranks above it (one pass).
  * Buffers may be HOST or DEVICE memory (detected). *n_out is always set; if
  * capacity < n the call copies nothing and returns LST_ERR_CAPACITY. Objects come in the
  * library's order; compare as sets. */
@@ -209,11 +224,11 @@ lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);
 
 /* Per-stage device timing. lst_set_timing(ctx, 1) resets the statistics and makes every
  * later launch (lst_run_event and lst_run_batch, graph launches included) record CUDA
- * events at the stage boundaries on the launch stream. lst_stage_times returns the mean
- * device time per launch of each stage in ms (0 bin, 1 md, 2 ls, 3 t3, 4 t5, 5 score) and
- * the number of launches averaged. */
+ * events at the stage boundaries on the launch stream. lst_stage_times fills ms[LST_N_STAGES]
+ * with the mean device time per launch of each stage in ms (0 bin, 1 md, 2 ls, 3 t3, 4 t5,
+ * 5 score, 6 track candidates) and returns the number of launches averaged. */
 lst_status lst_set_timing(lst_ctx ctx, int32_t enable);
-lst_status lst_stage_times(lst_ctx ctx, float *ms6, int64_t *n_launches);
+lst_status lst_stage_times(lst_ctx ctx, float *ms, int64_t *n_launches);
 
 /* ---------------------------------------------------------------------------------
  * Serving: continuous batching of events that arrive one by one (Section 3 runs events

@@ -32,6 +32,11 @@ __global__ void k_features(const EvDesc *, DevGeom, float, float *, int);
 __global__ void k_score_feat_fp32(const float *, int64_t, const float *, int, float *);
 __global__ void k_gather(const EvDesc *, int, int, int32_t *, float *, uint8_t *);
 __global__ void k_collect(const EvDesc *, int, int *);
+__global__ void k_tc_count(const EvDesc *, int);
+__global__ void k_tc_scan(const EvDesc *);
+__global__ void k_tc_scatter(const EvDesc *, int);
+__global__ void k_tc_decide(const EvDesc *, int);
+__global__ void k_gather_tc(const EvDesc *, int, int *, int32_t *, float *, uint8_t *);
 cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
                                      const float *, int, int *, long long, bool split);
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
@@ -113,7 +118,7 @@ struct Lane {
   uint64_t gen = 0;
   bool inflight = false;
   cudaEvent_t done = nullptr;
-  cudaEvent_t tev[7] = {};         // stage boundaries of the last launch (when timed)
+  cudaEvent_t tev[LST_N_STAGES + 1] = {};  // stage boundaries of the last launch (when timed)
   bool timed = false;
   cudaStream_t cap_stream = nullptr;
   std::map<long long, cudaGraphExec_t> graphs;
@@ -150,7 +155,7 @@ struct lst_ctx_s {
   int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
   // per-stage device times accumulated over timed launches
   bool timing = false;
-  double stage_sum[6] = {0};
+  double stage_sum[LST_N_STAGES] = {0};
   int64_t stage_n = 0;
   cudaStream_t aux = nullptr;
   void *scratch = nullptr;
@@ -241,6 +246,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
                o_t3c = take(4 * (size_t)md), o_t3u = take(16 * (size_t)t3), o_t3uk = take(4 * (size_t)t3);
   const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
                o_t5e = take((size_t)t5);
+  const size_t o_tcc = take(4 * (size_t)md), o_tcp = take(4 * (size_t)md), o_tcl = take(20 * (size_t)t5),
+               o_tcf = take((size_t)t5);
   const size_t o_cnt = take(4 * C_NCOUNTERS);
   if (s.mem) {
     CU(cudaDeviceSynchronize());
@@ -263,6 +270,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   d.t3_cnt = (int32_t *)(b + o_t3c); d.t3u_md = (int4 *)(b + o_t3u); d.t3u_kappa = (float *)(b + o_t3uk);
   d.t5_a = (int4 *)(b + o_t5a); d.t5_b = (int4 *)(b + o_t5b); d.t5_score = (float *)(b + o_t5s);
   d.t5_sel = (uint8_t *)(b + o_t5e); d.cnt = (int32_t *)(b + o_cnt);
+  d.tc_cnt = (int32_t *)(b + o_tcc); d.tc_pos = (int32_t *)(b + o_tcp); d.tc_list = (int32_t *)(b + o_tcl);
+  d.t5_tc = (uint8_t *)(b + o_tcf);
   s.hit_cap = H; s.md_cap = md; s.ls_cap = ls; s.t3_cap = t3; s.t5_cap = t5;
   d.md_cap = md; d.ls_cap = ls; d.t3_cap = t3; d.t5_cap = t5;
   return LST_OK;
@@ -320,7 +329,7 @@ lst_status lane_harvest(lst_ctx_s *c, Lane &L) {
     }
   }
   if (L.timed) {
-    for (int k = 0; k < 6; k++) {
+    for (int k = 0; k < LST_N_STAGES; k++) {
       float ms = 0.0f;
       CU(cudaEventElapsedTime(&ms, L.tev[k], L.tev[k + 1]));
       c->stage_sum[k] += ms;
@@ -365,6 +374,11 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
     k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
         L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
   mark(6);
+  k_tc_count<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_tc_scan<<<n, 1024, 0, st>>>(L.d_desc);
+  k_tc_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_tc_decide<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  mark(7);
   k_collect<<<(n + 127) / 128, 128, 0, st>>>(L.d_desc, n, L.d_counts);
   CU(cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int) * C_NCOUNTERS * n, cudaMemcpyDeviceToHost, st));
   CU(cudaGetLastError());
@@ -421,6 +435,33 @@ __global__ void k_collect(const EvDesc *__restrict__ evs, int n, int *out) {
     for (int k = 0; k < C_NCOUNTERS; k++) out[e * C_NCOUNTERS + k] = evs[e].cnt[k];
 }
 }  // namespace lstk
+
+namespace {
+// Track candidates of one event into caller buffers (device or host), any order.
+lst_status gather_tc(lst_ctx_s *c, const EvDesc *dd, int n_t5, int64_t n, int32_t *hit_idx, float *score,
+                     uint8_t *selected) {
+  const bool dev_out = is_device_ptr(hit_idx);
+  const size_t bytes = 256 + (dev_out ? 0 : (size_t)n * 40 + (size_t)n * 4 + (size_t)n);
+  void *tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, bytes, c->aux));
+  int *d_counter = (int *)tmp;
+  int32_t *d_idx = dev_out ? hit_idx : (int32_t *)((char *)tmp + 256);
+  float *d_sc = dev_out ? score : (float *)(d_idx + (size_t)n * 10);
+  uint8_t *d_sel = dev_out ? selected : (uint8_t *)(d_sc + n);
+  CU(cudaMemsetAsync(d_counter, 0, sizeof(int), c->aux));
+  const int grid = (int)std::min<int64_t>((n_t5 + 255) / 256, 4 * c->n_sm);
+  if (grid > 0) k_gather_tc<<<grid, 256, 0, c->aux>>>(dd, n_t5, d_counter, d_idx, d_sc, d_sel);
+  CU(cudaGetLastError());
+  if (!dev_out) {
+    CU(cudaMemcpyAsync(hit_idx, d_idx, (size_t)n * 40, cudaMemcpyDeviceToHost, c->aux));
+    if (score) CU(cudaMemcpyAsync(score, d_sc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->aux));
+    if (selected) CU(cudaMemcpyAsync(selected, d_sel, (size_t)n, cudaMemcpyDeviceToHost, c->aux));
+  }
+  CU(cudaFreeAsync(tmp, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+}  // namespace
 
 // =========================================================================== C-ABI
 extern "C" {
@@ -694,6 +735,7 @@ lst_status lst_event_counts(lst_event ev, lst_counts *out) {
   out->n_t3 = S.cnt[C_T3];
   out->n_t5 = S.cnt[C_T5];
   out->n_selected = S.cnt[C_NSEL];
+  out->n_tc = S.cnt[C_NTC];
   out->pairs[0] = (uint32_t)S.cnt[C_PMD];
   out->pairs[1] = (uint32_t)S.cnt[C_PLS];
   out->pairs[2] = (uint32_t)S.cnt[C_PT3];
@@ -728,13 +770,13 @@ static lst_status slot_desc_device(lst_ctx c, int si, EvDesc **dptr) {
 lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score, uint8_t *selected,
                               int64_t capacity, int64_t *n_out) {
   if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
-  if (kind < LST_MD || kind > LST_T5) return fail(LST_ERR_ARG, "bad kind");
+  if (kind < LST_MD || kind > LST_TC) return fail(LST_ERR_ARG, "bad kind");
   lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
   lst_status s = wait_event(ev);
   if (s != LST_OK) return s;
   const Slot &S = c->slots[ev->slot];
-  const int cs[4] = {C_MD, C_LS, C_T3, C_T5};
+  const int cs[5] = {C_MD, C_LS, C_T3, C_T5, C_NTC};
   const int64_t n = S.cnt[cs[kind]];
   *n_out = n;
   if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
@@ -745,6 +787,7 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
   EvDesc *dd;
   s = slot_desc_device(c, ev->slot, &dd);
   if (s != LST_OK) return s;
+  if (kind == LST_TC) return gather_tc(c, dd, (int)S.cnt[C_T5], n, hit_idx, score, selected);
   const bool dev_out = is_device_ptr(hit_idx);
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * c->n_sm);
   if (dev_out) {
@@ -925,9 +968,9 @@ lst_status lst_set_timing(lst_ctx c, int32_t enable) {
   return LST_OK;
 }
 
-lst_status lst_stage_times(lst_ctx c, float *ms6, int64_t *n_launches) {
-  if (!c || !ms6) return fail(LST_ERR_ARG, "null argument");
-  for (int k = 0; k < 6; k++) ms6[k] = c->stage_n ? (float)(c->stage_sum[k] / c->stage_n) : 0.0f;
+lst_status lst_stage_times(lst_ctx c, float *ms, int64_t *n_launches) {
+  if (!c || !ms) return fail(LST_ERR_ARG, "null argument");
+  for (int k = 0; k < LST_N_STAGES; k++) ms[k] = c->stage_n ? (float)(c->stage_sum[k] / c->stage_n) : 0.0f;
   if (n_launches) *n_launches = c->stage_n;
   return LST_OK;
 }
@@ -1018,7 +1061,7 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   res.counts.n_hits = r.n;
   if (cnt) {
     res.counts.n_md = cnt[C_MD]; res.counts.n_ls = cnt[C_LS]; res.counts.n_t3 = cnt[C_T3];
-    res.counts.n_t5 = cnt[C_T5]; res.counts.n_selected = cnt[C_NSEL];
+    res.counts.n_t5 = cnt[C_T5]; res.counts.n_selected = cnt[C_NSEL]; res.counts.n_tc = cnt[C_NTC];
     res.counts.pairs[0] = (uint32_t)cnt[C_PMD]; res.counts.pairs[1] = (uint32_t)cnt[C_PLS];
     res.counts.pairs[2] = (uint32_t)cnt[C_PT3]; res.counts.pairs[3] = (uint32_t)cnt[C_PT5];
   }

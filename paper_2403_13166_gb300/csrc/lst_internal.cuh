@@ -21,7 +21,8 @@ enum CounterSlot {
   C_MD = 0, C_LS = 1, C_T3 = 2, C_T5 = 3, C_FLAGS = 4, C_NSEL = 5,
   C_PMD = 6, C_PLS = 7, C_PT3 = 8, C_PT5 = 9,   // candidate pairs tested per step
   C_DBG_SITE = 10, C_DBG_VAL = 11,              // first failed bounds check (LST_CHECK builds)
-  C_NCOUNTERS = 12
+  C_NTC = 12,                                   // track candidates
+  C_NCOUNTERS = 13
 };
 enum Flags { F_INPUT = 1, F_OVF_MD = 2, F_OVF_LS = 4, F_OVF_T3 = 8, F_OVF_T5 = 16, F_CHECK = 32, F_TIMEOUT = 64 };
 
@@ -67,9 +68,12 @@ struct EvDesc {
   int32_t *t3_pos, *t3_cnt;    // [md_cap] per first MD: start of its range (end after the
                                // grouping scatter) and count
   int4 *t5_a;                  // [t5_cap] (md0, md1, md2, md3)
-  int4 *t5_b;                  // [t5_cap] (md4, t3a, t3b, -)
+  int4 *t5_b;                  // [t5_cap] (md4, t3a, t3b, bits of the circle-fit chi2)
   float *t5_score;             // [t5_cap]
   uint8_t *t5_sel;             // [t5_cap]
+  int32_t *tc_cnt, *tc_pos;    // [md_cap] selected T5s per MD, then the end of each MD's range
+  int32_t *tc_list;            // [5 t5_cap] selected T5s grouped by MD
+  uint8_t *t5_tc;              // [t5_cap] 1: the T5 is a track candidate
   int32_t *cnt;                // [C_NCOUNTERS]
 };
 
@@ -191,6 +195,60 @@ __device__ __forceinline__ bool t3_prefilter(const float4 P0, const float4 P1, c
 }
 
 // Step 4: five anchors in chain order; ka, kb the curvatures of T3a = (0,1,2), T3b = (2,3,4).
+// Circle-fit quality of the five anchors, FP32 (the selection the T5-DNN replaces, Section 2;
+// pre-DNN mode only). Coordinates relative to the middle anchor, u and v swapped when the
+// chord P0 -> P4 is longer in y than in x. Algebraic circle fit gamma (u^2 + v^2) + beta u -
+// v + alpha = 0, least squares in v - alpha - beta u - gamma (u^2 + v^2), normal equations by
+// Cramer's rule: regular for straight tracks (gamma = 0) and free of radius-sized
+// intermediates. Distance of an anchor to the circle: p = (gamma w + beta u - v + alpha) / nu,
+// nu = sqrt(beta^2 + 1 - 4 gamma alpha), A = gamma / nu, distance = 2 p / (1 + sqrt(1 + 4 A
+// p)); chi2 = sum of (distance / sigma)^2. Sums in chain order from zero, written as
+// left-to-right expressions; no contraction (-fmad=false), so every IEEE evaluation of this
+// tree gives the same bits. A degenerate system yields inf or NaN, which fails the cut.
+__device__ __forceinline__ float det3f(float a, float b, float c, float d, float e, float f, float g, float h,
+                                       float i) {
+  return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+__device__ __forceinline__ float t5_chi2(const float4 *P, float sigma) {
+  float u[5], v[5], w[5];
+  const bool swap = !(fabsf(P[4].x - P[0].x) >= fabsf(P[4].y - P[0].y));
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const float dx = P[i].x - P[2].x, dy = P[i].y - P[2].y;
+    u[i] = swap ? dy : dx;
+    v[i] = swap ? dx : dy;
+    w[i] = u[i] * u[i] + v[i] * v[i];
+  }
+  float su = 0.0f, sw = 0.0f, suu = 0.0f, suw = 0.0f, sww = 0.0f, sv = 0.0f, suv = 0.0f, swv = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    su = su + u[i];
+    sw = sw + w[i];
+    suu = suu + u[i] * u[i];
+    suw = suw + u[i] * w[i];
+    sww = sww + w[i] * w[i];
+    sv = sv + v[i];
+    suv = suv + u[i] * v[i];
+    swv = swv + w[i] * v[i];
+  }
+  const float n = 5.0f;
+  const float det = det3f(n, su, sw, su, suu, suw, sw, suw, sww);
+  const float alpha = det3f(sv, su, sw, suv, suu, suw, swv, suw, sww) / det;
+  const float beta = det3f(n, sv, sw, su, suv, suw, sw, swv, sww) / det;
+  const float gamma = det3f(n, su, sv, su, suu, suv, sw, suw, swv) / det;
+  const float nu = sqrtf(beta * beta + 1.0f - 4.0f * gamma * alpha);
+  const float A = gamma / nu;
+  float chi2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const float p = (gamma * w[i] + beta * u[i] - v[i] + alpha) / nu;
+    const float d = 2.0f * p / (1.0f + sqrtf(1.0f + 4.0f * A * p));
+    const float t = d / sigma;
+    chi2 = chi2 + t * t;
+  }
+  return chi2;
+}
+
 __device__ __forceinline__ bool t5_cut(const float4 *P, float ka, float kb, const lst_cuts &c) {
   if (!(ka * kb > 0.0f)) return false;                                   // same charge
   if (!(fabsf(ka - kb) <= c.t5_kappa_rel * 0.5f * (fabsf(ka) + fabsf(kb)) + c.t5_kappa_abs)) return false;
@@ -210,6 +268,9 @@ __device__ __forceinline__ bool t5_cut(const float4 *P, float ka, float kb, cons
     if (!(fabsf(P[j].z - (z0 + (z4 - z0) * S[j] / S[4])) <= c.t5_rz_tol)) return false;  // rz
   return true;
 }
+
+// Ranking value of a T5 among duplicates: the chi2, with NaN and +inf both +inf.
+__device__ __forceinline__ float tc_rank(float chi2) { return chi2 <= 3.40282347e38f ? chi2 : __int_as_float(0x7f800000); }
 
 // ------------------------------------------------------------------ accurate FP32 helpers
 // (features only; cut values above never use them)

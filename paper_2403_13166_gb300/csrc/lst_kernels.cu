@@ -655,9 +655,15 @@ __global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int 
         P[3] = ev.md_anchor[B3.y];
         P[4] = ev.md_anchor[B3.z];
         pass = t5_cut(P, w.ka[lo], ev.t3_kappa[tb], c);
+        float chi2 = 0.0f;
+        if (pass) {
+          // circle-fit quality: the pre-DNN mode cuts on it, the track candidates rank by it
+          chi2 = t5_chi2(P, c.hit_sigma);
+          if (c.t5_chi2_max > 0.0f && !(chi2 <= c.t5_chi2_max)) pass = false;
+        }
         const int4 A3 = ev.t3_md[w.ta[lo]];
         a = make_int4(A3.x, A3.y, A3.z, B3.y);
-        b = make_int4(B3.z, w.ta[lo], tb, 0);
+        b = make_int4(B3.z, w.ta[lo], tb, __float_as_int(chi2));
       }
       const unsigned bal = __ballot_sync(FULL, pass);
       if (bal) {

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
     if (valid) {
       if (FROM_EVENTS) {
         const EvDesc &ev = evs[e];
-        const bool sel = score >= c.wp;
+        const bool sel = c.t5_chi2_max > 0.0f || score >= c.wp;   // pre-DNN mode: chosen by the chi2 cut
         ev.t5_score[t] = score;
         ev.t5_sel[t] = sel ? 1 : 0;
         if (sel) atomicAdd(ev.cnt + C_NSEL, 1);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_score_fp32(const EvDesc *__restrict__ e
       float f[NFEAT];
       t5_features(ev, g, t, c.k_field, f);
       const float s = mlp_fp32(s_w, n_hidden, f);
-      sel = s >= c.wp;
+      sel = c.t5_chi2_max > 0.0f || s >= c.wp;     // pre-DNN mode: the chi2 cut selected it
       ev.t5_score[t] = s;
       ev.t5_sel[t] = sel ? 1 : 0;
     }
@@ -146,6 +146,35 @@ __global__ void k_gather(const EvDesc *__restrict__ ev_p, int kind, int n, int32
   }
 }
 
+// Hit-index tuples, scores and selection flags of the track candidates of one event, in
+// no particular order (counter: one int on the device, zeroed by the caller).
+__global__ void k_gather_tc(const EvDesc *__restrict__ ev_p, int n_t5, int *counter, int32_t *out, float *score,
+                            uint8_t *sel) {
+  const EvDesc &ev = *ev_p;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_t5; base += gridDim.x * blockDim.x) {
+    const int t = base + lane;
+    const bool keep = t < n_t5 && ev.t5_tc[t];
+    const unsigned bal = __ballot_sync(FULL, keep);
+    int o0 = 0;
+    if (lane == 0 && bal) o0 = atomicAdd(counter, __popc(bal));
+    o0 = __shfl_sync(FULL, o0, 0);
+    if (keep) {
+      const int o = o0 + __popc(bal & lanemask_lt());
+      const int4 a = ev.t5_a[t], b = ev.t5_b[t];
+      const int md[5] = {a.x, a.y, a.z, a.w, b.x};
+#pragma unroll
+      for (int i = 0; i < 5; i++) {
+        const int2 h = ev.md_hits[md[i]];
+        out[10 * (size_t)o + 2 * i] = h.x;
+        out[10 * (size_t)o + 2 * i + 1] = h.y;
+      }
+      if (score) score[o] = ev.t5_score[t];
+      if (sel) sel[o] = ev.t5_sel[t];
+    }
+  }
+}
+
 // Zero the per-event counters, sensor histogram and the per-MD range counts (units whose
 // MD range was dropped after an overflow must read as empty).
 __global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {
@@ -153,7 +182,7 @@ __global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   if (tid < C_NCOUNTERS) ev.cnt[tid] = 0;
   for (int i = tid; i < 2 * g.n_mod; i += st) ev.sens_cnt[i] = 0;
-  for (int i = tid; i < ev.md_cap; i += st) { ev.ls_cnt[i] = 0; ev.t3_cnt[i] = 0; }
+  for (int i = tid; i < ev.md_cap; i += st) { ev.ls_cnt[i] = 0; ev.t3_cnt[i] = 0; ev.tc_cnt[i] = 0; }
   for (int i = tid; i < g.n_mod; i += st) ev.md_cnt[i] = 0;
 }
 

@@ -20,9 +20,11 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblst.so")
 
 LST_OK, LST_ERR_ARG, LST_ERR_CAPACITY, LST_ERR_CUDA, LST_ERR_TIMEOUT, LST_ERR_NOT_READY, \
     LST_ERR_INPUT, LST_ERR_NOMEM = range(8)
-LST_MD, LST_LS, LST_T3, LST_T5 = range(4)
+LST_MD, LST_LS, LST_T3, LST_T5, LST_TC = range(5)
+N_STAGES = 7
+STAGES = ("bin", "md", "ls", "t3", "t5", "score", "tc")
 LST_FP32, LST_BF16, LST_BF16X3 = 0, 1, 2
-WIDTH = {LST_MD: 2, LST_LS: 4, LST_T3: 6, LST_T5: 10}
+WIDTH = {LST_MD: 2, LST_LS: 4, LST_T3: 6, LST_T5: 10, LST_TC: 10}
 NFEAT = 38
 
 
@@ -58,7 +60,7 @@ class lst_launch(C.Structure):
 class lst_counts(C.Structure):
     _fields_ = [("n_hits", C.c_int64), ("n_md", C.c_int64), ("n_ls", C.c_int64), ("n_t3", C.c_int64),
                 ("n_t5", C.c_int64), ("n_selected", C.c_int64), ("pairs", C.c_int64 * 4),
-                ("status", C.c_int32), ("overflow_mask", C.c_int32)]
+                ("status", C.c_int32), ("overflow_mask", C.c_int32), ("n_tc", C.c_int64)]
 
 
 _lib = None
@@ -178,11 +180,11 @@ class Event:
         c = lst_counts()
         _check(load_library().lst_event_counts(self.h, C.byref(c)), "lst_event_counts")
         return dict(n_hits=c.n_hits, md=c.n_md, ls=c.n_ls, t3=c.n_t3, t5=c.n_t5, selected=c.n_selected,
-                    pairs=list(c.pairs), status=c.status, overflow_mask=c.overflow_mask)
+                    tc=c.n_tc, pairs=list(c.pairs), status=c.status, overflow_mask=c.overflow_mask)
 
     def candidates(self, kind: int, out=None, score=None, selected=None):
-        """Hit tuples [n][2|4|6|10] (+ T5 score and selection). Host numpy by default; pass
-        torch CUDA tensors to receive device copies."""
+        """Hit tuples [n][2|4|6|10] (+ score and selection for T5s and track candidates).
+        Host numpy by default; pass torch CUDA tensors to receive device copies."""
         lib = load_library()
         n = C.c_int64(0)
         st = lib.lst_get_candidates(self.h, kind, None, None, None, 0, C.byref(n))
@@ -191,13 +193,13 @@ class Event:
         w = WIDTH[kind]
         if out is None:
             out = np.zeros((cnt, w), np.int32)
-            if kind == LST_T5:
+            if kind in (LST_T5, LST_TC):
                 score = np.zeros(cnt, np.float32)
                 selected = np.zeros(cnt, np.uint8)
         if cnt:
             _check(lib.lst_get_candidates(self.h, kind, _ptr(out), _ptr(score), _ptr(selected), cnt,
                                           C.byref(n)), "lst_get_candidates")
-        if kind == LST_T5:
+        if kind in (LST_T5, LST_TC):
             return out, score, selected
         return out
 
@@ -308,8 +310,8 @@ class Context:
         _check(load_library().lst_set_timing(self.h, int(on)), "lst_set_timing")
 
     def stage_times(self):
-        """Mean device ms per launch of (bin, md, ls, t3, t5, score), and the launch count."""
-        a = np.zeros(6, np.float32)
+        """Mean device ms per launch of each of STAGES, and the launch count."""
+        a = np.zeros(N_STAGES, np.float32)
         n = C.c_int64(0)
         _check(load_library().lst_stage_times(self.h, _ptr(a), C.byref(n)), "lst_stage_times")
         return a, n.value
@@ -434,7 +436,7 @@ class Server:
             r = self._buf[i]
             d = dict(tag=r.tag, status=r.status, t_arrival=r.t_arrival, t_admit=r.t_admit, t_launch=r.t_launch,
                      t_done=r.t_done, n_t5=r.n_t5, t5=r.counts.n_t5, md=r.counts.n_md, ls=r.counts.n_ls,
-                     t3=r.counts.n_t3, selected=r.counts.n_selected)
+                     t3=r.counts.n_t3, selected=r.counts.n_selected, tc=r.counts.n_tc)
             if r.t5_hits and r.n_t5:
                 n5 = r.n_t5
                 d["t5_hits"] = np.ctypeslib.as_array((C.c_int32 * (n5 * 10)).from_address(r.t5_hits)).reshape(n5, 10).copy()

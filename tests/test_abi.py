@@ -54,5 +54,5 @@ def test_structs_match_header_layout(libpath):
     assert ctypes.sizeof(lst.lst_cuts) == 13 * 4
     assert ctypes.sizeof(lst.lst_module) == 16
     assert ctypes.sizeof(lst.lst_config) == 32
-    assert ctypes.sizeof(lst.lst_counts) == 10 * 8 + 8
+    assert ctypes.sizeof(lst.lst_counts) == 10 * 8 + 8 + 8
     assert ctypes.sizeof(lst.lst_launch) == 8 * 4

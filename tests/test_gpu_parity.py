@@ -49,6 +49,13 @@ def compare(ev, ref, wp, check_features=False):
             f = ev.features()[og].astype(np.float64)
             df = np.abs(f - ref.t5_feat[oe])
             assert np.max(df) <= 4e-6, (np.max(df), np.unravel_index(np.argmax(df), df.shape))
+        # track candidates: the duplicate removal is exact (FP32 chi2 ranks); its input, the
+        # selection, matches whenever no score sits within the FP32 error of the working point
+        if np.array_equal(sel[og], ref.t5_sel[oe]):
+            tc = ev.candidates(lst.LST_TC)[0]
+            assert c["tc"] == len(tc) == int(ref.t5_tc.sum())
+            exp_tc = ref.tc_hits()
+            assert np.array_equal(tc[canon_order(tc)], exp_tc[canon_order(exp_tc)])
     return c
 
 
