@@ -332,6 +332,45 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
   return v;
 }
 
+// Exclusive prefix sums pos[i] = cnt[0] + ... + cnt[i-1] for i < n, by the whole CTA
+// (blockDim.x a multiple of 32, <= 1024): tiles of 4 consecutive elements per thread, so
+// that a warp reads 512 contiguous bytes, with the running total carried across tiles.
+__device__ __forceinline__ void block_exclusive_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ pos,
+                                                     int n) {
+  __shared__ int s_w[32];
+  __shared__ int s_carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 4 * blockDim.x) {
+    const int i0 = base + 4 * threadIdx.x;
+    int v[4], local = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      v[k] = i0 + k < n ? cnt[i0 + k] : 0;
+      local += v[k];
+    }
+    const int inc = warp_incl_scan(local);
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const int x = lane < nw ? s_w[lane] : 0;
+      const int xi = warp_incl_scan(x);
+      if (lane < nw) s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    int run = s_carry + s_w[wid] + inc - local;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (i0 + k < n) pos[i0 + k] = run;
+      run += v[k];
+    }
+    __syncthreads();                                   // s_carry and s_w read by all
+    if (threadIdx.x == blockDim.x - 1) s_carry = run;  // = carry + this tile's total
+    __syncthreads();
+  }
+}
+
 // Exclusive prefix over events of a per-event unit count, built in shared memory by
 // the whole block: pref[e] = sum_{f<e} count(f), pref[n] = total. n <= MAX_EVENTS.
 template <typename F>

@@ -549,28 +549,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
 __global__ void k_t3_scan(const EvDesc *__restrict__ evs) {
   const EvDesc &ev = evs[blockIdx.x];
   if (ev_void(ev)) return;
-  const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  int local = 0;
-  for (int k = 0; k < per && b0 + k < n; k++) local += ev.t3_cnt[b0 + k];
-  __shared__ int s_w[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int inc = warp_incl_scan(local);
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    const int v = lane < nw ? s_w[lane] : 0;
-    const int vi = warp_incl_scan(v);
-    if (lane < nw) s_w[lane] = vi - v;
-  }
-  __syncthreads();
-  int run = s_w[wid] + inc - local;
-  for (int k = 0; k < per && b0 + k < n; k++) {
-    ev.t3_pos[b0 + k] = run;
-    run += ev.t3_cnt[b0 + k];
-  }
+  block_exclusive_scan(ev.t3_cnt, ev.t3_pos, clamp_count(ev.cnt[C_MD], ev.md_cap));
 }
 
 // ... then a scatter into that order; afterwards t3_pos[md] holds the END of md's range.

@@ -10,9 +10,10 @@
 // duplicate ranks above it: one pass, so a T5 removed by a better duplicate still removes
 // the T5s it ranks above.
 //
-// GPU form: every duplicate shares an MD, so each selected T5 is listed under its 5 MDs
-// (count, per-event scan, scatter) and each T5 compares itself with the T5s listed under
-// its own MDs. All four kernels cover the whole batch in one launch each.
+// GPU form: every selected T5 is listed under its 5 MDs (count, per-event scan, scatter);
+// a duplicate of t shares >= 3 of t's 5 MDs, hence at least one of its middle three, so t
+// compares itself with the T5s listed under md1..md3. All four kernels cover the whole
+// batch in one launch each.
 #include "lst_internal.cuh"
 
 namespace lstk {
@@ -63,28 +64,7 @@ __global__ void __launch_bounds__(256) k_tc_count(const EvDesc *__restrict__ evs
 __global__ void k_tc_scan(const EvDesc *__restrict__ evs) {
   const EvDesc &ev = evs[blockIdx.x];
   if (ev_void(ev)) return;
-  const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  int local = 0;
-  for (int k = 0; k < per && b0 + k < n; k++) local += ev.tc_cnt[b0 + k];
-  __shared__ int s_w[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int inc = warp_incl_scan(local);
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    const int v = lane < nw ? s_w[lane] : 0;
-    const int vi = warp_incl_scan(v);
-    if (lane < nw) s_w[lane] = vi - v;
-  }
-  __syncthreads();
-  int run = s_w[wid] + inc - local;
-  for (int k = 0; k < per && b0 + k < n; k++) {
-    ev.tc_pos[b0 + k] = run;
-    run += ev.tc_cnt[b0 + k];
-  }
+  block_exclusive_scan(ev.tc_cnt, ev.tc_pos, clamp_count(ev.cnt[C_MD], ev.md_cap));
 }
 
 // List every selected T5 under each of its MDs; afterwards tc_pos[md] is the END of md's range.
@@ -125,7 +105,9 @@ __global__ void __launch_bounds__(256) k_tc_decide(const EvDesc *__restrict__ ev
         int mt[5];
         t5_mds(ev, t, mt);
         const float qt = tc_rank(__int_as_float(ev.t5_b[t].w));
-        for (int j = 0; j < 5 && keep; j++) {
+        // a duplicate shares >= 3 of t's 5 MDs, so at least one of t's middle three: the
+        // lists of md1..md3 (every selected T5 is listed under all 5 of its MDs) hold them all
+        for (int j = 1; j <= 3 && keep; j++) {
           const int end = ev.tc_pos[mt[j]], beg = end - ev.tc_cnt[mt[j]];
           for (int k = beg; k < end && keep; k++) {
             const int u = ev.tc_list[k];

@@ -478,6 +478,22 @@ def pileup_event(g: Geometry, index: int = 0, pileup: int = 200, config: int = 2
     return make_event(g, parts, rng, sigma=sigma, noise_frac=noise_frac, seed=seed)
 
 
+def muon_cube_event(g: Geometry, index: int = 0, n_muons: int = 20, config: int = 6,
+                    half: float = 2.5, sigma=HIT_SIGMA) -> Event:
+    """Section 3's displaced-track sample: muons produced at points uniform in a cube of
+    side 2 * half cm (5 cm) around the origin; pT log-uniform 1-20 GeV, |eta| < 2.4, no
+    pile-up, no noise."""
+    seed = 1000 * config + index
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pt = np.exp(rng.uniform(np.log(1.0), np.log(20.0), n_muons))
+    eta = rng.uniform(-2.4, 2.4, n_muons)
+    phi = rng.uniform(-np.pi, np.pi, n_muons)
+    q = rng.choice([-1.0, 1.0], n_muons)
+    v = rng.uniform(-half, half, (3, n_muons))
+    parts = _particles(pt, eta, phi, q, v[0], v[1], v[2], np.hypot(v[0], v[1]) > 0.0)
+    return make_event(g, parts, rng, sigma=sigma, noise_frac=0.0, seed=seed)
+
+
 def muon_event(g: Geometry, pts, etas, phis, qs, vertex=(0.0, 0.0, 0.0), sigma=0.0,
                seed=0) -> Event:
     """Explicit list of tracks (for closed-form and threshold tests)."""

@@ -56,7 +56,31 @@ def md_layers(sensor: np.ndarray, pid: np.ndarray, layer_of_module: np.ndarray, 
     return out
 
 
-def findable_t5(sensor, pid, layer_of_module, n_part, chains=((1, 2, 3, 4, 5), (2, 3, 4, 5, 6))):
-    """Particles with true mini-doublets in five consecutive barrel layers."""
+def _layer_chains(length: int = 5):
+    """Every sequence of `length` layers linked by the module map's layer relation: barrel
+    l -> l+1, any barrel layer -> first disk (7), disk d -> d+1 (one side per particle)."""
+    nxt = {l: ([l + 1] if l <= 5 else []) + [7] for l in range(1, 7)}
+    nxt.update({d: [d + 1] for d in range(7, 11)})
+    nxt[11] = []
+    out = []
+
+    def walk(ch):
+        if len(ch) == length:
+            out.append(tuple(ch))
+            return
+        for n in nxt[ch[-1]]:
+            walk(ch + [n])
+
+    for start in range(1, 12):
+        walk([start])
+    return tuple(out)
+
+
+T5_CHAINS = _layer_chains(5)
+
+
+def findable_t5(sensor, pid, layer_of_module, n_part, chains=T5_CHAINS):
+    """Particles with true mini-doublets in five layers that form a chain of the module map
+    (five consecutive barrel layers, a barrel run continued into the disks, or five disks)."""
     lay = md_layers(sensor, pid, layer_of_module, n_part)
     return np.array([p for p in range(n_part) if any(set(c) <= lay[p] for c in chains)], np.int64)
