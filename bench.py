@@ -293,6 +293,26 @@ def run_gpu(args, rank, world, local_rank, pool):
                  "ms_per_event": round(pms / n_plain, 4), "events": n_plain, "score_precision": "fp32",
                  "gpu_launches_per_event": KERNELS_PER_LAUNCH, "form": "one launch sequence per event, no graph"}
 
+    # ---------------- LS graph (Section 4): MD nodes, LS edges, exported as CSR on the device
+    graph = None
+    if not args.skip_plain:
+        caps = int(3 * max(n_hits)), int(20 * max(n_hits))
+        g_row = torch.empty(caps[0] + 1, dtype=torch.int32, device=dev)
+        g_col = torch.empty(caps[1], dtype=torch.int32, device=dev)
+        g_nf = torch.empty((caps[0], lst.GRAPH_NODE_FEATURES), dtype=torch.float32, device=dev)
+        g_ef = torch.empty((caps[1], lst.GRAPH_EDGE_FEATURES), dtype=torch.float32, device=dev)
+        times, sizes = [], []
+        for i in range(min(8, B)):
+            ev = ctx_p.run_event(*d_in[i], stream=stream)
+            sync_all()
+            t0 = time.perf_counter()
+            sizes.append(ev.ls_graph_into(g_row, g_col, g_nf, g_ef))
+            times.append(time.perf_counter() - t0)
+            ev.release()
+        graph = {"export_ms_per_event": round(1000 * float(np.median(times[1:] or times)), 4),
+                 "nodes_per_event": int(np.mean([s[0] for s in sizes])),
+                 "edges_per_event": int(np.mean([s[1] for s in sizes]))}
+
     # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
     h2d = int(sum(16 * n for n in n_hits))
@@ -334,6 +354,8 @@ def run_gpu(args, rank, world, local_rank, pool):
     roofline = roofline_entry(names[dom], float(stage_ms[dom]), B, mean_counts, pairs, float(np.mean(n_hits)),
                               clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
     roofline["stage_ms_per_launch"] = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
+    if graph is not None:   # the graph build inside the batched launch: grouping, MD and LS stages
+        graph["build_ms_per_event_batched"] = round(float(stage_ms[0] + stage_ms[1] + stage_ms[2]) / B, 4)
     roofline["launches_timed"] = int(n_launch)
 
     line = {
@@ -349,6 +371,7 @@ def run_gpu(args, rank, world, local_rank, pool):
                    "objects_per_event_mean": {k: int(v) for k, v in mean_counts.items()}},
         "plain": plain,
         "served": served,
+        "ls_graph": graph,
         "e2e": e2e,
         "roofline": roofline,
         "clocks": clk.summary(),

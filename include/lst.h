@@ -175,6 +175,24 @@ lst_status lst_event_counts(lst_event ev, lst_counts *out);
 lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score,
                               uint8_t *selected, int64_t capacity, int64_t *n_out);
 
+/* The event's LS graph, the GNN input that Section 4 proposes to build with LST: nodes are
+ * the MDs (ids = the order of lst_get_candidates(LST_MD)), directed edges the LSs from
+ * inner to outer MD, in CSR form by inner MD:
+ *   row_off   [n_nodes + 1] int32, row_off[n_nodes] = n_edges;
+ *   col       [n_edges] int32 outer-MD ids (edges of one node in no particular order);
+ *   node_feat [n_nodes][LST_GRAPH_NODE_FEATURES] float or NULL: anchor (lower-sensor) hit
+ *             x, y, z, r in cm, MD curvature in 1/cm (0 for endcap MDs), layer 1..11;
+ *   edge_feat [n_edges][LST_GRAPH_EDGE_FEATURES] float or NULL: LS curvature in 1/cm, z in cm
+ *             of the anchors' chord at r = 0 (z_a - r_a * ((z_b - z_a) / (r_b - r_a))).
+ * All buffers are HOST or all DEVICE memory (detected from row_off); node_cap / edge_cap
+ * are the node and edge capacities (row_off holds node_cap + 1 values). *n_nodes and
+ * *n_edges are always set; LST_ERR_CAPACITY (nothing copied) if a capacity is too small;
+ * row_off NULL: size query only. */
+#define LST_GRAPH_NODE_FEATURES 6
+#define LST_GRAPH_EDGE_FEATURES 2
+lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float *node_feat, float *edge_feat,
+                            int64_t node_cap, int64_t edge_cap, int64_t *n_nodes, int64_t *n_edges);
+
 /* Copies the 38 T5-DNN input features of every T5 (Section 2 list) as float [n][38]
  * (HOST or DEVICE); same size protocol as lst_get_candidates. */
 lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out);

@@ -37,6 +37,8 @@ __global__ void k_tc_scan(const EvDesc *);
 __global__ void k_tc_scatter(const EvDesc *, int);
 __global__ void k_tc_decide(const EvDesc *, int);
 __global__ void k_gather_tc(const EvDesc *, int, int *, int32_t *, float *, uint8_t *);
+__global__ void k_graph_rows(const EvDesc *, int, int32_t *);
+__global__ void k_graph_fill(const EvDesc *, DevGeom, int, const int32_t *, int32_t *, float *, float *);
 cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
                                      const float *, int, int *, long long, bool split);
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
@@ -809,6 +811,54 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
   if (kind == LST_T5 && score) CU(cudaMemcpyAsync(score, d_sc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->aux));
   if (kind == LST_T5 && selected) CU(cudaMemcpyAsync(selected, d_sel, (size_t)n, cudaMemcpyDeviceToHost, c->aux));
   CU(cudaFreeAsync(tmp, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+
+lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float *node_feat, float *edge_feat,
+                           int64_t node_cap, int64_t edge_cap, int64_t *n_nodes, int64_t *n_edges) {
+  if (!ev || !n_nodes || !n_edges) return fail(LST_ERR_ARG, "null argument");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  lst_status s = wait_event(ev);
+  if (s != LST_OK) return s;
+  const Slot &S = c->slots[ev->slot];
+  const int64_t nm = S.cnt[C_MD], nl = S.cnt[C_LS];
+  *n_nodes = nm;
+  *n_edges = nl;
+  if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
+  if (node_cap < nm || edge_cap < nl) return fail(LST_ERR_CAPACITY, "graph capacity below node / edge count");
+  if (!row_off) return LST_OK;                                        // size query
+  if (nl > 0 && !col) return fail(LST_ERR_ARG, "col is NULL");
+  EvDesc *dd;
+  s = slot_desc_device(c, ev->slot, &dd);
+  if (s != LST_OK) return s;
+  const bool dev_out = is_device_ptr(row_off);
+  const size_t b_row = 4 * (size_t)(nm + 1), b_col = 4 * (size_t)nl, b_nf = 24 * (size_t)nm, b_ef = 8 * (size_t)nl;
+  void *tmp = nullptr;
+  int32_t *d_row = row_off, *d_col = col;
+  float *d_nf = node_feat, *d_ef = edge_feat;
+  if (!dev_out) {
+    CU(cudaMallocAsync(&tmp, b_row + b_col + b_nf + b_ef + 1024, c->aux));
+    char *p = (char *)tmp;
+    d_row = (int32_t *)p; p += align_up(b_row, 256);
+    d_col = (int32_t *)p; p += align_up(b_col, 256);
+    d_nf = node_feat ? (float *)p : nullptr; p += align_up(b_nf, 256);
+    d_ef = edge_feat ? (float *)p : nullptr;
+  }
+  k_graph_rows<<<1, 1024, 0, c->aux>>>(dd, (int)nm, d_row);
+  if (nm > 0) {
+    const int grid = (int)std::min<int64_t>((nm + 255) / 256, 4 * c->n_sm);
+    k_graph_fill<<<grid, 256, 0, c->aux>>>(dd, c->g, (int)nm, d_row, d_col, d_nf, d_ef);
+  }
+  CU(cudaGetLastError());
+  if (!dev_out) {
+    CU(cudaMemcpyAsync(row_off, d_row, b_row, cudaMemcpyDeviceToHost, c->aux));
+    if (nl) CU(cudaMemcpyAsync(col, d_col, b_col, cudaMemcpyDeviceToHost, c->aux));
+    if (node_feat && nm) CU(cudaMemcpyAsync(node_feat, d_nf, b_nf, cudaMemcpyDeviceToHost, c->aux));
+    if (edge_feat && nl) CU(cudaMemcpyAsync(edge_feat, d_ef, b_ef, cudaMemcpyDeviceToHost, c->aux));
+    CU(cudaFreeAsync(tmp, c->aux));
+  }
   CU(cudaStreamSynchronize(c->aux));
   return LST_OK;
 }

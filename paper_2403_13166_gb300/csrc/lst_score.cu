@@ -175,6 +175,39 @@ __global__ void k_gather_tc(const EvDesc *__restrict__ ev_p, int n_t5, int *coun
   }
 }
 
+// LS graph of one event (MD nodes, LS edges from inner to outer MD): CSR row offsets by one
+// CTA, row_off[n_md] = number of edges.
+__global__ void k_graph_rows(const EvDesc *__restrict__ ev_p, int n_md, int32_t *row_off) {
+  const EvDesc &ev = *ev_p;
+  block_exclusive_scan(ev.ls_cnt, row_off, n_md);
+  if (threadIdx.x == 0) row_off[n_md] = n_md ? row_off[n_md - 1] + ev.ls_cnt[n_md - 1] : 0;
+}
+
+// ... then the edges of every MD (its LS range) and the node / edge features.
+__global__ void k_graph_fill(const EvDesc *__restrict__ ev_p, DevGeom g, int n_md, const int32_t *row_off,
+                             int32_t *col, float *node_feat, float *edge_feat) {
+  const EvDesc &ev = *ev_p;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_md; m += gridDim.x * blockDim.x) {
+    const float4 A = ev.md_anchor[m];
+    const int beg = ev.ls_start[m], cnt = ev.ls_cnt[m], o = row_off[m];
+    for (int k = 0; k < cnt; k++) {
+      const int l = beg + k, b = ev.ls_out[l];
+      col[o + k] = b;
+      if (edge_feat) {
+        const float4 B = ev.md_anchor[b];
+        edge_feat[2 * (size_t)(o + k)] = ev.ls_kappa[l];
+        edge_feat[2 * (size_t)(o + k) + 1] = A.z - A.w * ((B.z - A.z) / (B.w - A.w));   // z at r = 0
+      }
+    }
+    if (node_feat) {
+      float *f = node_feat + 6 * (size_t)m;
+      f[0] = A.x; f[1] = A.y; f[2] = A.z; f[3] = A.w;
+      f[4] = ev.md_kappa[m].x;
+      f[5] = (float)g.layer[ev.md_mod[m]];
+    }
+  }
+}
+
 // Zero the per-event counters, sensor histogram and the per-MD range counts (units whose
 // MD range was dropped after an overflow must read as empty).
 __global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {

@@ -22,6 +22,7 @@ LST_OK, LST_ERR_ARG, LST_ERR_CAPACITY, LST_ERR_CUDA, LST_ERR_TIMEOUT, LST_ERR_NO
     LST_ERR_INPUT, LST_ERR_NOMEM = range(8)
 LST_MD, LST_LS, LST_T3, LST_T5, LST_TC = range(5)
 N_STAGES = 7
+GRAPH_NODE_FEATURES, GRAPH_EDGE_FEATURES = 6, 2
 STAGES = ("bin", "md", "ls", "t3", "t5", "score", "tc")
 LST_FP32, LST_BF16, LST_BF16X3 = 0, 1, 2
 WIDTH = {LST_MD: 2, LST_LS: 4, LST_T3: 6, LST_T5: 10, LST_TC: 10}
@@ -80,6 +81,8 @@ _SIGS = {
     "lst_get_candidates": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                            C.POINTER(C.c_int64)],
     "lst_get_t5_features": [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)],
+    "lst_get_ls_graph": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                         C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "lst_score_t5": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p],
     "lst_event_release": [C.c_void_p],
     "lst_destroy": [C.c_void_p],
@@ -212,6 +215,32 @@ class Event:
         if n.value:
             _check(lib.lst_get_t5_features(self.h, _ptr(f), n.value, C.byref(n)), "lst_get_t5_features")
         return f
+
+    def ls_graph(self, features=True):
+        """The LS graph (MD nodes, LS edges) as host arrays: row_off [n+1], col [m], and with
+        features node_feat [n][6] (anchor x, y, z, r, MD curvature, layer) and edge_feat [m][2]
+        (LS curvature, chord z at r = 0)."""
+        lib = load_library()
+        nn, ne = C.c_int64(0), C.c_int64(0)
+        _check(lib.lst_get_ls_graph(self.h, None, None, None, None, 0, 0, C.byref(nn), C.byref(ne)),
+               "lst_get_ls_graph", ok=(LST_OK, LST_ERR_CAPACITY))
+        n, m = nn.value, ne.value
+        row = np.zeros(n + 1, np.int32)
+        col = np.zeros(max(m, 1), np.int32)
+        nf = np.zeros((n, GRAPH_NODE_FEATURES), np.float32) if features else None
+        ef = np.zeros((m, GRAPH_EDGE_FEATURES), np.float32) if features else None
+        _check(lib.lst_get_ls_graph(self.h, _ptr(row), _ptr(col), _ptr(nf), _ptr(ef), n, m, C.byref(nn),
+                                    C.byref(ne)), "lst_get_ls_graph")
+        return row, col[:m], nf, ef
+
+    def ls_graph_into(self, row_off, col, node_feat=None, edge_feat=None):
+        """Export into caller buffers (torch CUDA tensors or numpy arrays, all of one kind);
+        returns (n_nodes, n_edges)."""
+        nn, ne = C.c_int64(0), C.c_int64(0)
+        _check(load_library().lst_get_ls_graph(self.h, _ptr(row_off), _ptr(col), _ptr(node_feat), _ptr(edge_feat),
+                                               int(row_off.shape[0]) - 1, int(col.shape[0]), C.byref(nn),
+                                               C.byref(ne)), "lst_get_ls_graph")
+        return nn.value, ne.value
 
     def release(self):
         if self.h:
