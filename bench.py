@@ -220,11 +220,12 @@ def run_gpu(args, rank, world, local_rank, pool):
     # the plain form: one launch sequence per event, FP32 score
     ctx_p = lst.Context(local_rank, max_events=2, precision=lst.LST_FP32, use_graphs=0)
     ctx_p.load_geometry(g, cuts, flat, nh)
-    if args.tune:
-        from paper_2403_13166_gb300 import autotune
-        autotune.apply_cached(ctx, g)
     d_in = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in e[1:]] for e in evs]
     stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if args.tune:   # launch shapes from the project's autotuner (tuned once per GPU and workload)
+        from paper_2403_13166_gb300 import autotune
+        tuned = autotune.tune_or_load(ctx, d_in, device=local_rank, stream=stream)
 
     def sync_all():
         torch.cuda.synchronize(dev)
@@ -368,6 +369,8 @@ def run_gpu(args, rank, world, local_rank, pool):
                    "particles_per_vertex": PER_VERTEX, "hits_per_event_mean": int(np.mean(n_hits)),
                    "modules": g.n_mod, "score_precision": args.precision, "weights": wname, "cuts": args.cuts,
                    "graphs": True, "l2": f"inputs larger than L2 ({int(h2d / 2**20)} MiB of hits per step)",
+                   "launch": ctx.get_launch(), "autotuned": None if tuned is None else
+                   {"cached": tuned["cached"], "trials": len(tuned.get("trials", []))},
                    "objects_per_event_mean": {k: int(v) for k, v in mean_counts.items()}},
         "plain": plain,
         "served": served,
@@ -520,7 +523,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the launch-shape autotuner (default: tune once per GPU and workload)")
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000])
     ap.add_argument("--served-seconds", type=float, default=2.0)

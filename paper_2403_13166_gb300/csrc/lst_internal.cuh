@@ -131,6 +131,25 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
   return true;
 }
 
+// Necessary condition of ls_cut without division or square root. The z0 road and the
+// direction are ls_cut's own expressions. Bend: |cr| / (rA dT) <= X + e / dT with
+// X = rB kappa_max / 2 means |cr| <= rA (X dT + e), hence cr^2 <= rA^2 ((1 + 1/64) X^2 dT^2
+// + 65 e^2), because (u + e)^2 <= (1 + t) u^2 + (1 + 1/t) e^2 for every t > 0 (here t = 1/64).
+// The factor 1.002 and the 1e-12 cover the FP32 rounding of both forms (a few ulp), so a
+// pair rejected here always fails ls_cut; ls_cut alone decides the pairs that pass.
+// X is passed in (one value per outer MD).
+__device__ __forceinline__ bool ls_prefilter(const float4 A, const float4 B, float X, const lst_cuts &c) {
+  const float e = c.hit_err;
+  const float drr = B.w - A.w;
+  if (!(fabsf(A.z * drr - A.w * (B.z - A.z)) <= (c.z_lum + e) * fabsf(drr) + e * A.w)) return false;  // z0
+  const float dx = B.x - A.x, dy = B.y - A.y;
+  if (!(A.x * dx + A.y * dy > 0.0f)) return false;                     // direction
+  const float cr = A.x * dy - A.y * dx;
+  const float dT2 = dx * dx + dy * dy;
+  const float rhs = (A.w * A.w) * (1.015625f * (X * X) * dT2 + 65.0f * (e * e));
+  return cr * cr <= rhs * 1.002f + 1e-12f;                             // bend, squared
+}
+
 // Necessary condition of md_cut without division or square root (barrel), or the exact
 // direction test (endcap). hb2r2 = (rL * hb)^2 with hb = rL*(kappa_max/2) + e/g, the bend
 // bound of md_cut, precomputed per lower hit. Bend: |cr| <= rL dT hb. z road, multiplied

@@ -278,10 +278,23 @@ __global__ void k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
 constexpr int LS_IN_CHUNK = 64;
 struct LsEntry { int i; int md; float k; };
 
+// Per-warp staging of the LS tile: the warp's 32 target MDs, and a queue of the (inner,
+// target) pairs that passed ls_prefilter; the exact cut runs on 32 queued pairs at a time.
+struct LsWarp {
+  float4 B[32];          // target anchors
+  float kB[32];          // target MD curvatures (cut values)
+  int md[32];            // target MD ids
+  unsigned short q[64];  // queued pairs: inner index << 5 | target lane
+  unsigned char bB[32];  // target in the barrel
+};
+static_assert(sizeof(LsWarp) == 928, "the host sizes k_ls shared memory with 928 bytes per warp");
+
 __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
                                            lst_cuts c, int *work, int list_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_in = reinterpret_cast<float4 *>(smem_raw);                   // [LS_IN_CHUNK]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  LsWarp &w = reinterpret_cast<LsWarp *>(smem_raw)[wid];                 // [nwarps]
+  float4 *s_in = reinterpret_cast<float4 *>(smem_raw + nwarps * sizeof(LsWarp));  // [LS_IN_CHUNK]
   float *s_ink = reinterpret_cast<float *>(s_in + LS_IN_CHUNK);          // [LS_IN_CHUNK]
   int *s_cnt = reinterpret_cast<int *>(s_ink + LS_IN_CHUNK);             // [LS_IN_CHUNK]
   int *s_off = s_cnt + LS_IN_CHUNK;                                      // [LS_IN_CHUNK]
@@ -290,7 +303,6 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
   int *s_tbar = s_tstart + MAX_FANOUT;                                   // [MAX_FANOUT]
   LsEntry *s_list = reinterpret_cast<LsEntry *>(s_tbar + MAX_FANOUT);    // [list_cap]
   __shared__ int s_unit, s_nin, s_nlist, s_base;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int total = n_events * g.n_mod;
   for (;;) {
     // One thread fetches the unit and reads the event's state; the whole CTA then uses
@@ -347,14 +359,15 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       }
       if (threadIdx.x == 0) s_nlist = 0;
       __syncthreads();
-      // ---- tile: lanes over targets, loop over inner MDs
+      // ---- tile: lanes over targets, loop over inner MDs; the division-free necessary
+      // test runs on every pair, the exact cut on full warps of queued survivors (~9%)
       for (int pass_no = 0; pass_no < 2; pass_no++) {
         const bool writing = pass_no == 1;   // second sweep only after a list overflow
         for (int j0 = wid * 32; j0 < S; j0 += nwarps * 32) {
           const int j = j0 + lane;
           bool valid = j < S;
           float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-          float kB = 0.0f;
+          float kB = 0.0f, X = 0.0f;
           bool bB = false;
           int md = 0;
           if (valid) {
@@ -364,32 +377,67 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               B = ev.md_anchor[md];
               kB = ev.md_kappa[md].x;
               bB = s_tbar[t] != 0;
+              X = B.w * (0.5f * c.kappa_max);
             } else {
               valid = false;
             }
           }
-          for (int i = 0; i < nc; i++) {
+          w.B[lane] = B;
+          w.kB[lane] = kB;
+          w.md[lane] = md;
+          w.bB[lane] = bB ? 1 : 0;
+          __syncwarp();
+          // exact cut of the first n queued pairs (one per lane), results to the list
+          auto run_queue = [&](int n) {
+            bool pass = false;
+            int ie = 0, le = 0;
             float k = 0.0f;
-            const bool pass = valid && ls_cut(s_in[i], B, s_ink[i], kB, bA, bB, c, k);
+            if (lane < n) {
+              const int qe = w.q[lane];
+              ie = qe >> 5;
+              le = qe & 31;
+              pass = ls_cut(s_in[ie], w.B[le], s_ink[ie], w.kB[le], bA, w.bB[le] != 0, c, k);
+            }
             const unsigned bal = __ballot_sync(FULL, pass);
-            if (bal == 0) continue;
+            if (bal == 0) return;
             if (!writing) {
               int pos = 0;
-              if (lane == 0) {
-                pos = atomicAdd(&s_nlist, __popc(bal));
-                atomicAdd(&s_cnt[i], __popc(bal));
-              }
+              if (lane == 0) pos = atomicAdd(&s_nlist, __popc(bal));
               pos = __shfl_sync(FULL, pos, 0);
-              const int q = pos + __popc(bal & lanemask_lt());
-              if (pass && q < list_cap) s_list[q] = {i, md, k};
+              if (pass) {
+                atomicAdd(&s_cnt[ie], 1);
+                const int q = pos + __popc(bal & lanemask_lt());
+                if (q < list_cap) s_list[q] = {ie, w.md[le], k};
+              }
             } else if (pass) {
-              const int o = s_base + s_off[i] + atomicAdd(&s_cnt[i], 1);
-              if (!chk(ev, o, ev.ls_cap, 23)) continue;
-              ev.ls_in[o] = in0 + c0 + i;
-              ev.ls_out[o] = md;
-              ev.ls_kappa[o] = k;
+              const int o = s_base + s_off[ie] + atomicAdd(&s_cnt[ie], 1);
+              if (chk(ev, o, ev.ls_cap, 23)) {
+                ev.ls_in[o] = in0 + c0 + ie;
+                ev.ls_out[o] = w.md[le];
+                ev.ls_kappa[o] = k;
+              }
+            }
+          };
+          int qn = 0;
+          for (int i = 0; i < nc; i++) {
+            const bool cand = valid && ls_prefilter(s_in[i], B, X, c);
+            const unsigned bal = __ballot_sync(FULL, cand);
+            if (cand) w.q[qn + __popc(bal & lanemask_lt())] = (unsigned short)((i << 5) | lane);
+            qn += __popc(bal);
+            if (qn >= 32) {
+              __syncwarp();
+              run_queue(32);
+              __syncwarp();
+              if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
+              __syncwarp();
+              qn -= 32;
             }
           }
+          if (qn > 0) {
+            __syncwarp();
+            run_queue(qn);
+          }
+          __syncwarp();
         }
         __syncthreads();
         if (writing) break;
