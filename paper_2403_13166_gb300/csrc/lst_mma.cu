@@ -24,6 +24,8 @@
 // the rest of its work, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "lst_features.cuh"
 
 namespace lstk {
@@ -303,13 +305,29 @@ cudaError_t launch_score_bf16_features(int grid, cudaStream_t st, DevGeom g, lst
                                                      wait_limit);
   return cudaGetLastError();
 }
-// resident CTAs per SM, capped at 16 so that 16 x TMEM_COLS fits the 512 TMEM columns
+// Resident CTAs per SM of the score kernel, from its own footprint: registers (allocated
+// per warp in units of 256), static shared memory (+1 KB reserved per CTA), threads, and
+// tensor memory (512 columns per SM, TMEM_COLS per CTA). The runtime occupancy query is
+// used only when it reports more.
 int score_bf16_blocks_per_sm(bool split) {
-  int occ = 0;
-  const cudaError_t e = split ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true, true>, 128, 0)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_bf16<true, false>, 128, 0);
-  if (e != cudaSuccess || occ < 1) return 1;
-  return occ < 16 ? occ : 16;
+  const void *fn = split ? (const void *)k_score_bf16<true, true> : (const void *)k_score_bf16<true, false>;
+  cudaFuncAttributes a;
+  int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+    return 1;
+  const int warps = 128 / 32;
+  const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;
+  int occ = regs_sm / (regs_warp * warps);
+  occ = std::min(occ, smem_sm / ((int)a.sharedSizeBytes + 1024));
+  occ = std::min(occ, thr_sm / 128);
+  occ = std::min(occ, 512 / TMEM_COLS);
+  int api = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, (const void *)fn, 128, 0) == cudaSuccess && api > occ)
+    occ = std::min(api, 512 / TMEM_COLS);
+  return occ < 1 ? 1 : occ;
 }
 
 // BF16 weights in the core-matrix layout expected above, built on the host (see the layout
