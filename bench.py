@@ -445,9 +445,10 @@ FP32_OPS_PER_OBJECT = {"md": 30, "ls": 35, "t3": 30, "t5": 40}
 
 
 # DRAM bytes (read + write) per event of a kernel, from one ncu capture of a 16-event
-# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 230.6 MB for
-# k_ls); the traffic is the per-event output plus MD reads, so it scales with the events.
-TRAFFIC_PER_EVENT = {"ls": 230.6e6 / 16}
+# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 53.0 + 176.1
+# MB for k_ls); the traffic is the per-event output plus MD reads, so it scales with the
+# events.
+TRAFFIC_PER_EVENT = {"ls": 229.06e6 / 16}
 
 
 def traffic_per_launch(stage, events):
