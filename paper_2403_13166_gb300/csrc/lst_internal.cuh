@@ -139,15 +139,17 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
 // pair rejected here always fails ls_cut; ls_cut alone decides the pairs that pass.
 // X is passed in (one value per outer MD).
 __device__ __forceinline__ bool ls_prefilter(const float4 A, const float4 B, float X, const lst_cuts &c) {
+  // all three tests evaluated and combined without branches (no divergent early exits)
   const float e = c.hit_err;
   const float drr = B.w - A.w;
-  if (!(fabsf(A.z * drr - A.w * (B.z - A.z)) <= (c.z_lum + e) * fabsf(drr) + e * A.w)) return false;  // z0
+  const bool z0 = fabsf(A.z * drr - A.w * (B.z - A.z)) <= (c.z_lum + e) * fabsf(drr) + e * A.w;  // z0
   const float dx = B.x - A.x, dy = B.y - A.y;
-  if (!(A.x * dx + A.y * dy > 0.0f)) return false;                     // direction
+  const bool dir = A.x * dx + A.y * dy > 0.0f;                            // direction
   const float cr = A.x * dy - A.y * dx;
   const float dT2 = dx * dx + dy * dy;
   const float rhs = (A.w * A.w) * (1.015625f * (X * X) * dT2 + 65.0f * (e * e));
-  return cr * cr <= rhs * 1.002f + 1e-12f;                             // bend, squared
+  const bool bend = cr * cr <= rhs * 1.002f + 1e-12f;                     // bend, squared
+  return z0 & dir & bend;
 }
 
 // Necessary condition of md_cut without division or square root (barrel), or the exact

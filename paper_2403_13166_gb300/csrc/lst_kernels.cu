@@ -347,18 +347,27 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       }
       if (lane == 0) s_tpref[0] = 0;
     }
+    // the first chunk of inner MDs is loaded while warp 0 builds the target prefix
+    for (int t = threadIdx.x; t < min(LS_IN_CHUNK, n_in); t += blockDim.x) {
+      s_in[t] = ev.md_anchor[in0 + t];
+      s_ink[t] = ev.md_kappa[in0 + t].x;
+      s_cnt[t] = 0;
+    }
+    if (threadIdx.x == 0) s_nlist = 0;
     __syncthreads();
     const int S = s_tpref[nt];
     if (threadIdx.x == 0 && S) atomicAdd(ev.cnt + C_PLS, n_in * S);
     for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
       const int nc = min(LS_IN_CHUNK, n_in - c0);
-      for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-        s_in[t] = ev.md_anchor[in0 + c0 + t];
-        s_ink[t] = ev.md_kappa[in0 + c0 + t].x;
-        s_cnt[t] = 0;
+      if (c0 > 0) {
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+          s_in[t] = ev.md_anchor[in0 + c0 + t];
+          s_ink[t] = ev.md_kappa[in0 + c0 + t].x;
+          s_cnt[t] = 0;
+        }
+        if (threadIdx.x == 0) s_nlist = 0;
+        __syncthreads();
       }
-      if (threadIdx.x == 0) s_nlist = 0;
-      __syncthreads();
       // ---- tile: lanes over targets, loop over inner MDs; the division-free necessary
       // test runs on every pair, the exact cut on full warps of queued survivors (~9%)
       for (int pass_no = 0; pass_no < 2; pass_no++) {
@@ -419,8 +428,9 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             }
           };
           int qn = 0;
+#pragma unroll 2
           for (int i = 0; i < nc; i++) {
-            const bool cand = valid && ls_prefilter(s_in[i], B, X, c);
+            const bool cand = valid & ls_prefilter(s_in[i], B, X, c);
             const unsigned bal = __ballot_sync(FULL, cand);
             if (cand) w.q[qn + __popc(bal & lanemask_lt())] = (unsigned short)((i << 5) | lane);
             qn += __popc(bal);
@@ -460,15 +470,14 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
         }
         __syncthreads();
         const int base = s_base;
+        const int nlist = s_nlist;
         for (int t = threadIdx.x; t < nc; t += blockDim.x) {
           ev.ls_start[in0 + c0 + t] = base >= 0 ? base + s_off[t] : 0;
           ev.ls_cnt[in0 + c0 + t] = base >= 0 ? s_cnt[t] : 0;
+          s_cnt[t] = 0;                    // from here on: scatter cursors (same thread, same t)
         }
         __syncthreads();
-        const int nlist = s_nlist;
         if (base < 0) break;
-        for (int t = threadIdx.x; t < nc; t += blockDim.x) s_cnt[t] = 0;   // cursors
-        __syncthreads();
         if (nlist <= list_cap) {
           for (int q = threadIdx.x; q < nlist; q += blockDim.x) {
             const LsEntry r = s_list[q];
@@ -477,12 +486,14 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             ev.ls_out[o] = r.md;
             ev.ls_kappa[o] = r.k;
           }
-          __syncthreads();
           break;
         }
         // list overflow: sweep the tile again, writing in place
       }
-      __syncthreads();
+      // the next chunk reuses s_in / s_list / s_cnt; after a unit's last chunk the barrier
+      // of the next unit's fetch orders that reuse (thread 0 only writes s_unit / s_nin
+      // before it, which every thread has read at this unit's start)
+      if (c0 + LS_IN_CHUNK < n_in) __syncthreads();
     }
   }
 }
@@ -559,20 +570,18 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
       }
     };
     int qlen = 0;
-    for (int f0 = 0; f0 < tot; f0 += 32) {
-      const int f = f0 + lane;
-      bool pre = false;
-      int x = 0, md2 = 0;
-      if (f < tot) {
-        int lo = 0, hi = 31;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
-        x = lo;
-        const int prev = lo ? w.incl[lo - 1] : 0;
-        md2 = ev.ls_out[w.st2[lo] + (f - prev)];
-        pre = t3_prefilter(w.P0[lo], w.P1[lo], ev.md_anchor[md2], c);
-      }
+    // flat pair index f -> (LS1 lane x, outer MD); two pairs per lane and iteration so that
+    // the two dependent load chains (ls_out, then the anchor) are in flight together
+    auto decode = [&](int f, int &x) {
+      int lo = 0, hi = 31;
+      while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
+      x = lo;
+      const int prev = lo ? w.incl[lo - 1] : 0;
+      return w.st2[lo] + (f - prev);
+    };
+    auto enqueue = [&](bool pre, int x, int md2) {
       const unsigned bal = __ballot_sync(FULL, pre);
-      if (bal == 0) continue;
+      if (bal == 0) return;
       if (pre) {
         const int q = qlen + __popc(bal & lanemask_lt());
         w.qx[q] = x;
@@ -585,6 +594,19 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
         qlen -= 32;
         __syncwarp();
       }
+    };
+    for (int f0 = 0; f0 < tot; f0 += 64) {
+      const int fa = f0 + lane, fb = f0 + 32 + lane;
+      int xa = 0, xb = 0, mda = 0, mdb = 0;
+      if (fa < tot) mda = ev.ls_out[decode(fa, xa)];
+      if (fb < tot) mdb = ev.ls_out[decode(fb, xb)];
+      float4 Pa = make_float4(0.f, 0.f, 0.f, 0.f), Pb = Pa;
+      if (fa < tot) Pa = ev.md_anchor[mda];
+      if (fb < tot) Pb = ev.md_anchor[mdb];
+      const bool prea = fa < tot && t3_prefilter(w.P0[xa], w.P1[xa], Pa, c);
+      const bool preb = fb < tot && t3_prefilter(w.P0[xb], w.P1[xb], Pb, c);
+      enqueue(prea, xa, mda);
+      enqueue(preb, xb, mdb);
     }
     __syncwarp();
     if (qlen > 0) run_queue(0, qlen);
