@@ -213,6 +213,14 @@ lst_status lst_device_errors(lst_ctx ctx);
 /* Iteration limit of those device-side waits (default 2^26 polls). */
 lst_status lst_set_wait_limit(lst_ctx ctx, int64_t iterations);
 
+/* Test aid for the failure handling above (no counterpart in the paper). With on != 0 the
+ * tensor-core score kernels issue no MMA, so nothing ever arrives on the barrier they wait
+ * on: after the wait limit each CTA records LST_ERR_TIMEOUT, frees its tensor memory and
+ * returns, with nothing left in flight. The events of such a launch report
+ * LST_ERR_TIMEOUT, lst_device_errors returns it, and the context stays usable (on = 0
+ * restores normal scoring). */
+lst_status lst_test_skip_mma(lst_ctx ctx, int32_t on);
+
 /* Returns the event's slot to the context. */
 lst_status lst_event_release(lst_event ev);
 

@@ -40,9 +40,9 @@ __global__ void k_gather_tc(const EvDesc *, int, int *, int32_t *, float *, uint
 __global__ void k_graph_rows(const EvDesc *, int, int32_t *);
 __global__ void k_graph_fill(const EvDesc *, DevGeom, int, const int32_t *, int32_t *, float *, float *);
 cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
-                                     const float *, int, int *, long long, bool split);
+                                     const float *, int, int *, long long, bool split, int skip_mma);
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
-                                       const float *, int64_t, float *, int *, long long, bool split);
+                                       const float *, int64_t, float *, int *, long long, bool split, int skip_mma);
 int score_bf16_blocks_per_sm(bool split);
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
 }  // namespace lstk
@@ -143,6 +143,7 @@ struct lst_ctx_s {
   uint16_t *d_wpack = nullptr;   // BF16 weights in the tensor-core operand layout
   int *d_err = nullptr;          // device error word (bounded waits of the tensor-core kernel)
   long long wait_limit = 1ll << 26;
+  int skip_mma = 0;                // test aid: the tensor-core score kernels issue no MMA
   int grid_bf[2] = {0, 0};   // tensor-core score grid: plain BF16, split BF16
   std::vector<Slot> slots;
   std::vector<Lane> lanes;     // lane 0: lst_run_event; lanes 1..: batches, round robin
@@ -373,7 +374,8 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   mark(5);
   if (c->cfg.precision != LST_FP32)
     CU(launch_score_bf16_events(c->grid_bf[c->cfg.precision == LST_BF16X3], st, L.d_desc, n, g, c->cuts, c->d_wpack,
-                                c->d_w, c->n_hidden, c->d_err, c->wait_limit, c->cfg.precision == LST_BF16X3));
+                                c->d_w, c->n_hidden, c->d_err, c->wait_limit, c->cfg.precision == LST_BF16X3,
+                                c->skip_mma));
   else
     k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
         L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
@@ -683,7 +685,8 @@ lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float 
     S.busy = true;
     lst_event ev = new lst_event_s{c, si, es};
     *out = ev;
-    if (es != LST_OK) return fail(es, "invalid hit in input (sensor id or coordinate)");
+    if (es == LST_ERR_INPUT) return fail(es, "invalid hit in input (sensor id or coordinate)");
+    if (es != LST_OK) return fail(es, "a bounded device wait ran out (tensor-core score)");
     return LST_OK;
   }
   return fail(LST_ERR_CAPACITY, "object buffers kept overflowing");
@@ -912,7 +915,7 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
     const bool split = precision == LST_BF16X3;
     const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->grid_bf[split]);
     CU(launch_score_bf16_features(grid, st, c->g, c->cuts, c->d_wpack, c->d_w, c->n_hidden, feat, n, score_out,
-                                  c->d_err, c->wait_limit, split));
+                                  c->d_err, c->wait_limit, split, c->skip_mma));
   } else {
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->grid_sc);
     k_score_feat_fp32<<<grid, 256, (size_t)c->n_w * 4, st>>>(feat, n, c->d_w, c->n_hidden, score_out);
@@ -999,6 +1002,18 @@ lst_status lst_device_errors(lst_ctx c) {
   CU(cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
   CU(cudaMemset(c->d_err, 0, sizeof e));
   if (e) return fail((lst_status)e, "a bounded device wait ran out (tensor-core score)");
+  return LST_OK;
+}
+
+lst_status lst_test_skip_mma(lst_ctx c, int32_t on) {
+  if (!c) return fail(LST_ERR_ARG, "null ctx");
+  DeviceGuard gd(c->device);
+  CU(cudaDeviceSynchronize());
+  c->skip_mma = on ? 1 : 0;
+  for (auto &L : c->lanes) {                  // captured graphs hold the old kernel arguments
+    for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+    L.graphs.clear();
+  }
   return LST_OK;
 }
 

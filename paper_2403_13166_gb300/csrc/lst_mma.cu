@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
                                                    const float *__restrict__ wflat, int n_hidden,
                                                    const float *__restrict__ feat_in, int64_t n_rows,
                                                    float *__restrict__ score_out, int *err,
-                                                   long long wait_limit) {
+                                                   long long wait_limit, int skip_mma) {
   constexpr int NP = SPLIT ? 2 : 1;
   __shared__ __align__(1024) unsigned char sA[NP * A_BYTES];      // 12 KB per part
   __shared__ __align__(1024) unsigned char sW[NP * W_ELEMS * 2];  // 9 KB per part
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
       const int K = l == 0 ? K1 : 32;
       const uint32_t wofs = l == 0 ? 0 : (uint32_t)(32 * K1 * 2 + (l - 1) * 32 * 32 * 2);
       const uint32_t dcol = tmem;
-      if (tid == 0 && !s_abort) {
+      if (tid == 0 && !s_abort && !skip_mma) {   // skip_mma (test aid): nothing arrives on mbar
         fence_after();
         for (int k = 0; k < K / 16; k++) {
           const uint64_t da = make_desc(aA + k * 256, 128, (K / 8) * 128);
@@ -285,24 +285,24 @@ __global__ void __launch_bounds__(128) k_score_bf16(const EvDesc *__restrict__ e
 // Host-side launchers (kernel template instances stay in this translation unit).
 cudaError_t launch_score_bf16_events(int grid, cudaStream_t st, const EvDesc *evs, int n_events, DevGeom g,
                                      lst_cuts c, const uint16_t *wpack, const float *wflat, int n_hidden, int *err,
-                                     long long wait_limit, bool split) {
+                                     long long wait_limit, bool split, int skip_mma) {
   if (split)
     k_score_bf16<true, true><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr,
-                                                   err, wait_limit);
+                                                   err, wait_limit, skip_mma);
   else
     k_score_bf16<true, false><<<grid, 128, 0, st>>>(evs, n_events, g, c, wpack, wflat, n_hidden, nullptr, 0, nullptr,
-                                                    err, wait_limit);
+                                                    err, wait_limit, skip_mma);
   return cudaGetLastError();
 }
 cudaError_t launch_score_bf16_features(int grid, cudaStream_t st, DevGeom g, lst_cuts c, const uint16_t *wpack,
                                        const float *wflat, int n_hidden, const float *feat, int64_t n, float *out,
-                                       int *err, long long wait_limit, bool split) {
+                                       int *err, long long wait_limit, bool split, int skip_mma) {
   if (split)
     k_score_bf16<false, true><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err,
-                                                    wait_limit);
+                                                    wait_limit, skip_mma);
   else
     k_score_bf16<false, false><<<grid, 128, 0, st>>>(nullptr, 0, g, c, wpack, wflat, n_hidden, feat, n, out, err,
-                                                     wait_limit);
+                                                     wait_limit, skip_mma);
   return cudaGetLastError();
 }
 // Resident CTAs per SM of the score kernel, from its own footprint: registers (allocated

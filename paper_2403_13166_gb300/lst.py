@@ -87,6 +87,9 @@ _SIGS = {
     "lst_event_release": [C.c_void_p],
     "lst_destroy": [C.c_void_p],
     "lst_set_timing": [C.c_void_p, C.c_int32],
+    "lst_set_wait_limit": [C.c_void_p, C.c_int64],
+    "lst_device_errors": [C.c_void_p],
+    "lst_test_skip_mma": [C.c_void_p, C.c_int32],
     "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p],
@@ -289,7 +292,7 @@ class Context:
         ev = C.c_void_p()
         st = lib.lst_run_event(self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(sensor), n, _stream_handle(stream),
                                C.byref(ev))
-        _check(st, "lst_run_event", ok=(LST_OK, LST_ERR_INPUT))
+        _check(st, "lst_run_event", ok=(LST_OK, LST_ERR_INPUT, LST_ERR_TIMEOUT))
         return Event(self, ev, st)
 
     def run_batch(self, events, stream=None):
@@ -334,6 +337,17 @@ class Context:
         cur.update(kw)
         p = lst_launch(**cur)
         _check(load_library().lst_set_launch(self.h, C.byref(p)), "lst_set_launch")
+
+    def set_wait_limit(self, iterations: int):
+        _check(load_library().lst_set_wait_limit(self.h, int(iterations)), "lst_set_wait_limit")
+
+    def test_skip_mma(self, on=True):
+        """Failure-handling test aid: the tensor-core score kernels issue no MMA, so their
+        bounded waits run out (LST_ERR_TIMEOUT) with nothing in flight."""
+        _check(load_library().lst_test_skip_mma(self.h, int(on)), "lst_test_skip_mma")
+
+    def device_errors(self) -> int:
+        return load_library().lst_device_errors(self.h)
 
     def set_timing(self, on=True):
         _check(load_library().lst_set_timing(self.h, int(on)), "lst_set_timing")
