@@ -56,3 +56,30 @@ def test_structs_match_header_layout(libpath):
     assert ctypes.sizeof(lst.lst_config) == 32
     assert ctypes.sizeof(lst.lst_counts) == 10 * 8 + 8 + 8
     assert ctypes.sizeof(lst.lst_launch) == 8 * 4
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Every struct of include/lst.h, compiled by gcc: size and the offset of every field
+    must equal the binding's ctypes layout."""
+    from paper_2403_13166_gb300 import lst
+    structs = {"lst_module": lst.lst_module, "lst_cuts": lst.lst_cuts, "lst_mlp": lst.lst_mlp,
+               "lst_config": lst.lst_config, "lst_counts": lst.lst_counts, "lst_launch": lst.lst_launch,
+               "lst_serve_config": lst.lst_serve_config, "lst_serve_result": lst.lst_serve_result}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lst.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        sname, field, value = line.split()
+        got[(sname, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
