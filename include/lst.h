@@ -175,6 +175,15 @@ lst_status lst_event_counts(lst_event ev, lst_counts *out);
 lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score,
                               uint8_t *selected, int64_t capacity, int64_t *n_out);
 
+/* Batched form of lst_get_candidates for n events of one context (typically the events of
+ * one lst_run_batch): the objects of every event, concatenated in event order, with
+ * offsets[i] .. offsets[i+1] the rows of event i (offsets HOST [n + 1], always set). One
+ * synchronisation for the whole batch; with HOST buffers one copy per array (use pinned
+ * memory for full link bandwidth). Events whose status is not LST_OK contribute no rows.
+ * LST_ERR_CAPACITY (nothing copied) if capacity < offsets[n]. */
+lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kind, int32_t *hit_idx,
+                                    float *score, uint8_t *selected, int64_t capacity, int64_t *offsets);
+
 /* The event's LS graph, the GNN input that Section 4 proposes to build with LST: nodes are
  * the MDs (ids = the order of lst_get_candidates(LST_MD)), directed edges the LSs from
  * inner to outer MD, in CSR form by inner MD:

@@ -820,6 +820,74 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
   return LST_OK;
 }
 
+lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kind, int32_t *hit_idx, float *score,
+                                    uint8_t *selected, int64_t capacity, int64_t *offsets) {
+  if (!evs || n < 1 || !offsets) return fail(LST_ERR_ARG, "null argument or n < 1");
+  if (kind < LST_MD || kind > LST_TC) return fail(LST_ERR_ARG, "bad kind");
+  lst_ctx c = evs[0] ? evs[0]->ctx : nullptr;
+  if (!c) return fail(LST_ERR_ARG, "null event");
+  for (int i = 0; i < n; i++)
+    if (!evs[i] || evs[i]->ctx != c) return fail(LST_ERR_ARG, "events of one context expected");
+  DeviceGuard gd(c->device);
+  const int cs[5] = {C_MD, C_LS, C_T3, C_T5, C_NTC};
+  std::vector<EvDesc> desc(n);
+  offsets[0] = 0;
+  for (int i = 0; i < n; i++) {
+    lst_status s = wait_event(evs[i]);
+    if (s != LST_OK) return s;
+    const Slot &S = c->slots[evs[i]->slot];
+    desc[i] = S.d;
+    const int64_t k = evs[i]->status == LST_OK ? S.cnt[cs[kind]] : 0;
+    offsets[i + 1] = offsets[i] + k;
+  }
+  const int64_t total = offsets[n];
+  if (capacity < total) return fail(LST_ERR_CAPACITY, "output capacity below object count");
+  if (total == 0) return LST_OK;
+  if (!hit_idx) return fail(LST_ERR_ARG, "hit_idx is NULL");
+  const int width = kind == LST_MD ? 2 : kind == LST_LS ? 4 : kind == LST_T3 ? 6 : 10;
+  const bool t5like = kind == LST_T5 || kind == LST_TC;
+  const bool dev_out = is_device_ptr(hit_idx);
+  // device staging: descriptors, TC counters, and (host destination) the gathered arrays
+  const size_t b_desc = align_up(sizeof(EvDesc) * (size_t)n, 256), b_cnt = align_up(4 * (size_t)n, 256);
+  const size_t b_idx = dev_out ? 0 : align_up((size_t)total * width * 4, 256);
+  const size_t b_sc = dev_out ? 0 : align_up((size_t)total * 4, 256);
+  const size_t b_sel = dev_out ? 0 : align_up((size_t)total, 256);
+  void *tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, b_desc + b_cnt + b_idx + b_sc + b_sel, c->aux));
+  char *p = (char *)tmp;
+  EvDesc *d_desc = (EvDesc *)p;
+  int *d_cnt = (int *)(p + b_desc);
+  int32_t *d_idx = dev_out ? hit_idx : (int32_t *)(p + b_desc + b_cnt);
+  float *d_sc = dev_out ? score : (float *)(p + b_desc + b_cnt + b_idx);
+  uint8_t *d_sel = dev_out ? selected : (uint8_t *)(p + b_desc + b_cnt + b_idx + b_sc);
+  CU(cudaMemcpyAsync(d_desc, desc.data(), sizeof(EvDesc) * (size_t)n, cudaMemcpyHostToDevice, c->aux));
+  CU(cudaMemsetAsync(d_cnt, 0, 4 * (size_t)n, c->aux));
+  for (int i = 0; i < n; i++) {
+    const int64_t k = offsets[i + 1] - offsets[i];
+    if (k == 0) continue;
+    int32_t *o = d_idx + offsets[i] * width;
+    float *sc = t5like && d_sc ? d_sc + offsets[i] : nullptr;
+    uint8_t *se = t5like && d_sel ? d_sel + offsets[i] : nullptr;
+    if (kind == LST_TC) {
+      const int n5 = c->slots[evs[i]->slot].cnt[C_T5];
+      const int grid = (int)std::min<int64_t>((n5 + 255) / 256, 4 * c->n_sm);
+      k_gather_tc<<<std::max(grid, 1), 256, 0, c->aux>>>(d_desc + i, n5, d_cnt + i, o, sc, se);
+    } else {
+      const int grid = (int)std::min<int64_t>((k + 255) / 256, 4 * c->n_sm);
+      k_gather<<<grid, 256, 0, c->aux>>>(d_desc + i, kind, (int)k, o, sc, se);
+    }
+  }
+  CU(cudaGetLastError());
+  if (!dev_out) {
+    CU(cudaMemcpyAsync(hit_idx, d_idx, (size_t)total * width * 4, cudaMemcpyDeviceToHost, c->aux));
+    if (t5like && score) CU(cudaMemcpyAsync(score, d_sc, (size_t)total * 4, cudaMemcpyDeviceToHost, c->aux));
+    if (t5like && selected) CU(cudaMemcpyAsync(selected, d_sel, (size_t)total, cudaMemcpyDeviceToHost, c->aux));
+  }
+  CU(cudaFreeAsync(tmp, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+
 lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float *node_feat, float *edge_feat,
                            int64_t node_cap, int64_t edge_cap, int64_t *n_nodes, int64_t *n_edges) {
   if (!ev || !n_nodes || !n_edges) return fail(LST_ERR_ARG, "null argument");

@@ -81,6 +81,8 @@ _SIGS = {
     "lst_get_candidates": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                            C.POINTER(C.c_int64)],
     "lst_get_t5_features": [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)],
+    "lst_get_candidates_batch": [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_void_p],
     "lst_get_ls_graph": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                          C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "lst_score_t5": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p],
@@ -309,6 +311,30 @@ class Context:
         _check(lib.lst_run_batch(self.h, n, xs, ys, zs, ss, nh, _stream_handle(stream), out),
                "lst_run_batch")
         return [Event(self, C.c_void_p(out[i]), LST_ERR_NOT_READY) for i in range(n)]
+
+    def candidates_batch(self, events, kind: int, out=None, score=None, selected=None):
+        """Objects of several events in one call (lst_get_candidates_batch): returns (hits,
+        score, selected, offsets) with rows offsets[i]:offsets[i+1] for events[i]. Pass
+        preallocated (e.g. pinned) numpy buffers or torch CUDA tensors to avoid allocation;
+        they must hold all rows."""
+        lib = load_library()
+        n = len(events)
+        handles = (C.c_void_p * n)(*[e.h for e in events])
+        offs = np.zeros(n + 1, np.int64)
+        st = lib.lst_get_candidates_batch(handles, n, kind, None, None, None, 0, _ptr(offs))
+        _check(st, "lst_get_candidates_batch", ok=(LST_OK, LST_ERR_CAPACITY))
+        total = int(offs[-1])
+        t5like = kind in (LST_T5, LST_TC)
+        if out is None:
+            out = np.zeros((total, WIDTH[kind]), np.int32)
+            if t5like:
+                score = np.zeros(total, np.float32)
+                selected = np.zeros(total, np.uint8)
+        cap = int(out.shape[0])
+        if total:
+            _check(lib.lst_get_candidates_batch(handles, n, kind, _ptr(out), _ptr(score), _ptr(selected), cap,
+                                                _ptr(offs)), "lst_get_candidates_batch")
+        return out, score, selected, offs
 
     def score_t5(self, feat, out, precision=LST_FP32, stream=None):
         lib = load_library()

@@ -200,6 +200,30 @@ def test_batch_equals_single_and_graph_replay(ctx_full, geom_full, cuts, model):
     h.release()
 
 
+def test_batched_export_equals_per_event_export(ctx_full, geom_full):
+    evs = [synth.pileup_event(geom_full, i, pileup=pu, mean_per_vertex=96, config=4)
+           for i, pu in enumerate((40, 5, 0, 90))]
+    hs = ctx_full.run_batch([dev(e) for e in evs])
+    for kind in (lst.LST_LS, lst.LST_T5, lst.LST_TC):
+        out, score, sel, offs = ctx_full.candidates_batch(hs, kind)
+        assert offs[0] == 0 and len(out) == offs[-1]
+        d_out = torch.zeros((int(offs[-1]) + 7, lst.WIDTH[kind]), dtype=torch.int32, device="cuda")
+        _, _, _, offs2 = ctx_full.candidates_batch(hs, kind, d_out)
+        assert np.array_equal(offs, offs2)
+        dev_rows = d_out.cpu().numpy()
+        for i, h in enumerate(hs):
+            single = h.candidates(kind)
+            single = single[0] if kind in (lst.LST_T5, lst.LST_TC) else single
+            rows = out[offs[i]:offs[i + 1]]
+            assert np.array_equal(np.sort(rows, axis=0), np.sort(single, axis=0))
+            if kind != lst.LST_TC:   # the track-candidate gather has no fixed order
+                assert np.array_equal(dev_rows[offs[i]:offs[i + 1]], rows)
+            else:
+                assert np.array_equal(np.sort(dev_rows[offs[i]:offs[i + 1]], axis=0), np.sort(rows, axis=0))
+    for h in hs:
+        h.release()
+
+
 def test_host_inputs_match_device_inputs(ctx_full, geom_full, cuts, model):
     e = synth.pileup_event(geom_full, 6, pileup=25, mean_per_vertex=96)
     ref = oracle.run_event(geom_full, e, cuts, *model)
