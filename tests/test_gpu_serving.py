@@ -11,7 +11,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [lst.LST_FP32, lst.LST_BF16])
+def _overlapping(results):
+    """Pairs of requests whose [t_admit, t_done] intervals overlap (both on the GPU side)."""
+    r = sorted(results, key=lambda x: x["t_admit"])
+    return sum(1 for i in range(len(r)) for j in range(i + 1, len(r)) if r[j]["t_admit"] < r[i]["t_done"])
+
+
+@pytest.mark.parametrize("precision", [lst.LST_FP32, lst.LST_BF16, lst.LST_BF16X3])
 def test_served_results_equal_alone(geom_full, cuts, precision):
     w = synth.mlp_flat(synth.xavier_mlp())
     events = [synth.pileup_event(geom_full, i, pileup=pu, mean_per_vertex=96, config=5)
@@ -52,6 +58,32 @@ def test_served_results_equal_alone(geom_full, cuts, precision):
         o = np.lexsort(hh.T[::-1]) if len(hh) else np.zeros(0, int)
         assert np.array_equal(hh[o], h)
         assert np.array_equal(r["t5_score"][o], s)      # bit-identical: each row scored alone
+    assert _overlapping(list(results.values())) > 0   # requests were in flight together
+
+
+def test_memory_budget_admits_one_event_at_a_time(geom_full, cuts):
+    """With a budget below one event's estimated object-buffer memory, an event is only
+    admitted when nothing else is in flight; with a large budget they overlap."""
+    w = synth.mlp_flat(synth.xavier_mlp())
+    events = [synth.pileup_event(geom_full, i, pileup=pu, mean_per_vertex=96, config=5)
+              for i, pu in enumerate((150, 60, 180, 90, 120, 30))]
+    out = {}
+    for budget in (1, 64 << 30):
+        ctx = lst.Context(0, max_events=8, precision=lst.LST_BF16X3)
+        ctx.load_geometry(geom_full, cuts, w, 2)
+        srv = lst.Server(ctx, max_batch=4, lanes=2, mem_budget_bytes=budget, copy_t5=False)
+        for k, e in enumerate(events):
+            srv.submit(e.x, e.y, e.z, e.sensor, tag=k)
+        res = []
+        deadline = time.time() + 60
+        while len(res) < len(events) and time.time() < deadline:
+            res.extend(srv.poll(wait_ms=50))
+        srv.stop()
+        ctx.close()
+        assert len(res) == len(events) and all(r["status"] == lst.LST_OK for r in res)
+        out[budget] = _overlapping(res)
+    assert out[1] == 0
+    assert out[64 << 30] > 0
 
 
 def test_serve_rejects_bad_config(geom_full, cuts):
