@@ -368,6 +368,8 @@ def run_gpu(args, rank, world, local_rank, pool):
     roofline = roofline_entry(names[dom], float(stage_ms[dom]), B, mean_counts, pairs, float(np.mean(n_hits)),
                               clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
     roofline["stage_ms_per_launch"] = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
+    step = step_roofline(mean_counts, pairs, float(np.mean(n_hits)), float(np.mean(np.diff(g.map_off))),
+                         value, clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
     if graph is not None:   # the graph build inside the batched launch: grouping, MD and LS stages
         graph["build_ms_per_event_batched"] = round(float(stage_ms[0] + stage_ms[1] + stage_ms[2]) / B, 4)
     roofline["launches_timed"] = int(n_launch)
@@ -390,6 +392,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         "ls_graph": graph,
         "e2e": e2e,
         "roofline": roofline,
+        "step_roofline": step,
         "clocks": clk.summary(),
         "gpu_launches": KERNELS_PER_LAUNCH * args.steps,
     }
@@ -494,6 +497,34 @@ def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": None, "kernel": f"k_{stage}",
             "peak_note": "measured" if peaks else "fallback"}
+
+
+# Whole-step algorithmic work per event (every object read once per consuming stage and
+# written once; MDs read once as inner and once per module-map link as targets), and FP32
+# operations of the cut expression trees per candidate pair plus the network per T5.
+STEP_OPS_PER_PAIR = (25, 45, 40, 70)     # MD, LS, T3, T5
+MLP_FLOP_PER_T5 = 4544
+
+
+def step_roofline(counts, pairs, hits, fan, events_per_s, clocks, n_sm):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    by = (hits * (16 + 20 + 20) + counts["md"] * (28 + 28 * (1 + fan)) + counts["ls"] * (12 + 24)
+          + counts["t3"] * (12 + 24) + counts["t5"] * (20 + 5 * 16 + 5))
+    ops = sum(float(p) * k for p, k in zip(pairs, STEP_OPS_PER_PAIR)) + MLP_FLOP_PER_T5 * counts["t5"]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    gbs = by * events_per_s / 1e9
+    tops = ops * events_per_s / 1e12
+    return {"alg_bytes_per_event": int(by), "alg_fp32_ops_per_event": int(ops),
+            "achieved_GBs": round(gbs, 1), "hbm_peak_GBs": hbm, "hbm_frac": round(gbs / hbm, 4),
+            "achieved_TOPs": round(tops, 3), "alu_peak_TOPs": round(alu, 2), "alu_frac": round(tops / alu, 4),
+            "note": "mean module-map fan-out %.1f; FP32 ops per candidate pair MD/LS/T3/T5 = %s" % (
+                fan, "/".join(map(str, STEP_OPS_PER_PAIR)))}
 
 
 # ------------------------------------------------------------------ reference arm: the oracle
