@@ -176,7 +176,7 @@ namespace {
 constexpr int LS_IN_CHUNK_HOST = 64;   // k_ls inner-MD tile (LS_IN_CHUNK)
 constexpr int LS_WARP_BYTES = 928;      // sizeof(LsWarp): per-warp target staging and pair queue
 size_t ls_smem(const lst_ctx_s *c) {
-  return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES + (size_t)LS_IN_CHUNK_HOST * (16 + 4 + 4 + 4) +
+  return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES + (size_t)LS_IN_CHUNK_HOST * (16 + 16 + 4 + 4 + 4) +
          (3 * MAX_FANOUT + 1) * 4 + (size_t)c->ls_list * 12;
 }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }

@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   LsWarp &w = reinterpret_cast<LsWarp *>(smem_raw)[wid];                 // [nwarps]
   float4 *s_in = reinterpret_cast<float4 *>(smem_raw + nwarps * sizeof(LsWarp));  // [LS_IN_CHUNK]
-  float *s_ink = reinterpret_cast<float *>(s_in + LS_IN_CHUNK);          // [LS_IN_CHUNK]
+  float4 *s_inx = s_in + LS_IN_CHUNK;                                    // [LS_IN_CHUNK] |A|^2, rA^2, e rA + slack
+  float *s_ink = reinterpret_cast<float *>(s_inx + LS_IN_CHUNK);         // [LS_IN_CHUNK]
   int *s_cnt = reinterpret_cast<int *>(s_ink + LS_IN_CHUNK);             // [LS_IN_CHUNK]
   int *s_off = s_cnt + LS_IN_CHUNK;                                      // [LS_IN_CHUNK]
   int *s_tpref = s_off + LS_IN_CHUNK;                                    // [MAX_FANOUT + 1]
@@ -304,6 +305,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
   LsEntry *s_list = reinterpret_cast<LsEntry *>(s_tbar + MAX_FANOUT);    // [list_cap]
   __shared__ int s_unit, s_nin, s_nlist, s_base;
   const int total = n_events * g.n_mod;
+  const float k0 = 1.002f * 65.0f * (c.hit_err * c.hit_err), c1 = c.z_lum + c.hit_err;
   for (;;) {
     // One thread fetches the unit and reads the event's state; the whole CTA then uses
     // that one copy (the overflow flag may change under other CTAs at any time, and every
@@ -348,11 +350,14 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       if (lane == 0) s_tpref[0] = 0;
     }
     // the first chunk of inner MDs is loaded while warp 0 builds the target prefix
-    for (int t = threadIdx.x; t < min(LS_IN_CHUNK, n_in); t += blockDim.x) {
-      s_in[t] = ev.md_anchor[in0 + t];
-      s_ink[t] = ev.md_kappa[in0 + t].x;
+    auto load_inner = [&](int t, int i) {
+      const float4 A = ev.md_anchor[i];
+      s_in[t] = A;
+      s_inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
+      s_ink[t] = ev.md_kappa[i].x;
       s_cnt[t] = 0;
-    }
+    };
+    for (int t = threadIdx.x; t < min(LS_IN_CHUNK, n_in); t += blockDim.x) load_inner(t, in0 + t);
     if (threadIdx.x == 0) s_nlist = 0;
     __syncthreads();
     const int S = s_tpref[nt];
@@ -360,11 +365,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
     for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
       const int nc = min(LS_IN_CHUNK, n_in - c0);
       if (c0 > 0) {
-        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-          s_in[t] = ev.md_anchor[in0 + c0 + t];
-          s_ink[t] = ev.md_kappa[in0 + c0 + t].x;
-          s_cnt[t] = 0;
-        }
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) load_inner(t, in0 + c0 + t);
         if (threadIdx.x == 0) s_nlist = 0;
         __syncthreads();
       }
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           const int j = j0 + lane;
           bool valid = j < S;
           float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-          float kB = 0.0f, X = 0.0f;
+          float kB = 0.0f, k1 = 0.0f;
           bool bB = false;
           int md = 0;
           if (valid) {
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               B = ev.md_anchor[md];
               kB = ev.md_kappa[md].x;
               bB = s_tbar[t] != 0;
-              X = B.w * (0.5f * c.kappa_max);
+              const float X = B.w * (0.5f * c.kappa_max);
+              k1 = 1.002f * 1.015625f * X * X;
             } else {
               valid = false;
             }
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           int qn = 0;
 #pragma unroll 2
           for (int i = 0; i < nc; i++) {
-            const bool cand = valid & ls_prefilter(s_in[i], B, X, c);
+            const bool cand = valid & ls_prefilter(s_in[i], s_inx[i], B, k1, k0, c1);
             const unsigned bal = __ballot_sync(FULL, cand);
             if (cand) w.q[qn + __popc(bal & lanemask_lt())] = (unsigned short)((i << 5) | lane);
             qn += __popc(bal);
