@@ -180,7 +180,7 @@ size_t ls_smem(const lst_ctx_s *c) {
          (3 * MAX_FANOUT + 1) * 4 + (size_t)c->ls_list * 12;
 }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
-size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * (2 * 512 + 4 * 128 + 2 * 256); }
+size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * 3584; }   // sizeof(T3Warp)
 size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
 int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
 

@@ -502,16 +502,18 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
 
 // ===================================================================== steps 3 and 4
 // Both enumerate pairs (X1, X2) where X2 ranges over a contiguous list attached to the
-// middle MD of X1. A warp takes 32 consecutive X1 (one per lane, with its list length);
+// middle MD of X1. A warp takes 32 (T5) or 64 (T3: two per lane) consecutive X1 with their
+// list lengths;
 // an inclusive warp scan of the lengths maps each flat pair index to (X1, X2) by a binary
 // search in the warp's shared copy of the scan. Work is spread by static striding over
-// chunks of 32 X1 of all events (no atomics); pair counts are summed per warp and flushed
+// chunks of X1 of all events (no atomics); pair counts are summed per warp and flushed
 // once per event.
 struct T3Warp {
-  float4 P0[32], P1[32];
-  int incl[32], st2[32], md0[32], md1[32];
-  int qx[64], qmd[64];   // queue of pairs that passed t3_prefilter
+  float4 P0[64], P1[64];             // 64 first LSs per warp chunk: lanes lane and 32 + lane
+  int incl[64], st2[64], md0[64], md1[64];
+  int qx[64], qmd[64];               // queue of pairs that passed t3_prefilter
 };
+static_assert(sizeof(T3Warp) == 3584, "the host sizes k_t3 shared memory with 3584 bytes per warp");
 
 __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
   T3Warp &w = reinterpret_cast<T3Warp *>(smem_raw)[wid];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 31) / 32;
+    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 63) / 64;
   }, s_pref);
   const int total = s_pref[n_events];
   const int W = gridDim.x * nwarps;
@@ -534,21 +536,28 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     }
     const EvDesc &ev = evs[e];
     const int nls = clamp_count(ev.cnt[C_LS], ev.ls_cap);
-    const int l1 = (u - s_pref[e]) * 32 + lane;
-    int deg = 0;
-    if (l1 < nls) {
-      const int md0 = ev.ls_in[l1], md1 = ev.ls_out[l1];
-      deg = ev.ls_cnt[md1];
-      w.st2[lane] = ev.ls_start[md1];
-      w.md0[lane] = md0;
-      w.md1[lane] = md1;
-      w.P0[lane] = ev.md_anchor[md0];
-      w.P1[lane] = ev.md_anchor[md1];
+    // two first LSs per lane (slots lane and 32 + lane), their loads independent
+    int deg[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int l1 = (u - s_pref[e]) * 64 + 32 * h + lane;
+      if (l1 < nls) {
+        const int md0 = ev.ls_in[l1], md1 = ev.ls_out[l1];
+        deg[h] = ev.ls_cnt[md1];
+        w.st2[32 * h + lane] = ev.ls_start[md1];
+        w.md0[32 * h + lane] = md0;
+        w.md1[32 * h + lane] = md1;
+        w.P0[32 * h + lane] = ev.md_anchor[md0];
+        w.P1[32 * h + lane] = ev.md_anchor[md1];
+      }
     }
-    const int inc = warp_incl_scan(deg);
-    w.incl[lane] = inc;
+    const int inca = warp_incl_scan(deg[0]);
+    const int tota = __shfl_sync(FULL, inca, 31);
+    const int incb = tota + warp_incl_scan(deg[1]);
+    w.incl[lane] = inca;
+    w.incl[32 + lane] = incb;
     __syncwarp();
-    const int tot = __shfl_sync(FULL, inc, 31);
+    const int tot = __shfl_sync(FULL, incb, 31);
     acc += tot;
     // exact cut on queued pairs [q0, q0 + n): (LS1 lane, outer MD)
     auto run_queue = [&](int q0, int n) {
@@ -575,7 +584,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     // flat pair index f -> (LS1 lane x, outer MD); two pairs per lane and iteration so that
     // the two dependent load chains (ls_out, then the anchor) are in flight together
     auto decode = [&](int f, int &x) {
-      int lo = 0, hi = 31;
+      int lo = 0, hi = 63;
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
       x = lo;
       const int prev = lo ? w.incl[lo - 1] : 0;
