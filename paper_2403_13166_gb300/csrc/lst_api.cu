@@ -22,7 +22,9 @@ __global__ void k_bin_scatter(const EvDesc *, DevGeom);
 __global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts);
 __global__ void k_md_scan(const EvDesc *, DevGeom);
 __global__ void k_md_scatter(const EvDesc *, int);
-__global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, int);
+__global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, const int32_t *, int, int);
+__global__ void k_ls_scan(const EvDesc *);
+__global__ void k_ls_scatter(const EvDesc *, int);
 __global__ void k_t3(const EvDesc *, int, lst_cuts);
 __global__ void k_t3_scan(const EvDesc *);
 __global__ void k_t3_scatter(const EvDesc *, int);
@@ -136,6 +138,8 @@ struct lst_ctx_s {
   DevGeom g{};
   int8_t *d_subdet = nullptr, *d_layer = nullptr;
   int32_t *d_map_off = nullptr, *d_map_tgt = nullptr;
+  int32_t *d_ls_units = nullptr;  // [n_mod + 1] prefix of step-2 units per module for small launches
+  int ls_units_per_event = 0;
   lst_cuts cuts{};
   int n_hidden = 2;
   float *d_w = nullptr;
@@ -173,12 +177,9 @@ struct lst_event_s {
 
 namespace {
 
-constexpr int LS_IN_CHUNK_HOST = 64;   // k_ls inner-MD tile (LS_IN_CHUNK)
-constexpr int LS_WARP_BYTES = 928;      // sizeof(LsWarp): per-warp target staging and pair queue
-size_t ls_smem(const lst_ctx_s *c) {
-  return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES + (size_t)LS_IN_CHUNK_HOST * (16 + 16 + 4 + 4 + 4) +
-         (3 * MAX_FANOUT + 1) * 4 + (size_t)c->ls_list * 12;
-}
+constexpr int LS_WARP_BYTES = 4688;     // sizeof(LsWarp): each warp's targets, inner MDs and pair queue
+constexpr int LS_SMALL_TB = 8;          // target modules per step-2 unit in small launches
+size_t ls_smem(const lst_ctx_s *c) { return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES; }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
 size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * 3584; }   // sizeof(T3Warp)
 size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
@@ -247,6 +248,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
                o_umod = take(4 * (size_t)md), o_uh = take(8 * (size_t)md);
   const size_t o_lin = take(4 * (size_t)ls), o_lout = take(4 * (size_t)ls), o_lk = take(4 * (size_t)ls),
                o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
+  const size_t o_luin = take(4 * (size_t)ls), o_luout = take(4 * (size_t)ls), o_luk = take(4 * (size_t)ls),
+               o_lcur = take(4 * (size_t)md);
   const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
                o_t3c = take(4 * (size_t)md), o_t3u = take(16 * (size_t)t3), o_t3uk = take(4 * (size_t)t3);
   const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
@@ -271,6 +274,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   d.mdu_mod = (int32_t *)(b + o_umod); d.mdu_hits = (int2 *)(b + o_uh);
   d.ls_in = (int32_t *)(b + o_lin); d.ls_out = (int32_t *)(b + o_lout); d.ls_kappa = (float *)(b + o_lk);
   d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
+  d.lsu_in = (int32_t *)(b + o_luin); d.lsu_out = (int32_t *)(b + o_luout); d.lsu_kappa = (float *)(b + o_luk);
+  d.ls_cur = (int32_t *)(b + o_lcur);
   d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_pos = (int32_t *)(b + o_t3s);
   d.t3_cnt = (int32_t *)(b + o_t3c); d.t3u_md = (int4 *)(b + o_t3u); d.t3u_kappa = (float *)(b + o_t3uk);
   d.t5_a = (int4 *)(b + o_t5a); d.t5_b = (int4 *)(b + o_t5b); d.t5_score = (float *)(b + o_t5s);
@@ -364,7 +369,19 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   k_md_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
   k_md_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
   mark(2);
-  k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->ls_list);
+  {
+    // few events: units of LS_SMALL_TB target modules, so that dense modules spread over
+    // several warps; many events: one unit per module
+    const bool small = (long long)n * g.n_mod < 16ll * c->grid_ls * (c->ls_threads / 32);
+    if (small)
+      k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, c->d_ls_units,
+                                                         c->ls_units_per_event, LS_SMALL_TB);
+    else
+      k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, nullptr, g.n_mod,
+                                                         0);
+  }
+  k_ls_scan<<<n, 1024, 0, st>>>(L.d_desc);
+  k_ls_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
   mark(3);
   k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts);
   k_t3_scan<<<n, 1024, 0, st>>>(L.d_desc);
@@ -401,10 +418,11 @@ void grow_ratios(lst_ctx_s *c, const Slot &s, const int32_t *cnt) {
   const int f = cnt[C_FLAGS];
   const double n = std::max<double>(1.0, (double)s.n_hits);
   const double nmd = std::max<double>(1.0, std::ceil(c->r_md * n) + 256);
-  if (f & F_OVF_MD) c->r_md = std::max(c->r_md, (float)(1.3 * cnt[C_MD] / n));
-  if (f & F_OVF_LS) c->r_ls = std::max(c->r_ls, (float)(1.3 * cnt[C_LS] / nmd));
-  if (f & F_OVF_T3) c->r_t3 = std::max(c->r_t3, (float)(1.3 * cnt[C_T3] / nmd));
-  if (f & F_OVF_T5) c->r_t5 = std::max(c->r_t5, (float)(1.3 * cnt[C_T5] / nmd));
+  // the overflowed stage counted all its objects; at least double in any case
+  if (f & F_OVF_MD) c->r_md = std::max(2.0f * c->r_md, (float)(1.3 * cnt[C_MD] / n));
+  if (f & F_OVF_LS) c->r_ls = std::max(2.0f * c->r_ls, (float)(1.3 * cnt[C_LS] / nmd));
+  if (f & F_OVF_T3) c->r_t3 = std::max(2.0f * c->r_t3, (float)(1.3 * cnt[C_T3] / nmd));
+  if (f & F_OVF_T5) c->r_t5 = std::max(2.0f * c->r_t5, (float)(1.3 * cnt[C_T5] / nmd));
 }
 
 lst_status status_of(const int32_t *cnt) {
@@ -567,7 +585,9 @@ lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, c
     L.graphs.clear();
   }
   cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt); cudaFree(c->d_w);
+  cudaFree(c->d_ls_units);
   c->d_subdet = nullptr; c->d_layer = nullptr; c->d_map_off = nullptr; c->d_map_tgt = nullptr; c->d_w = nullptr;
+  c->d_ls_units = nullptr;
   std::vector<int8_t> sd(n_mod), ly(n_mod);
   for (int32_t m = 0; m < n_mod; m++) { sd[m] = (int8_t)mods[m].subdet; ly[m] = (int8_t)mods[m].layer; }
   CU(cudaMalloc(&c->d_subdet, n_mod));
@@ -578,6 +598,17 @@ lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, c
   CU(cudaMemcpy(c->d_layer, ly.data(), n_mod, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->d_map_off, map_off, 4 * ((size_t)n_mod + 1), cudaMemcpyHostToDevice));
   if (nl > 0) CU(cudaMemcpy(c->d_map_tgt, map_tgt, 4 * (size_t)nl, cudaMemcpyHostToDevice));
+  {
+    // step-2 units of small launches: LS_SMALL_TB target modules each (at least one per module)
+    std::vector<int32_t> uo((size_t)n_mod + 1, 0);
+    for (int32_t m = 0; m < n_mod; m++) {
+      const int32_t fan = map_off[m + 1] - map_off[m];
+      uo[m + 1] = uo[m] + std::max(1, (fan + LS_SMALL_TB - 1) / LS_SMALL_TB);
+    }
+    CU(cudaMalloc(&c->d_ls_units, 4 * ((size_t)n_mod + 1)));
+    CU(cudaMemcpy(c->d_ls_units, uo.data(), 4 * ((size_t)n_mod + 1), cudaMemcpyHostToDevice));
+    c->ls_units_per_event = uo[n_mod];
+  }
   c->n_hidden = nh;
   c->n_w = mlp_floats_host(nh);
   std::vector<float> w(c->n_w, 0.0f);
@@ -1018,6 +1049,7 @@ lst_status lst_destroy(lst_ctx c) {
     }
     for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); }
     cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt);
+    cudaFree(c->d_ls_units);
     cudaFree(c->d_w); cudaFree(c->scratch); cudaFree(c->d_wpack); cudaFree(c->d_err);
     if (c->aux) cudaStreamDestroy(c->aux);
   }

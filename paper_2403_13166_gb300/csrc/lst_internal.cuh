@@ -58,9 +58,12 @@ struct EvDesc {
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
   int32_t *md_cur;             // [n_mod] scatter cursor of the grouping
-  int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD
+  int32_t *lsu_in, *lsu_out;   // [ls_cap] LSs as found, any order
+  float *lsu_kappa;            // [ls_cap]
+  int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD, grouped by inner MD
   float *ls_kappa;             // [ls_cap]
   int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
+  int32_t *ls_cur;             // [md_cap] scatter cursor of the grouping
   int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, -), any order
   float *t3u_kappa;            // [t3_cap]
   int4 *t3_md;                 // [t3_cap] T3s grouped by first MD
@@ -438,6 +441,15 @@ __device__ __forceinline__ int clamp_count(int n, int cap) { return n < cap ? n 
 
 // An event whose input was invalid or whose buffers overflowed is skipped by every later
 // stage (its results are void and the host re-runs it with larger buffers).
+// Events voided before a stage starts: an invalid input or an overflow of an earlier stage
+// (`earlier`). Those flags are final when the stage's kernel starts, so every CTA of it sees
+// the same set and the per-event work prefixes agree between CTAs. A stage's own overflow
+// voids the event only for the host; the stage keeps counting its objects without storing
+// them, which tells the host how far to grow the buffer.
+__device__ __forceinline__ bool ev_void_before(const EvDesc &ev, int earlier) {
+  return (ev.cnt[C_FLAGS] & (F_INPUT | earlier)) != 0;
+}
+
 __device__ __forceinline__ bool ev_void(const EvDesc &ev) {
   return (ev.cnt[C_FLAGS] & (F_INPUT | F_OVF_MD | F_OVF_LS | F_OVF_T3 | F_OVF_T5 | F_CHECK)) != 0;
 }

@@ -268,112 +268,107 @@ __global__ void k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
 }
 
 // ===================================================================== step 2: line segments
-// One CTA per (event, module m). The target MDs (all MDs of the modules linked to m by
-// the module map, concatenated) are spread over the lanes: every lane holds one target MD
-// in registers and loops over the inner MDs of m, which sit in shared memory and are read
-// as broadcasts. A tile of 32 targets x IN_CHUNK inner MDs therefore costs one shared-memory
-// broadcast per pair and the FP32 cut. Passing pairs go to a shared list with per-inner-MD
-// counts; after the tile the CTA reserves one output range (one atomicAdd) and scatters
-// the list so that the LSs of each inner MD are contiguous.
+// One warp per (event, module m); the warps of a CTA never wait for one another. The
+// targets (all MDs of the modules linked to m by the module map) are spread over the lanes
+// 32 at a time and held in registers; the inner MDs of m sit in the warp's shared memory
+// in chunks of LS_IN_CHUNK and are read as broadcasts. Every (inner, target) pair goes
+// through the division-free necessary test; the survivors (~9%) are queued and run through
+// the exact FP32 cut 32 at a time. LSs go out in any order with a count per inner MD;
+// k_ls_scan / k_ls_scatter then group them by inner MD.
 constexpr int LS_IN_CHUNK = 64;
-struct LsEntry { int i; int md; float k; };
-
-// Per-warp staging of the LS tile: the warp's 32 target MDs, and a queue of the (inner,
-// target) pairs that passed ls_prefilter; the exact cut runs on 32 queued pairs at a time.
+constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
-  float4 B[32];          // target anchors
-  float kB[32];          // target MD curvatures (cut values)
-  int md[32];            // target MD ids
-  unsigned short q[64];  // queued pairs: inner index << 5 | target lane
-  unsigned char bB[32];  // target in the barrel
+  float4 in[LS_IN_CHUNK];                  // inner anchors
+  float4 inx[LS_IN_CHUNK];                 // |A|^2, rA^2, e rA + slack (ls_prefilter)
+  float4 B[32];                            // the 32 targets of the current group
+  float ink[LS_IN_CHUNK];                  // inner MD curvatures (cut values)
+  float kB[32];
+  int md[32];
+  int tpref[LS_TB + 4];                    // MD-count prefix over the target modules
+  int tstart[LS_TB];
+  unsigned short q[64];                    // queued pairs: inner index << 5 | target lane
+  unsigned char bB[32];
+  unsigned char tbar[LS_TB];
 };
-static_assert(sizeof(LsWarp) == 928, "the host sizes k_ls shared memory with 928 bytes per warp");
+static_assert(sizeof(LsWarp) == 4688, "the host sizes k_ls shared memory with 4688 bytes per warp");
 
+// Units: with unit_off == nullptr one unit per module (all its targets); otherwise
+// unit_off[m] .. unit_off[m + 1] are the units of module m, unit b taking the target
+// modules [b tbu, (b + 1) tbu) of its list (upe = units per event). LSs go out unordered,
+// so a module's pairs may be split over units freely.
 __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int n_events, DevGeom g,
-                                           lst_cuts c, int *work, int list_cap) {
+                                           lst_cuts c, int *work, const int32_t *__restrict__ unit_off, int upe,
+                                           int tbu) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  LsWarp &w = reinterpret_cast<LsWarp *>(smem_raw)[wid];                 // [nwarps]
-  float4 *s_in = reinterpret_cast<float4 *>(smem_raw + nwarps * sizeof(LsWarp));  // [LS_IN_CHUNK]
-  float4 *s_inx = s_in + LS_IN_CHUNK;                                    // [LS_IN_CHUNK] |A|^2, rA^2, e rA + slack
-  float *s_ink = reinterpret_cast<float *>(s_inx + LS_IN_CHUNK);         // [LS_IN_CHUNK]
-  int *s_cnt = reinterpret_cast<int *>(s_ink + LS_IN_CHUNK);             // [LS_IN_CHUNK]
-  int *s_off = s_cnt + LS_IN_CHUNK;                                      // [LS_IN_CHUNK]
-  int *s_tpref = s_off + LS_IN_CHUNK;                                    // [MAX_FANOUT + 1]
-  int *s_tstart = s_tpref + MAX_FANOUT + 1;                              // [MAX_FANOUT]
-  int *s_tbar = s_tstart + MAX_FANOUT;                                   // [MAX_FANOUT]
-  LsEntry *s_list = reinterpret_cast<LsEntry *>(s_tbar + MAX_FANOUT);    // [list_cap]
-  __shared__ int s_unit, s_nin, s_nlist, s_base;
-  const int total = n_events * g.n_mod;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  LsWarp &w = reinterpret_cast<LsWarp *>(smem_raw)[wid];
+  const int total = n_events * upe;
   const float k0 = 1.002f * 65.0f * (c.hit_err * c.hit_err), c1 = c.z_lum + c.hit_err;
   for (;;) {
-    // One thread fetches the unit and reads the event's state; the whole CTA then uses
-    // that one copy (the overflow flag may change under other CTAs at any time, and every
-    // thread must take the same path through the barriers below).
-    if (threadIdx.x == 0) {
-      const int uu = atomicAdd(work, 1);
-      int nin = 0;
-      if (uu < total) {
-        const int ee = uu / g.n_mod;
+    // lane 0 fetches the unit and reads the event's state once for the warp (other warps
+    // may set the overflow flag at any time; all lanes must take the same path)
+    int u = 0, n_in = 0, m = 0, ub = 0;
+    if (lane == 0) {
+      u = atomicAdd(work, 1);
+      if (u < total) {
+        const int ee = u / upe, v = u - ee * upe;
+        if (unit_off) {
+          int lo = 0, hi = g.n_mod;                    // last m with unit_off[m] <= v
+          while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (unit_off[mid] <= v) lo = mid; else hi = mid - 1; }
+          m = lo;
+          ub = v - unit_off[m];
+        } else {
+          m = v;
+        }
         const EvDesc &evv = evs[ee];
-        nin = ev_void(evv) ? 0 : evv.md_cnt[uu - ee * g.n_mod];
+        n_in = ev_void_before(evv, F_OVF_MD) ? 0 : evv.md_cnt[m];
       }
-      s_unit = uu;
-      s_nin = nin;
     }
-    __syncthreads();
-    const int u = s_unit;
+    u = __shfl_sync(FULL, u, 0);
+    n_in = __shfl_sync(FULL, n_in, 0);
+    m = __shfl_sync(FULL, m, 0);
+    ub = __shfl_sync(FULL, ub, 0);
     if (u >= total) break;
-    const int e = u / g.n_mod, m = u - e * g.n_mod;
+    if (n_in == 0) continue;
+    const int e = u / upe;
     const EvDesc &ev = evs[e];
-    const int n_in = s_nin;
-    if (n_in == 0) { __syncthreads(); continue; }
     const int in0 = ev.md_start[m];
     const bool bA = g.subdet[m] == 0;
-    // target list: prefix of MD counts over the module map of m
-    const int t0 = g.map_off[m], nt = min(g.map_off[m + 1] - t0, MAX_FANOUT);
-    if (wid == 0) {
-      int carry = 0;
-      for (int b = 0; b < nt; b += 32) {
+    const int t0 = g.map_off[m], nt_all = min(g.map_off[m + 1] - t0, MAX_FANOUT);
+    const int tb0 = unit_off ? ub * tbu : 0, tb1 = unit_off ? min(nt_all, tb0 + tbu) : nt_all;
+    int pairs = 0;
+    for (int b0 = tb0; b0 < tb1; b0 += LS_TB) {
+      const int nb = min(LS_TB, tb1 - b0);
+      __syncwarp();                                    // the previous batch's readers are done
+      int S = 0;
+      for (int b = 0; b < nb; b += 32) {
         const int t = b + lane;
         int cnt = 0, st = 0, bar = 0;
-        if (t < nt) {
-          const int mt = g.map_tgt[t0 + t];
+        if (t < nb) {
+          const int mt = g.map_tgt[t0 + b0 + t];
           cnt = ev.md_cnt[mt];
           st = ev.md_start[mt];
           bar = g.subdet[mt] == 0;
         }
         const int inc = warp_incl_scan(cnt);
-        if (t < nt) { s_tpref[t + 1] = carry + inc; s_tstart[t] = st; s_tbar[t] = bar; }
-        carry += __shfl_sync(FULL, inc, 31);
+        if (t < nb) { w.tpref[t + 1] = S + inc; w.tstart[t] = st; w.tbar[t] = bar; }
+        S += __shfl_sync(FULL, inc, 31);
       }
-      if (lane == 0) s_tpref[0] = 0;
-    }
-    // the first chunk of inner MDs is loaded while warp 0 builds the target prefix
-    auto load_inner = [&](int t, int i) {
-      const float4 A = ev.md_anchor[i];
-      s_in[t] = A;
-      s_inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
-      s_ink[t] = ev.md_kappa[i].x;
-      s_cnt[t] = 0;
-    };
-    for (int t = threadIdx.x; t < min(LS_IN_CHUNK, n_in); t += blockDim.x) load_inner(t, in0 + t);
-    if (threadIdx.x == 0) s_nlist = 0;
-    __syncthreads();
-    const int S = s_tpref[nt];
-    if (threadIdx.x == 0 && S) atomicAdd(ev.cnt + C_PLS, n_in * S);
-    for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
-      const int nc = min(LS_IN_CHUNK, n_in - c0);
-      if (c0 > 0) {
-        for (int t = threadIdx.x; t < nc; t += blockDim.x) load_inner(t, in0 + c0 + t);
-        if (threadIdx.x == 0) s_nlist = 0;
-        __syncthreads();
-      }
-      // ---- tile: lanes over targets, loop over inner MDs; the division-free necessary
-      // test runs on every pair, the exact cut on full warps of queued survivors (~9%)
-      for (int pass_no = 0; pass_no < 2; pass_no++) {
-        const bool writing = pass_no == 1;   // second sweep only after a list overflow
-        for (int j0 = wid * 32; j0 < S; j0 += nwarps * 32) {
+      if (lane == 0) w.tpref[0] = 0;
+      __syncwarp();
+      pairs += S;
+      if (S == 0) continue;
+      for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
+        const int nc = min(LS_IN_CHUNK, n_in - c0);
+        __syncwarp();                                  // the previous chunk's readers are done
+        for (int t = lane; t < nc; t += 32) {
+          const float4 A = ev.md_anchor[in0 + c0 + t];
+          w.in[t] = A;
+          w.inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
+          w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
+        }
+        __syncwarp();
+        for (int j0 = 0; j0 < S; j0 += 32) {
           const int j = j0 + lane;
           bool valid = j < S;
           float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -381,24 +376,25 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           bool bB = false;
           int md = 0;
           if (valid) {
-            const int t = find_event(s_tpref, nt + 1, j);
-            md = s_tstart[t] + (j - s_tpref[t]);
+            const int t = find_event(w.tpref, nb + 1, j);
+            md = w.tstart[t] + (j - w.tpref[t]);
             if (chk(ev, md, ev.md_cap, 21)) {
               B = ev.md_anchor[md];
               kB = ev.md_kappa[md].x;
-              bB = s_tbar[t] != 0;
+              bB = w.tbar[t] != 0;
               const float X = B.w * (0.5f * c.kappa_max);
               k1 = 1.002f * 1.015625f * X * X;
             } else {
               valid = false;
             }
           }
+          __syncwarp();                                // the previous group's queue readers are done
           w.B[lane] = B;
           w.kB[lane] = kB;
           w.md[lane] = md;
           w.bB[lane] = bB ? 1 : 0;
           __syncwarp();
-          // exact cut of the first n queued pairs (one per lane), results to the list
+          // exact cut of the first n queued pairs (one per lane); LSs out in any order
           auto run_queue = [&](int n) {
             bool pass = false;
             int ie = 0, le = 0;
@@ -407,32 +403,23 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               const int qe = w.q[lane];
               ie = qe >> 5;
               le = qe & 31;
-              pass = ls_cut(s_in[ie], w.B[le], s_ink[ie], w.kB[le], bA, w.bB[le] != 0, c, k);
+              pass = ls_cut(w.in[ie], w.B[le], w.ink[ie], w.kB[le], bA, w.bB[le] != 0, c, k);
             }
             const unsigned bal = __ballot_sync(FULL, pass);
             if (bal == 0) return;
-            if (!writing) {
-              int pos = 0;
-              if (lane == 0) pos = atomicAdd(&s_nlist, __popc(bal));
-              pos = __shfl_sync(FULL, pos, 0);
-              if (pass) {
-                atomicAdd(&s_cnt[ie], 1);
-                const int q = pos + __popc(bal & lanemask_lt());
-                if (q < list_cap) s_list[q] = {ie, w.md[le], k};
-              }
-            } else if (pass) {
-              const int o = s_base + s_off[ie] + atomicAdd(&s_cnt[ie], 1);
-              if (chk(ev, o, ev.ls_cap, 23)) {
-                ev.ls_in[o] = in0 + c0 + ie;
-                ev.ls_out[o] = w.md[le];
-                ev.ls_kappa[o] = k;
-              }
+            const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
+            if (pass && base >= 0) {
+              const int o = base + __popc(bal & lanemask_lt());
+              ev.lsu_in[o] = in0 + c0 + ie;
+              ev.lsu_out[o] = w.md[le];
+              ev.lsu_kappa[o] = k;
+              atomicAdd(ev.ls_cnt + in0 + c0 + ie, 1);
             }
           };
           int qn = 0;
 #pragma unroll 2
           for (int i = 0; i < nc; i++) {
-            const bool cand = valid & ls_prefilter(s_in[i], s_inx[i], B, k1, k0, c1);
+            const bool cand = valid & ls_prefilter(w.in[i], w.inx[i], B, k1, k0, c1);
             const unsigned bal = __ballot_sync(FULL, cand);
             if (cand) w.q[qn + __popc(bal & lanemask_lt())] = (unsigned short)((i << 5) | lane);
             qn += __popc(bal);
@@ -449,54 +436,40 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             __syncwarp();
             run_queue(qn);
           }
-          __syncwarp();
         }
-        __syncthreads();
-        if (writing) break;
-        // ---- per-inner-MD offsets, one reservation for the tile
-        if (wid == 0) {
-          int carry = 0;
-          for (int b = 0; b < nc; b += 32) {
-            const int t = b + lane;
-            const int v = t < nc ? s_cnt[t] : 0;
-            const int inc = warp_incl_scan(v);
-            if (t < nc) s_off[t] = carry + inc - v;
-            carry += __shfl_sync(FULL, inc, 31);
-          }
-          int base = 0;
-          if (lane == 0 && carry > 0) {
-            base = atomicAdd(ev.cnt + C_LS, carry);
-            if (base + carry > ev.ls_cap) { atomicOr(ev.cnt + C_FLAGS, F_OVF_LS); base = -1; }
-          }
-          if (lane == 0) s_base = carry > 0 ? base : -1;
-        }
-        __syncthreads();
-        const int base = s_base;
-        const int nlist = s_nlist;
-        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-          ev.ls_start[in0 + c0 + t] = base >= 0 ? base + s_off[t] : 0;
-          ev.ls_cnt[in0 + c0 + t] = base >= 0 ? s_cnt[t] : 0;
-          s_cnt[t] = 0;                    // from here on: scatter cursors (same thread, same t)
-        }
-        __syncthreads();
-        if (base < 0) break;
-        if (nlist <= list_cap) {
-          for (int q = threadIdx.x; q < nlist; q += blockDim.x) {
-            const LsEntry r = s_list[q];
-            const int o = base + s_off[r.i] + atomicAdd(&s_cnt[r.i], 1);
-            ev.ls_in[o] = in0 + c0 + r.i;
-            ev.ls_out[o] = r.md;
-            ev.ls_kappa[o] = r.k;
-          }
-          break;
-        }
-        // list overflow: sweep the tile again, writing in place
       }
-      // the next chunk reuses s_in / s_list / s_cnt; after a unit's last chunk the barrier
-      // of the next unit's fetch orders that reuse (thread 0 only writes s_unit / s_nin
-      // before it, which every thread has read at this unit's start)
-      if (c0 + LS_IN_CHUNK < n_in) __syncthreads();
     }
+    if (lane == 0 && pairs) atomicAdd(ev.cnt + C_PLS, n_in * pairs);
+  }
+}
+
+// LSs per inner MD -> ranges (one CTA per event) ...
+__global__ void k_ls_scan(const EvDesc *__restrict__ evs) {
+  const EvDesc &ev = evs[blockIdx.x];
+  if (ev_void(ev)) return;
+  const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
+  block_exclusive_scan(ev.ls_cnt, ev.ls_start, n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ev.ls_cur[i] = ev.ls_start[i];
+}
+
+// ... then the LSs into their inner MD's range.
+__global__ void k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_LS], ev.ls_cap);
+  }, s_pref);
+  const int total = s_pref[n_events];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    const int e = find_event(s_pref, n_events, u);
+    const EvDesc &ev = evs[e];
+    const int o = u - s_pref[e];
+    const int md = ev.lsu_in[o];
+    const int pos = atomicAdd(ev.ls_cur + md, 1);
+    if (!chk(ev, pos, ev.ls_cap, 24)) continue;
+    ev.ls_in[pos] = md;
+    ev.ls_out[pos] = ev.lsu_out[o];
+    ev.ls_kappa[pos] = ev.lsu_kappa[o];
   }
 }
 
@@ -522,7 +495,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
   T3Warp &w = reinterpret_cast<T3Warp *>(smem_raw)[wid];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 63) / 64;
+    return ev_void_before(ev, F_OVF_MD | F_OVF_LS) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 63) / 64;
   }, s_pref);
   const int total = s_pref[n_events];
   const int W = gridDim.x * nwarps;
@@ -666,7 +639,7 @@ __global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int 
   T5Warp &w = reinterpret_cast<T5Warp *>(smem_raw)[wid];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_T3], ev.t3_cap) + 31) / 32;
+    return ev_void_before(ev, F_OVF_MD | F_OVF_LS | F_OVF_T3) ? 0 : (clamp_count(ev.cnt[C_T3], ev.t3_cap) + 31) / 32;
   }, s_pref);
   const int total = s_pref[n_events];
   const int W = gridDim.x * nwarps;

@@ -160,6 +160,30 @@ def test_overflow_regrows_to_exact_result(geom_full, cuts, model):
     c.close()
 
 
+def test_batch_with_overflowing_events(geom_full, cuts, model):
+    """A batch in which the large events overflow their T3 buffer and the small ones do not:
+    the small ones must still be exact (the stage's work split between CTAs must not change
+    when an event overflows mid-kernel), and re-running the large ones regrows to exact."""
+    c = lst.Context(0, max_events=8, t3_per_md=0.01, t5_per_md=0.01)
+    c.load_geometry(geom_full, cuts, *model)
+    evs = [synth.pileup_event(geom_full, 50 + i, pileup=pu, mean_per_vertex=96, config=4)
+           for i, pu in enumerate((1, 200, 1, 120, 2))]
+    refs = [oracle.run_event(geom_full, e, cuts, *model) for e in evs]
+    hs = c.run_batch([dev(e) for e in evs])
+    st = [h.counts()["status"] for h in hs]
+    assert st[1] == lst.LST_ERR_CAPACITY and st[3] == lst.LST_ERR_CAPACITY
+    for k in (0, 2, 4):
+        assert st[k] == lst.LST_OK
+        compare(hs[k], refs[k], float(cuts["wp"]))
+    for h in hs:
+        h.release()
+    for k in (1, 3):
+        ev = c.run_event(*dev(evs[k]))
+        compare(ev, refs[k], float(cuts["wp"]))
+        ev.release()
+    c.close()
+
+
 def test_list_overflow_paths(geom_full, cuts, model):
     """Tiny candidate lists force the re-evaluation paths of the MD and LS kernels, odd CTA
     sizes change every work decomposition; results must not change."""
