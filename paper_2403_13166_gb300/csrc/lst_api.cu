@@ -246,10 +246,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
                o_mh = take(8 * (size_t)md), o_mst = take(4 * (size_t)nm), o_mcn = take(4 * (size_t)nm),
                o_mcur = take(4 * (size_t)nm), o_uanc = take(16 * (size_t)md), o_uk = take(8 * (size_t)md),
                o_umod = take(4 * (size_t)md), o_uh = take(8 * (size_t)md);
-  const size_t o_lin = take(4 * (size_t)ls), o_lout = take(4 * (size_t)ls), o_lk = take(4 * (size_t)ls),
-               o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
-  const size_t o_luin = take(4 * (size_t)ls), o_luout = take(4 * (size_t)ls), o_luk = take(4 * (size_t)ls),
-               o_lcur = take(4 * (size_t)md);
+  const size_t o_ls = take(16 * (size_t)ls), o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
+  const size_t o_lsu = take(16 * (size_t)ls), o_lcur = take(4 * (size_t)md);
   const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
                o_t3c = take(4 * (size_t)md), o_t3u = take(16 * (size_t)t3), o_t3uk = take(4 * (size_t)t3);
   const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
@@ -272,9 +270,9 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   d.md_hits = (int2 *)(b + o_mh); d.md_start = (int32_t *)(b + o_mst); d.md_cnt = (int32_t *)(b + o_mcn);
   d.md_cur = (int32_t *)(b + o_mcur); d.mdu_anchor = (float4 *)(b + o_uanc); d.mdu_kappa = (float2 *)(b + o_uk);
   d.mdu_mod = (int32_t *)(b + o_umod); d.mdu_hits = (int2 *)(b + o_uh);
-  d.ls_in = (int32_t *)(b + o_lin); d.ls_out = (int32_t *)(b + o_lout); d.ls_kappa = (float *)(b + o_lk);
+  d.ls = (int4 *)(b + o_ls);
   d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
-  d.lsu_in = (int32_t *)(b + o_luin); d.lsu_out = (int32_t *)(b + o_luout); d.lsu_kappa = (float *)(b + o_luk);
+  d.lsu = (int4 *)(b + o_lsu);
   d.ls_cur = (int32_t *)(b + o_lcur);
   d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_pos = (int32_t *)(b + o_t3s);
   d.t3_cnt = (int32_t *)(b + o_t3c); d.t3u_md = (int4 *)(b + o_t3u); d.t3u_kappa = (float *)(b + o_t3uk);

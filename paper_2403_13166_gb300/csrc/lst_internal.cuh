@@ -58,10 +58,9 @@ struct EvDesc {
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
   int32_t *md_cur;             // [n_mod] scatter cursor of the grouping
-  int32_t *lsu_in, *lsu_out;   // [ls_cap] LSs as found, any order
-  float *lsu_kappa;            // [ls_cap]
-  int32_t *ls_in, *ls_out;     // [ls_cap] inner / outer MD, grouped by inner MD
-  float *ls_kappa;             // [ls_cap]
+  int4 *lsu;                   // [ls_cap] LSs as found, any order: (inner MD, outer MD,
+                               // bits of the curvature, -), one 16-byte record each
+  int4 *ls;                    // [ls_cap] the same, grouped by inner MD
   int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
   int32_t *ls_cur;             // [md_cap] scatter cursor of the grouping
   int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, -), any order

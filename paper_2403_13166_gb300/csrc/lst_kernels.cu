@@ -410,9 +410,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
             if (pass && base >= 0) {
               const int o = base + __popc(bal & lanemask_lt());
-              ev.lsu_in[o] = in0 + c0 + ie;
-              ev.lsu_out[o] = w.md[le];
-              ev.lsu_kappa[o] = k;
+              ev.lsu[o] = make_int4(in0 + c0 + ie, w.md[le], __float_as_int(k), 0);
               atomicAdd(ev.ls_cnt + in0 + c0 + ie, 1);
             }
           };
@@ -464,12 +462,10 @@ __global__ void k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
     const int e = find_event(s_pref, n_events, u);
     const EvDesc &ev = evs[e];
     const int o = u - s_pref[e];
-    const int md = ev.lsu_in[o];
-    const int pos = atomicAdd(ev.ls_cur + md, 1);
+    const int4 r = ev.lsu[o];
+    const int pos = atomicAdd(ev.ls_cur + r.x, 1);
     if (!chk(ev, pos, ev.ls_cap, 24)) continue;
-    ev.ls_in[pos] = md;
-    ev.ls_out[pos] = ev.lsu_out[o];
-    ev.ls_kappa[pos] = ev.lsu_kappa[o];
+    ev.ls[pos] = r;                        // one 16-byte store
   }
 }
 
@@ -515,7 +511,8 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     for (int h = 0; h < 2; h++) {
       const int l1 = (u - s_pref[e]) * 64 + 32 * h + lane;
       if (l1 < nls) {
-        const int md0 = ev.ls_in[l1], md1 = ev.ls_out[l1];
+        const int4 L1 = ev.ls[l1];
+        const int md0 = L1.x, md1 = L1.y;
         deg[h] = ev.ls_cnt[md1];
         w.st2[32 * h + lane] = ev.ls_start[md1];
         w.md0[32 * h + lane] = md0;
@@ -555,7 +552,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     };
     int qlen = 0;
     // flat pair index f -> (LS1 lane x, outer MD); two pairs per lane and iteration so that
-    // the two dependent load chains (ls_out, then the anchor) are in flight together
+    // the two dependent load chains (the LS record, then the anchor) are in flight together
     auto decode = [&](int f, int &x) {
       int lo = 0, hi = 63;
       while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
@@ -582,8 +579,8 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     for (int f0 = 0; f0 < tot; f0 += 64) {
       const int fa = f0 + lane, fb = f0 + 32 + lane;
       int xa = 0, xb = 0, mda = 0, mdb = 0;
-      if (fa < tot) mda = ev.ls_out[decode(fa, xa)];
-      if (fb < tot) mdb = ev.ls_out[decode(fb, xb)];
+      if (fa < tot) mda = ev.ls[decode(fa, xa)].y;
+      if (fb < tot) mdb = ev.ls[decode(fb, xb)].y;
       float4 Pa = make_float4(0.f, 0.f, 0.f, 0.f), Pb = Pa;
       if (fa < tot) Pa = ev.md_anchor[mda];
       if (fb < tot) Pb = ev.md_anchor[mdb];

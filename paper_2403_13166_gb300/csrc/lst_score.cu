@@ -122,7 +122,8 @@ __global__ void k_gather(const EvDesc *__restrict__ ev_p, int kind, int n, int32
       out[2 * (size_t)t] = h.x;
       out[2 * (size_t)t + 1] = h.y;
     } else if (kind == LST_LS) {
-      const int2 a = ev.md_hits[ev.ls_in[t]], b = ev.md_hits[ev.ls_out[t]];
+      const int4 L = ev.ls[t];
+      const int2 a = ev.md_hits[L.x], b = ev.md_hits[L.y];
       int32_t *o = out + 4 * (size_t)t;
       o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
     } else if (kind == LST_T3) {
@@ -191,11 +192,12 @@ __global__ void k_graph_fill(const EvDesc *__restrict__ ev_p, DevGeom g, int n_m
     const float4 A = ev.md_anchor[m];
     const int beg = ev.ls_start[m], cnt = ev.ls_cnt[m], o = row_off[m];
     for (int k = 0; k < cnt; k++) {
-      const int l = beg + k, b = ev.ls_out[l];
+      const int4 L = ev.ls[beg + k];
+      const int b = L.y;
       col[o + k] = b;
       if (edge_feat) {
         const float4 B = ev.md_anchor[b];
-        edge_feat[2 * (size_t)(o + k)] = ev.ls_kappa[l];
+        edge_feat[2 * (size_t)(o + k)] = __int_as_float(L.z);
         edge_feat[2 * (size_t)(o + k) + 1] = A.z - A.w * ((B.z - A.z) / (B.w - A.w));   // z at r = 0
       }
     }
