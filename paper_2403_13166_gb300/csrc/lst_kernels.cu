@@ -579,8 +579,9 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     for (int f0 = 0; f0 < tot; f0 += 64) {
       const int fa = f0 + lane, fb = f0 + 32 + lane;
       int xa = 0, xb = 0, mda = 0, mdb = 0;
-      if (fa < tot) mda = ev.ls[decode(fa, xa)].y;
-      if (fb < tot) mdb = ev.ls[decode(fb, xb)].y;
+      const int *ls_words = reinterpret_cast<const int *>(ev.ls);   // field y: outer MD
+      if (fa < tot) mda = ls_words[4 * (size_t)decode(fa, xa) + 1];
+      if (fb < tot) mdb = ls_words[4 * (size_t)decode(fb, xb) + 1];
       float4 Pa = make_float4(0.f, 0.f, 0.f, 0.f), Pb = Pa;
       if (fa < tot) Pa = ev.md_anchor[mda];
       if (fb < tot) Pb = ev.md_anchor[mdb];
