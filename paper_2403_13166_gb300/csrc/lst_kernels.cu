@@ -191,9 +191,13 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
     };
     __syncwarp();
     int qlen = 0;
+    // the next upper hit is loaded while the current pair is tested (software pipelining)
+    float4 Unext = nup > 0 ? ev.hit[up0] : make_float4(0.f, 0.f, 0.f, 1.f);
     for (int j = 0; j < mx; j++) {
+      const float4 U = Unext;
+      if (j + 1 < nup) Unext = ev.hit[up0 + j + 1];
       bool pre = false;
-      if (j < nup) pre = md_prefilter(L, ev.hit[up0 + j], endcap, hb2r2, c);
+      if (j < nup) pre = md_prefilter(L, U, endcap, hb2r2, c);
       const unsigned bal = __ballot_sync(FULL, pre);
       if (bal == 0) continue;
       if (pre) {
