@@ -580,15 +580,24 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
         __syncwarp();
       }
     };
-    for (int f0 = 0; f0 < tot; f0 += 64) {
+    // software pipeline over chunks of 64 pairs: the next chunk's LS words are loaded while
+    // the current chunk's anchors arrive and its pairs are tested
+    const int *ls_words = reinterpret_cast<const int *>(ev.ls);   // field y: outer MD
+    auto fetch = [&](int f0, int &xa, int &xb, int &mda, int &mdb) {
       const int fa = f0 + lane, fb = f0 + 32 + lane;
-      int xa = 0, xb = 0, mda = 0, mdb = 0;
-      const int *ls_words = reinterpret_cast<const int *>(ev.ls);   // field y: outer MD
+      xa = xb = mda = mdb = 0;
       if (fa < tot) mda = ls_words[4 * (size_t)decode(fa, xa) + 1];
       if (fb < tot) mdb = ls_words[4 * (size_t)decode(fb, xb) + 1];
+    };
+    int nxa, nxb, nmda, nmdb;
+    fetch(0, nxa, nxb, nmda, nmdb);
+    for (int f0 = 0; f0 < tot; f0 += 64) {
+      const int fa = f0 + lane, fb = f0 + 32 + lane;
+      const int xa = nxa, xb = nxb, mda = nmda, mdb = nmdb;
       float4 Pa = make_float4(0.f, 0.f, 0.f, 0.f), Pb = Pa;
       if (fa < tot) Pa = ev.md_anchor[mda];
       if (fb < tot) Pb = ev.md_anchor[mdb];
+      if (f0 + 64 < tot) fetch(f0 + 64, nxa, nxb, nmda, nmdb);
       const bool prea = fa < tot && t3_prefilter(w.P0[xa], w.P1[xa], Pa, c);
       const bool preb = fb < tot && t3_prefilter(w.P0[xb], w.P1[xb], Pb, c);
       enqueue(prea, xa, mda);
