@@ -68,9 +68,9 @@ def _oracle_time(args):
     return dt, r.counts["t5"]
 
 
-# kernels of one launch sequence: reset, 3 grouping, 3 MD, LS, 3 T3, T5, score, 4 track
+# kernels of one launch sequence: reset, 3 grouping, 3 MD, 3 LS, 3 T3, T5, score, 4 track
 # candidate, counter collection
-KERNELS_PER_LAUNCH = 18
+KERNELS_PER_LAUNCH = 20
 
 # score arithmetic of the batched and served forms (the plain form is always FP32)
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}

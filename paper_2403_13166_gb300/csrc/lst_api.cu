@@ -16,9 +16,9 @@
 namespace lstk {
 // kernels (lst_kernels.cu, lst_score.cu, lst_mma.cu)
 __global__ void k_reset(const EvDesc *, DevGeom);
-__global__ void k_bin_count(const EvDesc *, DevGeom);
+__global__ void k_bin_count(const EvDesc *, int, DevGeom);
 __global__ void k_bin_scan(const EvDesc *, DevGeom);
-__global__ void k_bin_scatter(const EvDesc *, DevGeom);
+__global__ void k_bin_scatter(const EvDesc *, int, DevGeom);
 __global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts);
 __global__ void k_md_scan(const EvDesc *, DevGeom);
 __global__ void k_md_scatter(const EvDesc *, int);
@@ -160,6 +160,10 @@ struct lst_ctx_s {
   int t5_threads = 256;
   int sc_threads = 256;
   int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
+  // grids of the 256-thread grid-stride kernels: as many CTAs as are resident at once (an
+  // event-major loop must not leave a second wave of CTAs to redo every event)
+  int grid_bin_count = 0, grid_bin_scatter = 0, grid_md_scatter = 0, grid_ls_scatter = 0, grid_t3_scatter = 0;
+  int grid_tc_count = 0, grid_tc_scatter = 0, grid_tc_decide = 0;
   // per-stage device times accumulated over timed launches
   bool timing = false;
   double stage_sum[LST_N_STAGES] = {0};
@@ -214,6 +218,20 @@ lst_status compute_grids(lst_ctx_s *c) {
   const size_t sw = (size_t)mlp_floats_host(4) * 4;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_fp32, c->sc_threads, sw));
   c->grid_sc = std::max(1, occ) * c->n_sm;
+  auto resident = [&](const void *fn, int &grid) -> cudaError_t {
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, 256, 0);
+    grid = std::max(1, o) * c->n_sm;
+    return e;
+  };
+  CU(resident((const void *)k_bin_count, c->grid_bin_count));
+  CU(resident((const void *)k_bin_scatter, c->grid_bin_scatter));
+  CU(resident((const void *)k_md_scatter, c->grid_md_scatter));
+  CU(resident((const void *)k_ls_scatter, c->grid_ls_scatter));
+  CU(resident((const void *)k_t3_scatter, c->grid_t3_scatter));
+  CU(resident((const void *)k_tc_count, c->grid_tc_count));
+  CU(resident((const void *)k_tc_scatter, c->grid_tc_scatter));
+  CU(resident((const void *)k_tc_decide, c->grid_tc_decide));
   c->grid_bf[0] = score_bf16_blocks_per_sm(false) * c->n_sm;
   c->grid_bf[1] = score_bf16_blocks_per_sm(true) * c->n_sm;
   return LST_OK;
@@ -351,21 +369,20 @@ lst_status lane_harvest(lst_ctx_s *c, Lane &L) {
 // Enqueue the whole pipeline for the lane's current batch (desc already on device).
 lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool timed, bool capturing) {
   const DevGeom g = c->g;
-  const int bx = std::max(1, (4 * c->n_sm + n - 1) / n);
   // stage boundary events; inside a capture they become event-record nodes of the graph
   auto mark = [&](int i) {
     if (timed) cudaEventRecordWithFlags(L.tev[i], st, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   };
   mark(0);
   k_reset<<<dim3(std::max(1, c->n_sm / n + 1), n), 256, 0, st>>>(L.d_desc, g);
-  k_bin_count<<<dim3(bx, n), 256, 0, st>>>(L.d_desc, g);
+  k_bin_count<<<c->grid_bin_count, 256, 0, st>>>(L.d_desc, n, g);
   k_bin_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
-  k_bin_scatter<<<dim3(bx, n), 256, 0, st>>>(L.d_desc, g);
+  k_bin_scatter<<<c->grid_bin_scatter, 256, 0, st>>>(L.d_desc, n, g);
   CU(cudaMemsetAsync(L.d_work, 0, sizeof(int) * 16, st));
   mark(1);
   k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts);
   k_md_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
-  k_md_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_md_scatter<<<c->grid_md_scatter, 256, 0, st>>>(L.d_desc, n);
   mark(2);
   {
     // few events: units of LS_SMALL_TB target modules, so that dense modules spread over
@@ -379,11 +396,11 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
                                                          0);
   }
   k_ls_scan<<<n, 1024, 0, st>>>(L.d_desc);
-  k_ls_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_ls_scatter<<<c->grid_ls_scatter, 256, 0, st>>>(L.d_desc, n);
   mark(3);
   k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts);
   k_t3_scan<<<n, 1024, 0, st>>>(L.d_desc);
-  k_t3_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_t3_scatter<<<c->grid_t3_scatter, 256, 0, st>>>(L.d_desc, n);
   mark(4);
   k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
   mark(5);
@@ -395,10 +412,10 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
     k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
         L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
   mark(6);
-  k_tc_count<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_tc_count<<<c->grid_tc_count, 256, 0, st>>>(L.d_desc, n);
   k_tc_scan<<<n, 1024, 0, st>>>(L.d_desc);
-  k_tc_scatter<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
-  k_tc_decide<<<2 * c->n_sm, 256, 0, st>>>(L.d_desc, n);
+  k_tc_scatter<<<c->grid_tc_scatter, 256, 0, st>>>(L.d_desc, n);
+  k_tc_decide<<<c->grid_tc_decide, 256, 0, st>>>(L.d_desc, n);
   mark(7);
   k_collect<<<(n + 127) / 128, 128, 0, st>>>(L.d_desc, n, L.d_counts);
   CU(cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int) * C_NCOUNTERS * n, cudaMemcpyDeviceToHost, st));

@@ -16,20 +16,25 @@
 namespace lstk {
 
 // ===================================================================== step 0: hit binning
-// Count hits per sensor (validating sensor ids and coordinates). Sensors are keyed as
-// (sensor & 1) * n_mod + module, so that all lower-sensor hits come first in the grouped
-// order: key k < n_mod is the lower sensor of module k, key n_mod + k its upper sensor.
-__global__ void k_bin_count(const EvDesc *__restrict__ evs, DevGeom g) {
-  const EvDesc &ev = evs[blockIdx.y];
-  const int n = ev.n_hits, ns = 2 * g.n_mod;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int s = __ldg(ev.sensor + i);
-    const float x = __ldg(ev.x + i), y = __ldg(ev.y + i), z = __ldg(ev.z + i);
-    if (s < 0 || s >= ns || !isfinite(x) || !isfinite(y) || !isfinite(z)) {
-      atomicOr(ev.cnt + C_FLAGS, F_INPUT);
-      continue;
+// Count hits per sensor. Sensors are keyed as (sensor & 1) * n_mod + module, so that all
+// lower-sensor hits come first in the grouped order: key k < n_mod is the lower sensor of
+// module k, key n_mod + k its upper sensor. The whole grid walks the batch one event at a
+// time, so the sensor histogram (and in k_bin_scatter the output range) being filled is
+// one event's and stays in L2. Only the sensor ids are read here; the coordinates are
+// checked by k_bin_scatter (an invalid hit voids its event either way).
+__global__ void k_bin_count(const EvDesc *__restrict__ evs, int n_events, DevGeom g) {
+  const int ns = 2 * g.n_mod, tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int e = 0; e < n_events; e++) {
+    const EvDesc &ev = evs[e];
+    const int n = ev.n_hits;
+    for (int i = tid; i < n; i += st) {
+      const int s = __ldg(ev.sensor + i);
+      if (s < 0 || s >= ns) {
+        atomicOr(ev.cnt + C_FLAGS, F_INPUT);
+        continue;
+      }
+      atomicAdd(ev.sens_cnt + (s & 1) * g.n_mod + (s >> 1), 1);
     }
-    atomicAdd(ev.sens_cnt + (s & 1) * g.n_mod + (s >> 1), 1);
   }
 }
 
@@ -69,23 +74,35 @@ __global__ void k_bin_scan(const EvDesc *__restrict__ evs, DevGeom g) {
   if (ns == 0 && threadIdx.x == 0) ev.sens_off[0] = 0;
 }
 
-// Scatter hits into sensor order as float4 (x, y, z, r) with r = sqrtf(x*x + y*y).
-__global__ void k_bin_scatter(const EvDesc *__restrict__ evs, DevGeom g) {
-  const EvDesc &ev = evs[blockIdx.y];
-  const int n = ev.n_hits, ns = 2 * g.n_mod;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int s = __ldg(ev.sensor + i);
-    const float x = __ldg(ev.x + i), y = __ldg(ev.y + i), z = __ldg(ev.z + i);
-    if (s < 0 || s >= ns || !isfinite(x) || !isfinite(y) || !isfinite(z)) continue;
-    const int key = (s & 1) * g.n_mod + (s >> 1);
-    const int pos = ev.sens_off[key] + atomicAdd(ev.sens_cnt + key, 1);
-    ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
-    ev.hit_orig[pos] = i;
-    ev.hit_mod[pos] = s >> 1;
+// Scatter hits into sensor order as float4 (x, y, z, r) with r = sqrtf(x*x + y*y), event
+// by event like k_bin_count. A hit with a non-finite coordinate is placed like any other
+// (the counts stay consistent) and voids its event.
+__global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevGeom g) {
+  const int ns = 2 * g.n_mod, tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int e = 0; e < n_events; e++) {
+    const EvDesc &ev = evs[e];
+    const int n = ev.n_hits;
+    for (int i = tid; i < n; i += st) {
+      const int s = __ldg(ev.sensor + i);
+      const float x = __ldg(ev.x + i), y = __ldg(ev.y + i), z = __ldg(ev.z + i);
+      if (s < 0 || s >= ns) continue;
+      if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(ev.cnt + C_FLAGS, F_INPUT);
+      const int key = (s & 1) * g.n_mod + (s >> 1);
+      const int pos = ev.sens_off[key] + atomicAdd(ev.sens_cnt + key, 1);
+      ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
+      ev.hit_orig[pos] = i;
+      ev.hit_mod[pos] = s >> 1;
+    }
   }
 }
 
 // ===================================================================== shared machinery
+// The grouping scatters (k_md_scatter, k_ls_scatter, k_t3_scatter) walk the batch one event
+// at a time with the whole grid, SCATTER_ILP objects per thread and trip: the loads of all
+// of them go out before the first cursor atomic, and the output range being filled is one
+// event's, which stays in L2 until its sectors are complete.
+constexpr int SCATTER_ILP = 4;
+
 // Reserve n output slots: one atomicAdd per warp. Returns the base or -1 if the buffer
 // would overflow (then the flag is set; the counter still records the demand).
 __device__ __forceinline__ int warp_reserve(int *counter, int *flags, int flag, int n, int cap) {
@@ -250,24 +267,30 @@ __global__ void k_md_scan(const EvDesc *__restrict__ evs, DevGeom g) {
 }
 
 // ... then a scatter into module order.
-__global__ void k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
-  __shared__ int s_pref[MAX_EVENTS + 1];
-  block_event_prefix(n_events, [&](int e) {
+__global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
+  const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int e = 0; e < n_events; e++) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_MD], ev.md_cap);
-  }, s_pref);
-  const int total = s_pref[n_events];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
-    const int e = find_event(s_pref, n_events, u);
-    const EvDesc &ev = evs[e];
-    const int o = u - s_pref[e];
-    const int m = ev.mdu_mod[o];
-    const int pos = atomicAdd(ev.md_cur + m, 1);
-    if (!chk(ev, pos, ev.md_cap, 14)) continue;
-    ev.md_anchor[pos] = ev.mdu_anchor[o];
-    ev.md_kappa[pos] = ev.mdu_kappa[o];
-    ev.md_mod[pos] = m;
-    ev.md_hits[pos] = ev.mdu_hits[o];
+    if (ev_void(ev)) continue;
+    const int64_t n = clamp_count(ev.cnt[C_MD], ev.md_cap);
+    for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
+      int m[SCATTER_ILP], pos[SCATTER_ILP];
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) m[k] = ev.mdu_mod[o0 + k * st];
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) pos[k] = atomicAdd(ev.md_cur + m[k], 1);
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++) {
+        const int64_t o = o0 + k * st;
+        if (o >= n || !chk(ev, pos[k], ev.md_cap, 14)) continue;
+        ev.md_anchor[pos[k]] = ev.mdu_anchor[o];
+        ev.md_kappa[pos[k]] = ev.mdu_kappa[o];
+        ev.md_mod[pos[k]] = m[k];
+        ev.md_hits[pos[k]] = ev.mdu_hits[o];
+      }
+    }
   }
 }
 
@@ -455,21 +478,25 @@ __global__ void k_ls_scan(const EvDesc *__restrict__ evs) {
 }
 
 // ... then the LSs into their inner MD's range.
-__global__ void k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
-  __shared__ int s_pref[MAX_EVENTS + 1];
-  block_event_prefix(n_events, [&](int e) {
+__global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
+  const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int e = 0; e < n_events; e++) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_LS], ev.ls_cap);
-  }, s_pref);
-  const int total = s_pref[n_events];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
-    const int e = find_event(s_pref, n_events, u);
-    const EvDesc &ev = evs[e];
-    const int o = u - s_pref[e];
-    const int4 r = ev.lsu[o];
-    const int pos = atomicAdd(ev.ls_cur + r.x, 1);
-    if (!chk(ev, pos, ev.ls_cap, 24)) continue;
-    ev.ls[pos] = r;                        // one 16-byte store
+    if (ev_void(ev)) continue;
+    const int64_t n = clamp_count(ev.cnt[C_LS], ev.ls_cap);
+    for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
+      int4 r[SCATTER_ILP];
+      int pos[SCATTER_ILP];
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) r[k] = ev.lsu[o0 + k * st];
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) pos[k] = atomicAdd(ev.ls_cur + r[k].x, 1);
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n && chk(ev, pos[k], ev.ls_cap, 24)) ev.ls[pos[k]] = r[k];   // one 16-byte store
+    }
   }
 }
 
@@ -618,21 +645,26 @@ __global__ void k_t3_scan(const EvDesc *__restrict__ evs) {
 }
 
 // ... then a scatter into that order; afterwards t3_pos[md] holds the END of md's range.
-__global__ void k_t3_scatter(const EvDesc *__restrict__ evs, int n_events) {
-  __shared__ int s_pref[MAX_EVENTS + 1];
-  block_event_prefix(n_events, [&](int e) {
+__global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ evs, int n_events) {
+  const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int e = 0; e < n_events; e++) {
     const EvDesc &ev = evs[e];
-    return ev_void(ev) ? 0 : clamp_count(ev.cnt[C_T3], ev.t3_cap);
-  }, s_pref);
-  const int total = s_pref[n_events];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
-    const int e = find_event(s_pref, n_events, u);
-    const EvDesc &ev = evs[e];
-    const int o = u - s_pref[e];
-    const int4 t = ev.t3u_md[o];
-    const int pos = atomicAdd(ev.t3_pos + t.x, 1);
-    ev.t3_md[pos] = t;
-    ev.t3_kappa[pos] = ev.t3u_kappa[o];
+    if (ev_void(ev)) continue;
+    const int64_t n = clamp_count(ev.cnt[C_T3], ev.t3_cap);
+    for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
+      int4 t[SCATTER_ILP];
+      float k3[SCATTER_ILP];
+      int pos[SCATTER_ILP];
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) { t[k] = ev.t3u_md[o0 + k * st]; k3[k] = ev.t3u_kappa[o0 + k * st]; }
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) pos[k] = atomicAdd(ev.t3_pos + t[k].x, 1);
+#pragma unroll
+      for (int k = 0; k < SCATTER_ILP; k++)
+        if (o0 + k * st < n) { ev.t3_md[pos[k]] = t[k]; ev.t3_kappa[pos[k]] = k3[k]; }
+    }
   }
 }
 
