@@ -161,6 +161,42 @@ __device__ __forceinline__ bool ls_prefilter(const float4 A, const float4 Ax, co
   return z0 & dir & bend;
 }
 
+// Necessary condition of the two curvature-consistency cuts of ls_cut (barrel MDs), for the
+// pairs that passed ls_prefilter. With M = rA rB dT > 0 and k = 2 cr / M (cr = A x B, the
+// exact identity used above), |kA - k| <= 2 (e/g) / rA + 2 (e/dT) / rB is, multiplied by M,
+//   |kA rA u - 2 cr| <= G u + 2 e rA      with u = rB dT, G = 2 e / g,
+// and |kB - k| <= 2 (e/g) / rB + 2 (e/dT) / rB is
+//   |kB rB v - 2 cr| <= G v + 2 e rA      with v = rA dT.
+// dT comes from the approximate reciprocal square root (relative error below 2^-22).
+// Rounding, in relative terms so that it holds for any coordinates: the exact cut in FP32
+// can accept a pair whose real-arithmetic condition fails by up to 2.4e-7 of its bound plus
+// (14 |k| + 1) eps-sized terms, which times M stay below 2.4e-7 (G u + 2 e rA) + 9.6e-7 v
+// + 6e-8 |kA rA u|; the FP32 evaluation below errs by at most 5e-7 of |kA rA u| (or |kB rB v|)
+// and 4.8e-7 rA rB (cr's cancellation). The bound is therefore widened by the factor
+// (1 + 1e-6) on G and 2e, by 1e-6 (|p| + rA rB + v), and by 0.01 absolute. dT2 = 0 or a
+// subnormal dT2 gives a NaN or infinite side and the pair passes (the exact cut decides).
+// Checked over all candidate pairs of three PU200-like events: 1.81-1.88% pass against
+// 1.80-1.87% accepted, none of the 3.3 M LSs missed.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ bool ls_kappa_prefilter(const float4 A, const float4 B, float kA, float kB, bool bA,
+                                                   bool bB, float Gp, float ce) {
+  const float dx = B.x - A.x, dy = B.y - A.y;
+  const float dT2 = __fmaf_rn(dx, dx, dy * dy);
+  const float dT = dT2 * rsqrt_approx(dT2);
+  const float cr2 = 2.0f * __fmaf_rn(A.x, B.y, -(A.y * B.x));
+  const float u = B.w * dT, v = A.w * dT;
+  const float c0 = __fmaf_rn(ce, A.w, 0.01f);                 // 2 e rA (1 + 1e-6) + 0.01
+  const float s0 = __fmaf_rn(A.w, B.w, v);                     // rA rB + v
+  const float pa = kA * A.w * u, pb = kB * B.w * v;
+  const bool fa = __fmaf_rn(-1e-6f, fabsf(pa) + s0, fabsf(pa - cr2)) > __fmaf_rn(Gp, u, c0);
+  const bool fb = __fmaf_rn(-1e-6f, fabsf(pb) + s0, fabsf(pb - cr2)) > __fmaf_rn(Gp, v, c0);
+  return !((bA & fa) | (bB & fb));
+}
+
 // Necessary condition of md_cut without division or square root (barrel), or the exact
 // direction test (endcap). hb2r2 = (rL * hb)^2 with hb = rL*(kappa_max/2) + e/g, the bend
 // bound of md_cut, precomputed per lower hit. Bend: |cr| <= rL dT hb. z road, multiplied

@@ -299,15 +299,19 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
 // targets (all MDs of the modules linked to m by the module map) are spread over the lanes
 // 32 at a time and held in registers; the inner MDs of m sit in the warp's shared memory
 // in chunks of LS_IN_CHUNK and are read as broadcasts. Every (inner, target) pair goes
-// through the division-free necessary test; the survivors (~9%) are queued and run through
-// the exact FP32 cut 32 at a time. LSs go out in any order with a count per inner MD;
-// k_ls_scan / k_ls_scatter then group them by inner MD.
+// through the division-free necessary test; the survivors (~9%) are queued and, 32 at a time,
+// through the necessary curvature-consistency test (~1.8% of all pairs pass), whose survivors
+// wait in a second queue that lives for the whole unit and run through the exact FP32 cut
+// 32 at a time. LSs go out in any order with a count per inner MD; k_ls_scan /
+// k_ls_scatter then group them by inner MD.
 constexpr int LS_IN_CHUNK = 64;
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
   float4 in[LS_IN_CHUNK];                  // inner anchors
   float4 inx[LS_IN_CHUNK];                 // |A|^2, rA^2, e rA + slack (ls_prefilter)
   float4 B[32];                            // the 32 targets of the current group
+  int2 q2[64];                             // pairs past the curvature test: inner MD, target MD
+                                           // (bit 31: target in the barrel), global indices
   float ink[LS_IN_CHUNK];                  // inner MD curvatures (cut values)
   float kB[32];
   int md[32];
@@ -317,7 +321,7 @@ struct LsWarp {
   unsigned char bB[32];
   unsigned char tbar[LS_TB];
 };
-static_assert(sizeof(LsWarp) == 4688, "the host sizes k_ls shared memory with 4688 bytes per warp");
+static_assert(sizeof(LsWarp) == 5200, "the host sizes k_ls shared memory with 5200 bytes per warp");
 
 // Units: with unit_off == nullptr one unit per module (all its targets); otherwise
 // unit_off[m] .. unit_off[m + 1] are the units of module m, unit b taking the target
@@ -331,6 +335,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
   LsWarp &w = reinterpret_cast<LsWarp *>(smem_raw)[wid];
   const int total = n_events * upe;
   const float k0 = 1.002f * 65.0f * (c.hit_err * c.hit_err), c1 = c.z_lum + c.hit_err;
+  const float Gp = 2.0f * (c.hit_err / c.sensor_gap) * 1.000001f, ce = 2.0f * c.hit_err * 1.000001f;
   for (;;) {
     // lane 0 fetches the unit and reads the event's state once for the warp (other warps
     // may set the overflow flag at any time; all lanes must take the same path)
@@ -364,6 +369,27 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
     const int t0 = g.map_off[m], nt_all = min(g.map_off[m + 1] - t0, MAX_FANOUT);
     const int tb0 = unit_off ? ub * tbu : 0, tb1 = unit_off ? min(nt_all, tb0 + tbu) : nt_all;
     int pairs = 0;
+    int q2n = 0;
+    // exact cut of the first n pairs of the second queue (one per lane); LSs out in any order
+    auto run_exact = [&](int n) {
+      bool pass = false;
+      int gi = 0, gm = 0;
+      float k = 0.0f;
+      if (lane < n) {
+        const int2 qe = w.q2[lane];
+        gi = qe.x;
+        gm = qe.y & 0x7fffffff;
+        pass = ls_cut(ev.md_anchor[gi], ev.md_anchor[gm], ev.md_kappa[gi].x, ev.md_kappa[gm].x, bA, qe.y < 0, c, k);
+      }
+      const unsigned bal = __ballot_sync(FULL, pass);
+      if (bal == 0) return;
+      const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
+      if (pass && base >= 0) {
+        const int o = base + __popc(bal & lanemask_lt());
+        ev.lsu[o] = make_int4(gi, gm, __float_as_int(k), 0);
+        atomicAdd(ev.ls_cnt + gi, 1);
+      }
+    };
     for (int b0 = tb0; b0 < tb1; b0 += LS_TB) {
       const int nb = min(LS_TB, tb1 - b0);
       __syncwarp();                                    // the previous batch's readers are done
@@ -421,24 +447,27 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           w.md[lane] = md;
           w.bB[lane] = bB ? 1 : 0;
           __syncwarp();
-          // exact cut of the first n queued pairs (one per lane); LSs out in any order
-          auto run_queue = [&](int n) {
+          // curvature test of the first n queued pairs; survivors join the second queue
+          auto run_kappa = [&](int n) {
             bool pass = false;
-            int ie = 0, le = 0;
-            float k = 0.0f;
+            int2 ent = make_int2(0, 0);
             if (lane < n) {
               const int qe = w.q[lane];
-              ie = qe >> 5;
-              le = qe & 31;
-              pass = ls_cut(w.in[ie], w.B[le], w.ink[ie], w.kB[le], bA, w.bB[le] != 0, c, k);
+              const int ie = qe >> 5, le = qe & 31;
+              const bool b2 = w.bB[le] != 0;
+              pass = ls_kappa_prefilter(w.in[ie], w.B[le], w.ink[ie], w.kB[le], bA, b2, Gp, ce);
+              ent = make_int2(in0 + c0 + ie, b2 ? (w.md[le] | (int)0x80000000u) : w.md[le]);
             }
             const unsigned bal = __ballot_sync(FULL, pass);
-            if (bal == 0) return;
-            const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
-            if (pass && base >= 0) {
-              const int o = base + __popc(bal & lanemask_lt());
-              ev.lsu[o] = make_int4(in0 + c0 + ie, w.md[le], __float_as_int(k), 0);
-              atomicAdd(ev.ls_cnt + in0 + c0 + ie, 1);
+            if (pass) w.q2[q2n + __popc(bal & lanemask_lt())] = ent;
+            q2n += __popc(bal);
+            if (q2n >= 32) {
+              __syncwarp();
+              run_exact(32);
+              __syncwarp();
+              if (lane + 32 < q2n) w.q2[lane] = w.q2[lane + 32];
+              __syncwarp();
+              q2n -= 32;
             }
           };
           int qn = 0;
@@ -450,7 +479,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             qn += __popc(bal);
             if (qn >= 32) {
               __syncwarp();
-              run_queue(32);
+              run_kappa(32);
               __syncwarp();
               if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
               __syncwarp();
@@ -459,10 +488,14 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           }
           if (qn > 0) {
             __syncwarp();
-            run_queue(qn);
+            run_kappa(qn);
           }
         }
       }
+    }
+    if (q2n > 0) {
+      __syncwarp();
+      run_exact(q2n);
     }
     if (lane == 0 && pairs) atomicAdd(ev.cnt + C_PLS, n_in * pairs);
   }
