@@ -414,11 +414,20 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
         const int nc = min(LS_IN_CHUNK, n_in - c0);
         __syncwarp();                                  // the previous chunk's readers are done
-        for (int t = lane; t < nc; t += 32) {
-          const float4 A = ev.md_anchor[in0 + c0 + t];
-          w.in[t] = A;
-          w.inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
-          w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
+        // padded to a multiple of 8 with NaN anchors, which fail every comparison of the test
+        const int nc8 = (nc + 7) & ~7;
+        for (int t = lane; t < nc8; t += 32) {
+          if (t < nc) {
+            const float4 A = ev.md_anchor[in0 + c0 + t];
+            w.in[t] = A;
+            w.inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
+            w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
+          } else {
+            const float nan = __int_as_float(0x7fc00000);
+            w.in[t] = make_float4(nan, nan, nan, nan);
+            w.inx[t] = make_float4(nan, nan, nan, nan);
+            w.ink[t] = 0.0f;
+          }
         }
         __syncwarp();
         for (int j0 = 0; j0 < S; j0 += 32) {
@@ -470,20 +479,39 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               q2n -= 32;
             }
           };
+          // each lane tests its target against the inner MDs 32 at a time, collecting the
+          // survivors as a bit mask (no warp-wide step in the loop), then the masks are drained
+          // into the queue, one pair per lane and round
           int qn = 0;
-#pragma unroll 2
-          for (int i = 0; i < nc; i++) {
-            const bool cand = valid & ls_prefilter(w.in[i], w.inx[i], B, k1, k0, c1);
-            const unsigned bal = __ballot_sync(FULL, cand);
-            if (cand) w.q[qn + __popc(bal & lanemask_lt())] = (unsigned short)((i << 5) | lane);
-            qn += __popc(bal);
-            if (qn >= 32) {
-              __syncwarp();
-              run_kappa(32);
-              __syncwarp();
-              if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
-              __syncwarp();
-              qn -= 32;
+          for (int i0 = 0; i0 < nc; i0 += 32) {
+            const int n8 = min(32, nc8 - i0);
+            unsigned mask = 0;
+            if (valid) {
+              for (int i = 0; i < n8; i += 8) {
+                unsigned bits = 0;
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                  bits |= ls_prefilter(w.in[i0 + i + k], w.inx[i0 + i + k], B, k1, k0, c1) ? 1u << k : 0u;
+                mask |= bits << i;
+              }
+            }
+            for (;;) {
+              const unsigned act = __ballot_sync(FULL, mask != 0);
+              if (act == 0) break;
+              if (mask != 0) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                w.q[qn + __popc(act & lanemask_lt())] = (unsigned short)(((i0 + i) << 5) | lane);
+              }
+              qn += __popc(act);
+              if (qn >= 32) {
+                __syncwarp();
+                run_kappa(32);
+                __syncwarp();
+                if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
+                __syncwarp();
+                qn -= 32;
+              }
             }
           }
           if (qn > 0) {
