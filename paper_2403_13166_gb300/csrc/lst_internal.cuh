@@ -236,28 +236,34 @@ __device__ __forceinline__ bool t3_cut(const float4 P0, const float4 P1, const f
   return true;
 }
 
-// Necessary condition of t3_cut without division or IEEE square root. pT: |2 cr| <=
-// K a b c  <=>  4 cr^2 <= K^2 a^2 b^2 c^2 (K = kappa_max * factor). rz: the same residual
-// multiplied by (s01 + s12) > 0, with a, b from the approximate rsqrt (relative error
-// ~1e-7) and kappa^2 from the squares; the slack (1e-3 relative, 1e-4 cm absolute) is far
-// above the approximation and rounding errors, so a rejected triplet always fails t3_cut.
-__device__ __forceinline__ bool t3_prefilter(const float4 P0, const float4 P1, const float4 P2,
-                                             const lst_cuts &c) {
-  const float ax = P1.x - P0.x, ay = P1.y - P0.y;
-  const float bx = P2.x - P1.x, by = P2.y - P1.y;
-  const float cx = P2.x - P0.x, cy = P2.y - P0.y;
-  const float a2 = ax * ax + ay * ay, b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
-  const float cr = ax * cy - ay * cx;
-  const float K = c.kappa_max * c.t3_kappa_factor;
-  const float abc2 = a2 * b2 * c2;
-  const bool pt = 4.0f * cr * cr <= K * K * abc2 * 1.001f + 1e-12f;
-  const float k2 = __fdividef(4.0f * cr * cr, fmaxf(abc2, 1e-30f));   // kappa^2, approximate
-  const float a = a2 * rsqrtf(fmaxf(a2, 1e-30f)), b = b2 * rsqrtf(fmaxf(b2, 1e-30f));
-  const float s01 = a * (1.0f + a2 * k2 * (1.0f / 24.0f));
-  const float s12 = b * (1.0f + b2 * k2 * (1.0f / 24.0f));
-  const float lhs = fabsf((P1.z - P0.z) * (s01 + s12) - (P2.z - P0.z) * s01);
-  const bool rz = lhs <= (c.t3_rz_tol * 1.001f + 1e-4f) * (s01 + s12);
-  return pt & rz;
+// Necessary condition of t3_cut without division or IEEE square root, from per-first-LS
+// values Q0 = (x1, y1, z1, z1 - z0), Q1 = (ax, ay, a^2, a) and a3 = a^3 (a = |P1 - P0|_T)
+// and the third anchor P2. pT: |2 cr| <= K a b c  <=>  4 cr^2 <= K^2 a^2 b^2 c^2 (K =
+// kappa_max * factor), with cr = a x b (= a x c, the cut's form) and c = a + b. rz: the
+// residual z1 - zp multiplied by S = s01 + s12 >= 0, written as (z1 - z0) s12 - (z2 - z1)
+// s01, with b from the approximate rsqrt and kappa^2 / 24 from the approximate reciprocal
+// (relative errors ~1e-7). The slack (1e-3 relative on K^2 and the tolerance, 3e-4 cm
+// absolute on the residual) is far above the approximation and rounding errors (below
+// 1.5e-4 cm on the residual for coordinates within 300 cm), so a rejected triplet always
+// fails t3_cut.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ bool t3_prefilter(const float4 Q0, const float4 Q1, float a3, const float4 P2, float K2,
+                                             float tolp) {
+  const float bx = P2.x - Q0.x, by = P2.y - Q0.y;
+  const float cx = Q1.x + bx, cy = Q1.y + by;
+  const float b2 = __fmaf_rn(bx, bx, by * by), c2 = __fmaf_rn(cx, cx, cy * cy);
+  const float t = 2.0f * __fmaf_rn(Q1.x, by, -(Q1.y * bx));          // 2 cr
+  const float abc2 = Q1.z * b2 * c2, tt = t * t;
+  const bool pt = tt <= __fmaf_rn(K2, abc2, 1e-12f);
+  const float k24 = tt * rcp_approx(fmaxf(abc2, 1e-30f)) * (1.0f / 24.0f);
+  const float b = b2 * rsqrt_approx(fmaxf(b2, 1e-30f));
+  const float s01 = __fmaf_rn(a3, k24, Q1.w), s12 = __fmaf_rn(b * b2, k24, b);
+  const float lhs = __fmaf_rn(Q0.w, s12, -((P2.z - Q0.z) * s01));
+  return pt & (fabsf(lhs) <= tolp * (s01 + s12));
 }
 
 // Step 4: five anchors in chain order; ka, kb the curvatures of T3a = (0,1,2), T3b = (2,3,4).

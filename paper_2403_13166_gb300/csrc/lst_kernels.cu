@@ -564,17 +564,22 @@ __global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ e
 // ===================================================================== steps 3 and 4
 // Both enumerate pairs (X1, X2) where X2 ranges over a contiguous list attached to the
 // middle MD of X1. A warp takes 32 (T5) or 64 (T3: two per lane) consecutive X1 with their
-// list lengths;
-// an inclusive warp scan of the lengths maps each flat pair index to (X1, X2) by a binary
-// search in the warp's shared copy of the scan. Work is spread by static striding over
-// chunks of X1 of all events (no atomics); pair counts are summed per warp and flushed
-// once per event.
+// list lengths; a warp scan of the lengths gives each X1 its range of flat pair indices.
+// Work is spread by static striding over chunks of X1 of all events (no atomics); pair
+// counts are summed per warp and flushed once per event.
+//
+// Step 3 maps the flat pair indices of a 64-pair chunk to their first LS by marks: every
+// first LS with pairs whose range starts in the chunk writes its slot at its start, and a
+// prefix maximum over the 64 positions (carried from chunk to chunk) gives each position
+// its owner. The prefilter works from per-first-LS values computed once (Q0, Q1, a^3).
 struct T3Warp {
-  float4 P0[64], P1[64];             // 64 first LSs per warp chunk: lanes lane and 32 + lane
-  int incl[64], st2[64], md0[64], md1[64];
+  float4 Q0[64], Q1[64];             // 64 first LSs per warp chunk: lanes lane and 32 + lane
+  float a3[64];
+  int base[64], md0[64], md1[64];    // base: LS-list start minus the exclusive pair offset
+  int mark[64];
   int qx[64], qmd[64];               // queue of pairs that passed t3_prefilter
 };
-static_assert(sizeof(T3Warp) == 3584, "the host sizes k_t3 shared memory with 3584 bytes per warp");
+static_assert(sizeof(T3Warp) == 3840, "the host sizes k_t3 shared memory with 3840 bytes per warp");
 
 __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -587,6 +592,8 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
   }, s_pref);
   const int total = s_pref[n_events];
   const int W = gridDim.x * nwarps;
+  const float K = c.kappa_max * c.t3_kappa_factor;
+  const float K2 = K * K * 1.001f, tolp = c.t3_rz_tol * 1.001f + 3e-4f;
   int cur = -1, acc = 0;
   for (int u = blockIdx.x * nwarps + wid; u < total; u += W) {
     const int e = find_event(s_pref, n_events, u);
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
     const EvDesc &ev = evs[e];
     const int nls = clamp_count(ev.cnt[C_LS], ev.ls_cap);
     // two first LSs per lane (slots lane and 32 + lane), their loads independent
-    int deg[2] = {0, 0};
+    int deg[2] = {0, 0}, st2[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int l1 = (u - s_pref[e]) * 64 + 32 * h + lane;
@@ -606,22 +613,27 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
         const int4 L1 = ev.ls[l1];
         const int md0 = L1.x, md1 = L1.y;
         deg[h] = ev.ls_cnt[md1];
-        w.st2[32 * h + lane] = ev.ls_start[md1];
+        st2[h] = ev.ls_start[md1];
         w.md0[32 * h + lane] = md0;
         w.md1[32 * h + lane] = md1;
-        w.P0[32 * h + lane] = ev.md_anchor[md0];
-        w.P1[32 * h + lane] = ev.md_anchor[md1];
+        const float4 P0 = ev.md_anchor[md0], P1 = ev.md_anchor[md1];
+        const float ax = P1.x - P0.x, ay = P1.y - P0.y;
+        const float a2 = __fmaf_rn(ax, ax, ay * ay);
+        const float a = a2 * rsqrt_approx(fmaxf(a2, 1e-30f));
+        w.Q0[32 * h + lane] = make_float4(P1.x, P1.y, P1.z, P1.z - P0.z);
+        w.Q1[32 * h + lane] = make_float4(ax, ay, a2, a);
+        w.a3[32 * h + lane] = a * a2;
       }
     }
     const int inca = warp_incl_scan(deg[0]);
     const int tota = __shfl_sync(FULL, inca, 31);
     const int incb = tota + warp_incl_scan(deg[1]);
-    w.incl[lane] = inca;
-    w.incl[32 + lane] = incb;
-    __syncwarp();
+    const int exa = inca - deg[0], exb = incb - deg[1];       // first flat pair index of each slot
+    w.base[lane] = st2[0] - exa;
+    w.base[32 + lane] = st2[1] - exb;
     const int tot = __shfl_sync(FULL, incb, 31);
     acc += tot;
-    // exact cut on queued pairs [q0, q0 + n): (LS1 lane, outer MD)
+    // exact cut on queued pairs [q0, q0 + n): (LS1 slot, outer MD)
     auto run_queue = [&](int q0, int n) {
       bool pass = false;
       float k = 0.0f;
@@ -629,7 +641,7 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
       if (lane < n) {
         x = w.qx[q0 + lane];
         md2 = w.qmd[q0 + lane];
-        pass = t3_cut(w.P0[x], w.P1[x], ev.md_anchor[md2], c, k);
+        pass = t3_cut(ev.md_anchor[w.md0[x]], ev.md_anchor[w.md1[x]], ev.md_anchor[md2], c, k);
       }
       const unsigned bal = __ballot_sync(FULL, pass);
       if (bal) {
@@ -643,15 +655,6 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
       }
     };
     int qlen = 0;
-    // flat pair index f -> (LS1 lane x, outer MD); two pairs per lane and iteration so that
-    // the two dependent load chains (the LS record, then the anchor) are in flight together
-    auto decode = [&](int f, int &x) {
-      int lo = 0, hi = 63;
-      while (lo < hi) { const int mid = (lo + hi) >> 1; if (w.incl[mid] > f) hi = mid; else lo = mid + 1; }
-      x = lo;
-      const int prev = lo ? w.incl[lo - 1] : 0;
-      return w.st2[lo] + (f - prev);
-    };
     auto enqueue = [&](bool pre, int x, int md2) {
       const unsigned bal = __ballot_sync(FULL, pre);
       if (bal == 0) return;
@@ -668,17 +671,37 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
         __syncwarp();
       }
     };
+    // owners of the chunk's positions f0 + lane (xa) and f0 + 32 + lane (xb), then the outer
+    // MD of each pair from its LS record (field y)
+    int carry = -1;
+    const int *ls_words = reinterpret_cast<const int *>(ev.ls);
+    auto fetch = [&](int f0, int &xa, int &xb, int &mda, int &mdb) {
+      __syncwarp();                                  // the previous chunk's mark readers are done
+      w.mark[lane] = -1;
+      w.mark[32 + lane] = -1;
+      __syncwarp();
+      if (deg[0] > 0 && exa >= f0 && exa < f0 + 64) w.mark[exa - f0] = lane;
+      if (deg[1] > 0 && exb >= f0 && exb < f0 + 64) w.mark[exb - f0] = 32 + lane;
+      __syncwarp();
+      int ma = max(w.mark[lane], carry), mb = w.mark[32 + lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ta = __shfl_up_sync(FULL, ma, o), tb = __shfl_up_sync(FULL, mb, o);
+        if (lane >= o) { ma = max(ma, ta); mb = max(mb, tb); }
+      }
+      mb = max(mb, __shfl_sync(FULL, ma, 31));
+      carry = __shfl_sync(FULL, mb, 31);
+      const int fa = f0 + lane, fb = f0 + 32 + lane;
+      xa = fa < tot ? ma : 0;
+      xb = fb < tot ? mb : 0;
+      mda = mdb = 0;
+      if (fa < tot) mda = ls_words[4 * (size_t)(w.base[xa] + fa) + 1];
+      if (fb < tot) mdb = ls_words[4 * (size_t)(w.base[xb] + fb) + 1];
+    };
     // software pipeline over chunks of 64 pairs: the next chunk's LS words are loaded while
     // the current chunk's anchors arrive and its pairs are tested
-    const int *ls_words = reinterpret_cast<const int *>(ev.ls);   // field y: outer MD
-    auto fetch = [&](int f0, int &xa, int &xb, int &mda, int &mdb) {
-      const int fa = f0 + lane, fb = f0 + 32 + lane;
-      xa = xb = mda = mdb = 0;
-      if (fa < tot) mda = ls_words[4 * (size_t)decode(fa, xa) + 1];
-      if (fb < tot) mdb = ls_words[4 * (size_t)decode(fb, xb) + 1];
-    };
-    int nxa, nxb, nmda, nmdb;
-    fetch(0, nxa, nxb, nmda, nmdb);
+    int nxa = 0, nxb = 0, nmda = 0, nmdb = 0;
+    if (tot > 0) fetch(0, nxa, nxb, nmda, nmdb);
     for (int f0 = 0; f0 < tot; f0 += 64) {
       const int fa = f0 + lane, fb = f0 + 32 + lane;
       const int xa = nxa, xb = nxb, mda = nmda, mdb = nmdb;
@@ -686,8 +709,8 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
       if (fa < tot) Pa = ev.md_anchor[mda];
       if (fb < tot) Pb = ev.md_anchor[mdb];
       if (f0 + 64 < tot) fetch(f0 + 64, nxa, nxb, nmda, nmdb);
-      const bool prea = fa < tot && t3_prefilter(w.P0[xa], w.P1[xa], Pa, c);
-      const bool preb = fb < tot && t3_prefilter(w.P0[xb], w.P1[xb], Pb, c);
+      const bool prea = fa < tot && t3_prefilter(w.Q0[xa], w.Q1[xa], w.a3[xa], Pa, K2, tolp);
+      const bool preb = fb < tot && t3_prefilter(w.Q0[xb], w.Q1[xb], w.a3[xb], Pb, K2, tolp);
       enqueue(prea, xa, mda);
       enqueue(preb, xb, mdb);
     }
@@ -729,6 +752,8 @@ __global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ e
   }
 }
 
+// Step 4 maps a flat pair index to its first T3 by a binary search in the warp's shared copy
+// of the inclusive scan (32 entries).
 struct T5Warp {
   int incl[32], st2[32], ta[32];
   float ka[32];
