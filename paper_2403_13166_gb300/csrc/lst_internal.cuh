@@ -147,13 +147,13 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
 // bend, against bounds of at least 0.29 and 5.6) cover that, so a pair rejected here always
 // fails ls_cut (checked over all 59.5 M candidate pairs of a PU200-like event: 9.00% pass
 // this test, 8.92% the exact bend, none missed).
-// Ax = (|A|^2, rA^2, e rA + 0.05, -) per inner MD; k1 = 1.002 * (1 + 1/64) X^2 per outer MD,
+// Ax = (|A|^2 - 0.05, rA^2, e rA + 0.05, -) per inner MD; k1 = 1.002 * (1 + 1/64) X^2 per outer MD,
 // k0 = 1.002 * 65 e^2, c1 = z_lum + e.
 __device__ __forceinline__ bool ls_prefilter(const float4 A, const float4 Ax, const float4 B, float k1, float k0,
                                              float c1) {
   const float p = __fmaf_rn(A.z, B.w, -(A.w * B.z));
   const bool z0 = fabsf(p) <= __fmaf_rn(c1, fabsf(B.w - A.w), Ax.z);
-  const bool dir = __fmaf_rn(A.x, B.x, A.y * B.y) - Ax.x > -0.05f;
+  const bool dir = __fmaf_rn(A.x, B.x, A.y * B.y) > Ax.x;
   const float cr = __fmaf_rn(A.x, B.y, -(A.y * B.x));
   const float dx = B.x - A.x, dy = B.y - A.y;
   const float dT2 = __fmaf_rn(dx, dx, dy * dy);

@@ -308,7 +308,7 @@ constexpr int LS_IN_CHUNK = 64;
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
   float4 in[LS_IN_CHUNK];                  // inner anchors
-  float4 inx[LS_IN_CHUNK];                 // |A|^2, rA^2, e rA + slack (ls_prefilter)
+  float4 inx[LS_IN_CHUNK];                 // |A|^2 - slack, rA^2, e rA + slack (ls_prefilter)
   float4 B[32];                            // the 32 targets of the current group
   int2 q2[64];                             // pairs past the curvature test: inner MD, target MD
                                            // (bit 31: target in the barrel), global indices
@@ -414,13 +414,13 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       for (int c0 = 0; c0 < n_in; c0 += LS_IN_CHUNK) {
         const int nc = min(LS_IN_CHUNK, n_in - c0);
         __syncwarp();                                  // the previous chunk's readers are done
-        // padded to a multiple of 8 with NaN anchors, which fail every comparison of the test
-        const int nc8 = (nc + 7) & ~7;
-        for (int t = lane; t < nc8; t += 32) {
+        // padded to a multiple of 4 with NaN anchors, which fail every comparison of the test
+        const int nc4 = (nc + 3) & ~3;
+        for (int t = lane; t < nc4; t += 32) {
           if (t < nc) {
             const float4 A = ev.md_anchor[in0 + c0 + t];
             w.in[t] = A;
-            w.inx[t] = make_float4(A.x * A.x + A.y * A.y, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
+            w.inx[t] = make_float4(A.x * A.x + A.y * A.y - 0.05f, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
             w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
           } else {
             const float nan = __int_as_float(0x7fc00000);
@@ -484,13 +484,13 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           // into the queue, one pair per lane and round
           int qn = 0;
           for (int i0 = 0; i0 < nc; i0 += 32) {
-            const int n8 = min(32, nc8 - i0);
+            const int n4 = min(32, nc4 - i0);
             unsigned mask = 0;
             if (valid) {
-              for (int i = 0; i < n8; i += 8) {
+              for (int i = 0; i < n4; i += 4) {
                 unsigned bits = 0;
 #pragma unroll
-                for (int k = 0; k < 8; k++)
+                for (int k = 0; k < 4; k++)
                   bits |= ls_prefilter(w.in[i0 + i + k], w.inx[i0 + i + k], B, k1, k0, c1) ? 1u << k : 0u;
                 mask |= bits << i;
               }
