@@ -157,15 +157,14 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
     int nup = 0, up0 = 0;
     bool endcap = false;
     float4 L = make_float4(0.f, 0.f, 0.f, 1.f);
-    float hb2r2 = 0.0f;
+    MdLow q{};
     if (h < ev.sens_off[nm]) {
       const int m = ev.hit_mod[h];
       up0 = ev.sens_off[nm + m];
       nup = ev.sens_off[nm + m + 1] - up0;
       endcap = g.subdet[m] != 0;
       L = ev.hit[h];
-      const float hb = L.w * (0.5f * c.kappa_max) + c.hit_err / c.sensor_gap;
-      hb2r2 = (L.w * hb) * (L.w * hb);
+      q = md_low(L, endcap, c);
       w.L[lane] = L;
       w.lo[lane] = h;
       w.mod[lane] = m;
@@ -208,26 +207,37 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
     };
     __syncwarp();
     int qlen = 0;
-    // the next upper hit is loaded while the current pair is tested (software pipelining)
-    float4 Unext = nup > 0 ? ev.hit[up0] : make_float4(0.f, 0.f, 0.f, 1.f);
-    for (int j = 0; j < mx; j++) {
-      const float4 U = Unext;
-      if (j + 1 < nup) Unext = ev.hit[up0 + j + 1];
-      bool pre = false;
-      if (j < nup) pre = md_prefilter(L, U, endcap, hb2r2, c);
-      const unsigned bal = __ballot_sync(FULL, pre);
-      if (bal == 0) continue;
-      if (pre) {
-        const int q = qlen + __popc(bal & lanemask_lt());
-        w.qx[q] = lane;
-        w.qu[q] = up0 + j;
+    // each lane tests its lower hit against the upper hits of its module 32 at a time (the
+    // next upper hit loaded while the current pair is tested), collecting the survivors as a
+    // bit mask with no warp-wide step in the loop; the masks are then drained into the queue
+    for (int j0 = 0; j0 < mx; j0 += 32) {
+      unsigned mask = 0;
+      const int jn = min(nup - j0, 32);
+      if (jn > 0) {
+        float4 Unext = ev.hit[up0 + j0];
+        for (int j = 0; j < jn; j++) {
+          const float4 U = Unext;
+          if (j + 1 < jn) Unext = ev.hit[up0 + j0 + j + 1];
+          mask |= (md_prefilter(L, U, endcap, q, c) ? 1u : 0u) << j;
+        }
       }
-      qlen += __popc(bal);
-      if (qlen >= 32) {
-        __syncwarp();
-        run_queue(qlen - 32, 32);
-        qlen -= 32;
-        __syncwarp();
+      for (;;) {
+        const unsigned act = __ballot_sync(FULL, mask != 0);
+        if (act == 0) break;
+        if (mask != 0) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int qi = qlen + __popc(act & lanemask_lt());
+          w.qx[qi] = lane;
+          w.qu[qi] = up0 + j0 + j;
+        }
+        qlen += __popc(act);
+        if (qlen >= 32) {
+          __syncwarp();
+          run_queue(qlen - 32, 32);
+          qlen -= 32;
+          __syncwarp();
+        }
       }
     }
     __syncwarp();
