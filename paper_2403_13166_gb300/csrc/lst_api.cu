@@ -246,6 +246,32 @@ void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5)
   t5 = (int)std::min(std::ceil(c->r_t5 * nmd) + 1024, 2.0e9);
 }
 
+// Byte offsets of one event's buffers in its slot allocation (H hits, nm modules, md/ls/t3/t5
+// object capacities); `total` is the allocation size.
+struct SlotLayout {
+  size_t hit, orig, hmod, scnt, soff, manc, mk, mmod, mh, mst, mcn, mcur, uanc, uk, umod, uh;
+  size_t ls, lst, lcn, lsu, lcur, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl, tcf, cnt;
+  size_t total;
+};
+SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, size_t t5) {
+  SlotLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  L.hit = take(16 * (size_t)H); L.orig = take(4 * (size_t)H); L.hmod = take(4 * (size_t)H);
+  L.scnt = take(4 * 2 * nm); L.soff = take(4 * (2 * nm + 1));
+  L.manc = take(16 * md); L.mk = take(8 * md); L.mmod = take(4 * md); L.mh = take(8 * md);
+  L.mst = take(4 * nm); L.mcn = take(4 * nm); L.mcur = take(4 * nm);
+  L.uanc = take(16 * md); L.uk = take(8 * md); L.umod = take(4 * md); L.uh = take(8 * md);
+  L.ls = take(16 * ls); L.lst = take(4 * md); L.lcn = take(4 * md); L.lsu = take(16 * ls); L.lcur = take(4 * md);
+  L.t3 = take(16 * t3); L.t3k = take(4 * t3); L.t3s = take(4 * md); L.t3c = take(4 * md);
+  L.t3u = take(16 * t3); L.t3uk = take(4 * t3);
+  L.t5a = take(16 * t5); L.t5b = take(16 * t5); L.t5s = take(4 * t5); L.t5e = take(t5);
+  L.tcc = take(4 * md); L.tcp = take(4 * md); L.tcl = take(20 * t5); L.tcf = take(t5);
+  L.cnt = take(4 * C_NCOUNTERS);
+  L.total = off;
+  return L;
+}
+
 lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   int md, ls, t3, t5;
   caps_for(c, n_hits, md, ls, t3, t5);
@@ -255,24 +281,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   // grow with headroom
   const int64_t H = std::max<int64_t>(s.hit_cap, (int64_t)(hcap * 1.1));
   md = std::max(s.md_cap, md); ls = std::max(s.ls_cap, ls); t3 = std::max(s.t3_cap, t3); t5 = std::max(s.t5_cap, t5);
-  const int nm = c->g.n_mod;
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  const size_t o_hit = take(16 * H), o_orig = take(4 * H), o_hmod = take(4 * H);
-  const size_t o_scnt = take(4 * (size_t)2 * nm), o_soff = take(4 * ((size_t)2 * nm + 1));
-  const size_t o_manc = take(16 * (size_t)md), o_mk = take(8 * (size_t)md), o_mmod = take(4 * (size_t)md),
-               o_mh = take(8 * (size_t)md), o_mst = take(4 * (size_t)nm), o_mcn = take(4 * (size_t)nm),
-               o_mcur = take(4 * (size_t)nm), o_uanc = take(16 * (size_t)md), o_uk = take(8 * (size_t)md),
-               o_umod = take(4 * (size_t)md), o_uh = take(8 * (size_t)md);
-  const size_t o_ls = take(16 * (size_t)ls), o_lst = take(4 * (size_t)md), o_lcn = take(4 * (size_t)md);
-  const size_t o_lsu = take(16 * (size_t)ls), o_lcur = take(4 * (size_t)md);
-  const size_t o_t3 = take(16 * (size_t)t3), o_t3k = take(4 * (size_t)t3), o_t3s = take(4 * (size_t)md),
-               o_t3c = take(4 * (size_t)md), o_t3u = take(16 * (size_t)t3), o_t3uk = take(4 * (size_t)t3);
-  const size_t o_t5a = take(16 * (size_t)t5), o_t5b = take(16 * (size_t)t5), o_t5s = take(4 * (size_t)t5),
-               o_t5e = take((size_t)t5);
-  const size_t o_tcc = take(4 * (size_t)md), o_tcp = take(4 * (size_t)md), o_tcl = take(20 * (size_t)t5),
-               o_tcf = take((size_t)t5);
-  const size_t o_cnt = take(4 * C_NCOUNTERS);
+  const SlotLayout L = slot_layout(H, (size_t)c->g.n_mod, md, ls, t3, t5);
+  const size_t off = L.total;
   if (s.mem) {
     CU(cudaDeviceSynchronize());
     cudaFree(s.mem);
@@ -282,22 +292,22 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   s.bytes = off;
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
-  d.hit = (float4 *)(b + o_hit); d.hit_orig = (int32_t *)(b + o_orig); d.hit_mod = (int32_t *)(b + o_hmod);
-  d.sens_cnt = (int32_t *)(b + o_scnt); d.sens_off = (int32_t *)(b + o_soff);
-  d.md_anchor = (float4 *)(b + o_manc); d.md_kappa = (float2 *)(b + o_mk); d.md_mod = (int32_t *)(b + o_mmod);
-  d.md_hits = (int2 *)(b + o_mh); d.md_start = (int32_t *)(b + o_mst); d.md_cnt = (int32_t *)(b + o_mcn);
-  d.md_cur = (int32_t *)(b + o_mcur); d.mdu_anchor = (float4 *)(b + o_uanc); d.mdu_kappa = (float2 *)(b + o_uk);
-  d.mdu_mod = (int32_t *)(b + o_umod); d.mdu_hits = (int2 *)(b + o_uh);
-  d.ls = (int4 *)(b + o_ls);
-  d.ls_start = (int32_t *)(b + o_lst); d.ls_cnt = (int32_t *)(b + o_lcn);
-  d.lsu = (int4 *)(b + o_lsu);
-  d.ls_cur = (int32_t *)(b + o_lcur);
-  d.t3_md = (int4 *)(b + o_t3); d.t3_kappa = (float *)(b + o_t3k); d.t3_pos = (int32_t *)(b + o_t3s);
-  d.t3_cnt = (int32_t *)(b + o_t3c); d.t3u_md = (int4 *)(b + o_t3u); d.t3u_kappa = (float *)(b + o_t3uk);
-  d.t5_a = (int4 *)(b + o_t5a); d.t5_b = (int4 *)(b + o_t5b); d.t5_score = (float *)(b + o_t5s);
-  d.t5_sel = (uint8_t *)(b + o_t5e); d.cnt = (int32_t *)(b + o_cnt);
-  d.tc_cnt = (int32_t *)(b + o_tcc); d.tc_pos = (int32_t *)(b + o_tcp); d.tc_list = (int32_t *)(b + o_tcl);
-  d.t5_tc = (uint8_t *)(b + o_tcf);
+  d.hit = (float4 *)(b + L.hit); d.hit_orig = (int32_t *)(b + L.orig); d.hit_mod = (int32_t *)(b + L.hmod);
+  d.sens_cnt = (int32_t *)(b + L.scnt); d.sens_off = (int32_t *)(b + L.soff);
+  d.md_anchor = (float4 *)(b + L.manc); d.md_kappa = (float2 *)(b + L.mk); d.md_mod = (int32_t *)(b + L.mmod);
+  d.md_hits = (int2 *)(b + L.mh); d.md_start = (int32_t *)(b + L.mst); d.md_cnt = (int32_t *)(b + L.mcn);
+  d.md_cur = (int32_t *)(b + L.mcur); d.mdu_anchor = (float4 *)(b + L.uanc); d.mdu_kappa = (float2 *)(b + L.uk);
+  d.mdu_mod = (int32_t *)(b + L.umod); d.mdu_hits = (int2 *)(b + L.uh);
+  d.ls = (int4 *)(b + L.ls);
+  d.ls_start = (int32_t *)(b + L.lst); d.ls_cnt = (int32_t *)(b + L.lcn);
+  d.lsu = (int4 *)(b + L.lsu);
+  d.ls_cur = (int32_t *)(b + L.lcur);
+  d.t3_md = (int4 *)(b + L.t3); d.t3_kappa = (float *)(b + L.t3k); d.t3_pos = (int32_t *)(b + L.t3s);
+  d.t3_cnt = (int32_t *)(b + L.t3c); d.t3u_md = (int4 *)(b + L.t3u); d.t3u_kappa = (float *)(b + L.t3uk);
+  d.t5_a = (int4 *)(b + L.t5a); d.t5_b = (int4 *)(b + L.t5b); d.t5_score = (float *)(b + L.t5s);
+  d.t5_sel = (uint8_t *)(b + L.t5e); d.cnt = (int32_t *)(b + L.cnt);
+  d.tc_cnt = (int32_t *)(b + L.tcc); d.tc_pos = (int32_t *)(b + L.tcp); d.tc_list = (int32_t *)(b + L.tcl);
+  d.t5_tc = (uint8_t *)(b + L.tcf);
   s.hit_cap = H; s.md_cap = md; s.ls_cap = ls; s.t3_cap = t3; s.t5_cap = t5;
   d.md_cap = md; d.ls_cap = ls; d.t3_cap = t3; d.t5_cap = t5;
   return LST_OK;
@@ -1203,13 +1213,13 @@ struct ServeReq {
   int retries = 0;
 };
 
-// estimated device bytes of one event's object buffers (the slot layout of slot_alloc)
+// estimated device bytes of one event: its slot allocation (slot_layout) plus the hit input
+// buffer (16 bytes per hit)
 size_t est_bytes(const lst_ctx_s *c, int64_t n) {
   int md, ls, t3, t5;
   caps_for(c, n, md, ls, t3, t5);
-  const size_t nm = (size_t)c->g.n_mod;
-  return (size_t)n * 24 + nm * 8 * 4 + (size_t)md * (16 + 8 + 4 + 8 + 8 + 16 + 8 + 4 + 8) +
-         (size_t)ls * 12 + (size_t)t3 * 40 + (size_t)t5 * 37 + (size_t)n * 16;
+  const int64_t H = (int64_t)(std::max<int64_t>(n, 1024) * 1.1);
+  return slot_layout(H, (size_t)c->g.n_mod, md, ls, t3, t5).total + (size_t)n * 16;
 }
 
 }  // namespace
