@@ -249,8 +249,8 @@ void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5)
 // Byte offsets of one event's buffers in its slot allocation (H hits, nm modules, md/ls/t3/t5
 // object capacities); `total` is the allocation size.
 struct SlotLayout {
-  size_t hit, orig, hmod, scnt, soff, manc, mk, mmod, mh, mst, mcn, mcur, uanc, uk, umod, uh;
-  size_t ls, lst, lcn, lsu, lcur, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl, tcf, cnt;
+  size_t hit, orig, hmod, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank;
+  size_t ls, lst, lcn, lsu, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl, tcf, cnt;
   size_t total;
 };
 SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, size_t t5) {
@@ -258,11 +258,13 @@ SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, si
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   L.hit = take(16 * (size_t)H); L.orig = take(4 * (size_t)H); L.hmod = take(4 * (size_t)H);
+  L.hrank = take(4 * (size_t)H);
   L.scnt = take(4 * 2 * nm); L.soff = take(4 * (2 * nm + 1));
   L.manc = take(16 * md); L.mk = take(8 * md); L.mmod = take(4 * md); L.mh = take(8 * md);
-  L.mst = take(4 * nm); L.mcn = take(4 * nm); L.mcur = take(4 * nm);
+  L.mst = take(4 * nm); L.mcn = take(4 * nm);
   L.uanc = take(16 * md); L.uk = take(8 * md); L.umod = take(4 * md); L.uh = take(8 * md);
-  L.ls = take(16 * ls); L.lst = take(4 * md); L.lcn = take(4 * md); L.lsu = take(16 * ls); L.lcur = take(4 * md);
+  L.urank = take(4 * md);
+  L.ls = take(16 * ls); L.lst = take(4 * md); L.lcn = take(4 * md); L.lsu = take(16 * ls);
   L.t3 = take(16 * t3); L.t3k = take(4 * t3); L.t3s = take(4 * md); L.t3c = take(4 * md);
   L.t3u = take(16 * t3); L.t3uk = take(4 * t3);
   L.t5a = take(16 * t5); L.t5b = take(16 * t5); L.t5s = take(4 * t5); L.t5e = take(t5);
@@ -293,15 +295,15 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
   d.hit = (float4 *)(b + L.hit); d.hit_orig = (int32_t *)(b + L.orig); d.hit_mod = (int32_t *)(b + L.hmod);
+  d.hit_rank = (int32_t *)(b + L.hrank);
   d.sens_cnt = (int32_t *)(b + L.scnt); d.sens_off = (int32_t *)(b + L.soff);
   d.md_anchor = (float4 *)(b + L.manc); d.md_kappa = (float2 *)(b + L.mk); d.md_mod = (int32_t *)(b + L.mmod);
   d.md_hits = (int2 *)(b + L.mh); d.md_start = (int32_t *)(b + L.mst); d.md_cnt = (int32_t *)(b + L.mcn);
-  d.md_cur = (int32_t *)(b + L.mcur); d.mdu_anchor = (float4 *)(b + L.uanc); d.mdu_kappa = (float2 *)(b + L.uk);
-  d.mdu_mod = (int32_t *)(b + L.umod); d.mdu_hits = (int2 *)(b + L.uh);
+  d.mdu_anchor = (float4 *)(b + L.uanc); d.mdu_kappa = (float2 *)(b + L.uk);
+  d.mdu_mod = (int32_t *)(b + L.umod); d.mdu_hits = (int2 *)(b + L.uh); d.mdu_rank = (int32_t *)(b + L.urank);
   d.ls = (int4 *)(b + L.ls);
   d.ls_start = (int32_t *)(b + L.lst); d.ls_cnt = (int32_t *)(b + L.lcn);
   d.lsu = (int4 *)(b + L.lsu);
-  d.ls_cur = (int32_t *)(b + L.lcur);
   d.t3_md = (int4 *)(b + L.t3); d.t3_kappa = (float *)(b + L.t3k); d.t3_pos = (int32_t *)(b + L.t3s);
   d.t3_cnt = (int32_t *)(b + L.t3c); d.t3u_md = (int4 *)(b + L.t3u); d.t3u_kappa = (float *)(b + L.t3uk);
   d.t5_a = (int4 *)(b + L.t5a); d.t5_b = (int4 *)(b + L.t5b); d.t5_score = (float *)(b + L.t5s);

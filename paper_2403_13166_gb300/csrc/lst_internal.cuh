@@ -45,30 +45,30 @@ struct EvDesc {
   float4 *hit;                 // [n_hits] hits grouped by sensor: x, y, z, r
   int32_t *hit_orig;           // [n_hits] original index of each grouped hit
   int32_t *hit_mod;            // [n_hits] module of each grouped hit
-  int32_t *sens_cnt;           // [2 n_mod] histogram by key, then scatter cursor
+  int32_t *sens_cnt;           // [2 n_mod] histogram by key
+  int32_t *hit_rank;           // [n_hits] rank of each input hit within its key (input order)
   int32_t *sens_off;           // [2 n_mod + 1] key k < n_mod: lower sensor of module k,
                                // key n_mod + k: upper sensor of module k
   float4 *mdu_anchor;          // [md_cap] MDs as found, any order (same fields as below)
   float2 *mdu_kappa;
   int32_t *mdu_mod;
   int2 *mdu_hits;
+  int32_t *mdu_rank;           // [md_cap] rank of each MD within its module
   float4 *md_anchor;           // [md_cap] MDs grouped by module: lower-sensor hit (anchor) x, y, z, r
   float2 *md_kappa;            // [md_cap] (cut curvature, feature curvature); 0 for endcap
   int32_t *md_mod;             // [md_cap] module
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
-  int32_t *md_cur;             // [n_mod] scatter cursor of the grouping
   int4 *lsu;                   // [ls_cap] LSs as found, any order: (inner MD, outer MD,
-                               // bits of the curvature, -), one 16-byte record each
-  int4 *ls;                    // [ls_cap] the same, grouped by inner MD
+                               // bits of the curvature, rank within the inner MD)
+  int4 *ls;                    // [ls_cap] grouped by inner MD: (inner MD, outer MD, bits of
+                               // the curvature, 0), one 16-byte record each
   int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
-  int32_t *ls_cur;             // [md_cap] scatter cursor of the grouping
-  int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, -), any order
+  int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, rank within md0), any order
   float *t3u_kappa;            // [t3_cap]
-  int4 *t3_md;                 // [t3_cap] T3s grouped by first MD
+  int4 *t3_md;                 // [t3_cap] T3s grouped by first MD (md0, md1, md2, 0)
   float *t3_kappa;             // [t3_cap]
-  int32_t *t3_pos, *t3_cnt;    // [md_cap] per first MD: start of its range (end after the
-                               // grouping scatter) and count
+  int32_t *t3_pos, *t3_cnt;    // [md_cap] per first MD: start of its range and count
   int4 *t5_a;                  // [t5_cap] (md0, md1, md2, md3)
   int4 *t5_b;                  // [t5_cap] (md4, t3a, t3b, bits of the circle-fit chi2)
   float *t5_score;             // [t5_cap]

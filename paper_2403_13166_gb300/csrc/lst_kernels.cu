@@ -20,8 +20,9 @@ namespace lstk {
 // lower-sensor hits come first in the grouped order: key k < n_mod is the lower sensor of
 // module k, key n_mod + k its upper sensor. The whole grid walks the batch one event at a
 // time, so the sensor histogram (and in k_bin_scatter the output range) being filled is
-// one event's and stays in L2. Only the sensor ids are read here; the coordinates are
-// checked by k_bin_scatter (an invalid hit voids its event either way).
+// one event's and stays in L2. Each hit keeps the value its atomicAdd returned, its rank
+// within its sensor. Only the sensor ids are read here; the coordinates are checked by
+// k_bin_scatter (an invalid hit voids its event either way).
 __global__ void k_bin_count(const EvDesc *__restrict__ evs, int n_events, DevGeom g) {
   const int ns = 2 * g.n_mod, tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -33,13 +34,12 @@ __global__ void k_bin_count(const EvDesc *__restrict__ evs, int n_events, DevGeo
         atomicOr(ev.cnt + C_FLAGS, F_INPUT);
         continue;
       }
-      atomicAdd(ev.sens_cnt + (s & 1) * g.n_mod + (s >> 1), 1);
+      ev.hit_rank[i] = atomicAdd(ev.sens_cnt + (s & 1) * g.n_mod + (s >> 1), 1);
     }
   }
 }
 
-// Exclusive scan of the sensor histogram (one CTA per event); re-zeroes the histogram so
-// it serves as the scatter cursor.
+// Exclusive scan of the sensor histogram (one CTA per event).
 __global__ void k_bin_scan(const EvDesc *__restrict__ evs, DevGeom g) {
   const EvDesc &ev = evs[blockIdx.x];
   const int ns = 2 * g.n_mod;
@@ -66,7 +66,6 @@ __global__ void k_bin_scan(const EvDesc *__restrict__ evs, DevGeom g) {
     if (s < ns) {
       const int c = ev.sens_cnt[s];
       ev.sens_off[s] = run;
-      ev.sens_cnt[s] = 0;
       run += c;
     }
   }
@@ -75,8 +74,9 @@ __global__ void k_bin_scan(const EvDesc *__restrict__ evs, DevGeom g) {
 }
 
 // Scatter hits into sensor order as float4 (x, y, z, r) with r = sqrtf(x*x + y*y), event
-// by event like k_bin_count. A hit with a non-finite coordinate is placed like any other
-// (the counts stay consistent) and voids its event.
+// by event like k_bin_count, each to its sensor's offset plus its rank (no atomics). A hit
+// with a non-finite coordinate is placed like any other (the counts stay consistent) and
+// voids its event.
 __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevGeom g) {
   const int ns = 2 * g.n_mod, tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -88,7 +88,7 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
       if (s < 0 || s >= ns) continue;
       if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(ev.cnt + C_FLAGS, F_INPUT);
       const int key = (s & 1) * g.n_mod + (s >> 1);
-      const int pos = ev.sens_off[key] + atomicAdd(ev.sens_cnt + key, 1);
+      const int pos = ev.sens_off[key] + ev.hit_rank[i];
       ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
       ev.hit_orig[pos] = i;
       ev.hit_mod[pos] = s >> 1;
@@ -97,10 +97,12 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
 }
 
 // ===================================================================== shared machinery
-// The grouping scatters (k_md_scatter, k_ls_scatter, k_t3_scatter) walk the batch one event
-// at a time with the whole grid, SCATTER_ILP objects per thread and trip: the loads of all
-// of them go out before the first cursor atomic, and the output range being filled is one
-// event's, which stays in L2 until its sectors are complete.
+// The grouping scatters (k_md_scatter, k_ls_scatter, k_t3_scatter) need no atomics: the
+// producer counted each object with an atomicAdd on its group's counter and kept the value
+// it returned (the object's rank in its group), so the position is the group's start (an
+// exclusive scan of the counts) plus the rank. They walk the batch one event at a time with
+// the whole grid, SCATTER_ILP objects per thread and trip, and the output range being filled
+// is one event's, which stays in L2 until its sectors are complete.
 constexpr int SCATTER_ILP = 4;
 
 // Reserve n output slots: one atomicAdd per warp. Returns the base or -1 if the buffer
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
             ev.mdu_kappa[o] = make_float2(kc, kf);
             ev.mdu_mod[o] = w.mod[x];
             ev.mdu_hits[o] = make_int2(ev.hit_orig[w.lo[x]], ev.hit_orig[uh]);
-            atomicAdd(ev.md_cnt + w.mod[x], 1);
+            ev.mdu_rank[o] = atomicAdd(ev.md_cnt + w.mod[x], 1);
           }
         }
       }
@@ -271,12 +273,12 @@ __global__ void k_md_scan(const EvDesc *__restrict__ evs, DevGeom g) {
   int run = s_w[wid] + inc - local;
   for (int k = 0; k < per && b0 + k < n; k++) {
     ev.md_start[b0 + k] = run;
-    ev.md_cur[b0 + k] = run;
     run += ev.md_cnt[b0 + k];
   }
 }
 
-// ... then a scatter into module order.
+// ... then a scatter into module order: each MD to its module's start plus the rank the
+// producer drew when it counted the MD.
 __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
   const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
         if (o0 + k * st < n) m[k] = ev.mdu_mod[o0 + k * st];
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = atomicAdd(ev.md_cur + m[k], 1);
+        if (o0 + k * st < n) pos[k] = ev.md_start[m[k]] + ev.mdu_rank[o0 + k * st];
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++) {
         const int64_t o = o0 + k * st;
@@ -396,8 +398,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
       if (pass && base >= 0) {
         const int o = base + __popc(bal & lanemask_lt());
-        ev.lsu[o] = make_int4(gi, gm, __float_as_int(k), 0);
-        atomicAdd(ev.ls_cnt + gi, 1);
+        ev.lsu[o] = make_int4(gi, gm, __float_as_int(k), atomicAdd(ev.ls_cnt + gi, 1));
       }
     };
     for (int b0 = tb0; b0 < tb1; b0 += LS_TB) {
@@ -545,10 +546,9 @@ __global__ void k_ls_scan(const EvDesc *__restrict__ evs) {
   if (ev_void(ev)) return;
   const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
   block_exclusive_scan(ev.ls_cnt, ev.ls_start, n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ev.ls_cur[i] = ev.ls_start[i];
 }
 
-// ... then the LSs into their inner MD's range.
+// ... then the LSs into their inner MD's range (start plus the rank k_ls drew).
 __global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
   const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -563,10 +563,11 @@ __global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ e
         if (o0 + k * st < n) r[k] = ev.lsu[o0 + k * st];
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = atomicAdd(ev.ls_cur + r[k].x, 1);
+        if (o0 + k * st < n) pos[k] = ev.ls_start[r[k].x] + r[k].w;
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n && chk(ev, pos[k], ev.ls_cap, 24)) ev.ls[pos[k]] = r[k];   // one 16-byte store
+        if (o0 + k * st < n && chk(ev, pos[k], ev.ls_cap, 24))
+          ev.ls[pos[k]] = make_int4(r[k].x, r[k].y, r[k].z, 0);                // one 16-byte store
     }
   }
 }
@@ -658,9 +659,8 @@ __global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int 
         const int base = warp_reserve(ev.cnt + C_T3, ev.cnt + C_FLAGS, F_OVF_T3, __popc(bal), ev.t3_cap);
         if (pass && base >= 0) {
           const int o = base + __popc(bal & lanemask_lt());
-          ev.t3u_md[o] = make_int4(w.md0[x], w.md1[x], md2, 0);
+          ev.t3u_md[o] = make_int4(w.md0[x], w.md1[x], md2, atomicAdd(ev.t3_cnt + w.md0[x], 1));
           ev.t3u_kappa[o] = k;
-          atomicAdd(ev.t3_cnt + w.md0[x], 1);
         }
       }
     };
@@ -738,7 +738,8 @@ __global__ void k_t3_scan(const EvDesc *__restrict__ evs) {
   block_exclusive_scan(ev.t3_cnt, ev.t3_pos, clamp_count(ev.cnt[C_MD], ev.md_cap));
 }
 
-// ... then a scatter into that order; afterwards t3_pos[md] holds the END of md's range.
+// ... then a scatter into that order: each T3 to the start of its first MD's range plus the
+// rank the producer drew when it counted the T3.
 __global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ evs, int n_events) {
   const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -754,10 +755,10 @@ __global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ e
         if (o0 + k * st < n) { t[k] = ev.t3u_md[o0 + k * st]; k3[k] = ev.t3u_kappa[o0 + k * st]; }
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = atomicAdd(ev.t3_pos + t[k].x, 1);
+        if (o0 + k * st < n) pos[k] = ev.t3_pos[t[k].x] + t[k].w;
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) { ev.t3_md[pos[k]] = t[k]; ev.t3_kappa[pos[k]] = k3[k]; }
+        if (o0 + k * st < n) { ev.t3_md[pos[k]] = make_int4(t[k].x, t[k].y, t[k].z, 0); ev.t3_kappa[pos[k]] = k3[k]; }
     }
   }
 }
@@ -797,7 +798,7 @@ __global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int 
     if (ta < nt3) {
       const int4 A3 = ev.t3_md[ta];
       deg = ev.t3_cnt[A3.z];
-      w.st2[lane] = ev.t3_pos[A3.z] - deg;
+      w.st2[lane] = ev.t3_pos[A3.z];
       w.ta[lane] = ta;
       w.ka[lane] = ev.t3_kappa[ta];
       w.md1[lane] = A3.y;
