@@ -330,11 +330,14 @@ def run_gpu(args, rank, world, local_rank, pool):
             h.release()
         return int(offs[-1]) * (40 + 4 + 1) + 8 * (B + 1)
 
+    # two streams in turn, so that batch k+1's host-to-device copies overlap batch k's kernels
+    e2e_streams = [stream, torch.cuda.Stream(dev)]
+
     def e2e_run(steps):
         # batch k+1 is enqueued (H2D + kernels) before batch k's results are read back
         prev, d2h = None, 0
-        for _ in range(steps):
-            hs = ctx.run_batch(pinned, stream)
+        for k in range(steps):
+            hs = ctx.run_batch(pinned, e2e_streams[k % 2])
             if prev is not None:
                 d2h += export(prev)
             prev = hs

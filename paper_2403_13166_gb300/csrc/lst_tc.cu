@@ -84,32 +84,35 @@ __global__ void __launch_bounds__(256) k_tc_scatter(const EvDesc *__restrict__ e
   }
 }
 
-// The track-candidate decision of every T5 of the batch, and the count per event.
+// The track-candidate decision of every T5 of the batch, and the count per event. TC_LANES
+// lanes share one T5 and walk its three lists in an interleaved way, so that a warp holds
+// 32 / TC_LANES T5s and the lanes of a long list do not wait alone.
+constexpr int TC_LANES = 4;
 __global__ void __launch_bounds__(256) k_tc_decide(const EvDesc *__restrict__ evs, int n_events) {
   __shared__ int s_pref[MAX_EVENTS + 1];
   block_event_prefix(n_events, [&](int e) { return t5_total(evs[e]); }, s_pref);
   const int total = s_pref[n_events];
-  const int lane = threadIdx.x & 31;
-  const int stride = gridDim.x * blockDim.x;
-  // warp-uniform trip count so that the per-event count below sees the full warp
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    const int uu = base + lane;
-    bool keep = false;
-    int e = 0;
+  const int lane = threadIdx.x & 31, sub = lane / TC_LANES, sl = lane % TC_LANES;
+  const int stride = gridDim.x * (blockDim.x / TC_LANES);
+  // warp-uniform trip count so that the votes below see the full warp
+  for (int base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / TC_LANES; base < total; base += stride) {
+    const int uu = base + sub;
+    bool sel = false, beaten = false;
+    int e = 0, t = 0;
     if (uu < total) {
       e = find_event(s_pref, n_events, uu);
       const EvDesc &ev = evs[e];
-      const int t = uu - s_pref[e];
-      keep = ev.t5_sel[t] != 0;
-      if (keep) {
+      t = uu - s_pref[e];
+      sel = ev.t5_sel[t] != 0;
+      if (sel) {
         int mt[5];
         t5_mds(ev, t, mt);
         const float qt = tc_rank(__int_as_float(ev.t5_b[t].w));
         // a duplicate shares >= 3 of t's 5 MDs, so at least one of t's middle three: the
         // lists of md1..md3 (every selected T5 is listed under all 5 of its MDs) hold them all
-        for (int j = 1; j <= 3 && keep; j++) {
+        for (int j = 1; j <= 3 && !beaten; j++) {
           const int end = ev.tc_pos[mt[j]], beg = end - ev.tc_cnt[mt[j]];
-          for (int k = beg; k < end && keep; k++) {
+          for (int k = beg + sl; k < end && !beaten; k += TC_LANES) {
             const int u = ev.tc_list[k];
             if (u == t) continue;
             const int4 ua = ev.t5_a[u], ub = ev.t5_b[u];
@@ -121,14 +124,18 @@ __global__ void __launch_bounds__(256) k_tc_decide(const EvDesc *__restrict__ ev
               for (int b = 0; b < 5; b++) shared += mt[a] == mu[b];
             if (shared < TC_MIN_SHARED) continue;
             const float qu = tc_rank(__int_as_float(ub.w));
-            if (qu < qt || (qu == qt && key_less(ev, mu, mt))) keep = false;
+            if (qu < qt || (qu == qt && key_less(ev, mu, mt))) beaten = true;
           }
         }
       }
-      ev.t5_tc[t] = keep ? 1 : 0;
     }
-    const unsigned act = __ballot_sync(FULL, uu < total);
-    if (uu < total) {
+    const unsigned gmask = ((1u << TC_LANES) - 1) << (sub * TC_LANES);
+    const unsigned vb = __ballot_sync(FULL, beaten);        // every lane votes (not under &&)
+    const bool keep = sel && (vb & gmask) == 0;
+    if (uu < total && sl == 0) evs[e].t5_tc[t] = keep ? 1 : 0;
+    const bool lead = uu < total && sl == 0;
+    const unsigned act = __ballot_sync(FULL, lead);
+    if (lead) {
       const unsigned same = __match_any_sync(act, e);
       const unsigned kb = __ballot_sync(act, keep) & same;
       if ((same & lanemask_lt()) == 0 && kb) atomicAdd(evs[e].cnt + C_NTC, __popc(kb));
