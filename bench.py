@@ -374,7 +374,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     step = step_roofline(mean_counts, pairs, float(np.mean(n_hits)), float(np.mean(np.diff(g.map_off))),
                          value, clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
     if graph is not None:   # the graph build inside the batched launch: grouping, MD and LS stages
-        graph["build_ms_per_event_batched"] = round(float(stage_ms[0] + stage_ms[1] + stage_ms[2]) / B, 4)
+        graph["build_ms_per_event_batched"] = round(float(sum(stage_ms[:4])) / B, 4)
     roofline["launches_timed"] = int(n_launch)
 
     line = {
@@ -466,10 +466,10 @@ STRICT_OPS = {"ls": (12, 35)}
 
 
 # DRAM bytes (read + write) per event of a kernel, from one ncu capture of a 16-event
-# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 53.0 + 176.1
-# MB for k_ls); the traffic is the per-event output plus MD reads, so it scales with the
-# events.
-TRAFFIC_PER_EVENT = {"ls": 229.06e6 / 16}
+# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 59.18 +
+# 238.40 MB for k_ls); the traffic is the per-event LS output plus MD reads, so it scales
+# with the events.
+TRAFFIC_PER_EVENT = {"ls": 297.58e6 / 16}
 
 
 def traffic_per_launch(stage, events):

@@ -47,9 +47,9 @@ typedef enum lst_status {
  * removal (see lst_get_candidates). */
 typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3, LST_TC = 4 } lst_kind;
 
-/* Timed stages of one launch (lst_stage_times): hit grouping, steps 1-4, score, track
- * candidates. */
-#define LST_N_STAGES 7
+/* Timed stages of one launch (lst_stage_times): hit grouping, step 1, step 2 (the LS
+ * kernel, then the grouping of the LSs by inner MD), steps 3-4, score, track candidates. */
+#define LST_N_STAGES 8
 /* Arithmetic of the T5-DNN score (Section 2 network). LST_FP32: CUDA cores. LST_BF16:
  * tensor cores, BF16 operands, FP32 accumulation. LST_BF16X3: tensor cores, each operand
  * split into BF16 hi + lo parts and hi*hi + lo*hi + hi*lo accumulated in FP32 (about 16
@@ -260,8 +260,8 @@ lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);
 /* Per-stage device timing. lst_set_timing(ctx, 1) resets the statistics and makes every
  * later launch (lst_run_event and lst_run_batch, graph launches included) record CUDA
  * events at the stage boundaries on the launch stream. lst_stage_times fills ms[LST_N_STAGES]
- * with the mean device time per launch of each stage in ms (0 bin, 1 md, 2 ls, 3 t3, 4 t5,
- * 5 score, 6 track candidates) and returns the number of launches averaged. */
+ * with the mean device time per launch of each stage in ms (0 bin, 1 md, 2 ls, 3 ls_group,
+ * 4 t3, 5 t5, 6 score, 7 track candidates) and returns the number of launches averaged. */
 lst_status lst_set_timing(lst_ctx ctx, int32_t enable);
 lst_status lst_stage_times(lst_ctx ctx, float *ms, int64_t *n_launches);
 

@@ -32,7 +32,7 @@ SPACE = {
     "t5_threads": (64, 128, 256),
     "sc_threads": (128, 256),
 }
-STAGE = {"md_threads": 1, "ls_threads": 2, "ls_list": 2, "t3_threads": 3, "t5_threads": 4, "sc_threads": 5}
+STAGE = {"md_threads": 1, "ls_threads": 2, "ls_list": 2, "t3_threads": 4, "t5_threads": 5, "sc_threads": 6}
 COUNT_KEYS = ("md", "ls", "t3", "t5", "tc", "selected")
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned", "launch_cache.json")
 

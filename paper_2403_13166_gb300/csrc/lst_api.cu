@@ -407,15 +407,16 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
       k_ls<<<c->grid_ls, c->ls_threads, ls_smem(c), st>>>(L.d_desc, n, g, c->cuts, L.d_work + 1, nullptr, g.n_mod,
                                                          0);
   }
+  mark(3);
   k_ls_scan<<<n, 1024, 0, st>>>(L.d_desc);
   k_ls_scatter<<<c->grid_ls_scatter, 256, 0, st>>>(L.d_desc, n);
-  mark(3);
+  mark(4);
   k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts);
   k_t3_scan<<<n, 1024, 0, st>>>(L.d_desc);
   k_t3_scatter<<<c->grid_t3_scatter, 256, 0, st>>>(L.d_desc, n);
-  mark(4);
-  k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
   mark(5);
+  k_t5<<<c->grid_t5, c->t5_threads, t5_smem(c), st>>>(L.d_desc, n, c->cuts);
+  mark(6);
   if (c->cfg.precision != LST_FP32)
     CU(launch_score_bf16_events(c->grid_bf[c->cfg.precision == LST_BF16X3], st, L.d_desc, n, g, c->cuts, c->d_wpack,
                                 c->d_w, c->n_hidden, c->d_err, c->wait_limit, c->cfg.precision == LST_BF16X3,
@@ -423,12 +424,12 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   else
     k_score_fp32<<<c->grid_sc, c->sc_threads, (size_t)mlp_floats_host(c->n_hidden) * 4, st>>>(
         L.d_desc, n, g, c->cuts, c->d_w, c->n_hidden);
-  mark(6);
+  mark(7);
   k_tc_count<<<c->grid_tc_count, 256, 0, st>>>(L.d_desc, n);
   k_tc_scan<<<n, 1024, 0, st>>>(L.d_desc);
   k_tc_scatter<<<c->grid_tc_scatter, 256, 0, st>>>(L.d_desc, n);
   k_tc_decide<<<c->grid_tc_decide, 256, 0, st>>>(L.d_desc, n);
-  mark(7);
+  mark(8);
   k_collect<<<(n + 127) / 128, 128, 0, st>>>(L.d_desc, n, L.d_counts);
   CU(cudaMemcpyAsync(L.h_counts, L.d_counts, sizeof(int) * C_NCOUNTERS * n, cudaMemcpyDeviceToHost, st));
   CU(cudaGetLastError());

@@ -21,9 +21,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblst.so")
 LST_OK, LST_ERR_ARG, LST_ERR_CAPACITY, LST_ERR_CUDA, LST_ERR_TIMEOUT, LST_ERR_NOT_READY, \
     LST_ERR_INPUT, LST_ERR_NOMEM = range(8)
 LST_MD, LST_LS, LST_T3, LST_T5, LST_TC = range(5)
-N_STAGES = 7
+N_STAGES = 8
 GRAPH_NODE_FEATURES, GRAPH_EDGE_FEATURES = 6, 2
-STAGES = ("bin", "md", "ls", "t3", "t5", "score", "tc")
+STAGES = ("bin", "md", "ls", "ls_group", "t3", "t5", "score", "tc")
 LST_FP32, LST_BF16, LST_BF16X3 = 0, 1, 2
 WIDTH = {LST_MD: 2, LST_LS: 4, LST_T3: 6, LST_T5: 10, LST_TC: 10}
 NFEAT = 38
