@@ -1,0 +1,188 @@
+"""The necessary tests that the CUDA kernels run before the exact FP32 cuts (md_prefilter,
+ls_prefilter + ls_kappa_prefilter, t3_prefilter in csrc/lst_internal.cuh) must never
+reject an object the exact cut accepts; their rounding slacks are argued in the header
+comments. Here each test is restated in float32 numpy (a fused multiply-add as an exact
+float64 product plus a sum rounded once to float32; the approximate reciprocal and
+reciprocal square root perturbed by +-2e-7 relative, above their documented error) and
+evaluated on every MD, LS and T3 the oracle accepts in one PU200-like event: none may fail.
+A sample of candidate pairs also checks that the LS tests are selective. CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_13166_gb300 import synth
+
+f32, f64 = np.float32, np.float64
+APPROX = (1.0 - 2e-7, 1.0 + 2e-7)
+
+
+def fma(a, b, c):
+    return (np.asarray(a, f64) * np.asarray(b, f64) + np.asarray(c, f64)).astype(f32)
+
+
+def full(shape, v):
+    return np.full(shape, f32(v), f32)
+
+
+@pytest.fixture(scope="module")
+def event(geom_full, cuts):
+    e = synth.pileup_event(geom_full, 11, pileup=200, mean_per_vertex=96)
+    r = oracle.run_event(geom_full, e, cuts, None)
+    x, y, z = (a.astype(f32) for a in (e.x, e.y, e.z))
+    r_ = np.sqrt(x * x + y * y).astype(f32)
+    return e, r, (x, y, z, r_)
+
+
+def md_prefilter(L, U, endcap, c):
+    """md_prefilter / md_low of csrc/lst_internal.cuh, float32."""
+    Lx, Ly, Lz, Lr = L
+    Ux, Uy, Uz, Ur = U
+    km, e, gap, zl = (f32(c[k]) for k in ("kappa_max", "hit_err", "sensor_gap", "z_lum"))
+    with np.errstate(all="ignore"):
+        dx, dy, dz = Ux - Lx, Uy - Ly, Uz - Lz
+        dt = Lx * dx + Ly * dy
+        cr = fma(Lx, dy, -(Ly * dx))
+        # endcap
+        az, r2 = np.abs(Lz), Lr * Lr
+        wz = np.where(az > zl, r2 * zl / (az - zl), f32(np.inf)).astype(f32)
+        erz, erl = e * Lr * az, e * Lr
+        S = Lr * (f32(0.5) * km)
+        T = (S / np.sqrt(f32(1.0) - S * S)).astype(f32)
+        t1, t2 = dt * az, np.abs(dz) * r2
+        rr = fma(np.abs(dz), wz, erz)
+        road = np.abs(t1 - t2) <= rr + f32(1e-3) * (np.abs(t1) + t2 + rr) + f32(1e-6)
+        bb = fma(dt, T, erl)
+        bend_e = np.abs(cr) <= bb + f32(1e-3) * (np.abs(dt * T) + erl) + f32(1e-6)
+        ec = (dt > 0) & (dz * Lz > 0) & road & bend_e
+        # barrel
+        hb = Lr * (f32(0.5) * km) + e / gap
+        hb2r2 = (Lr * hb) * (Lr * hb) * f32(1.001)
+        dT2 = fma(dx, dx, dy * dy)
+        bend = cr * cr <= fma(hb2r2, dT2, full(dT2.shape, 1e-9))
+        dr = Ur - Lr
+        a, b = dz * Lr, Lz * dr
+        rhs = fma(full(dr.shape, zl), dr, erl)
+        zr = np.abs(a - b) <= rhs + f32(1e-3) * (np.abs(a) + np.abs(b) + np.abs(rhs)) + f32(1e-6)
+        br = (dt > 0) & bend & zr
+    return np.where(endcap, ec, br)
+
+
+def ls_prefilters(A, B, kA, kB, bA, bB, c, rel):
+    """ls_prefilter and ls_kappa_prefilter, float32 (rel: the rsqrt approximation)."""
+    Ax, Ay, Az, Ar = A
+    Bx, By, Bz, Br = B
+    km, e, gap, zl = (f32(c[k]) for k in ("kappa_max", "hit_err", "sensor_gap", "z_lum"))
+    with np.errstate(all="ignore"):
+        # first test
+        a2 = Ax * Ax + Ay * Ay - f32(0.05)
+        X = Br * (f32(0.5) * km)
+        k1 = f32(1.002) * f32(1.015625) * X * X
+        k0 = f32(1.002) * f32(65.0) * (e * e)
+        p = fma(Az, Br, -(Ar * Bz))
+        z0 = np.abs(p) <= fma(full(p.shape, zl + e), np.abs(Br - Ar), e * Ar + f32(0.05))
+        dirn = fma(Ax, Bx, Ay * By) > a2
+        cr = fma(Ax, By, -(Ay * Bx))
+        dx, dy = Bx - Ax, By - Ay
+        dT2 = fma(dx, dx, dy * dy)
+        bend = cr * cr <= fma(Ar * Ar, fma(k1, dT2, full(dT2.shape, k0)), full(dT2.shape, 0.05))
+        first = z0 & dirn & bend
+        # curvature test
+        Gp = f32(f32(2.0) * (e / gap) * f32(1.000001))
+        ce = f32(f32(2.0) * e * f32(1.000001))
+        dT = (dT2 * (f32(1.0) / np.sqrt(dT2)) * f32(rel)).astype(f32)
+        cr2 = f32(2.0) * cr
+        u, v = Br * dT, Ar * dT
+        c0 = fma(full(Ar.shape, ce), Ar, full(Ar.shape, 0.01))
+        s0 = fma(Ar, Br, v)
+        pa, pb = kA * Ar * u, kB * Br * v
+        fa = fma(full(pa.shape, -1e-6), np.abs(pa) + s0, np.abs(pa - cr2)) > fma(full(u.shape, Gp), u, c0)
+        fb = fma(full(pb.shape, -1e-6), np.abs(pb) + s0, np.abs(pb - cr2)) > fma(full(v.shape, Gp), v, c0)
+        second = ~((bA & fa) | (bB & fb))
+    return first, second
+
+
+def t3_prefilter(P0, P1, P2, c, rel):
+    """t3_prefilter from the per-first-LS values, float32."""
+    K = f32(c["kappa_max"]) * f32(c["t3_kappa_factor"])
+    K2 = f32(K * K * f32(1.001))
+    tolp = f32(f32(c["t3_rz_tol"]) * f32(1.001) + f32(3e-4))
+    with np.errstate(all="ignore"):
+        ax, ay = P1[0] - P0[0], P1[1] - P0[1]
+        a2 = fma(ax, ax, ay * ay)
+        a = (a2 * (f32(1.0) / np.sqrt(np.maximum(a2, f32(1e-30)))) * f32(rel)).astype(f32)
+        a3 = a * a2
+        dz01 = P1[2] - P0[2]
+        bx, by = P2[0] - P1[0], P2[1] - P1[1]
+        cx, cy = ax + bx, ay + by
+        b2, c2 = fma(bx, bx, by * by), fma(cx, cx, cy * cy)
+        t = f32(2.0) * fma(ax, by, -(ay * bx))
+        abc2, tt = a2 * b2 * c2, t * t
+        pt = tt <= fma(full(abc2.shape, K2), abc2, full(abc2.shape, 1e-12))
+        k24 = ((tt * (f32(1.0) / np.maximum(abc2, f32(1e-30)))) * f32(rel)).astype(f32) * f32(1.0 / 24.0)
+        b = (b2 * (f32(1.0) / np.sqrt(np.maximum(b2, f32(1e-30)))) * f32(rel)).astype(f32)
+        s01, s12 = fma(a3, k24, a), fma(b * b2, k24, b)
+        lhs = fma(dz01, s12, -((P2[2] - P1[2]) * s01))
+    return pt & (np.abs(lhs) <= tolp * (s01 + s12))
+
+
+def test_md_prefilter_keeps_every_mini_doublet(event, geom_full, cuts):
+    e, r, H = event
+    lo, up = r.md_lo, r.md_up
+    endcap = geom_full.subdet[r.md_mod] != 0
+    ok = md_prefilter(tuple(h[lo] for h in H), tuple(h[up] for h in H), endcap, cuts)
+    assert len(lo) > 100_000 and ok.all(), int((~ok).sum())
+
+
+def test_ls_prefilters_keep_every_line_segment(event, geom_full, cuts):
+    e, r, H = event
+    anchors = tuple(h[r.md_lo] for h in H)
+    A = tuple(a[r.ls_in] for a in anchors)
+    B = tuple(a[r.ls_out] for a in anchors)
+    kA, kB = r.md_kappa[r.ls_in].astype(f32), r.md_kappa[r.ls_out].astype(f32)
+    bA, bB = geom_full.subdet[r.md_mod[r.ls_in]] == 0, geom_full.subdet[r.md_mod[r.ls_out]] == 0
+    assert len(r.ls_in) > 1_000_000
+    for rel in APPROX:
+        first, second = ls_prefilters(A, B, kA, kB, bA, bB, cuts, rel)
+        assert first.all(), int((~first).sum())
+        assert second.all(), int((~second).sum())
+
+
+def test_ls_prefilters_are_selective(event, geom_full, cuts):
+    """Over all candidate pairs of 300 modules: the first test keeps about a tenth, the
+    curvature test brings it close to the accepted fraction."""
+    e, r, H = event
+    g = geom_full
+    anchors = tuple(h[r.md_lo] for h in H)
+    kap = r.md_kappa.astype(f32)
+    order = np.argsort(r.md_mod, kind="stable")
+    cnt = np.bincount(r.md_mod, minlength=g.n_mod)
+    start = np.concatenate([[0], np.cumsum(cnt)])
+    acc = set(zip(r.ls_in.tolist(), r.ls_out.tolist()))
+    n = n1 = n2 = n_acc = 0
+    for m in np.flatnonzero(cnt)[::max(1, len(np.flatnonzero(cnt)) // 300)]:
+        ia = order[start[m]:start[m + 1]]
+        tg = g.map_tgt[g.map_off[m]:g.map_off[m + 1]]
+        ib = np.concatenate([order[start[t]:start[t + 1]] for t in tg]) if len(tg) else np.zeros(0, int)
+        if len(ib) == 0:
+            continue
+        ii, jj = np.repeat(ia, len(ib)), np.tile(ib, len(ia))
+        first, second = ls_prefilters(tuple(a[ii] for a in anchors), tuple(a[jj] for a in anchors), kap[ii],
+                                      kap[jj], np.full(len(ii), g.subdet[m] == 0),
+                                      g.subdet[r.md_mod[jj]] == 0, cuts, 1.0)
+        n += len(ii)
+        n1 += int(first.sum())
+        n2 += int((first & second).sum())
+        n_acc += sum((a, b) in acc for a, b in zip(ii.tolist(), jj.tolist()))
+    assert n > 1_000_000
+    assert n_acc <= n2 <= 1.05 * n_acc + 10
+    assert n2 < 0.3 * n1 < 0.05 * n
+
+
+def test_t3_prefilter_keeps_every_triplet(event, cuts):
+    e, r, H = event
+    anchors = tuple(h[r.md_lo] for h in H)
+    P = [tuple(a[r.t3_md[:, k]] for a in anchors) for k in range(3)]
+    assert len(r.t3_md) > 100_000
+    for rel in APPROX:
+        ok = t3_prefilter(P[0], P[1], P[2], cuts, rel)
+        assert ok.all(), int((~ok).sum())
