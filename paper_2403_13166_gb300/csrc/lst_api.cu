@@ -1243,11 +1243,20 @@ struct lst_server_s {
   std::vector<ServeReq> inflight[2];
   cudaStream_t st[2] = {nullptr, nullptr};
   size_t mem_in_use = 0;
+  // pinned staging of one lane batch's T5 results (one batched export per finished batch)
+  int32_t *stage_hits = nullptr;
+  float *stage_score = nullptr;
+  uint8_t *stage_sel = nullptr;
+  int64_t stage_cap = 0;
 };
 
 namespace {
 
-void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t *cnt) {
+// One finished request: its result (counts, times, and a copy of its T5 tuples, scores and
+// selection flags from the batch's staging, if any) goes to the done queue; the slot and its
+// memory budget are released.
+void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t *cnt, const int32_t *t5_hits,
+                  const float *t5_score, const uint8_t *t5_sel, int64_t n5) {
   lst_ctx_s *c = S->c;
   lst_serve_result res;
   std::memset(&res, 0, sizeof res);
@@ -1264,18 +1273,18 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   res.t_arrival = r.t_arrival;
   res.t_admit = r.t_admit;
   res.t_launch = r.t_launch;
-  if (status == LST_OK && S->cfg.copy_t5 && cnt && cnt[C_T5] > 0) {
-    const int64_t n5 = cnt[C_T5];
+  if (status == LST_OK && t5_hits && n5 > 0) {
     res.t5_hits = (int32_t *)std::malloc((size_t)n5 * 10 * 4);
     res.t5_score = (float *)std::malloc((size_t)n5 * 4);
     res.t5_sel = (uint8_t *)std::malloc((size_t)n5);
-    lst_event_s ev{c, r.slot, LST_OK};
-    int64_t got = 0;
-    if (!res.t5_hits || !res.t5_score || !res.t5_sel ||
-        lst_get_candidates(&ev, LST_T5, res.t5_hits, res.t5_score, res.t5_sel, n5, &got) != LST_OK) {
+    if (!res.t5_hits || !res.t5_score || !res.t5_sel) {
       res.status = LST_ERR_CUDA;
+    } else {
+      std::memcpy(res.t5_hits, t5_hits, (size_t)n5 * 10 * 4);
+      std::memcpy(res.t5_score, t5_score, (size_t)n5 * 4);
+      std::memcpy(res.t5_sel, t5_sel, (size_t)n5);
+      res.n_t5 = n5;
     }
-    res.n_t5 = got;
   }
   res.t_done = now_s();
   c->slots[r.slot].busy = false;
@@ -1283,6 +1292,60 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   std::lock_guard<std::mutex> lk(S->mu);
   S->done.push_back(res);
   S->cv.notify_all();
+}
+
+// Finish the requests of one lane batch: the T5 results of every successful event are
+// exported together (lst_get_candidates_batch into the server's pinned staging: one gather
+// per event on the auxiliary stream, one copy, one synchronisation), then split per request.
+void serve_finish_batch(lst_server_s *S, std::vector<ServeReq> &done, const std::vector<lst_status> &st) {
+  lst_ctx_s *c = S->c;
+  std::vector<lst_event_s> evs;
+  std::vector<int> which;
+  int64_t total = 0;
+  if (S->cfg.copy_t5) {
+    for (size_t k = 0; k < done.size(); k++) {
+      const int32_t *cnt = c->slots[done[k].slot].cnt;
+      if (st[k] == LST_OK && cnt[C_T5] > 0) {
+        evs.push_back(lst_event_s{c, done[k].slot, LST_OK});
+        which.push_back((int)k);
+        total += cnt[C_T5];
+      }
+    }
+  }
+  std::vector<int64_t> offs(evs.size() + 1, 0);
+  lst_status xs = LST_OK;
+  if (!evs.empty()) {
+    if (S->stage_cap < total) {
+      cudaFreeHost(S->stage_hits);
+      cudaFreeHost(S->stage_score);
+      cudaFreeHost(S->stage_sel);
+      S->stage_hits = nullptr; S->stage_score = nullptr; S->stage_sel = nullptr; S->stage_cap = 0;
+      const int64_t cap = total + total / 4 + 1024;
+      if (cudaMallocHost(&S->stage_hits, (size_t)cap * 10 * 4) == cudaSuccess &&
+          cudaMallocHost(&S->stage_score, (size_t)cap * 4) == cudaSuccess &&
+          cudaMallocHost(&S->stage_sel, (size_t)cap) == cudaSuccess)
+        S->stage_cap = cap;
+    }
+    std::vector<lst_event> hs(evs.size());
+    for (size_t i = 0; i < evs.size(); i++) hs[i] = &evs[i];
+    xs = S->stage_cap >= total ? lst_get_candidates_batch(hs.data(), (int32_t)hs.size(), LST_T5, S->stage_hits,
+                                                          S->stage_score, S->stage_sel, S->stage_cap, offs.data())
+                               : LST_ERR_CUDA;
+  }
+  size_t j = 0;
+  for (size_t k = 0; k < done.size(); k++) {
+    const int32_t *cnt = c->slots[done[k].slot].cnt;          // the lane was harvested
+    if (j < which.size() && which[j] == (int)k) {
+      if (xs == LST_OK)
+        serve_finish(S, done[k], st[k], cnt, S->stage_hits + offs[j] * 10, S->stage_score + offs[j],
+                     S->stage_sel + offs[j], offs[j + 1] - offs[j]);
+      else
+        serve_finish(S, done[k], LST_ERR_CUDA, cnt, nullptr, nullptr, nullptr, 0);
+      j++;
+    } else {
+      serve_finish(S, done[k], st[k], cnt, nullptr, nullptr, nullptr, 0);
+    }
+  }
 }
 
 void serve_loop(lst_server_s *S) {
@@ -1342,7 +1405,7 @@ void serve_loop(lst_server_s *S) {
       for (auto &r : batch) r.t_launch = tl;
       if (st == LST_OK) st = run_lane(c, L, (int)batch.size(), ids.data(), S->st[li], true, false);
       if (st != LST_OK) {
-        for (auto &r : batch) serve_finish(S, r, st, nullptr);
+        for (auto &r : batch) serve_finish(S, r, st, nullptr, nullptr, nullptr, nullptr, 0);
         continue;
       }
       S->inflight[li] = std::move(batch);
@@ -1355,6 +1418,8 @@ void serve_loop(lst_server_s *S) {
       const cudaError_t q = cudaEventQuery(L.done);
       if (q == cudaErrorNotReady) continue;
       lst_status st = q == cudaSuccess ? lane_harvest(c, L) : LST_ERR_CUDA;
+      std::vector<ServeReq> fin;
+      std::vector<lst_status> fst;
       for (auto &r : S->inflight[li]) {
         Slot &sl = c->slots[r.slot];
         const lst_status es = st != LST_OK ? st : status_of(sl.cnt);
@@ -1364,7 +1429,13 @@ void serve_loop(lst_server_s *S) {
           S->ready.push_front(r);
           continue;
         }
-        serve_finish(S, r, es, st == LST_OK ? sl.cnt : nullptr);
+        fin.push_back(r);
+        fst.push_back(es);
+      }
+      if (st != LST_OK) {
+        for (auto &r : fin) serve_finish(S, r, st, nullptr, nullptr, nullptr, nullptr, 0);
+      } else {
+        serve_finish_batch(S, fin, fst);
       }
       S->inflight[li].clear();
       progress = true;
@@ -1457,6 +1528,9 @@ lst_status lst_serve_stop(lst_server S) {
   if (S->th.joinable()) S->th.join();
   for (auto &r : S->done) lst_serve_free_result(&r);
   for (auto &s : S->st) if (s) cudaStreamDestroy(s);
+  cudaFreeHost(S->stage_hits);
+  cudaFreeHost(S->stage_score);
+  cudaFreeHost(S->stage_sel);
   delete S;
   return LST_OK;
 }
