@@ -16,6 +16,12 @@
 namespace lstk {
 
 // ===================================================================== step 0: hit binning
+// The grouping scatters of MDs and T3s (an event has fewer of them than the grid has
+// threads) walk the batch GROUP_EV events at a time, each thread taking the same index in
+// all of them, so that GROUP_EV independent dependency chains (load -> dependent offset
+// load -> store) are in flight per thread. The hit binning walks one event at a time: side
+// by side it was slower.
+constexpr int GROUP_EV = 4;
 // Count hits per sensor. Sensors are keyed as (sensor & 1) * n_mod + module, so that all
 // lower-sensor hits come first in the grouped order: key k < n_mod is the lower sensor of
 // module k, key n_mod + k its upper sensor. The whole grid walks the batch one event at a
@@ -100,9 +106,9 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
 // The grouping scatters (k_md_scatter, k_ls_scatter, k_t3_scatter) need no atomics: the
 // producer counted each object with an atomicAdd on its group's counter and kept the value
 // it returned (the object's rank in its group), so the position is the group's start (an
-// exclusive scan of the counts) plus the rank. They walk the batch one event at a time with
-// the whole grid, SCATTER_ILP objects per thread and trip, and the output range being filled
-// is one event's, which stays in L2 until its sectors are complete.
+// exclusive scan of the counts) plus the rank. k_ls_scatter walks the batch one event at a
+// time with the whole grid, SCATTER_ILP LSs per thread and trip (an event has more LSs than
+// the grid has threads); k_md_scatter and k_t3_scatter take GROUP_EV events side by side.
 constexpr int SCATTER_ILP = 4;
 
 // Reserve n output slots: one atomicAdd per warp. Returns the base or -1 if the buffer
@@ -280,23 +286,30 @@ __global__ void k_md_scan(const EvDesc *__restrict__ evs, DevGeom g) {
 // ... then a scatter into module order: each MD to its module's start plus the rank the
 // producer drew when it counted the MD.
 __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
-  const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  for (int e = 0; e < n_events; e++) {
-    const EvDesc &ev = evs[e];
-    if (ev_void(ev)) continue;
-    const int64_t n = clamp_count(ev.cnt[C_MD], ev.md_cap);
-    for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
-      int m[SCATTER_ILP], pos[SCATTER_ILP];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int e0 = 0; e0 < n_events; e0 += GROUP_EV) {
+    int n[GROUP_EV], nmax = 0;
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) m[k] = ev.mdu_mod[o0 + k * st];
+    for (int k = 0; k < GROUP_EV; k++) {
+      n[k] = 0;
+      if (e0 + k < n_events) {
+        const EvDesc &ev = evs[e0 + k];
+        n[k] = ev_void(ev) ? 0 : clamp_count(ev.cnt[C_MD], ev.md_cap);
+      }
+      nmax = max(nmax, n[k]);
+    }
+    for (int o = tid; o < nmax; o += st) {
+      int m[GROUP_EV], pos[GROUP_EV];
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = ev.md_start[m[k]] + ev.mdu_rank[o0 + k * st];
+      for (int k = 0; k < GROUP_EV; k++)
+        if (o < n[k]) { m[k] = evs[e0 + k].mdu_mod[o]; pos[k] = evs[e0 + k].mdu_rank[o]; }
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++) {
-        const int64_t o = o0 + k * st;
-        if (o >= n || !chk(ev, pos[k], ev.md_cap, 14)) continue;
+      for (int k = 0; k < GROUP_EV; k++)
+        if (o < n[k]) pos[k] += evs[e0 + k].md_start[m[k]];
+#pragma unroll
+      for (int k = 0; k < GROUP_EV; k++) {
+        const EvDesc &ev = evs[e0 + k];
+        if (o >= n[k] || !chk(ev, pos[k], ev.md_cap, 14)) continue;
         ev.md_anchor[pos[k]] = ev.mdu_anchor[o];
         ev.md_kappa[pos[k]] = ev.mdu_kappa[o];
         ev.md_mod[pos[k]] = m[k];
@@ -741,24 +754,34 @@ __global__ void k_t3_scan(const EvDesc *__restrict__ evs) {
 // ... then a scatter into that order: each T3 to the start of its first MD's range plus the
 // rank the producer drew when it counted the T3.
 __global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ evs, int n_events) {
-  const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  for (int e = 0; e < n_events; e++) {
-    const EvDesc &ev = evs[e];
-    if (ev_void(ev)) continue;
-    const int64_t n = clamp_count(ev.cnt[C_T3], ev.t3_cap);
-    for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
-      int4 t[SCATTER_ILP];
-      float k3[SCATTER_ILP];
-      int pos[SCATTER_ILP];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int e0 = 0; e0 < n_events; e0 += GROUP_EV) {
+    int n[GROUP_EV], nmax = 0;
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) { t[k] = ev.t3u_md[o0 + k * st]; k3[k] = ev.t3u_kappa[o0 + k * st]; }
+    for (int k = 0; k < GROUP_EV; k++) {
+      n[k] = 0;
+      if (e0 + k < n_events) {
+        const EvDesc &ev = evs[e0 + k];
+        n[k] = ev_void(ev) ? 0 : clamp_count(ev.cnt[C_T3], ev.t3_cap);
+      }
+      nmax = max(nmax, n[k]);
+    }
+    for (int o = tid; o < nmax; o += st) {
+      int4 t[GROUP_EV];
+      float k3[GROUP_EV];
+      int pos[GROUP_EV];
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = ev.t3_pos[t[k].x] + t[k].w;
+      for (int k = 0; k < GROUP_EV; k++)
+        if (o < n[k]) { t[k] = evs[e0 + k].t3u_md[o]; k3[k] = evs[e0 + k].t3u_kappa[o]; }
 #pragma unroll
-      for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) { ev.t3_md[pos[k]] = make_int4(t[k].x, t[k].y, t[k].z, 0); ev.t3_kappa[pos[k]] = k3[k]; }
+      for (int k = 0; k < GROUP_EV; k++)
+        if (o < n[k]) pos[k] = evs[e0 + k].t3_pos[t[k].x] + t[k].w;
+#pragma unroll
+      for (int k = 0; k < GROUP_EV; k++)
+        if (o < n[k]) {
+          evs[e0 + k].t3_md[pos[k]] = make_int4(t[k].x, t[k].y, t[k].z, 0);
+          evs[e0 + k].t3_kappa[pos[k]] = k3[k];
+        }
     }
   }
 }
