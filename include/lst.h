@@ -248,7 +248,7 @@ const char *lst_last_error(void);
  * results never depend on these values, only the speed does. */
 typedef struct lst_launch {
     int32_t md_threads, md_buf;    /* step 1: CTA size; md_buf is unused (kept for layout) */
-    int32_t ls_threads, ls_list;   /* step 2: CTA size, shared candidate list entries per tile */
+    int32_t ls_threads, ls_list;   /* step 2: CTA size; ls_list is unused (kept for layout) */
     int32_t t3_threads;            /* step 3: CTA size */
     int32_t t5_threads;            /* step 4: CTA size */
     int32_t sc_threads;            /* score: CTA size */

@@ -1,7 +1,7 @@
 """Launch-shape autotuner for the batched pipeline.
 
 Each tunable of lst_launch belongs to one stage (CTA sizes of steps 1-4 and of the FP32
-score, the shared candidate-list length of the LS tile), and the library times every
+score), and the library times every
 stage separately (lst_stage_times, CUDA events inside the launch). The tuner therefore
 does coordinate descent: for one parameter at a time it replays the caller's own batch
 with every candidate value and keeps the value whose stage time is lowest (by more than
@@ -26,12 +26,13 @@ from . import lst
 
 SPACE = {
     "ls_threads": (64, 96, 128, 160, 192, 256),
-    "ls_list": (256, 512, 1024, 2048, 4096),
     "md_threads": (64, 128, 192, 256),
     "t3_threads": (64, 128, 192, 256),
     "t5_threads": (64, 128, 256),
     "sc_threads": (128, 256),
 }
+# ls_list is unused by the library (kept in lst_launch for layout); listed so that an
+# explicit space may still name it
 STAGE = {"md_threads": 1, "ls_threads": 2, "ls_list": 2, "t3_threads": 4, "t5_threads": 5, "sc_threads": 6}
 COUNT_KEYS = ("md", "ls", "t3", "t5", "tc", "selected")
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned", "launch_cache.json")

@@ -476,7 +476,6 @@ __device__ __forceinline__ void block_exclusive_scan(const int32_t *__restrict__
 // the whole block: pref[e] = sum_{f<e} count(f), pref[n] = total. n <= MAX_EVENTS.
 template <typename F>
 __device__ void block_event_prefix(int n, F count, int *pref) {
-  __shared__ int s_part[MAX_EVENTS / 32 + 1];
   for (int base = 0; base < n; base += blockDim.x) {
     const int e = base + threadIdx.x;
     if (e < n) pref[e + 1] = count(e);
@@ -493,7 +492,6 @@ __device__ void block_event_prefix(int n, F count, int *pref) {
     }
     if (threadIdx.x == 0) pref[0] = 0;
   }
-  (void)s_part;
   __syncthreads();
 }
 
