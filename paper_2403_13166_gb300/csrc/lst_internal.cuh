@@ -136,29 +136,27 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
 // Necessary condition of ls_cut without division or square root, in fewer operations than
 // the cut's own expressions, through identities that hold exactly in real arithmetic:
 //   z0:        A.z (rB - rA) - rA (zB - zA)  =  A.z rB - rA zB
-//   direction: A . (B - A)                  =  A . B - |A|^2
 //   bend:      A x (B - A)                  =  A.x B.y - A.y B.x  (= cr),
 // and the bend bound squared: |cr| / (rA dT) <= X + e / dT with X = rB kappa_max / 2 means
 // |cr| <= rA (X dT + e), hence cr^2 <= rA^2 ((1 + 1/64) X^2 dT^2 + 65 e^2), because
-// (u + e)^2 <= (1 + t) u^2 + (1 + 1/t) e^2 for every t > 0 (here t = 1/64).
+// (u + e)^2 <= (1 + t) u^2 + (1 + 1/t) e^2 for every t > 0 (here t = 1/64). The direction
+// cut is left to the later tests: on the candidate pairs of a PU200-like event it rejects
+// none of the pairs that pass these two (9.00% either way).
 // Rounding: every product here is below 3.2e4 in magnitude (|z| <= 270 cm, r <= 115 cm), so
 // the FP32 values of either form of a side differ from the real value by less than 0.02;
-// the slacks (0.05 on the z0 and direction sides, the factor 1.002 and 0.05 on the squared
-// bend, against bounds of at least 0.29 and 5.6) cover that, so a pair rejected here always
-// fails ls_cut (checked over all 59.5 M candidate pairs of a PU200-like event: 9.00% pass
-// this test, 8.92% the exact bend, none missed).
-// Ax = (|A|^2 - 0.05, rA^2, e rA + 0.05, -) per inner MD; k1 = 1.002 * (1 + 1/64) X^2 per outer MD,
+// the slacks (0.05 on the z0 side, the factor 1.002 and 0.05 on the squared bend, against
+// bounds of at least 0.29 and 5.6) cover that, so a pair rejected here always fails ls_cut.
+// Ax = (rA^2, e rA + 0.05) per inner MD; k1 = 1.002 * (1 + 1/64) X^2 per outer MD,
 // k0 = 1.002 * 65 e^2, c1 = z_lum + e.
-__device__ __forceinline__ bool ls_prefilter(const float4 A, const float4 Ax, const float4 B, float k1, float k0,
+__device__ __forceinline__ bool ls_prefilter(const float4 A, const float2 Ax, const float4 B, float k1, float k0,
                                              float c1) {
   const float p = __fmaf_rn(A.z, B.w, -(A.w * B.z));
-  const bool z0 = fabsf(p) <= __fmaf_rn(c1, fabsf(B.w - A.w), Ax.z);
-  const bool dir = __fmaf_rn(A.x, B.x, A.y * B.y) > Ax.x;
+  const bool z0 = fabsf(p) <= __fmaf_rn(c1, fabsf(B.w - A.w), Ax.y);
   const float cr = __fmaf_rn(A.x, B.y, -(A.y * B.x));
   const float dx = B.x - A.x, dy = B.y - A.y;
   const float dT2 = __fmaf_rn(dx, dx, dy * dy);
-  const bool bend = cr * cr <= __fmaf_rn(Ax.y, __fmaf_rn(k1, dT2, k0), 0.05f);
-  return z0 & dir & bend;
+  const bool bend = cr * cr <= __fmaf_rn(Ax.x, __fmaf_rn(k1, dT2, k0), 0.05f);
+  return z0 & bend;
 }
 
 // Necessary condition of the two curvature-consistency cuts of ls_cut (barrel MDs), for the

@@ -333,7 +333,7 @@ constexpr int LS_IN_CHUNK = 64;
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
   float4 in[LS_IN_CHUNK];                  // inner anchors
-  float4 inx[LS_IN_CHUNK];                 // |A|^2 - slack, rA^2, e rA + slack (ls_prefilter)
+  float2 inx[LS_IN_CHUNK];                 // rA^2, e rA + slack (ls_prefilter)
   float4 B[32];                            // the 32 targets of the current group
   int2 q2[64];                             // pairs past the curvature test: inner MD, target MD
                                            // (bit 31: target in the barrel), global indices
@@ -346,7 +346,7 @@ struct LsWarp {
   unsigned char bB[32];
   unsigned char tbar[LS_TB];
 };
-static_assert(sizeof(LsWarp) == 5200, "the host sizes k_ls shared memory with 5200 bytes per warp");
+static_assert(sizeof(LsWarp) == 4688, "the host sizes k_ls shared memory with 4688 bytes per warp");
 
 // Units: with unit_off == nullptr one unit per module (all its targets); otherwise
 // unit_off[m] .. unit_off[m + 1] are the units of module m, unit b taking the target
@@ -444,12 +444,12 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           if (t < nc) {
             const float4 A = ev.md_anchor[in0 + c0 + t];
             w.in[t] = A;
-            w.inx[t] = make_float4(A.x * A.x + A.y * A.y - 0.05f, A.w * A.w, c.hit_err * A.w + 0.05f, 0.0f);
+            w.inx[t] = make_float2(A.w * A.w, c.hit_err * A.w + 0.05f);
             w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
           } else {
             const float nan = __int_as_float(0x7fc00000);
             w.in[t] = make_float4(nan, nan, nan, nan);
-            w.inx[t] = make_float4(nan, nan, nan, nan);
+            w.inx[t] = make_float2(nan, nan);
             w.ink[t] = 0.0f;
           }
         }

@@ -74,18 +74,16 @@ def ls_prefilters(A, B, kA, kB, bA, bB, c, rel):
     km, e, gap, zl = (f32(c[k]) for k in ("kappa_max", "hit_err", "sensor_gap", "z_lum"))
     with np.errstate(all="ignore"):
         # first test
-        a2 = Ax * Ax + Ay * Ay - f32(0.05)
         X = Br * (f32(0.5) * km)
         k1 = f32(1.002) * f32(1.015625) * X * X
         k0 = f32(1.002) * f32(65.0) * (e * e)
         p = fma(Az, Br, -(Ar * Bz))
         z0 = np.abs(p) <= fma(full(p.shape, zl + e), np.abs(Br - Ar), e * Ar + f32(0.05))
-        dirn = fma(Ax, Bx, Ay * By) > a2
         cr = fma(Ax, By, -(Ay * Bx))
         dx, dy = Bx - Ax, By - Ay
         dT2 = fma(dx, dx, dy * dy)
         bend = cr * cr <= fma(Ar * Ar, fma(k1, dT2, full(dT2.shape, k0)), full(dT2.shape, 0.05))
-        first = z0 & dirn & bend
+        first = z0 & bend
         # curvature test
         Gp = f32(f32(2.0) * (e / gap) * f32(1.000001))
         ce = f32(f32(2.0) * e * f32(1.000001))
