@@ -466,10 +466,10 @@ STRICT_OPS = {"ls": (12, 35)}
 
 
 # DRAM bytes (read + write) per event of a kernel, from one ncu capture of a 16-event
-# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 59.18 +
-# 238.40 MB for k_ls); the traffic is the per-event LS output plus MD reads, so it scales
+# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 59.10 +
+# 238.30 MB for k_ls); the traffic is the per-event LS output plus MD reads, so it scales
 # with the events.
-TRAFFIC_PER_EVENT = {"ls": 297.58e6 / 16}
+TRAFFIC_PER_EVENT = {"ls": 297.40e6 / 16}
 
 
 def traffic_per_launch(stage, events):
@@ -577,7 +577,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--precision", default="bf16x3", choices=list(PRECISIONS))
     ap.add_argument("--plain-events", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
