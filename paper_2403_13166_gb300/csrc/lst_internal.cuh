@@ -196,14 +196,15 @@ __device__ __forceinline__ bool ls_kappa_prefilter(const float4 A, const float4 
 }
 
 // Necessary condition of md_cut without division or square root. Per lower hit L (MdLow):
-//   barrel: hb2r2 = (rL hb)^2 with hb = rL (kappa_max / 2) + e / g, the bend bound of md_cut.
+//   barrel: hb2r2 = (rL * hb)^2 with hb = rL (kappa_max / 2) + e / g, the bend bound of md_cut.
 //     Bend: |cr| <= rL dT hb. z road, multiplied by rL > 0: |dz rL - zL dr| <= Zl dr + e rL.
 //   endcap: the z road multiplied by rL |zL| > 0: |dt |zL| - |dz| rL^2| <= |dz| wz + e rL |zL|
 //     with wz = rL^2 Zl / (|zL| - Zl) (infinite, so no test, for |zL| <= Zl); the bend
 //     multiplied by rL: |cr| <= dt T + e rL with md_cut's own T(rL).
-// The direction tests are md_cut's own expressions (same FP32 values). The slack (1e-3 of the
-// terms' magnitudes) covers FP32 rounding, so a pair rejected here always fails md_cut too
-// (checked over all candidate pairs of a PU200-like event: 3.04% of barrel and 4.23% of
+// md_cut's direction conditions are left to md_cut: on the candidate pairs of a PU200-like
+// event they reject none of the pairs that pass the road and bend tests. The slack (1e-3 of
+// the terms' magnitudes) covers FP32 rounding, so a pair rejected here always fails md_cut
+// too (checked over all candidate pairs of a PU200-like event: 3.04% of barrel and 4.23% of
 // endcap pairs pass, exactly the MD fractions, none missed).
 struct MdLow {
   float hb2r2;                     // barrel
@@ -225,22 +226,22 @@ __device__ __forceinline__ MdLow md_low(const float4 L, bool endcap, const lst_c
 __device__ __forceinline__ bool md_prefilter(const float4 L, const float4 U, bool endcap, const MdLow &q,
                                              const lst_cuts &c) {
   const float dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
-  const float dt = L.x * dx + L.y * dy;                   // md_cut's direction expression
   const float cr = __fmaf_rn(L.x, dy, -(L.y * dx));
   if (endcap) {
+    const float dt = L.x * dx + L.y * dy;
     const float t1 = dt * q.az, t2 = fabsf(dz) * q.r2;
     const float rr = __fmaf_rn(fabsf(dz), q.wz, q.erz);
     const bool road = fabsf(t1 - t2) <= rr + 1e-3f * (fabsf(t1) + t2 + rr) + 1e-6f;
     const float bb = __fmaf_rn(dt, q.T, q.erl);
     const bool bend = fabsf(cr) <= bb + 1e-3f * (fabsf(dt * q.T) + q.erl) + 1e-6f;
-    return (dt > 0.0f) & (dz * L.z > 0.0f) & road & bend;
+    return road & bend;
   }
   const float dT2 = __fmaf_rn(dx, dx, dy * dy);
   const bool bend = cr * cr <= __fmaf_rn(q.hb2r2, dT2, 1e-9f);
   const float dr = U.w - L.w;
   const float a = dz * L.w, b = L.z * dr, rhs = __fmaf_rn(c.z_lum, dr, q.erl);
   const bool zr = fabsf(a - b) <= rhs + 1e-3f * (fabsf(a) + fabsf(b) + fabsf(rhs)) + 1e-6f;
-  return (dt > 0.0f) & bend & zr;
+  return bend & zr;
 }
 
 // Step 3: anchors of md0, md1, md2 along the chain (LS1.out == LS2.in).

@@ -53,7 +53,7 @@ def md_prefilter(L, U, endcap, c):
         road = np.abs(t1 - t2) <= rr + f32(1e-3) * (np.abs(t1) + t2 + rr) + f32(1e-6)
         bb = fma(dt, T, erl)
         bend_e = np.abs(cr) <= bb + f32(1e-3) * (np.abs(dt * T) + erl) + f32(1e-6)
-        ec = (dt > 0) & (dz * Lz > 0) & road & bend_e
+        ec = road & bend_e
         # barrel
         hb = Lr * (f32(0.5) * km) + e / gap
         hb2r2 = (Lr * hb) * (Lr * hb) * f32(1.001)
@@ -63,7 +63,7 @@ def md_prefilter(L, U, endcap, c):
         a, b = dz * Lr, Lz * dr
         rhs = fma(full(dr.shape, zl), dr, erl)
         zr = np.abs(a - b) <= rhs + f32(1e-3) * (np.abs(a) + np.abs(b) + np.abs(rhs)) + f32(1e-6)
-        br = (dt > 0) & bend & zr
+        br = bend & zr
     return np.where(endcap, ec, br)
 
 
