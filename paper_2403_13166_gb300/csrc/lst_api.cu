@@ -1227,6 +1227,24 @@ size_t est_bytes(const lst_ctx_s *c, int64_t n) {
 
 }  // namespace
 
+// Pinned host staging of one finished lane batch's T5 results (one batched export). The
+// results of the batch point into it until lst_serve_poll copies them out on the polling
+// thread; it returns to the pool when the last of them has been copied.
+struct ServeStage {
+  int32_t *hits = nullptr;
+  float *score = nullptr;
+  uint8_t *sel = nullptr;
+  int64_t cap = 0;
+  int pending = 0;                      // guarded by the server's mu
+};
+
+// A finished request: its result, and where its T5 rows sit in a stage (if anywhere).
+struct ServeDone {
+  lst_serve_result res;
+  ServeStage *stage = nullptr;
+  int64_t row = 0, n5 = 0;
+};
+
 struct lst_server_s {
   lst_ctx c = nullptr;
   lst_serve_config cfg{};
@@ -1234,7 +1252,8 @@ struct lst_server_s {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<ServeReq> submitted;       // guarded by mu
-  std::deque<lst_serve_result> done;    // guarded by mu
+  std::deque<ServeDone> done;           // guarded by mu
+  std::vector<ServeStage *> stages;     // every stage; guarded by mu
   bool stop = false;                    // guarded by mu
   std::string error;                    // guarded by mu
   // worker-only state
@@ -1243,22 +1262,18 @@ struct lst_server_s {
   std::vector<ServeReq> inflight[2];
   cudaStream_t st[2] = {nullptr, nullptr};
   size_t mem_in_use = 0;
-  // pinned staging of one lane batch's T5 results (one batched export per finished batch)
-  int32_t *stage_hits = nullptr;
-  float *stage_score = nullptr;
-  uint8_t *stage_sel = nullptr;
-  int64_t stage_cap = 0;
 };
 
 namespace {
 
-// One finished request: its result (counts, times, and a copy of its T5 tuples, scores and
-// selection flags from the batch's staging, if any) goes to the done queue; the slot and its
-// memory budget are released.
-void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t *cnt, const int32_t *t5_hits,
-                  const float *t5_score, const uint8_t *t5_sel, int64_t n5) {
+// One finished request: its result (counts, times, and where its T5 tuples, scores and
+// selection flags sit in the batch's stage, if anywhere) goes to the done queue; the slot and
+// its memory budget are released. The stage's pending count was raised by the caller.
+void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t *cnt, ServeStage *stage,
+                  int64_t row, int64_t n5) {
   lst_ctx_s *c = S->c;
-  lst_serve_result res;
+  ServeDone d;
+  lst_serve_result &res = d.res;
   std::memset(&res, 0, sizeof res);
   res.tag = r.tag;
   res.status = status;
@@ -1273,30 +1288,49 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   res.t_arrival = r.t_arrival;
   res.t_admit = r.t_admit;
   res.t_launch = r.t_launch;
-  if (status == LST_OK && t5_hits && n5 > 0) {
-    res.t5_hits = (int32_t *)std::malloc((size_t)n5 * 10 * 4);
-    res.t5_score = (float *)std::malloc((size_t)n5 * 4);
-    res.t5_sel = (uint8_t *)std::malloc((size_t)n5);
-    if (!res.t5_hits || !res.t5_score || !res.t5_sel) {
-      res.status = LST_ERR_CUDA;
-    } else {
-      std::memcpy(res.t5_hits, t5_hits, (size_t)n5 * 10 * 4);
-      std::memcpy(res.t5_score, t5_score, (size_t)n5 * 4);
-      std::memcpy(res.t5_sel, t5_sel, (size_t)n5);
-      res.n_t5 = n5;
-    }
-  }
-  res.t_done = now_s();
+  res.t_done = now_s();                 // the results are on the host (pinned staging)
+  d.stage = stage;
+  d.row = row;
+  d.n5 = n5;
   c->slots[r.slot].busy = false;
   S->mem_in_use -= std::min(S->mem_in_use, r.est);
   std::lock_guard<std::mutex> lk(S->mu);
-  S->done.push_back(res);
+  S->done.push_back(d);
   S->cv.notify_all();
 }
 
+// A stage with room for n T5 rows and no pending results (grown or added if none).
+ServeStage *serve_stage(lst_server_s *S, int64_t n) {
+  ServeStage *free_small = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (ServeStage *g : S->stages) {
+      if (g->pending) continue;
+      if (g->cap >= n) return g;
+      free_small = g;
+    }
+  }
+  ServeStage *g = free_small;
+  if (!g) {
+    g = new ServeStage();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stages.push_back(g);
+  }
+  cudaFreeHost(g->hits);
+  cudaFreeHost(g->score);
+  cudaFreeHost(g->sel);
+  g->hits = nullptr; g->score = nullptr; g->sel = nullptr; g->cap = 0;
+  const int64_t cap = n + n / 4 + 1024;
+  if (cudaMallocHost(&g->hits, (size_t)cap * 10 * 4) == cudaSuccess &&
+      cudaMallocHost(&g->score, (size_t)cap * 4) == cudaSuccess && cudaMallocHost(&g->sel, (size_t)cap) == cudaSuccess)
+    g->cap = cap;
+  return g->cap >= n ? g : nullptr;
+}
+
 // Finish the requests of one lane batch: the T5 results of every successful event are
-// exported together (lst_get_candidates_batch into the server's pinned staging: one gather
-// per event on the auxiliary stream, one copy, one synchronisation), then split per request.
+// exported together (lst_get_candidates_batch into a pinned stage: one gather per event on
+// the auxiliary stream, one copy, one synchronisation); each request's result then refers
+// to its rows of the stage, which lst_serve_poll copies out on the polling thread.
 void serve_finish_batch(lst_server_s *S, std::vector<ServeReq> &done, const std::vector<lst_status> &st) {
   lst_ctx_s *c = S->c;
   std::vector<lst_event_s> evs;
@@ -1313,37 +1347,31 @@ void serve_finish_batch(lst_server_s *S, std::vector<ServeReq> &done, const std:
     }
   }
   std::vector<int64_t> offs(evs.size() + 1, 0);
+  ServeStage *g = nullptr;
   lst_status xs = LST_OK;
   if (!evs.empty()) {
-    if (S->stage_cap < total) {
-      cudaFreeHost(S->stage_hits);
-      cudaFreeHost(S->stage_score);
-      cudaFreeHost(S->stage_sel);
-      S->stage_hits = nullptr; S->stage_score = nullptr; S->stage_sel = nullptr; S->stage_cap = 0;
-      const int64_t cap = total + total / 4 + 1024;
-      if (cudaMallocHost(&S->stage_hits, (size_t)cap * 10 * 4) == cudaSuccess &&
-          cudaMallocHost(&S->stage_score, (size_t)cap * 4) == cudaSuccess &&
-          cudaMallocHost(&S->stage_sel, (size_t)cap) == cudaSuccess)
-        S->stage_cap = cap;
-    }
+    g = serve_stage(S, total);
     std::vector<lst_event> hs(evs.size());
     for (size_t i = 0; i < evs.size(); i++) hs[i] = &evs[i];
-    xs = S->stage_cap >= total ? lst_get_candidates_batch(hs.data(), (int32_t)hs.size(), LST_T5, S->stage_hits,
-                                                          S->stage_score, S->stage_sel, S->stage_cap, offs.data())
-                               : LST_ERR_CUDA;
+    xs = g ? lst_get_candidates_batch(hs.data(), (int32_t)hs.size(), LST_T5, g->hits, g->score, g->sel, g->cap,
+                                      offs.data())
+           : LST_ERR_CUDA;
+    if (xs == LST_OK) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      g->pending += (int)which.size();
+    }
   }
   size_t j = 0;
   for (size_t k = 0; k < done.size(); k++) {
     const int32_t *cnt = c->slots[done[k].slot].cnt;          // the lane was harvested
     if (j < which.size() && which[j] == (int)k) {
       if (xs == LST_OK)
-        serve_finish(S, done[k], st[k], cnt, S->stage_hits + offs[j] * 10, S->stage_score + offs[j],
-                     S->stage_sel + offs[j], offs[j + 1] - offs[j]);
+        serve_finish(S, done[k], st[k], cnt, g, offs[j], offs[j + 1] - offs[j]);
       else
-        serve_finish(S, done[k], LST_ERR_CUDA, cnt, nullptr, nullptr, nullptr, 0);
+        serve_finish(S, done[k], LST_ERR_CUDA, cnt, nullptr, 0, 0);
       j++;
     } else {
-      serve_finish(S, done[k], st[k], cnt, nullptr, nullptr, nullptr, 0);
+      serve_finish(S, done[k], st[k], cnt, nullptr, 0, 0);
     }
   }
 }
@@ -1405,7 +1433,7 @@ void serve_loop(lst_server_s *S) {
       for (auto &r : batch) r.t_launch = tl;
       if (st == LST_OK) st = run_lane(c, L, (int)batch.size(), ids.data(), S->st[li], true, false);
       if (st != LST_OK) {
-        for (auto &r : batch) serve_finish(S, r, st, nullptr, nullptr, nullptr, nullptr, 0);
+        for (auto &r : batch) serve_finish(S, r, st, nullptr, nullptr, 0, 0);
         continue;
       }
       S->inflight[li] = std::move(batch);
@@ -1433,7 +1461,7 @@ void serve_loop(lst_server_s *S) {
         fst.push_back(es);
       }
       if (st != LST_OK) {
-        for (auto &r : fin) serve_finish(S, r, st, nullptr, nullptr, nullptr, nullptr, 0);
+        for (auto &r : fin) serve_finish(S, r, st, nullptr, nullptr, 0, 0);
       } else {
         serve_finish_batch(S, fin, fst);
       }
@@ -1497,15 +1525,43 @@ lst_status lst_serve_submit(lst_server S, const float *x, const float *y, const 
 
 lst_status lst_serve_poll(lst_server S, lst_serve_result *out, int32_t max, int32_t *n_out, int32_t wait_ms) {
   if (!S || !n_out || (max > 0 && !out)) return fail(LST_ERR_ARG, "null argument");
-  std::unique_lock<std::mutex> lk(S->mu);
-  if (S->done.empty() && wait_ms > 0)
-    S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
-  int n = 0;
-  while (n < max && !S->done.empty()) {
-    out[n++] = S->done.front();
-    S->done.pop_front();
+  std::vector<ServeDone> got;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->done.empty() && wait_ms > 0)
+      S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+    while ((int)got.size() < max && !S->done.empty()) {
+      got.push_back(S->done.front());
+      S->done.pop_front();
+    }
   }
-  *n_out = n;
+  // copies out of the stages on this (the polling) thread, then the stages are released
+  for (size_t i = 0; i < got.size(); i++) {
+    ServeDone &d = got[i];
+    lst_serve_result &res = d.res;
+    if (d.stage && d.n5 > 0) {
+      const int64_t n5 = d.n5;
+      res.t5_hits = (int32_t *)std::malloc((size_t)n5 * 10 * 4);
+      res.t5_score = (float *)std::malloc((size_t)n5 * 4);
+      res.t5_sel = (uint8_t *)std::malloc((size_t)n5);
+      if (!res.t5_hits || !res.t5_score || !res.t5_sel) {
+        lst_serve_free_result(&res);
+        res.status = LST_ERR_CUDA;
+      } else {
+        std::memcpy(res.t5_hits, d.stage->hits + d.row * 10, (size_t)n5 * 10 * 4);
+        std::memcpy(res.t5_score, d.stage->score + d.row, (size_t)n5 * 4);
+        std::memcpy(res.t5_sel, d.stage->sel + d.row, (size_t)n5);
+        res.n_t5 = n5;
+      }
+    }
+    out[i] = res;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto &d : got)
+      if (d.stage) d.stage->pending--;
+  }
+  *n_out = (int32_t)got.size();
   return LST_OK;
 }
 
@@ -1526,11 +1582,13 @@ lst_status lst_serve_stop(lst_server S) {
     S->cv.notify_all();
   }
   if (S->th.joinable()) S->th.join();
-  for (auto &r : S->done) lst_serve_free_result(&r);
   for (auto &s : S->st) if (s) cudaStreamDestroy(s);
-  cudaFreeHost(S->stage_hits);
-  cudaFreeHost(S->stage_score);
-  cudaFreeHost(S->stage_sel);
+  for (ServeStage *g : S->stages) {
+    cudaFreeHost(g->hits);
+    cudaFreeHost(g->score);
+    cudaFreeHost(g->sel);
+    delete g;
+  }
   delete S;
   return LST_OK;
 }
