@@ -276,10 +276,11 @@ lst_status lst_stage_times(lst_ctx ctx, float *ms, int64_t *n_launches);
  * new batch starts while the previous one is still running.
  *   submit: x, y, z, sensor are HOST arrays that must stay valid until the request's
  *           result has been polled; t_arrival is the request time on lst_clock() (<= 0:
- *           now); the latency of a request is t_done - t_arrival.
+ *           now); the latency of a request is t_done - t_arrival, t_done being the time
+ *           its results reached host memory (the library's pinned staging).
  *   poll:   returns up to `max` finished requests (waiting up to wait_ms for the first);
- *           each result owns host copies of its T5 tuples when copy_t5 is set
- *           (lst_serve_free_result frees them).
+ *           each result owns host copies of its T5 tuples when copy_t5 is set, made by
+ *           this call on the calling thread (lst_serve_free_result frees them).
  *   stop:   finishes every submitted request, then joins the worker. */
 typedef struct lst_serve_config {
     int32_t max_batch;          /* events per batched launch, 1..max_events */
