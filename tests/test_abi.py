@@ -83,3 +83,28 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_binding_constants_match_the_c_header(tmp_path):
+    """Enum values and #define constants of include/lst.h, compiled by gcc, equal the
+    binding's Python constants."""
+    from paper_2403_13166_gb300 import lst
+    names = {"LST_OK": lst.LST_OK, "LST_ERR_ARG": lst.LST_ERR_ARG, "LST_ERR_CAPACITY": lst.LST_ERR_CAPACITY,
+             "LST_ERR_CUDA": lst.LST_ERR_CUDA, "LST_ERR_TIMEOUT": lst.LST_ERR_TIMEOUT,
+             "LST_ERR_NOT_READY": lst.LST_ERR_NOT_READY, "LST_ERR_INPUT": lst.LST_ERR_INPUT,
+             "LST_ERR_NOMEM": lst.LST_ERR_NOMEM, "LST_MD": lst.LST_MD, "LST_LS": lst.LST_LS,
+             "LST_T3": lst.LST_T3, "LST_T5": lst.LST_T5, "LST_TC": lst.LST_TC, "LST_FP32": lst.LST_FP32,
+             "LST_BF16": lst.LST_BF16, "LST_BF16X3": lst.LST_BF16X3, "LST_N_STAGES": lst.N_STAGES,
+             "LST_GRAPH_NODE_FEATURES": lst.GRAPH_NODE_FEATURES,
+             "LST_GRAPH_EDGE_FEATURES": lst.GRAPH_EDGE_FEATURES}
+    lines = ['#include <stdio.h>', '#include "lst.h"', 'int main(void) {']
+    lines += [f'  printf("{k} %d\\n", (int){k});' for k in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = dict(zip(out[::2], map(int, out[1::2])))
+    assert got == names
+    assert len(lst.STAGES) == lst.N_STAGES
