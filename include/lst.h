@@ -280,7 +280,9 @@ lst_status lst_stage_times(lst_ctx ctx, float *ms, int64_t *n_launches);
  *           its results reached host memory (the library's pinned staging).
  *   poll:   returns up to `max` finished requests (waiting up to wait_ms for the first);
  *           each result owns host copies of its T5 tuples when copy_t5 is set, made by
- *           this call on the calling thread (lst_serve_free_result frees them).
+ *           this call on the calling thread (lst_serve_free_result frees them). Until its
+ *           results are polled, a finished batch keeps its pinned staging (about 45 bytes
+ *           per T5); a caller that stops polling makes the library allocate more staging.
  *   stop:   finishes every submitted request, then joins the worker. */
 typedef struct lst_serve_config {
     int32_t max_batch;          /* events per batched launch, 1..max_events */
