@@ -555,10 +555,10 @@ def run_reference(args, pool, n_cores):
     wall = time.perf_counter() - t0
     oracle_s = sum(busy)
     value = per_step * args.steps / oracle_s
-    return {"metric": METRIC, "value": round(value, 3), "unit": "events/s", "n_gpus": 0,
+    return {"metric": METRIC, "value": round(value, 3), "unit": "events/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * oracle_s / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic", "impl": "reference",
+            "data": "synthetic", "impl": "reference", "hardware": f"{n_cores} host cores, no GPU",
             "config": {"workload": "pu200_like_batched", "events_per_step": per_step, "pileup": PILEUP,
                        "particles_per_vertex": PER_VERTEX, "cuts": args.cuts},
             "cpu_baseline": {"value": round(value, 3), "unit": "events/s", "cores": n_cores, "kind": "oracle",
