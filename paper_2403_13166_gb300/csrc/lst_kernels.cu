@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
 // through the division-free necessary test; the survivors (~9%) are queued and, 32 at a time,
 // through the necessary curvature-consistency test (~1.8% of all pairs pass), whose survivors
 // wait in a second queue that lives for the whole unit and run through the exact FP32 cut
-// 32 at a time. LSs go out in any order with a count per inner MD; k_ls_scan /
-// k_ls_scatter then group them by inner MD.
+// 32 at a time. LSs go out in any order, each with its rank among its inner MD's LSs (the
+// value of the counting atomicAdd); k_ls_scan / k_ls_scatter then group them by inner MD.
 constexpr int LS_IN_CHUNK = 64;
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
