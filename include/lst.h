@@ -230,6 +230,14 @@ lst_status lst_set_wait_limit(lst_ctx ctx, int64_t iterations);
  * restores normal scoring). */
 lst_status lst_test_skip_mma(lst_ctx ctx, int32_t on);
 
+/* Test aid for allocation failures (no counterpart in the paper). The next n allocations
+ * of event buffers (an event slot's object arena when it is created or grown, and the
+ * device staging of host inputs) fail as cudaMalloc fails when the device is out of
+ * memory: the call that needed the buffer returns LST_ERR_NOMEM, no event is produced,
+ * the slot stays free with no buffer, and the next call allocates normally. n = 0 clears
+ * pending failures. */
+lst_status lst_test_fail_alloc(lst_ctx ctx, int32_t n);
+
 /* Returns the event's slot to the context. */
 lst_status lst_event_release(lst_event ev);
 
@@ -341,8 +349,8 @@ lst_status lst_serve_stop(lst_server s);
  *             an invalid sensor id or a non-finite coordinate.
  * Asynchronous on cuda_stream; MDs come in no particular order (compare as sets).
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture. Every call reuses the same scratch and clears what must start at
+ * (cudaGetSymbolAddress, with that device current) and the device's SM count, which sizes
+ * the grids; make that first call before any stream capture. Every call reuses the same scratch and clears what must start at
  * zero; calls that overlap on the GPU (other streams, other threads) race on it and
  * must be serialised by the caller. */
 #define LST_NOALLOC_MAX_HITS 524288

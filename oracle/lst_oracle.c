@@ -58,6 +58,7 @@ typedef struct {
 typedef struct {
     int64_t n_md, n_ls, n_t3, n_t5;
     int64_t pairs[4];                     /* candidate pairs tested per step */
+    int64_t near[4];                      /* of those, tested pairs near a cut boundary */
     int32_t *md_lo, *md_up, *md_mod;       /* original hit indices, module */
     float *md_kappa;                       /* signed curvature estimate (0 for endcap) */
     int32_t *ls_in, *ls_out;               /* MD indices */
@@ -95,6 +96,19 @@ static hit mkhit(const float *x, const float *y, const float *z, int32_t i) {
     return h;
 }
 
+/* ------------------------------------------------------------------ near-boundary count */
+/* Bookkeeping for the parity report; it decides nothing. A tolerance comparison
+ * lhs <= rhs whose sides differ by at most 1e-5 of rhs marks the candidate being tested as
+ * near a cut boundary, where a different rounding of the same expression could flip the
+ * decision; the event driver counts such candidates per step (oresult.near). */
+static _Thread_local int g_near;
+
+static int cut_le(float lhs, float rhs)
+{
+    if (fabs((double)lhs - (double)rhs) <= 1e-5 * fabs((double)rhs)) g_near = 1;
+    return lhs <= rhs;
+}
+
 /* ------------------------------------------------------------------ step 1: MD cuts */
 /* Lower hit L, upper hit U of one module. Returns 1 if the pair is a mini-doublet. */
 int oracle_md_cut(const float *Lp, const float *Up, int endcap, const ocuts *c, float *kappa)
@@ -108,10 +122,10 @@ int oracle_md_cut(const float *Lp, const float *Up, int endcap, const ocuts *c, 
     if (!endcap) {
         if (!(dt > 0.0f)) return 0;                                       /* MD-dir */
         float sa = cr / (rL * dT);
-        if (!(fabsf(sa) <= rL * (0.5f * c->kappa_max) + c->hit_err / c->sensor_gap))
+        if (!cut_le(fabsf(sa), rL * (0.5f * c->kappa_max) + c->hit_err / c->sensor_gap))
             return 0;                                                      /* MD-bend */
         float dr = U.r - L.r;
-        if (!(fabsf(dz - (L.z / rL) * dr) <= (c->z_lum / rL) * dr + c->hit_err))
+        if (!cut_le(fabsf(dz - (L.z / rL) * dr), (c->z_lum / rL) * dr + c->hit_err))
             return 0;                                                      /* MD-z */
         *kappa = 2.0f * sa / rL;
         return 1;
@@ -120,11 +134,11 @@ int oracle_md_cut(const float *Lp, const float *Up, int endcap, const ocuts *c, 
     float para = dt / rL, perp = cr / rL;
     float azl = fabsf(L.z), adz = fabsf(dz);
     float pe = adz * rL / azl;
-    if (!(fabsf(para - pe) <= adz * rL * c->z_lum / (azl * (azl - c->z_lum)) + c->hit_err))
+    if (!cut_le(fabsf(para - pe), adz * rL * c->z_lum / (azl * (azl - c->z_lum)) + c->hit_err))
         return 0;                                                          /* MD-z */
     float S = rL * (0.5f * c->kappa_max);
     float T = S / sqrtf(1.0f - S * S);
-    if (!(fabsf(perp) <= para * T + c->hit_err)) return 0;                /* MD-bend */
+    if (!cut_le(fabsf(perp), para * T + c->hit_err)) return 0;            /* MD-bend */
     *kappa = 0.0f;
     return 1;
 }
@@ -137,7 +151,7 @@ int oracle_ls_cut(const float *Ap, const float *Bp, float kA, float kB, int bA, 
     float xa = Ap[0], ya = Ap[1], za = Ap[2], ra = Ap[3];
     float xb = Bp[0], yb = Bp[1], zb = Bp[2], rb = Bp[3];
     float e = c->hit_err;
-    if (!(fabsf(za * (rb - ra) - ra * (zb - za)) <= (c->z_lum + e) * fabsf(rb - ra) + e * ra))
+    if (!cut_le(fabsf(za * (rb - ra) - ra * (zb - za)), (c->z_lum + e) * fabsf(rb - ra) + e * ra))
         return 0;                                                          /* LS-z0 */
     float dx = xb - xa, dy = yb - ya;
     float dT = sqrtf(dx * dx + dy * dy);
@@ -145,11 +159,11 @@ int oracle_ls_cut(const float *Ap, const float *Bp, float kA, float kB, int bA, 
     float dt = xa * dx + ya * dy;
     if (!(dt > 0.0f)) return 0;                                           /* LS-dir */
     float sl = cr / (ra * dT);
-    if (!(fabsf(sl) <= rb * (0.5f * c->kappa_max) + e / dT)) return 0;    /* LS-bend */
+    if (!cut_le(fabsf(sl), rb * (0.5f * c->kappa_max) + e / dT)) return 0; /* LS-bend */
     float k = 2.0f * sl / rb;
-    if (bA && !(fabsf(kA - k) <= 2.0f * (e / c->sensor_gap) / ra + 2.0f * (e / dT) / rb))
+    if (bA && !cut_le(fabsf(kA - k), 2.0f * (e / c->sensor_gap) / ra + 2.0f * (e / dT) / rb))
         return 0;                                                          /* LS-kappa, inner */
-    if (bB && !(fabsf(kB - k) <= 2.0f * (e / c->sensor_gap) / rb + 2.0f * (e / dT) / rb))
+    if (bB && !cut_le(fabsf(kB - k), 2.0f * (e / c->sensor_gap) / rb + 2.0f * (e / dT) / rb))
         return 0;                                                          /* LS-kappa, outer */
     *kappa = k;
     return 1;
@@ -170,11 +184,11 @@ int oracle_t3_cut(const float *P0, const float *P1, const float *P2, const ocuts
     float cc = sqrtf(d02x * d02x + d02y * d02y);
     float cr = d01x * d02y - d01y * d02x;
     float k3 = 2.0f * cr / (a * b * cc);
-    if (!(fabsf(k3) <= c->kappa_max * c->t3_kappa_factor)) return 0;      /* T3-pT */
+    if (!cut_le(fabsf(k3), c->kappa_max * c->t3_kappa_factor)) return 0;  /* T3-pT */
     float s01 = a * (1.0f + a * a * k3 * k3 / 24.0f);
     float s12 = b * (1.0f + b * b * k3 * k3 / 24.0f);
     float zp = z0 + (z2 - z0) * s01 / (s01 + s12);
-    if (!(fabsf(z1 - zp) <= c->t3_rz_tol)) return 0;                      /* T3-rz */
+    if (!cut_le(fabsf(z1 - zp), c->t3_rz_tol)) return 0;                  /* T3-rz */
     *kappa = k3;
     return 1;
 }
@@ -241,7 +255,7 @@ float oracle_t5_chi2(const float *P, float sigma)
 int oracle_t5_cut(const float *P, float ka, float kb, const ocuts *c)
 {
     if (!(ka * kb > 0.0f)) return 0;                                      /* T5-q */
-    if (!(fabsf(ka - kb) <= c->t5_kappa_rel * 0.5f * (fabsf(ka) + fabsf(kb)) + c->t5_kappa_abs))
+    if (!cut_le(fabsf(ka - kb), c->t5_kappa_rel * 0.5f * (fabsf(ka) + fabsf(kb)) + c->t5_kappa_abs))
         return 0;                                                          /* T5-kappa */
     float kbar = 0.5f * (ka + kb);
     float S[5];
@@ -255,9 +269,9 @@ int oracle_t5_cut(const float *P, float ka, float kb, const ocuts *c)
     float z0 = P[2], z4 = P[18];
     for (int j = 1; j <= 3; j++) {
         float zj = P[4 * j + 2];
-        if (!(fabsf(zj - (z0 + (z4 - z0) * S[j] / S[4])) <= c->t5_rz_tol)) return 0;  /* T5-rz */
+        if (!cut_le(fabsf(zj - (z0 + (z4 - z0) * S[j] / S[4])), c->t5_rz_tol)) return 0;  /* T5-rz */
     }
-    if (c->t5_chi2_max > 0.0f && !(oracle_t5_chi2(P, c->hit_sigma) <= c->t5_chi2_max))
+    if (c->t5_chi2_max > 0.0f && !cut_le(oracle_t5_chi2(P, c->hit_sigma), c->t5_chi2_max))
         return 0;                                                          /* pre-DNN chi2 */
     return 1;
 }
@@ -470,7 +484,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
                     float L[4], U[4], k;
                     fill_md_anchor(&H[sidx[a]], L);
                     fill_md_anchor(&H[sidx[b]], U);
-                    if (oracle_md_cut(L, U, endcap, c, &k)) {
+                    g_near = 0;
+                    int ok = oracle_md_cut(L, U, endcap, c, &k);
+                    out->near[0] += g_near;
+                    if (ok) {
                         md_t *d = vpush(&mds);
                         d->lo = sidx[a]; d->up = sidx[b]; d->mod = m; d->kappa = k;
                     }
@@ -484,7 +501,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
                     float L[4], U[4], k;
                     fill_md_anchor(&H[i], L);
                     fill_md_anchor(&H[j], U);
-                    if (oracle_md_cut(L, U, endcap, c, &k)) {
+                    g_near = 0;
+                    int ok = oracle_md_cut(L, U, endcap, c, &k);
+                    out->near[0] += g_near;
+                    if (ok) {
                         md_t *d = vpush(&mds);
                         d->lo = (int32_t)i; d->up = (int32_t)j; d->mod = m; d->kappa = k;
                     }
@@ -512,7 +532,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
                     for (int64_t j = mdoff[mt]; j < mdoff[mt + 1]; j++) {
                         out->pairs[1]++;
                         float B[4], k; fill_md_anchor(&H[MD[j].lo], B);
-                        if (oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k)) {
+                        g_near = 0;
+                        int ok = oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k);
+                        out->near[1] += g_near;
+                        if (ok) {
                             ls_t *s = vpush(&lss); s->in = (int32_t)i; s->out = (int32_t)j; s->kappa = k;
                         }
                     }
@@ -523,7 +546,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
                     if (!layer_adjacent(g->layer[m], g->side[m], g->layer[mt], g->side[mt])) continue;
                     out->pairs[1]++;
                     float B[4], k; fill_md_anchor(&H[MD[j].lo], B);
-                    if (oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k)) {
+                    g_near = 0;
+                    int ok = oracle_ls_cut(A, B, MD[i].kappa, MD[j].kappa, bA, g->subdet[mt] == 0, c, &k);
+                    out->near[1] += g_near;
+                    if (ok) {
                         ls_t *s = vpush(&lss); s->in = (int32_t)i; s->out = (int32_t)j; s->kappa = k;
                     }
                 }
@@ -547,7 +573,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
             fill_md_anchor(&H[MD[LS[s1].in].lo], P0);
             fill_md_anchor(&H[MD[LS[s1].out].lo], P1);
             fill_md_anchor(&H[MD[LS[s2].out].lo], P2);
-            if (oracle_t3_cut(P0, P1, P2, c, &k)) {
+            g_near = 0;
+            int ok = oracle_t3_cut(P0, P1, P2, c, &k);
+            out->near[2] += g_near;
+            if (ok) {
                 t3_t *t = vpush(&t3s);
                 t->ls1 = (int32_t)s1; t->ls2 = (int32_t)s2;
                 t->md[0] = LS[s1].in; t->md[1] = LS[s1].out; t->md[2] = LS[s2].out;
@@ -571,7 +600,10 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
             int32_t md5[5] = {T3[a].md[0], T3[a].md[1], T3[a].md[2], T3[b].md[1], T3[b].md[2]};
             float P[20];
             for (int i = 0; i < 5; i++) fill_md_anchor(&H[MD[md5[i]].lo], P + 4 * i);
-            if (oracle_t5_cut(P, T3[a].kappa, T3[b].kappa, c)) {
+            g_near = 0;
+            int ok = oracle_t5_cut(P, T3[a].kappa, T3[b].kappa, c);
+            out->near[3] += g_near;
+            if (ok) {
                 t5_t *q = vpush(&t5s);
                 q->t3a = (int32_t)a; q->t3b = (int32_t)b;
                 memcpy(q->md, md5, sizeof md5);

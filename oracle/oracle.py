@@ -37,7 +37,7 @@ class _Mlp(C.Structure):
 
 class _Result(C.Structure):
     _fields_ = [("n_md", C.c_int64), ("n_ls", C.c_int64), ("n_t3", C.c_int64), ("n_t5", C.c_int64),
-                ("pairs", C.c_int64 * 4),
+                ("pairs", C.c_int64 * 4), ("near", C.c_int64 * 4),
                 ("md_lo", C.c_void_p), ("md_up", C.c_void_p), ("md_mod", C.c_void_p),
                 ("md_kappa", C.c_void_p),
                 ("ls_in", C.c_void_p), ("ls_out", C.c_void_p), ("ls_kappa", C.c_void_p),
@@ -181,6 +181,7 @@ def mlp_forward(flat: np.ndarray, n_hidden: int, feat: np.ndarray) -> float:
 @dataclass
 class OracleResult:
     pairs: np.ndarray
+    near: np.ndarray        # tested pairs per step with a tolerance comparison within 1e-5 of its bound
     md_lo: np.ndarray
     md_up: np.ndarray
     md_mod: np.ndarray
@@ -260,7 +261,7 @@ def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -
     try:
         n1, n2, n3, n4 = res.n_md, res.n_ls, res.n_t3, res.n_t5
         out = OracleResult(
-            pairs=np.array(list(res.pairs), np.int64),
+            pairs=np.array(list(res.pairs), np.int64), near=np.array(list(res.near), np.int64),
             md_lo=_arr(res.md_lo, n1, np.int32), md_up=_arr(res.md_up, n1, np.int32),
             md_mod=_arr(res.md_mod, n1, np.int32), md_kappa=_arr(res.md_kappa, n1, np.float32),
             ls_in=_arr(res.ls_in, n2, np.int32), ls_out=_arr(res.ls_out, n2, np.int32),

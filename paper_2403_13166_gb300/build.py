@@ -28,15 +28,19 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+    """Compile (what is out of date) and link <out_dir>/liblst.so; returns its path. A
+    variant build (extra_flags, e.g. -DLST_CHECK for the bounds-checked kernels) must use
+    an out_dir of its own."""
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "liblst.so")
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "lst.h"))
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or not _newer(o, [s] + headers + [__file__]):
             jobs.append([NVCC, *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o])
@@ -50,11 +54,11 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if jobs or not os.path.exists(lib):
+        tmp = lib + f".{os.getpid()}.tmp"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -148,6 +149,7 @@ struct lst_ctx_s {
   int *d_err = nullptr;          // device error word (bounded waits of the tensor-core kernel)
   long long wait_limit = 1ll << 26;
   int skip_mma = 0;                // test aid: the tensor-core score kernels issue no MMA
+  std::atomic<int> fail_allocs{0};  // test aid: that many event-buffer allocations fail next
   int grid_bf[2] = {0, 0};   // tensor-core score grid: plain BF16, split BF16
   std::vector<Slot> slots;
   std::vector<Lane> lanes;     // lane 0: lst_run_event; lanes 1..: batches, round robin
@@ -274,6 +276,14 @@ SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, si
   return L;
 }
 
+// test aid (lst_test_fail_alloc): consume one pending injected allocation failure
+bool injected_alloc_failure(lst_ctx_s *c) {
+  int v = c->fail_allocs.load();
+  while (v > 0)
+    if (c->fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   int md, ls, t3, t5;
   caps_for(c, n_hits, md, ls, t3, t5);
@@ -290,6 +300,8 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
     cudaFree(s.mem);
     s.mem = nullptr;
   }
+  if (injected_alloc_failure(c))
+    return fail(LST_ERR_NOMEM, "cudaMalloc(event buffers): injected failure (lst_test_fail_alloc)");
   CU(cudaMalloc(&s.mem, off));
   s.bytes = off;
   char *b = (char *)s.mem;
@@ -318,7 +330,6 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
 // stage host inputs into the slot's own device buffer (copies on `st`)
 lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, const float *z,
                        const int32_t *sensor, int64_t n, cudaStream_t st) {
-  (void)c;
   s.d.n_hits = (int32_t)n;
   s.n_hits = n;
   const bool dev = n == 0 || is_device_ptr(x);
@@ -327,7 +338,9 @@ lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, co
     return LST_OK;
   }
   if (s.in_cap < n) {
-    if (s.in_mem) { CU(cudaDeviceSynchronize()); cudaFree(s.in_mem); s.in_mem = nullptr; }
+    if (s.in_mem) { CU(cudaDeviceSynchronize()); cudaFree(s.in_mem); s.in_mem = nullptr; s.in_cap = 0; }
+    if (injected_alloc_failure(c))
+      return fail(LST_ERR_NOMEM, "cudaMalloc(input staging): injected failure (lst_test_fail_alloc)");
     const int64_t cap = (int64_t)(n * 1.1) + 1024;
     CU(cudaMalloc(&s.in_mem, (size_t)cap * 16));
     s.in_cap = cap;
@@ -1100,7 +1113,8 @@ lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
   if (p->md_buf < 1 || p->ls_list < 1) return fail(LST_ERR_ARG, "sizes must be >= 1");
   DeviceGuard gd(c->device);
   CU(cudaDeviceSynchronize());
-  lst_ctx_s old = *c;
+  struct { int md_threads, md_buf, ls_threads, ls_list, t3_threads, t5_threads, sc_threads; } old = {
+      c->md_threads, c->md_buf, c->ls_threads, c->ls_list, c->t3_threads, c->t5_threads, c->sc_threads};
   c->md_threads = p->md_threads; c->md_buf = p->md_buf;
   c->ls_threads = p->ls_threads; c->ls_list = p->ls_list;
   c->t3_threads = p->t3_threads; c->t5_threads = p->t5_threads;
@@ -1130,6 +1144,12 @@ lst_status lst_device_errors(lst_ctx c) {
   CU(cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
   CU(cudaMemset(c->d_err, 0, sizeof e));
   if (e) return fail((lst_status)e, "a bounded device wait ran out (tensor-core score)");
+  return LST_OK;
+}
+
+lst_status lst_test_fail_alloc(lst_ctx c, int32_t n) {
+  if (!c || n < 0) return fail(LST_ERR_ARG, "null ctx or negative count");
+  c->fail_allocs.store(n);
   return LST_OK;
 }
 

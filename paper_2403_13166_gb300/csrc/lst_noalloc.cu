@@ -163,20 +163,29 @@ __global__ void k_na_finish(unsigned char *base, int64_t *md_count_out) {
   *md_count_out = s.ctr[NA_FLAGS] ? -1 : (int64_t)n;
 }
 
-// Device address of the scratch array, looked up once per device (with that device current).
+// Device address of the scratch array and the SM count, looked up once per device (with
+// that device current).
 std::mutex g_na_mutex;
 unsigned char *g_na_ptr[64] = {nullptr};
+int g_na_sms[64] = {0};
 
-lst_status na_setup(int device, unsigned char **out, const char **why) {
+lst_status na_setup(int device, unsigned char **out, int *sms, const char **why) {
   std::lock_guard<std::mutex> lk(g_na_mutex);
   if (device < 0 || device >= 64) { *why = "device ordinal above 63"; return LST_ERR_ARG; }
   if (!g_na_ptr[device]) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess || !p) { *why = e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address"; return LST_ERR_CUDA; }
+    int n_sm = 0;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess || !p || n_sm <= 0) {
+      *why = e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address or no SMs";
+      return LST_ERR_CUDA;
+    }
     g_na_ptr[device] = static_cast<unsigned char *>(p);
+    g_na_sms[device] = n_sm;
   }
   *out = g_na_ptr[device];
+  *sms = g_na_sms[device];
   return LST_OK;
 }
 
@@ -200,22 +209,24 @@ extern "C" lst_status lst_find_minidoublets_noalloc(lst_ctx ctx, const float *x,
   if (n_hits > 0 && (!x || !y || !z || !sensor)) return reject(LST_ERR_ARG, "null hit array");
   if (capacity > 0 && !md_hits) return reject(LST_ERR_ARG, "null md_hits with capacity > 0");
   int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != device && cudaSetDevice(device) != cudaSuccess) return LST_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return reject(LST_ERR_CUDA, cudaGetErrorString(e));
+  if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return reject(LST_ERR_CUDA, cudaGetErrorString(e));
   unsigned char *base = nullptr;
+  int sms = 0;
   const char *why = nullptr;
-  lst_status st = na_setup(device, &base, &why);
+  lst_status st = na_setup(device, &base, &sms, &why);
   if (st == LST_OK) {
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int ns = 2 * g.n_mod, n = (int)n_hits;
-    const int grid = 2 * 152;
+    const int grid = 2 * sms;   // two 256-thread CTAs per SM for the grid-stride kernels
     k_na_clear<<<grid, 256, 0, s>>>(base, ns);
     k_na_count<<<grid, 256, 0, s>>>(base, x, y, z, sensor, n, ns);
     k_na_scan<<<1, 1024, 0, s>>>(base, ns);
     k_na_scatter<<<grid, 256, 0, s>>>(base, x, y, z, sensor, n, ns);
     k_na_md<<<grid, 256, 0, s>>>(base, g, c, md_hits, md_kappa, (long long)capacity);
     k_na_finish<<<1, 1, 0, s>>>(base, md_count);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) { st = LST_ERR_CUDA; lstk::set_last_error(cudaGetErrorString(e)); }
   } else {
     lstk::set_last_error(why);

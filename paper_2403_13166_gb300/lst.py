@@ -92,6 +92,7 @@ _SIGS = {
     "lst_set_wait_limit": [C.c_void_p, C.c_int64],
     "lst_device_errors": [C.c_void_p],
     "lst_test_skip_mma": [C.c_void_p, C.c_int32],
+    "lst_test_fail_alloc": [C.c_void_p, C.c_int32],
     "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p],
@@ -103,6 +104,49 @@ _SIGS = {
 #: limits of lst_find_minidoublets_noalloc's fixed scratch array (include/lst.h)
 NOALLOC_MAX_HITS = 524288
 NOALLOC_MAX_SENSORS = 32768
+
+
+def noalloc_arguments(device, x, y, z, sensor, md_hits, md_kappa, md_count):
+    """Check the buffers of lst_find_minidoublets_noalloc, whose kernels trust their sizes:
+    every buffer a contiguous torch tensor on `device`; x, y, z float32 and sensor int32 of
+    one length; md_hits int32 of shape (cap, 2); md_kappa None or float32 with at least cap
+    elements; md_count int64 with at least one element. Returns (n_hits, cap); raises
+    ValueError naming the first buffer that does not fit."""
+    import torch
+
+    def tensor(name, a, dtype):
+        if not isinstance(a, torch.Tensor):
+            raise ValueError(f"{name}: expected a torch tensor on {device}, got {type(a).__name__}")
+        if a.device != device:
+            raise ValueError(f"{name}: on {a.device}, expected {device}")
+        if a.dtype != dtype:
+            raise ValueError(f"{name}: dtype {a.dtype}, expected {dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: not contiguous")
+        return a
+
+    n = None
+    for name, a, dt in (("x", x, torch.float32), ("y", y, torch.float32), ("z", z, torch.float32),
+                        ("sensor", sensor, torch.int32)):
+        tensor(name, a, dt)
+        if a.dim() != 1:
+            raise ValueError(f"{name}: expected one dimension, got shape {tuple(a.shape)}")
+        if n is None:
+            n = int(a.shape[0])
+        elif int(a.shape[0]) != n:
+            raise ValueError(f"{name}: length {int(a.shape[0])}, expected {n} (the length of x)")
+    tensor("md_hits", md_hits, torch.int32)
+    if md_hits.dim() != 2 or int(md_hits.shape[1]) != 2:
+        raise ValueError(f"md_hits: expected shape (capacity, 2), got {tuple(md_hits.shape)}")
+    cap = int(md_hits.shape[0])
+    if md_kappa is not None:
+        tensor("md_kappa", md_kappa, torch.float32)
+        if md_kappa.numel() < cap:
+            raise ValueError(f"md_kappa: {md_kappa.numel()} elements, fewer than the capacity {cap}")
+    tensor("md_count", md_count, torch.int64)
+    if md_count.numel() < 1:
+        raise ValueError("md_count: empty")
+    return n, cap
 
 
 def load_library(path: str = LIB_PATH):
@@ -346,10 +390,13 @@ class Context:
         allocate while they run, e.g. inside a framework that owns all device memory). All
         buffers are the caller's device tensors: md_hits int32 [cap, 2], md_kappa float32
         [cap] or None, md_count int64 [1] (count found, or -1 for an invalid hit).
-        Returns the lst_status; raises on errors other than success."""
-        cap = int(md_hits.shape[0]) if md_hits is not None else 0
+        Returns the lst_status; raises ValueError for a buffer of the wrong kind, type,
+        shape or device (before anything is launched) and LstError on other failures."""
+        import torch
+        n, cap = noalloc_arguments(torch.device("cuda", self.device), x, y, z, sensor, md_hits, md_kappa,
+                                   md_count)
         st = load_library().lst_find_minidoublets_noalloc(
-            self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(sensor), int(x.shape[0]), _ptr(md_hits), _ptr(md_kappa),
+            self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(sensor), n, _ptr(md_hits), _ptr(md_kappa),
             cap, _ptr(md_count), _stream_handle(stream))
         return _check(st, "lst_find_minidoublets_noalloc")
 
@@ -371,6 +418,11 @@ class Context:
         """Failure-handling test aid: the tensor-core score kernels issue no MMA, so their
         bounded waits run out (LST_ERR_TIMEOUT) with nothing in flight."""
         _check(load_library().lst_test_skip_mma(self.h, int(on)), "lst_test_skip_mma")
+
+    def test_fail_alloc(self, n=1):
+        """Failure-handling test aid: the next n event-buffer allocations fail as if the
+        device were out of memory (LST_ERR_NOMEM); n = 0 clears them."""
+        _check(load_library().lst_test_fail_alloc(self.h, int(n)), "lst_test_fail_alloc")
 
     def device_errors(self) -> int:
         return load_library().lst_device_errors(self.h)

@@ -18,8 +18,7 @@ WP_BAND = 1e-5
 KINDS = ((lst.LST_MD, "md_hits"), (lst.LST_LS, "ls_hits"), (lst.LST_T3, "t3_hits"), (lst.LST_T5, "t5_hits"))
 
 
-def canon_order(a):
-    return np.lexsort(a.T[::-1]) if len(a) else np.zeros(0, np.int64)
+from lst_parity import canon_order, expected_tc, near_boundary
 
 
 def dev(e):
@@ -49,13 +48,15 @@ def compare(ev, ref, wp, check_features=False):
             f = ev.features()[og].astype(np.float64)
             df = np.abs(f - ref.t5_feat[oe])
             assert np.max(df) <= 4e-6, (np.max(df), np.unravel_index(np.argmax(df), df.shape))
-        # track candidates: the duplicate removal is exact (FP32 chi2 ranks); its input, the
-        # selection, matches whenever no score sits within the FP32 error of the working point
+        # track candidates: the duplicate removal is exact (FP32 chi2 ranks); compared on
+        # every event against the oracle's removal run on the GPU's own selection flags
+        tc = ev.candidates(lst.LST_TC)[0]
+        exp_tc = expected_tc(ref, sel, og, oe)
+        assert c["tc"] == len(tc) == len(exp_tc)
+        assert np.array_equal(tc[canon_order(tc)], exp_tc[canon_order(exp_tc)])
         if np.array_equal(sel[og], ref.t5_sel[oe]):
-            tc = ev.candidates(lst.LST_TC)[0]
-            assert c["tc"] == len(tc) == int(ref.t5_tc.sum())
-            exp_tc = ref.tc_hits()
-            assert np.array_equal(tc[canon_order(tc)], exp_tc[canon_order(exp_tc)])
+            assert len(tc) == int(ref.t5_tc.sum())
+    near_boundary(ref)
     return c
 
 

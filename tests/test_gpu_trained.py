@@ -14,7 +14,9 @@ cannot hold here and is replaced by the checks below.
   * FP32 and split-BF16 (LST_BF16X3) scores against the FP64 oracle within the stated
     bounds FP32_TRAINED_TOL and BF16X3_TOL, selection flips only where the FP64 score lies
     within the observed error of the working point;
-  * plain BF16 is reported (error, flips) but has no bound for these networks."""
+  * plain BF16 is reported (error, flips) but has no bound for these networks;
+  * track candidates equal the oracle's duplicate removal run on the GPU's own selection
+    flags, at every precision."""
 import numpy as np
 import pytest
 
@@ -30,8 +32,7 @@ BF16X3_TOL = 1e-2
 U32 = 2.0 ** -24
 
 
-def canon_order(a):
-    return np.lexsort(a.T[::-1]) if len(a) else np.zeros(0, np.int64)
+from lst_parity import canon_order, expected_tc
 
 
 def dev(e):
@@ -111,6 +112,11 @@ def test_trained_network_parity(geom_full, event, depth):
         if prec != lst.LST_BF16:
             near = np.abs(s_ref - wp) <= max(err, 1e-5)
             assert np.all((sel[og].astype(bool) == (s_ref >= wp)) | near)
+        # track candidates, every precision (plain BF16 included, with its many flips):
+        # the oracle's duplicate removal on the GPU's own selection flags
+        tc = ev.candidates(lst.LST_TC)[0]
+        exp_tc = expected_tc(ref, sel, og, oe)
+        assert np.array_equal(tc[canon_order(tc)], exp_tc[canon_order(exp_tc)])
         ev.release()
         c.close()
 

@@ -19,16 +19,16 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MUTANTS = {
-    "LS kappa, inner MD check removed": ("if (bA && !(", "if (0 && bA && !("),
-    "LS kappa, outer MD check removed": ("if (bB && !(", "if (0 && bB && !("),
+    "LS kappa, inner MD check removed": ("if (bA && !cut_le(", "if (0 && bA && !cut_le("),
+    "LS kappa, outer MD check removed": ("if (bB && !cut_le(", "if (0 && bB && !cut_le("),
     "LS kappa, outer bound doubled": (
         "2.0f * (e / c->sensor_gap) / rb + 2.0f * (e / dT) / rb",
         "2.0f * (2.0f * (e / c->sensor_gap) / rb + 2.0f * (e / dT) / rb)"),
     "LS kappa, inner bound at the outer radius": (
         "2.0f * (e / c->sensor_gap) / ra", "2.0f * (e / c->sensor_gap) / rb"),
     "endcap MD bend removed": (
-        "if (!(fabsf(perp) <= para * T + c->hit_err)) return 0;",
-        "if (0 && !(fabsf(perp) <= para * T + c->hit_err)) return 0;"),
+        "if (!cut_le(fabsf(perp), para * T + c->hit_err)) return 0;",
+        "if (0 && !cut_le(fabsf(perp), para * T + c->hit_err)) return 0;"),
     "endcap MD bend uses sin for tan": ("float T = S / sqrtf(1.0f - S * S);", "float T = S;"),
     "endcap MD road x3": ("adz * rL * c->z_lum / (azl", "3.0f * adz * rL * c->z_lum / (azl"),
     "barrel MD bend error dropped": (
@@ -39,8 +39,8 @@ MUTANTS = {
     "LS road error over the lever arm dropped": ("fabsf(rb - ra) + e * ra))", "fabsf(rb - ra)))"),
     "LS curvature without the factor 2": ("float k = 2.0f * sl / rb;", "float k = sl / rb;"),
     "T3 pT removed": (
-        "if (!(fabsf(k3) <= c->kappa_max * c->t3_kappa_factor)) return 0;",
-        "if (0 && !(fabsf(k3) <= c->kappa_max * c->t3_kappa_factor)) return 0;"),
+        "if (!cut_le(fabsf(k3), c->kappa_max * c->t3_kappa_factor)) return 0;",
+        "if (0 && !cut_le(fabsf(k3), c->kappa_max * c->t3_kappa_factor)) return 0;"),
     "T3 arc-length series dropped": ("float s01 = a * (1.0f + a * a * k3 * k3 / 24.0f);", "float s01 = a;"),
     "T5 charge test removed": ("if (!(ka * kb > 0.0f)) return 0;", "if (0) return 0;"),
     "T5 kappa relative tolerance x3": ("c->t5_kappa_rel * 0.5f", "3.0f * c->t5_kappa_rel * 0.5f"),
