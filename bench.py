@@ -487,17 +487,23 @@ def roofline_entry(stage, ms, B, counts, pairs, hits, clocks, n_sm):
         k = ["md", "ls", "t3", "t5"].index(stage)
         ops = B * pairs[k] * FP32_OPS_PER_PAIR[stage]
         sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12       # FP32 peak, an FMA counted as 2
+        issue = peak / 2                                   # one FP32 operation per lane per clock
         achieved = ops / (ms / 1000.0) / 1e12
         out = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(stage, B), "kernel": f"k_{stage}",
-               "peak_note": f"FP32 lanes x SM clock: {n_sm} SMs x 128 x {sm_mhz:.0f} MHz (non-FMA ops)",
+               "peak_note": f"FP32 peak: {n_sm} SMs x 128 lanes x 2 (FMA) x {sm_mhz:.0f} MHz (SM clock "
+                            f"sampled during the timed region)",
+               "peak_issue": round(issue, 2), "frac_issue": round(achieved / issue, 4),
+               "issue_note": "the cut code may not contract a*b+c (bit-exact FP32 parity), so one FP32 "
+                             "operation per lane per clock is its ceiling",
                "ops_per_pair": FP32_OPS_PER_PAIR[stage]}
         if stage in STRICT_OPS:
             a, b = STRICT_OPS[stage]
             strict = B * (pairs[k] * a + counts[stage] * b) / (ms / 1000.0) / 1e12
             out["achieved_strict"] = round(strict, 3)
             out["frac_strict"] = round(strict / peak, 4)
+            out["frac_strict_issue"] = round(strict / issue, 4)
         return out
     # score / bin: HBM bound
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -529,12 +535,13 @@ def step_roofline(counts, pairs, hits, fan, events_per_s, clocks, n_sm):
     ops = sum(float(p) * k for p, k in zip(pairs, STEP_OPS_PER_PAIR)) + MLP_FLOP_PER_T5 * counts["t5"]
     hbm = peaks.get("hbm_gbs", 6800.0)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    alu = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     gbs = by * events_per_s / 1e9
     tops = ops * events_per_s / 1e12
     return {"alg_bytes_per_event": int(by), "alg_fp32_ops_per_event": int(ops),
             "achieved_GBs": round(gbs, 1), "hbm_peak_GBs": hbm, "hbm_frac": round(gbs / hbm, 4),
             "achieved_TOPs": round(tops, 3), "alu_peak_TOPs": round(alu, 2), "alu_frac": round(tops / alu, 4),
+            "alu_issue_frac": round(2 * tops / alu, 4),
             "note": "mean module-map fan-out %.1f; FP32 ops per candidate pair MD/LS/T3/T5 = %s" % (
                 fan, "/".join(map(str, STEP_OPS_PER_PAIR)))}
 

@@ -260,7 +260,8 @@ typedef struct lst_launch {
     int32_t t3_threads;            /* step 3: CTA size */
     int32_t t5_threads;            /* step 4: CTA size */
     int32_t sc_threads;            /* score: CTA size */
-    int32_t reserved;
+    int32_t t3_mds;                /* step 3: middle MDs per warp unit, 1..32; 0 = chosen per
+                                      launch from its event count */
 } lst_launch;
 lst_status lst_get_launch(lst_ctx ctx, lst_launch *out);
 lst_status lst_set_launch(lst_ctx ctx, const lst_launch *in);

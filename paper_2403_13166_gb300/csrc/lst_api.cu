@@ -26,7 +26,7 @@ __global__ void k_md_scatter(const EvDesc *, int);
 __global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, const int32_t *, int, int);
 __global__ void k_ls_scan(const EvDesc *);
 __global__ void k_ls_scatter(const EvDesc *, int);
-__global__ void k_t3(const EvDesc *, int, lst_cuts);
+__global__ void k_t3(const EvDesc *, int, lst_cuts, int *, int);
 __global__ void k_t3_scan(const EvDesc *);
 __global__ void k_t3_scatter(const EvDesc *, int);
 __global__ void k_t5(const EvDesc *, int, lst_cuts);
@@ -159,6 +159,7 @@ struct lst_ctx_s {
   int md_threads = 256, md_buf = 128;
   int ls_threads = 128, ls_list = 1024;
   int t3_threads = 256;
+  int t3_mds = 0;                  // step-3 unit size in middle MDs; 0: chosen per launch
   int t5_threads = 256;
   int sc_threads = 256;
   int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
@@ -187,7 +188,7 @@ constexpr int LS_WARP_BYTES = 4688;     // sizeof(LsWarp): each warp's targets, 
 constexpr int LS_SMALL_TB = 8;          // target modules per step-2 unit in small launches
 size_t ls_smem(const lst_ctx_s *c) { return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES; }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
-size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * 3840; }   // sizeof(T3Warp)
+size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * 6288; }   // sizeof(T3Warp)
 size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
 int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
 
@@ -252,7 +253,8 @@ void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5)
 // object capacities); `total` is the allocation size.
 struct SlotLayout {
   size_t hit, orig, hmod, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank;
-  size_t ls, lst, lcn, lsu, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl, tcf, cnt;
+  size_t lin, lout, lst, lcn, lost, locn, lsu, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl,
+      tcf, cnt;
   size_t total;
 };
 SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, size_t t5) {
@@ -266,7 +268,8 @@ SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, si
   L.mst = take(4 * nm); L.mcn = take(4 * nm);
   L.uanc = take(16 * md); L.uk = take(8 * md); L.umod = take(4 * md); L.uh = take(8 * md);
   L.urank = take(4 * md);
-  L.ls = take(16 * ls); L.lst = take(4 * md); L.lcn = take(4 * md); L.lsu = take(16 * ls);
+  L.lin = take(4 * ls); L.lout = take(4 * ls);
+  L.lst = take(4 * md); L.lcn = take(4 * md); L.lost = take(4 * md); L.locn = take(4 * md); L.lsu = take(16 * ls);
   L.t3 = take(16 * t3); L.t3k = take(4 * t3); L.t3s = take(4 * md); L.t3c = take(4 * md);
   L.t3u = take(16 * t3); L.t3uk = take(4 * t3);
   L.t5a = take(16 * t5); L.t5b = take(16 * t5); L.t5s = take(4 * t5); L.t5e = take(t5);
@@ -313,8 +316,9 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   d.md_hits = (int2 *)(b + L.mh); d.md_start = (int32_t *)(b + L.mst); d.md_cnt = (int32_t *)(b + L.mcn);
   d.mdu_anchor = (float4 *)(b + L.uanc); d.mdu_kappa = (float2 *)(b + L.uk);
   d.mdu_mod = (int32_t *)(b + L.umod); d.mdu_hits = (int2 *)(b + L.uh); d.mdu_rank = (int32_t *)(b + L.urank);
-  d.ls = (int4 *)(b + L.ls);
+  d.ls_to = (int32_t *)(b + L.lin); d.ls_from = (int32_t *)(b + L.lout);
   d.ls_start = (int32_t *)(b + L.lst); d.ls_cnt = (int32_t *)(b + L.lcn);
+  d.lso_start = (int32_t *)(b + L.lost); d.lso_cnt = (int32_t *)(b + L.locn);
   d.lsu = (int4 *)(b + L.lsu);
   d.t3_md = (int4 *)(b + L.t3); d.t3_kappa = (float *)(b + L.t3k); d.t3_pos = (int32_t *)(b + L.t3s);
   d.t3_cnt = (int32_t *)(b + L.t3c); d.t3u_md = (int4 *)(b + L.t3u); d.t3u_kappa = (float *)(b + L.t3uk);
@@ -421,10 +425,13 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
                                                          0);
   }
   mark(3);
-  k_ls_scan<<<n, 1024, 0, st>>>(L.d_desc);
+  k_ls_scan<<<2 * n, 1024, 0, st>>>(L.d_desc);
   k_ls_scatter<<<c->grid_ls_scatter, 256, 0, st>>>(L.d_desc, n);
   mark(4);
-  k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts);
+  // step-3 units: few middle MDs when few events share the launch, so that the heaviest
+  // unit (the longest warp) stays short against the launch
+  const int t3_mds = c->t3_mds > 0 ? c->t3_mds : (n >= 16 ? 16 : n >= 4 ? 4 : 2);
+  k_t3<<<c->grid_t3, c->t3_threads, t3_smem(c), st>>>(L.d_desc, n, c->cuts, L.d_work + 2, t3_mds);
   k_t3_scan<<<n, 1024, 0, st>>>(L.d_desc);
   k_t3_scatter<<<c->grid_t3_scatter, 256, 0, st>>>(L.d_desc, n);
   mark(5);
@@ -1101,7 +1108,7 @@ lst_status lst_destroy(lst_ctx c) {
 lst_status lst_get_launch(lst_ctx c, lst_launch *o) {
   if (!c || !o) return fail(LST_ERR_ARG, "null argument");
   *o = lst_launch{c->md_threads, c->md_buf, c->ls_threads, c->ls_list, c->t3_threads, c->t5_threads,
-                  c->sc_threads, 0};
+                  c->sc_threads, c->t3_mds};
   return LST_OK;
 }
 
@@ -1111,6 +1118,7 @@ lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
   for (int t : th)
     if (t < 32 || t > 256 || t % 32) return fail(LST_ERR_ARG, "threads must be a multiple of 32 in 32..256");
   if (p->md_buf < 1 || p->ls_list < 1) return fail(LST_ERR_ARG, "sizes must be >= 1");
+  if (p->t3_mds < 0 || p->t3_mds > 32) return fail(LST_ERR_ARG, "t3_mds outside 0..32");
   DeviceGuard gd(c->device);
   CU(cudaDeviceSynchronize());
   struct { int md_threads, md_buf, ls_threads, ls_list, t3_threads, t5_threads, sc_threads; } old = {
@@ -1119,6 +1127,7 @@ lst_status lst_set_launch(lst_ctx c, const lst_launch *p) {
   c->ls_threads = p->ls_threads; c->ls_list = p->ls_list;
   c->t3_threads = p->t3_threads; c->t5_threads = p->t5_threads;
   c->sc_threads = p->sc_threads;
+  c->t3_mds = p->t3_mds;
   int dev_smem = 0;
   CU(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   if (ls_smem(c) > (size_t)dev_smem - 2048 || md_smem(c) > (size_t)dev_smem || t3_smem(c) > (size_t)dev_smem - 4096) {

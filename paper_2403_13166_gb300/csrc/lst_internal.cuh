@@ -59,11 +59,12 @@ struct EvDesc {
   int32_t *md_mod;             // [md_cap] module
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
-  int4 *lsu;                   // [ls_cap] LSs as found, any order: (inner MD, outer MD,
-                               // bits of the curvature, rank within the inner MD)
-  int4 *ls;                    // [ls_cap] grouped by inner MD: (inner MD, outer MD, bits of
-                               // the curvature, 0), one 16-byte record each
-  int32_t *ls_start, *ls_cnt;  // [md_cap] LSs of each inner MD: contiguous range
+  int4 *lsu;                   // [ls_cap] LSs as found, any order: (inner MD, outer MD, rank
+                               // within the inner MD's LSs, rank within the outer MD's LSs)
+  int32_t *ls_to;              // [ls_cap] LSs grouped by inner MD: the outer MD of each
+  int32_t *ls_from;            // [ls_cap] LSs grouped by outer MD: the inner MD of each
+  int32_t *ls_start, *ls_cnt;  // [md_cap] per MD: start and length of its range in ls_to
+  int32_t *lso_start, *lso_cnt;  // [md_cap] per MD: start and length of its range in ls_from
   int4 *t3u_md;                // [t3_cap] T3s as found (md0, md1, md2, rank within md0), any order
   float *t3u_kappa;            // [t3_cap]
   int4 *t3_md;                 // [t3_cap] T3s grouped by first MD (md0, md1, md2, 0)
@@ -131,6 +132,16 @@ __device__ __forceinline__ bool ls_cut(const float4 A, const float4 B, float kA,
   if (bB && !(fabsf(kB - k) <= 2.0f * (e / c.sensor_gap) / B.w + 2.0f * (e / dT) / B.w)) return false;
   kappa = k;
   return true;
+}
+
+// The curvature ls_cut assigns to an accepted LS: the same FP32 expression tree, so the
+// value is bit-identical to the cut's.
+__device__ __forceinline__ float ls_curvature(const float4 A, const float4 B) {
+  const float dx = B.x - A.x, dy = B.y - A.y;
+  const float dT = sqrtf(dx * dx + dy * dy);
+  const float cr = A.x * dy - A.y * dx;
+  const float sl = cr / (A.w * dT);
+  return 2.0f * sl / B.w;
 }
 
 // Necessary condition of ls_cut without division or square root, in fewer operations than
@@ -264,34 +275,31 @@ __device__ __forceinline__ bool t3_cut(const float4 P0, const float4 P1, const f
   return true;
 }
 
-// Necessary condition of t3_cut without division or IEEE square root, from per-first-LS
-// values Q0 = (x1, y1, z1, z1 - z0), Q1 = (ax, ay, a^2, a) and a3 = a^3 (a = |P1 - P0|_T)
-// and the third anchor P2. pT: |2 cr| <= K a b c  <=>  4 cr^2 <= K^2 a^2 b^2 c^2 (K =
-// kappa_max * factor), with cr = a x b (= a x c, the cut's form) and c = a + b. rz: the
-// residual z1 - zp multiplied by S = s01 + s12 >= 0, written as (z1 - z0) s12 - (z2 - z1)
-// s01, with b from the approximate rsqrt and kappa^2 / 24 from the approximate reciprocal
-// (relative errors ~1e-7). The slack (1e-3 relative on K^2 and the tolerance, 3e-4 cm
-// absolute on the residual) is far above the approximation and rounding errors (below
-// 1.5e-4 cm on the residual for coordinates within 300 cm), so a rejected triplet always
-// fails t3_cut.
+// Necessary condition of t3_cut without division or IEEE square root, from the chords of
+// the two LSs alone: a = P1 - P0 (first LS) and b = P2 - P1 (second LS), each given as
+// (dx, dy, dz, transverse length) from the FP32 differences t3_cut itself forms. It tests
+// the rz cut only (the pT cut, which keeps ~80% of the candidate pairs, is left to t3_cut):
+// the residual z1 - zp multiplied by S = s01 + s12 >= 0, written as (z1 - z0) s12 -
+// (z2 - z1) s01, with the curvature of the three anchors from cr = a x b (= a x c, the cut's
+// form), c = a + b, kappa^2 / 24 = 4 cr^2 / (24 a^2 b^2 c^2) through the approximate
+// reciprocal (relative error ~1e-7). Per first LS the lane holds (ax, ay, z1 - z0, a) plus
+// a^2 = ax^2 + ay^2 and a^3. The slack (1e-3 relative on the tolerance, 3e-4 cm absolute on
+// the residual) is far above the approximation and rounding errors (below 1.5e-4 cm on the
+// residual for coordinates within 300 cm), so a rejected triplet always fails t3_cut.
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ bool t3_prefilter(const float4 Q0, const float4 Q1, float a3, const float4 P2, float K2,
-                                             float tolp) {
-  const float bx = P2.x - Q0.x, by = P2.y - Q0.y;
-  const float cx = Q1.x + bx, cy = Q1.y + by;
-  const float b2 = __fmaf_rn(bx, bx, by * by), c2 = __fmaf_rn(cx, cx, cy * cy);
-  const float t = 2.0f * __fmaf_rn(Q1.x, by, -(Q1.y * bx));          // 2 cr
-  const float abc2 = Q1.z * b2 * c2, tt = t * t;
-  const bool pt = tt <= __fmaf_rn(K2, abc2, 1e-12f);
-  const float k24 = tt * rcp_approx(fmaxf(abc2, 1e-30f)) * (1.0f / 24.0f);
-  const float b = b2 * rsqrt_approx(fmaxf(b2, 1e-30f));
-  const float s01 = __fmaf_rn(a3, k24, Q1.w), s12 = __fmaf_rn(b * b2, k24, b);
-  const float lhs = __fmaf_rn(Q0.w, s12, -((P2.z - Q0.z) * s01));
-  return pt & (fabsf(lhs) <= tolp * (s01 + s12));
+__device__ __forceinline__ bool t3_prefilter(const float4 A, float a2, float a3, const float4 B, float tolp) {
+  const float cx = A.x + B.x, cy = A.y + B.y;
+  const float b2 = __fmaf_rn(B.x, B.x, B.y * B.y), c2 = __fmaf_rn(cx, cx, cy * cy);
+  const float cr = __fmaf_rn(A.x, B.y, -(A.y * B.x));
+  const float abc2 = a2 * b2 * c2;
+  const float k24 = (cr * cr) * rcp_approx(fmaxf(abc2, 1e-30f)) * (4.0f / 24.0f);
+  const float s01 = __fmaf_rn(a3, k24, A.w), s12 = __fmaf_rn(B.w * b2, k24, B.w);
+  const float lhs = __fmaf_rn(A.z, s12, -(B.z * s01));
+  return fabsf(lhs) <= tolp * (s01 + s12);
 }
 
 // Step 4: five anchors in chain order; ka, kb the curvatures of T3a = (0,1,2), T3b = (2,3,4).

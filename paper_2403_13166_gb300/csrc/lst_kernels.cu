@@ -108,8 +108,9 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
 // it returned (the object's rank in its group), so the position is the group's start (an
 // exclusive scan of the counts) plus the rank. k_ls_scatter walks the batch one event at a
 // time with the whole grid, SCATTER_ILP LSs per thread and trip (an event has more LSs than
-// the grid has threads); k_md_scatter and k_t3_scatter take GROUP_EV events side by side.
-constexpr int SCATTER_ILP = 4;
+// the grid has threads), and writes one MD index per LS into each of two lists;
+// k_md_scatter and k_t3_scatter take GROUP_EV events side by side.
+constexpr int SCATTER_ILP = 8;
 
 // Reserve n output slots: one atomicAdd per warp. Returns the base or -1 if the buffer
 // would overflow (then the flag is set; the counter still records the demand).
@@ -327,8 +328,9 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
 // through the division-free necessary test; the survivors (~9%) are queued and, 32 at a time,
 // through the necessary curvature-consistency test (~1.8% of all pairs pass), whose survivors
 // wait in a second queue that lives for the whole unit and run through the exact FP32 cut
-// 32 at a time. LSs go out in any order, each with its rank among its inner MD's LSs (the
-// value of the counting atomicAdd); k_ls_scan / k_ls_scatter then group them by inner MD.
+// 32 at a time. LSs go out in any order, each with its ranks among the LSs of its inner and
+// of its outer MD (the values of the counting atomicAdds); k_ls_scan / k_ls_scatter then
+// list every LS by inner MD (its outer MD) and by outer MD (its inner MD).
 constexpr int LS_IN_CHUNK = 64;
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
@@ -395,15 +397,16 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
     const int tb0 = unit_off ? ub * tbu : 0, tb1 = unit_off ? min(nt_all, tb0 + tbu) : nt_all;
     int pairs = 0;
     int q2n = 0;
-    // exact cut of the first n pairs of the second queue (one per lane); LSs out in any order
+    // exact cut of the first n pairs of the second queue (one per lane); LSs out in any order,
+    // each with its ranks among the LSs of its inner and of its outer MD
     auto run_exact = [&](int n) {
       bool pass = false;
       int gi = 0, gm = 0;
-      float k = 0.0f;
       if (lane < n) {
         const int2 qe = w.q2[lane];
         gi = qe.x;
         gm = qe.y & 0x7fffffff;
+        float k;
         pass = ls_cut(ev.md_anchor[gi], ev.md_anchor[gm], ev.md_kappa[gi].x, ev.md_kappa[gm].x, bA, qe.y < 0, c, k);
       }
       const unsigned bal = __ballot_sync(FULL, pass);
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
       const int base = warp_reserve(ev.cnt + C_LS, ev.cnt + C_FLAGS, F_OVF_LS, __popc(bal), ev.ls_cap);
       if (pass && base >= 0) {
         const int o = base + __popc(bal & lanemask_lt());
-        ev.lsu[o] = make_int4(gi, gm, __float_as_int(k), atomicAdd(ev.ls_cnt + gi, 1));
+        ev.lsu[o] = make_int4(gi, gm, atomicAdd(ev.ls_cnt + gi, 1), atomicAdd(ev.lso_cnt + gm, 1));
       }
     };
     for (int b0 = tb0; b0 < tb1; b0 += LS_TB) {
@@ -553,15 +556,19 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
   }
 }
 
-// LSs per inner MD -> ranges (one CTA per event) ...
+// LSs per inner MD and per outer MD -> ranges (two CTAs per event, one per list) ...
 __global__ void k_ls_scan(const EvDesc *__restrict__ evs) {
-  const EvDesc &ev = evs[blockIdx.x];
+  const EvDesc &ev = evs[blockIdx.x >> 1];
   if (ev_void(ev)) return;
   const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
-  block_exclusive_scan(ev.ls_cnt, ev.ls_start, n);
+  if (blockIdx.x & 1)
+    block_exclusive_scan(ev.lso_cnt, ev.lso_start, n);
+  else
+    block_exclusive_scan(ev.ls_cnt, ev.ls_start, n);
 }
 
-// ... then the LSs into their inner MD's range (start plus the rank k_ls drew).
+// ... then each LS into both lists at the range start plus the rank k_ls drew: under its
+// inner MD the outer MD's index, under its outer MD the inner MD's index.
 __global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ evs, int n_events) {
   const int64_t tid = blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
   for (int e = 0; e < n_events; e++) {
@@ -570,178 +577,258 @@ __global__ void __launch_bounds__(256) k_ls_scatter(const EvDesc *__restrict__ e
     const int64_t n = clamp_count(ev.cnt[C_LS], ev.ls_cap);
     for (int64_t o0 = tid; o0 < n; o0 += SCATTER_ILP * st) {
       int4 r[SCATTER_ILP];
-      int pos[SCATTER_ILP];
+      int pi[SCATTER_ILP], po[SCATTER_ILP];
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
         if (o0 + k * st < n) r[k] = ev.lsu[o0 + k * st];
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n) pos[k] = ev.ls_start[r[k].x] + r[k].w;
+        if (o0 + k * st < n) {
+          pi[k] = ev.ls_start[r[k].x] + r[k].z;
+          po[k] = ev.lso_start[r[k].y] + r[k].w;
+        }
 #pragma unroll
       for (int k = 0; k < SCATTER_ILP; k++)
-        if (o0 + k * st < n && chk(ev, pos[k], ev.ls_cap, 24))
-          ev.ls[pos[k]] = make_int4(r[k].x, r[k].y, r[k].z, 0);                // one 16-byte store
+        if (o0 + k * st < n) {
+          if (chk(ev, pi[k], ev.ls_cap, 24)) ev.ls_to[pi[k]] = r[k].y;
+          if (chk(ev, po[k], ev.ls_cap, 25)) ev.ls_from[po[k]] = r[k].x;
+        }
     }
   }
 }
 
-// ===================================================================== steps 3 and 4
-// Both enumerate pairs (X1, X2) where X2 ranges over a contiguous list attached to the
-// middle MD of X1. A warp takes 32 (T5) or 64 (T3: two per lane) consecutive X1 with their
-// list lengths; a warp scan of the lengths gives each X1 its range of flat pair indices.
-// Work is spread by static striding over chunks of X1 of all events (no atomics); pair
-// counts are summed per warp and flushed once per event.
-//
-// Step 3 maps the flat pair indices of a 64-pair chunk to their first LS by marks: every
-// first LS with pairs whose range starts in the chunk writes its slot at its start, and a
-// prefix maximum over the 64 positions (carried from chunk to chunk) gives each position
-// its owner. The prefilter works from per-first-LS values computed once (Q0, Q1, a^3).
+// ===================================================================== step 3: triplets
+// A T3 is a pair (LS1, LS2) that shares its middle MD m (LS1.out == LS2.in == m), so the
+// candidate pairs of m are I(m) x O(m): I(m) the LSs ending at m (their inner MDs in list
+// ls_from), O(m) those starting at m (their outer MDs in list ls_to). The prefilter needs
+// only the two chords P1 - P0 and P2 - P1, formed once per LS and middle MD from the MD
+// anchors (the FP32 differences the cut itself forms), so no candidate pair touches global
+// memory. A warp takes a unit of mdu (<= 32) consecutive middle MDs of one event (units
+// pulled from a counter); MDs lacking I or O items drop out of both sides. The unit's O
+// items are staged in the warp's shared memory in windows of T3_OCAP, the I items of the MDs
+// meeting the window in chunks of T3_ICAP (all loads of a lane in flight at once); then each
+// lane takes an I item and loops over its own MD's O items in the window. Survivors are kept
+// as bit masks, drained into a warp queue of MD triples and run through the exact FP32 cut
+// 32 at a time with their anchors gathered by MD index.
+constexpr int T3_OCAP = 128, T3_ICAP = 96;
 struct T3Warp {
-  float4 Q0[64], Q1[64];             // 64 first LSs per warp chunk: lanes lane and 32 + lane
-  float a3[64];
-  int base[64], md0[64], md1[64];    // base: LS-list start minus the exclusive pair offset
-  int mark[64];
-  int qx[64], qmd[64];               // queue of pairs that passed t3_prefilter
+  float4 O[T3_OCAP];          // window's O items: chord P2 - P1 (bx, by, bz) and |(bx, by)|
+  float4 I[T3_ICAP];          // chunk's I items: chord P1 - P0 (ax, ay, az) and |(ax, ay)|
+  float4 P1[32];              // anchors of the unit's middle MDs
+  int omd[T3_OCAP];           // outer MD of each O item (md2)
+  int imd[T3_ICAP];           // inner MD of each I item (md0)
+  int ioff[33], ooff[33];     // exclusive prefixes over the unit's MDs of the I and O counts
+  int ist[32], ost[32];       // each MD's start in ls_from and in ls_to
+  int q0[64], q1[64], q2[64]; // queued MD triples
 };
-static_assert(sizeof(T3Warp) == 3840, "the host sizes k_t3 shared memory with 3840 bytes per warp");
+static_assert(sizeof(T3Warp) == 6288, "the host sizes k_t3 shared memory with 6288 bytes per warp");
 
-__global__ void __launch_bounds__(256) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
+// the last k in [0, 31] with off[k] <= f, for non-decreasing off[0..32], off[0] <= f < off[32]
+__device__ __forceinline__ int t3_owner(const int *off, int f) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1)
+    if (off[lo + step] <= f) lo += step;
+  return lo;
+}
+
+// Stage items [f0, f1) of a unit's flat item space into shared memory: item f belongs to
+// the unit's MD k = t3_owner(off, f), its far MD is list[st[k] + f - off[k]] and its chord
+// runs from P1[k] to that MD's anchor (towards it when `out`, else from it). A lane takes
+// two items per pass and issues both loads of each step before using either.
+__device__ __forceinline__ void t3_stage(const EvDesc &ev, const int32_t *__restrict__ list, const int *off,
+                                         const int *st, const float4 *P1, bool out, int f0, int f1, float4 *dst,
+                                         int *dmd) {
+  const int lane = threadIdx.x & 31;
+  for (int fb = f0; fb < f1; fb += 64) {
+    int md[2], k[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int f = fb + 32 * j + lane;
+      md[j] = 0;
+      k[j] = 0;
+      if (f < f1) {
+        k[j] = t3_owner(off, f);
+        const int p = st[k[j]] + (f - off[k[j]]);
+        if (chk(ev, p, ev.ls_cap, 31)) md[j] = list[p];
+        if (!chk(ev, md[j], ev.md_cap, 32)) md[j] = 0;
+      }
+    }
+    float4 Q[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+      if (fb + 32 * j + lane < f1) Q[j] = ev.md_anchor[md[j]];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int f = fb + 32 * j + lane;
+      if (f < f1) {
+        const float4 M = P1[k[j]];
+        const float dx = out ? Q[j].x - M.x : M.x - Q[j].x;
+        const float dy = out ? Q[j].y - M.y : M.y - Q[j].y;
+        const float dz = out ? Q[j].z - M.z : M.z - Q[j].z;
+        dst[f - f0] = make_float4(dx, dy, dz, sqrtf(dx * dx + dy * dy));
+        dmd[f - f0] = md[j];
+      }
+    }
+  }
+}
+
+// The exact cut behind a call boundary: it runs on ~2% of the candidate pairs, and its
+// square roots and divisions would otherwise raise the register demand of the pair loop.
+__device__ __noinline__ bool t3_cut_call(const float4 P0, const float4 P1, const float4 P2, const lst_cuts &c,
+                                         float &kappa) {
+  return t3_cut(P0, P1, P2, c, kappa);
+}
+
+__global__ void __launch_bounds__(256, 4) k_t3(const EvDesc *__restrict__ evs, int n_events, lst_cuts c, int *work,
+                                           int mdu) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_pref[MAX_EVENTS + 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   T3Warp &w = reinterpret_cast<T3Warp *>(smem_raw)[wid];
   block_event_prefix(n_events, [&](int e) {
     const EvDesc &ev = evs[e];
-    return ev_void_before(ev, F_OVF_MD | F_OVF_LS) ? 0 : (clamp_count(ev.cnt[C_LS], ev.ls_cap) + 63) / 64;
+    return ev_void_before(ev, F_OVF_MD | F_OVF_LS) ? 0 : (clamp_count(ev.cnt[C_MD], ev.md_cap) + mdu - 1) / mdu;
   }, s_pref);
   const int total = s_pref[n_events];
-  const int W = gridDim.x * nwarps;
-  const float K = c.kappa_max * c.t3_kappa_factor;
-  const float K2 = K * K * 1.001f, tolp = c.t3_rz_tol * 1.001f + 3e-4f;
-  int cur = -1, acc = 0;
-  for (int u = blockIdx.x * nwarps + wid; u < total; u += W) {
+  const float tolp = c.t3_rz_tol * 1.001f + 3e-4f;
+  int cur = -1, qn = 0;            // event of the queued triples, queue length
+  // exact cut of the first n queued triples (one per lane) of event `cur`
+  auto run_queue = [&](int n) {
+    const EvDesc &ev = evs[cur];
+    bool pass = false;
+    float k = 0.0f;
+    int md0 = 0, md1 = 0, md2 = 0;
+    if (lane < n) {
+      md0 = w.q0[lane];
+      md1 = w.q1[lane];
+      md2 = w.q2[lane];
+      pass = t3_cut_call(ev.md_anchor[md0], ev.md_anchor[md1], ev.md_anchor[md2], c, k);
+    }
+    const unsigned bal = __ballot_sync(FULL, pass);
+    if (bal) {
+      const int base = warp_reserve(ev.cnt + C_T3, ev.cnt + C_FLAGS, F_OVF_T3, __popc(bal), ev.t3_cap);
+      if (pass && base >= 0) {
+        const int o = base + __popc(bal & lanemask_lt());
+        ev.t3u_md[o] = make_int4(md0, md1, md2, atomicAdd(ev.t3_cnt + md0, 1));
+        ev.t3u_kappa[o] = k;
+      }
+    }
+  };
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(work, 1);
+    u = __shfl_sync(FULL, u, 0);
+    if (u >= total) break;
     const int e = find_event(s_pref, n_events, u);
-    if (e != cur) {
-      if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT3, acc);
-      acc = 0;
+    if (e != cur) {                               // the queue holds triples of one event
+      if (qn > 0) {
+        __syncwarp();
+        run_queue(qn);
+        qn = 0;
+      }
       cur = e;
     }
     const EvDesc &ev = evs[e];
-    const int nls = clamp_count(ev.cnt[C_LS], ev.ls_cap);
-    // two first LSs per lane (slots lane and 32 + lane), their loads independent
-    int deg[2] = {0, 0}, st2[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int l1 = (u - s_pref[e]) * 64 + 32 * h + lane;
-      if (l1 < nls) {
-        const int4 L1 = ev.ls[l1];
-        const int md0 = L1.x, md1 = L1.y;
-        deg[h] = ev.ls_cnt[md1];
-        st2[h] = ev.ls_start[md1];
-        w.md0[32 * h + lane] = md0;
-        w.md1[32 * h + lane] = md1;
-        const float4 P0 = ev.md_anchor[md0], P1 = ev.md_anchor[md1];
-        const float ax = P1.x - P0.x, ay = P1.y - P0.y;
-        const float a2 = __fmaf_rn(ax, ax, ay * ay);
-        const float a = a2 * rsqrt_approx(fmaxf(a2, 1e-30f));
-        w.Q0[32 * h + lane] = make_float4(P1.x, P1.y, P1.z, P1.z - P0.z);
-        w.Q1[32 * h + lane] = make_float4(ax, ay, a2, a);
-        w.a3[32 * h + lane] = a * a2;
-      }
+    const int nmd = clamp_count(ev.cnt[C_MD], ev.md_cap);
+    const int m0 = (u - s_pref[e]) * mdu;
+    const int m = m0 + lane;
+    int nI = 0, nO = 0, sI = 0, sO = 0;
+    if (lane < mdu && m < nmd) {
+      nI = ev.lso_cnt[m];
+      nO = ev.ls_cnt[m];
+      sI = ev.lso_start[m];
+      sO = ev.ls_start[m];
     }
-    const int inca = warp_incl_scan(deg[0]);
-    const int tota = __shfl_sync(FULL, inca, 31);
-    const int incb = tota + warp_incl_scan(deg[1]);
-    const int exa = inca - deg[0], exb = incb - deg[1];       // first flat pair index of each slot
-    w.base[lane] = st2[0] - exa;
-    w.base[32 + lane] = st2[1] - exb;
-    const int tot = __shfl_sync(FULL, incb, 31);
-    acc += tot;
-    // exact cut on queued pairs [q0, q0 + n): (LS1 slot, outer MD)
-    auto run_queue = [&](int q0, int n) {
-      bool pass = false;
-      float k = 0.0f;
-      int x = 0, md2 = 0;
-      if (lane < n) {
-        x = w.qx[q0 + lane];
-        md2 = w.qmd[q0 + lane];
-        pass = t3_cut(ev.md_anchor[w.md0[x]], ev.md_anchor[w.md1[x]], ev.md_anchor[md2], c, k);
-      }
-      const unsigned bal = __ballot_sync(FULL, pass);
-      if (bal) {
-        const int base = warp_reserve(ev.cnt + C_T3, ev.cnt + C_FLAGS, F_OVF_T3, __popc(bal), ev.t3_cap);
-        if (pass && base >= 0) {
-          const int o = base + __popc(bal & lanemask_lt());
-          ev.t3u_md[o] = make_int4(w.md0[x], w.md1[x], md2, atomicAdd(ev.t3_cnt + w.md0[x], 1));
-          ev.t3u_kappa[o] = k;
+    const int np = nI * nO;
+    if (np == 0) nI = nO = 0;
+    float4 P1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (np) P1 = ev.md_anchor[m];
+    const int incI = warp_incl_scan(nI), incO = warp_incl_scan(nO), incP = warp_incl_scan(np);
+    __syncwarp();                                  // the previous unit's table readers are done
+    w.ioff[lane] = incI - nI;
+    w.ooff[lane] = incO - nO;
+    w.ist[lane] = sI;
+    w.ost[lane] = sO;
+    w.P1[lane] = P1;
+    if (lane == 31) {
+      w.ioff[32] = incI;
+      w.ooff[32] = incO;
+      if (incP) atomicAdd(ev.cnt + C_PT3, incP);
+    }
+    const int TO = __shfl_sync(FULL, incO, 31);
+    __syncwarp();
+    for (int f0 = 0; f0 < TO; f0 += T3_OCAP) {
+      const int f1 = min(TO, f0 + T3_OCAP);
+      const int ka = t3_owner(w.ooff, f0), kb = t3_owner(w.ooff, f1 - 1);
+      const int g1 = w.ioff[kb + 1];
+      for (int c0 = w.ioff[ka]; c0 < g1; c0 += T3_ICAP) {
+        const int c1 = min(g1, c0 + T3_ICAP);
+        __syncwarp();                              // the previous chunk's readers are done
+        if (c0 == w.ioff[ka]) t3_stage(ev, ev.ls_to, w.ooff, w.ost, w.P1, true, f0, f1, w.O, w.omd);
+        t3_stage(ev, ev.ls_from, w.ioff, w.ist, w.P1, false, c0, c1, w.I, w.imd);
+        __syncwarp();
+        for (int gb = c0; gb < c1; gb += 32) {
+          const int gi = gb + lane;
+          int s = 0, len = 0, kI = 0;
+          float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (gi < c1) {
+            kI = t3_owner(w.ioff, gi);
+            A = w.I[gi - c0];
+            const int os = max(w.ooff[kI], f0), oe = min(w.ooff[kI + 1], f1);
+            s = os - f0;
+            len = max(0, oe - os);
+          }
+          const float a2 = __fmaf_rn(A.x, A.x, A.y * A.y), a3 = A.w * a2;
+          int maxlen = len;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(FULL, maxlen, o));
+          for (int k0 = 0; k0 < maxlen; k0 += 32) {
+            const int kn = min(32, maxlen - k0);
+            unsigned mask = 0;
+            for (int k = 0; k < kn; k += 2) {      // branch-free: slots past the lane's range
+#pragma unroll                                      // are read (clamped) and masked off
+              for (int j = 0; j < 2; j++) {
+                const int kk = k0 + k + j;
+                const float4 B = w.O[min(s + kk, T3_OCAP - 1)];
+                const bool p = t3_prefilter(A, a2, a3, B, tolp);
+                mask |= (p && kk < len) ? 1u << (k + j) : 0u;
+              }
+            }
+            for (;;) {                             // drain the masks into the queue
+              const unsigned act = __ballot_sync(FULL, mask != 0);
+              if (act == 0) break;
+              if (mask != 0) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int q = qn + __popc(act & lanemask_lt());
+                w.q0[q] = w.imd[gi - c0];
+                w.q1[q] = m0 + kI;
+                w.q2[q] = w.omd[s + k0 + k];
+              }
+              qn += __popc(act);
+              if (qn >= 32) {
+                __syncwarp();
+                run_queue(32);
+                __syncwarp();
+                if (lane + 32 < qn) {
+                  w.q0[lane] = w.q0[lane + 32];
+                  w.q1[lane] = w.q1[lane + 32];
+                  w.q2[lane] = w.q2[lane + 32];
+                }
+                __syncwarp();
+                qn -= 32;
+              }
+            }
+          }
         }
       }
-    };
-    int qlen = 0;
-    auto enqueue = [&](bool pre, int x, int md2) {
-      const unsigned bal = __ballot_sync(FULL, pre);
-      if (bal == 0) return;
-      if (pre) {
-        const int q = qlen + __popc(bal & lanemask_lt());
-        w.qx[q] = x;
-        w.qmd[q] = md2;
-      }
-      qlen += __popc(bal);
-      if (qlen >= 32) {
-        __syncwarp();
-        run_queue(qlen - 32, 32);
-        qlen -= 32;
-        __syncwarp();
-      }
-    };
-    // owners of the chunk's positions f0 + lane (xa) and f0 + 32 + lane (xb), then the outer
-    // MD of each pair from its LS record (field y)
-    int carry = -1;
-    const int *ls_words = reinterpret_cast<const int *>(ev.ls);
-    auto fetch = [&](int f0, int &xa, int &xb, int &mda, int &mdb) {
-      __syncwarp();                                  // the previous chunk's mark readers are done
-      w.mark[lane] = -1;
-      w.mark[32 + lane] = -1;
-      __syncwarp();
-      if (deg[0] > 0 && exa >= f0 && exa < f0 + 64) w.mark[exa - f0] = lane;
-      if (deg[1] > 0 && exb >= f0 && exb < f0 + 64) w.mark[exb - f0] = 32 + lane;
-      __syncwarp();
-      int ma = max(w.mark[lane], carry), mb = w.mark[32 + lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int ta = __shfl_up_sync(FULL, ma, o), tb = __shfl_up_sync(FULL, mb, o);
-        if (lane >= o) { ma = max(ma, ta); mb = max(mb, tb); }
-      }
-      mb = max(mb, __shfl_sync(FULL, ma, 31));
-      carry = __shfl_sync(FULL, mb, 31);
-      const int fa = f0 + lane, fb = f0 + 32 + lane;
-      xa = fa < tot ? ma : 0;
-      xb = fb < tot ? mb : 0;
-      mda = mdb = 0;
-      if (fa < tot) mda = ls_words[4 * (size_t)(w.base[xa] + fa) + 1];
-      if (fb < tot) mdb = ls_words[4 * (size_t)(w.base[xb] + fb) + 1];
-    };
-    // software pipeline over chunks of 64 pairs: the next chunk's LS words are loaded while
-    // the current chunk's anchors arrive and its pairs are tested
-    int nxa = 0, nxb = 0, nmda = 0, nmdb = 0;
-    if (tot > 0) fetch(0, nxa, nxb, nmda, nmdb);
-    for (int f0 = 0; f0 < tot; f0 += 64) {
-      const int fa = f0 + lane, fb = f0 + 32 + lane;
-      const int xa = nxa, xb = nxb, mda = nmda, mdb = nmdb;
-      float4 Pa = make_float4(0.f, 0.f, 0.f, 0.f), Pb = Pa;
-      if (fa < tot) Pa = ev.md_anchor[mda];
-      if (fb < tot) Pb = ev.md_anchor[mdb];
-      if (f0 + 64 < tot) fetch(f0 + 64, nxa, nxb, nmda, nmdb);
-      const bool prea = fa < tot && t3_prefilter(w.Q0[xa], w.Q1[xa], w.a3[xa], Pa, K2, tolp);
-      const bool preb = fb < tot && t3_prefilter(w.Q0[xb], w.Q1[xb], w.a3[xb], Pb, K2, tolp);
-      enqueue(prea, xa, mda);
-      enqueue(preb, xb, mdb);
     }
-    __syncwarp();
-    if (qlen > 0) run_queue(0, qlen);
-    __syncwarp();
   }
-  if (cur >= 0 && lane == 0 && acc) atomicAdd(evs[cur].cnt + C_PT3, acc);
+  if (qn > 0) {
+    __syncwarp();
+    run_queue(qn);
+  }
 }
 
 // T3s grouped by first MD: exclusive scan of the per-MD counts (one CTA per event) ...
@@ -786,8 +873,13 @@ __global__ void __launch_bounds__(256) k_t3_scatter(const EvDesc *__restrict__ e
   }
 }
 
-// Step 4 maps a flat pair index to its first T3 by a binary search in the warp's shared copy
-// of the inclusive scan (32 entries).
+// ===================================================================== step 4: quintuplets
+// Pairs (T3a, T3b) with T3b in the list of T3s whose first MD is T3a's last MD. A warp takes
+// 32 consecutive T3a with their list lengths; a warp scan of the lengths gives each T3a its
+// range of flat pair indices, and a flat index maps to its T3a by a binary search in the
+// warp's shared copy of the inclusive scan (32 entries). Work is spread by static striding
+// over chunks of T3a of all events (no atomics); pair counts are summed per warp and
+// flushed once per event.
 struct T5Warp {
   int incl[32], st2[32], ta[32];
   float ka[32];

@@ -122,7 +122,7 @@ __global__ void k_gather(const EvDesc *__restrict__ ev_p, int kind, int n, int32
       out[2 * (size_t)t] = h.x;
       out[2 * (size_t)t + 1] = h.y;
     } else if (kind == LST_LS) {
-      const int4 L = ev.ls[t];
+      const int4 L = ev.lsu[t];
       const int2 a = ev.md_hits[L.x], b = ev.md_hits[L.y];
       int32_t *o = out + 4 * (size_t)t;
       o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
@@ -192,12 +192,11 @@ __global__ void k_graph_fill(const EvDesc *__restrict__ ev_p, DevGeom g, int n_m
     const float4 A = ev.md_anchor[m];
     const int beg = ev.ls_start[m], cnt = ev.ls_cnt[m], o = row_off[m];
     for (int k = 0; k < cnt; k++) {
-      const int4 L = ev.ls[beg + k];
-      const int b = L.y;
+      const int b = ev.ls_to[beg + k];
       col[o + k] = b;
       if (edge_feat) {
         const float4 B = ev.md_anchor[b];
-        edge_feat[2 * (size_t)(o + k)] = __int_as_float(L.z);
+        edge_feat[2 * (size_t)(o + k)] = ls_curvature(A, B);
         edge_feat[2 * (size_t)(o + k) + 1] = A.z - A.w * ((B.z - A.z) / (B.w - A.w));   // z at r = 0
       }
     }
@@ -217,7 +216,12 @@ __global__ void k_reset(const EvDesc *__restrict__ evs, DevGeom g) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   if (tid < C_NCOUNTERS) ev.cnt[tid] = 0;
   for (int i = tid; i < 2 * g.n_mod; i += st) ev.sens_cnt[i] = 0;
-  for (int i = tid; i < ev.md_cap; i += st) { ev.ls_cnt[i] = 0; ev.t3_cnt[i] = 0; ev.tc_cnt[i] = 0; }
+  for (int i = tid; i < ev.md_cap; i += st) {
+    ev.ls_cnt[i] = 0;
+    ev.lso_cnt[i] = 0;
+    ev.t3_cnt[i] = 0;
+    ev.tc_cnt[i] = 0;
+  }
   for (int i = tid; i < g.n_mod; i += st) ev.md_cnt[i] = 0;
 }
 

@@ -55,7 +55,7 @@ class lst_config(C.Structure):
 
 class lst_launch(C.Structure):
     _fields_ = [(f, C.c_int32) for f in ("md_threads", "md_buf", "ls_threads", "ls_list", "t3_threads",
-                                          "t5_threads", "sc_threads", "reserved")]
+                                          "t5_threads", "sc_threads", "t3_mds")]
 
 
 class lst_counts(C.Structure):

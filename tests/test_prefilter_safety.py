@@ -100,27 +100,24 @@ def ls_prefilters(A, B, kA, kB, bA, bB, c, rel):
 
 
 def t3_prefilter(P0, P1, P2, c, rel):
-    """t3_prefilter from the per-first-LS values, float32."""
-    K = f32(c["kappa_max"]) * f32(c["t3_kappa_factor"])
-    K2 = f32(K * K * f32(1.001))
+    """t3_prefilter (rz test) from the two LS chords (a = P1 - P0, b = P2 - P1 with their
+    transverse lengths sqrtf(dx*dx + dy*dy), correctly rounded), float32."""
     tolp = f32(f32(c["t3_rz_tol"]) * f32(1.001) + f32(3e-4))
     with np.errstate(all="ignore"):
-        ax, ay = P1[0] - P0[0], P1[1] - P0[1]
+        ax, ay, az = P1[0] - P0[0], P1[1] - P0[1], P1[2] - P0[2]
+        bx, by, bz = P2[0] - P1[0], P2[1] - P1[1], P2[2] - P1[2]
+        a = np.sqrt(ax * ax + ay * ay).astype(f32)
+        b = np.sqrt(bx * bx + by * by).astype(f32)
         a2 = fma(ax, ax, ay * ay)
-        a = (a2 * (f32(1.0) / np.sqrt(np.maximum(a2, f32(1e-30)))) * f32(rel)).astype(f32)
         a3 = a * a2
-        dz01 = P1[2] - P0[2]
-        bx, by = P2[0] - P1[0], P2[1] - P1[1]
         cx, cy = ax + bx, ay + by
         b2, c2 = fma(bx, bx, by * by), fma(cx, cx, cy * cy)
-        t = f32(2.0) * fma(ax, by, -(ay * bx))
-        abc2, tt = a2 * b2 * c2, t * t
-        pt = tt <= fma(full(abc2.shape, K2), abc2, full(abc2.shape, 1e-12))
-        k24 = ((tt * (f32(1.0) / np.maximum(abc2, f32(1e-30)))) * f32(rel)).astype(f32) * f32(1.0 / 24.0)
-        b = (b2 * (f32(1.0) / np.sqrt(np.maximum(b2, f32(1e-30)))) * f32(rel)).astype(f32)
+        cr = fma(ax, by, -(ay * bx))
+        abc2 = a2 * b2 * c2
+        k24 = ((cr * cr) * ((f32(1.0) / np.maximum(abc2, f32(1e-30))) * f32(rel)).astype(f32)) * f32(4.0 / 24.0)
         s01, s12 = fma(a3, k24, a), fma(b * b2, k24, b)
-        lhs = fma(dz01, s12, -((P2[2] - P1[2]) * s01))
-    return pt & (np.abs(lhs) <= tolp * (s01 + s12))
+        lhs = fma(az, s12, -(bz * s01))
+    return np.abs(lhs) <= tolp * (s01 + s12)
 
 
 def test_md_prefilter_keeps_every_mini_doublet(event, geom_full, cuts):
