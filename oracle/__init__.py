@@ -22,7 +22,7 @@ Parity status per function (pins live in tests/test_oracle_*.py):
       holds no duplicates, one track candidate per isolated muon.
 """
 from .oracle import (OracleResult, build_oracle, md_cut, ls_cut, t3_cut, t5_cut, t5_chi2,
-                     tc_select, t5_features, mlp_forward, run_event)
+                     tc_select, t5_features, mlp_forward, pixel_match, run_event)
 
 __all__ = ["OracleResult", "build_oracle", "md_cut", "ls_cut", "t3_cut", "t5_cut", "t5_chi2",
-           "tc_select", "t5_features", "mlp_forward", "run_event"]
+           "tc_select", "t5_features", "mlp_forward", "pixel_match", "run_event"]

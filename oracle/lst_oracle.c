@@ -70,7 +70,15 @@ typedef struct {
     uint8_t *t5_sel;
     float *t5_chi2;                        /* [n] circle-fit chi2 of the five anchors */
     uint8_t *t5_tc;                        /* [n] 1: the T5 is a track candidate */
+    int64_t n_pix;                         /* pixel-seed track candidates (steps 5-8) */
+    int32_t *pix_tc;                       /* [n_pix][3]: type (5 pT5, 6 T5, 7 pT3, 8 pLS),
+                                              pLS index (-1 for type 6), T5 / T3 index (-1 for 8) */
+    int64_t pix_ties;                      /* greedy choices between edges of equal residual */
 } oresult;
+
+typedef struct {
+    float kappa_rel, kappa_abs, rz_tol, cos_dphi, dm_abs, dm_rel;
+} opcuts;
 
 /* ------------------------------------------------------------------ growable arrays */
 typedef struct { void *p; int64_t n, cap; size_t es; } vec;
@@ -438,6 +446,209 @@ void oracle_tc_select(int64_t n, const int32_t *md, const int32_t *key, const fl
     free(list);
 }
 
+static void fill_md_anchor(const hit *H, float *a) { a[0] = H->x; a[1] = H->y; a[2] = H->z; a[3] = H->r; }
+
+/* ------------------------------------------------------------------ pixel seeds */
+/* Table 1 steps 0 and 5-8. A pixel seed (pLS) is four inner-tracker hits H1..H4 (inner
+ * first), made upstream. It is matched to an outer object (a T5 by its first T3, or a T3)
+ * whose first anchors are P0, P1 and whose curvature is ko (the T3's three-point value) when
+ * the two are consistent with one helix (Section 1). Project specification, FP32, only + - *
+ * / sqrt, so that the GPU reaches the same decisions:
+ *   window: the azimuth of P0 as seen from the beamline lies within acos(cos_dphi) of H4's,
+ *     H4 . P0 >= cos_dphi |H4|_T |P0|_T, and the r-z slopes agree, |m_p - m_o| <=
+ *     dm_abs + dm_rel |m_o| with m_p = (z4 - z1) / (r4 - r1) and m_o = (z1' - z0) /
+ *     (r1' - r0) (P0 -> P1);
+ *   pT: |kp - ko| <= rel (|kp| + |ko|) / 2 + abs, kp the seed's curvature through H1, H3, H4;
+ *   circle: the same test for kx, the curvature through H1, H4 and P0 (the seed and the
+ *     object on one circle);
+ *   rz: H4's z against its interpolation between H1 and P0 along the arc (the T3 form, with
+ *     the mean curvature (kx + ko) / 2): |z4 - zp| <= rz_tol.
+ * Matches rank by that rz residual, then by |kx - ko|, then by the seed's index, then by the
+ * object's hit tuple (original hit indices, lexicographic): objects built on the same anchors
+ * tie in every measure, and the tuple decides between them whatever their storage order.
+ * Every curvature is the signed three-point value 2 (B - A) x (C - A) / (|B-A| |C-B| |C-A|). */
+static float pix_curv3(const float *A, const float *B, const float *C)
+{
+    float d01x = B[0] - A[0], d01y = B[1] - A[1];
+    float d12x = C[0] - B[0], d12y = C[1] - B[1];
+    float d02x = C[0] - A[0], d02y = C[1] - A[1];
+    float a = sqrtf(d01x * d01x + d01y * d01y);
+    float b = sqrtf(d12x * d12x + d12y * d12y);
+    float c = sqrtf(d02x * d02x + d02y * d02y);
+    float cr = d01x * d02y - d01y * d02x;
+    return 2.0f * cr / (a * b * c);
+}
+
+static int pix_kappa_ok(float k1, float k2, const opcuts *pc)
+{
+    return fabsf(k1 - k2) <= pc->kappa_rel * 0.5f * (fabsf(k1) + fabsf(k2)) + pc->kappa_abs;
+}
+
+/* H: the seed's hits [4][3]; P0, P1: (x, y, z, r) of the object's first two anchors.
+ * Returns 1 and the ranking pair (rz residual, |kx - ko|) if the seed and the object match. */
+int oracle_pixel_match(const float *H, const float *P0, const float *P1, float ko, const opcuts *pc,
+                       float *resid)
+{
+    const float *H1 = H, *H3 = H + 6, *H4 = H + 9;
+    float r1 = sqrtf(H1[0] * H1[0] + H1[1] * H1[1]);
+    float r4 = sqrtf(H4[0] * H4[0] + H4[1] * H4[1]);
+    if (!(H4[0] * P0[0] + H4[1] * P0[1] >= pc->cos_dphi * (r4 * P0[3]))) return 0;   /* azimuth */
+    float mp = (H4[2] - H1[2]) / (r4 - r1);
+    float mo = (P1[2] - P0[2]) / (P1[3] - P0[3]);
+    if (!(fabsf(mp - mo) <= pc->dm_abs + pc->dm_rel * fabsf(mo))) return 0;          /* slope */
+    float kp = pix_curv3(H1, H3, H4);
+    if (!pix_kappa_ok(kp, ko, pc)) return 0;                                        /* pT */
+    float kx = pix_curv3(H1, H4, P0);
+    if (!pix_kappa_ok(kx, ko, pc)) return 0;                                        /* circle */
+    float kbar = 0.5f * (kx + ko);
+    float ax = H4[0] - H1[0], ay = H4[1] - H1[1], bx = P0[0] - H4[0], by = P0[1] - H4[1];
+    float a = sqrtf(ax * ax + ay * ay), b = sqrtf(bx * bx + by * by);
+    float s14 = a * (1.0f + a * a * kbar * kbar / 24.0f);
+    float s40 = b * (1.0f + b * b * kbar * kbar / 24.0f);
+    float zp = H1[2] + (P0[2] - H1[2]) * s14 / (s14 + s40);
+    float res = fabsf(H4[2] - zp);
+    if (!(res <= pc->rz_tol)) return 0;                                             /* rz */
+    resid[0] = res;
+    resid[1] = fabsf(kx - ko);
+    return 1;
+}
+
+typedef struct { float res, dk; int32_t p, o, rank; } pedge;
+
+static int pedge_cmp(const void *a, const void *b)
+{
+    const pedge *x = a, *y = b;
+    if (x->res != y->res) return x->res < y->res ? -1 : 1;
+    if (x->dk != y->dk) return x->dk < y->dk ? -1 : 1;
+    if (x->p != y->p) return x->p < y->p ? -1 : 1;
+    return (x->rank > y->rank) - (x->rank < y->rank);
+}
+
+typedef struct { int32_t key[10]; int32_t o; } pobj;
+
+static int pobj_cmp(const void *a, const void *b)
+{
+    const pobj *x = a, *y = b;
+    for (int k = 0; k < 10; k++)
+        if (x->key[k] != y->key[k]) return x->key[k] < y->key[k] ? -1 : 1;
+    return 0;
+}
+
+/* rank[o] = position of object o in the lexicographic order of its hit tuple key[o][0..w) */
+static void pix_ranks(const int32_t *key, int w, int64_t n, int32_t *rank)
+{
+    pobj *v = malloc(sizeof(pobj) * (size_t)(n ? n : 1));
+    for (int64_t o = 0; o < n; o++) {
+        for (int k = 0; k < 10; k++) v[o].key[k] = k < w ? key[(size_t)w * o + k] : 0;
+        v[o].o = (int32_t)o;
+    }
+    qsort(v, (size_t)n, sizeof(pobj), pobj_cmp);
+    for (int64_t i = 0; i < n; i++) rank[v[i].o] = (int32_t)i;
+    free(v);
+}
+
+/* One-to-one matching of seeds and objects, preferring the better rank: the edges in
+ * ascending (rz residual, |kx - ko|, seed, object hit tuple) order, each taken when both its
+ * ends are still free. Objects with elig[o] == 0 and seeds with pused[p] != 0 take part in no
+ * edge. obj_p[o] receives the seed taken by object o (or stays -1); pused marks taken seeds.
+ * Counts in *ties the edges taken while an edge equal in (residual, |kx - ko|) and sharing an
+ * end was left, i.e. where the seed index or the hit tuple decided. */
+static void pix_greedy(const float *pls, int64_t n_pls, int64_t n_obj, const uint8_t *elig,
+                       const float *P0s, const float *P1s, const float *kos, const int32_t *rank,
+                       const opcuts *pc, int32_t *obj_p, uint8_t *pused, int64_t *ties)
+{
+    vec E; vinit(&E, sizeof(pedge));
+    for (int64_t p = 0; p < n_pls; p++) {
+        if (pused[p]) continue;
+        for (int64_t o = 0; o < n_obj; o++) {
+            if (!elig[o]) continue;
+            float r[2];
+            if (oracle_pixel_match(pls + 12 * p, P0s + 4 * o, P1s + 4 * o, kos[o], pc, r)) {
+                pedge *e = vpush(&E);
+                e->res = r[0]; e->dk = r[1]; e->p = (int32_t)p; e->o = (int32_t)o; e->rank = rank[o];
+            }
+        }
+    }
+    pedge *ed = E.p;
+    qsort(ed, (size_t)E.n, sizeof(pedge), pedge_cmp);
+    uint8_t *otaken = calloc((size_t)(n_obj ? n_obj : 1), 1);
+    for (int64_t i = 0; i < E.n; i++) {
+        if (pused[ed[i].p] || otaken[ed[i].o]) continue;
+        pused[ed[i].p] = 1;
+        otaken[ed[i].o] = 1;
+        obj_p[ed[i].o] = ed[i].p;
+        for (int64_t j = i + 1; j < E.n && ed[j].res == ed[i].res && ed[j].dk == ed[i].dk; j++)
+            if (ed[j].p == ed[i].p || ed[j].o == ed[i].o) (*ties)++;
+    }
+    free(otaken);
+    free(E.p);
+}
+
+/* Table 1 steps 5-8 from the event's track-candidate T5s (t5_tc), all T3s and the seeds:
+ *   5 pT5: seeds matched one-to-one to track-candidate T5s (by the T5's first T3);
+ *   6 T5: track-candidate T5s left without a seed;
+ *   7 pT3: the remaining seeds matched one-to-one to T3s not in a pT5 (a T3 is in a pT5
+ *     when each of its three MDs belongs to a pT5's T5);
+ *   8 pLS: seeds used by neither. */
+static void pix_tcs(const float *pls, int64_t n_pls, const opcuts *pc, const hit *H, const md_t *MD,
+                    int64_t n_md, const t3_t *T3, int64_t n_t3, const t5_t *T5, int64_t n_t5,
+                    const uint8_t *t5_tc, oresult *out)
+{
+    uint8_t *pused = calloc((size_t)(n_pls ? n_pls : 1), 1);
+    int64_t nt5 = n_t5 ? n_t5 : 1, nt3 = n_t3 ? n_t3 : 1;
+    float *P0 = malloc(16 * (size_t)(nt5 > nt3 ? nt5 : nt3)), *P1 = malloc(16 * (size_t)(nt5 > nt3 ? nt5 : nt3));
+    float *ko = malloc(4 * (size_t)(nt5 > nt3 ? nt5 : nt3));
+    int32_t *t5p = malloc(4 * (size_t)nt5), *t3p = malloc(4 * (size_t)nt3);
+    uint8_t *elig = malloc((size_t)(nt5 > nt3 ? nt5 : nt3));
+    int32_t *key = malloc(40 * (size_t)(nt5 > nt3 ? nt5 : nt3)), *rank = malloc(4 * (size_t)(nt5 > nt3 ? nt5 : nt3));
+    for (int64_t t = 0; t < n_t5; t++)
+        for (int j = 0; j < 5; j++) {
+            key[10 * t + 2 * j] = MD[T5[t].md[j]].lo;
+            key[10 * t + 2 * j + 1] = MD[T5[t].md[j]].up;
+        }
+    pix_ranks(key, 10, n_t5, rank);
+    for (int64_t t = 0; t < n_t5; t++) {
+        fill_md_anchor(&H[MD[T5[t].md[0]].lo], P0 + 4 * t);
+        fill_md_anchor(&H[MD[T5[t].md[1]].lo], P1 + 4 * t);
+        ko[t] = T3[T5[t].t3a].kappa;
+        elig[t] = t5_tc[t];
+        t5p[t] = -1;
+    }
+    pix_greedy(pls, n_pls, n_t5, elig, P0, P1, ko, rank, pc, t5p, pused, &out->pix_ties);
+    uint8_t *mdin = calloc((size_t)(n_md ? n_md : 1), 1);
+    for (int64_t t = 0; t < n_t5; t++)
+        if (t5p[t] >= 0)
+            for (int j = 0; j < 5; j++) mdin[T5[t].md[j]] = 1;
+    for (int64_t u = 0; u < n_t3; u++)
+        for (int j = 0; j < 3; j++) {
+            key[6 * u + 2 * j] = MD[T3[u].md[j]].lo;
+            key[6 * u + 2 * j + 1] = MD[T3[u].md[j]].up;
+        }
+    pix_ranks(key, 6, n_t3, rank);
+    for (int64_t u = 0; u < n_t3; u++) {
+        fill_md_anchor(&H[MD[T3[u].md[0]].lo], P0 + 4 * u);
+        fill_md_anchor(&H[MD[T3[u].md[1]].lo], P1 + 4 * u);
+        ko[u] = T3[u].kappa;
+        elig[u] = !(mdin[T3[u].md[0]] && mdin[T3[u].md[1]] && mdin[T3[u].md[2]]);
+        t3p[u] = -1;
+    }
+    pix_greedy(pls, n_pls, n_t3, elig, P0, P1, ko, rank, pc, t3p, pused, &out->pix_ties);
+    vec R; vinit(&R, 12);
+    for (int64_t t = 0; t < n_t5; t++) {
+        if (!t5_tc[t]) continue;
+        int32_t *row = vpush(&R);
+        row[0] = t5p[t] >= 0 ? 5 : 6; row[1] = t5p[t]; row[2] = (int32_t)t;
+    }
+    for (int64_t u = 0; u < n_t3; u++)
+        if (t3p[u] >= 0) { int32_t *row = vpush(&R); row[0] = 7; row[1] = t3p[u]; row[2] = (int32_t)u; }
+    for (int64_t p = 0; p < n_pls; p++)
+        if (!pused[p]) { int32_t *row = vpush(&R); row[0] = 8; row[1] = (int32_t)p; row[2] = -1; }
+    out->n_pix = R.n;
+    out->pix_tc = R.p ? R.p : malloc(12);
+    free(pused); free(P0); free(P1); free(ko); free(t5p); free(t3p); free(elig); free(mdin);
+    free(key); free(rank);
+}
+
 /* ------------------------------------------------------------------ event driver */
 static int layer_adjacent(int la, int sa, int lb, int sb)
 {
@@ -447,11 +658,10 @@ static int layer_adjacent(int la, int sa, int lb, int sb)
     return 0;
 }
 
-static void fill_md_anchor(const hit *H, float *a) { a[0] = H->x; a[1] = H->y; a[2] = H->z; a[3] = H->r; }
 
 int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
                const int32_t *sensor, int64_t n_hits, const ocuts *c, const omlp *mlp,
-               int brute, oresult *out)
+               int brute, const float *pls, int64_t n_pls, const opcuts *pc, oresult *out)
 {
     memset(out, 0, sizeof *out);
     int32_t nm = g->n_mod;
@@ -670,6 +880,9 @@ int oracle_run(const ogeom *g, const float *x, const float *y, const float *z,
         oracle_tc_select(t5s.n, out->t5_md, key, out->t5_chi2, out->t5_sel, mds.n, brute, out->t5_tc);
         free(key);
     }
+
+    /* ---- pixel seeds: track candidates of steps 5-8 ---- */
+    if (pls && pc) pix_tcs(pls, n_pls, pc, H, MD, mds.n, T3, t3s.n, T5, t5s.n, out->t5_tc, out);
     free(H); free(soff); free(sidx); free(mdoff); free(lsoff); free(t3off);
     free(mds.p); free(lss.p); free(t3s.p); free(t5s.p);
     return 0;
@@ -679,7 +892,7 @@ void oracle_free(oresult *r)
 {
     void *ps[] = {r->md_lo, r->md_up, r->md_mod, r->md_kappa, r->ls_in, r->ls_out, r->ls_kappa,
                   r->t3_ls1, r->t3_ls2, r->t3_md, r->t3_kappa, r->t5_t3a, r->t5_t3b, r->t5_md,
-                  r->t5_feat, r->t5_score, r->t5_sel, r->t5_chi2, r->t5_tc};
+                  r->t5_feat, r->t5_score, r->t5_sel, r->t5_chi2, r->t5_tc, r->pix_tc};
     for (size_t i = 0; i < sizeof ps / sizeof ps[0]; i++) free(ps[i]);
     memset(r, 0, sizeof *r);
 }

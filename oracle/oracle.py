@@ -45,7 +45,15 @@ class _Result(C.Structure):
                 ("t3_kappa", C.c_void_p),
                 ("t5_t3a", C.c_void_p), ("t5_t3b", C.c_void_p), ("t5_md", C.c_void_p),
                 ("t5_feat", C.c_void_p), ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p),
-                ("t5_chi2", C.c_void_p), ("t5_tc", C.c_void_p)]
+                ("t5_chi2", C.c_void_p), ("t5_tc", C.c_void_p),
+                ("n_pix", C.c_int64), ("pix_tc", C.c_void_p), ("pix_ties", C.c_int64)]
+
+
+PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "cos_dphi", "dm_abs", "dm_rel")
+
+
+class _PCuts(C.Structure):
+    _fields_ = [(f, C.c_float) for f in PIXEL_CUT_FIELDS]
 
 
 def build_oracle(force: bool = False) -> str:
@@ -67,7 +75,10 @@ def _load():
             lib.oracle_run.restype = C.c_int
             lib.oracle_run.argtypes = [C.POINTER(_Geom), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int64, C.POINTER(_Cuts), C.POINTER(_Mlp),
-                                       C.c_int, C.POINTER(_Result)]
+                                       C.c_int, C.c_void_p, C.c_int64, C.POINTER(_PCuts),
+                                       C.POINTER(_Result)]
+            lib.oracle_pixel_match.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                               C.POINTER(_PCuts), C.c_void_p]
             lib.oracle_free.argtypes = [C.POINTER(_Result)]
             lib.oracle_md_cut.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(_Cuts),
                                           C.POINTER(C.c_float)]
@@ -129,6 +140,23 @@ def t5_cut(P, ka, kb, cuts):
     lib = _load()
     P = _f32(np.asarray(P).ravel(), 20)
     return bool(lib.oracle_t5_cut(P.ctypes.data, float(ka), float(kb), C.byref(_cuts(cuts))))
+
+
+def _pcuts(pcuts: dict) -> _PCuts:
+    return _PCuts(*[float(np.float32(pcuts[f])) for f in PIXEL_CUT_FIELDS])
+
+
+def pixel_match(H, P0, P1, ko, pcuts):
+    """One seed / object match: H the seed's hits [4][3], P0 and P1 the object's first two
+    anchors (x, y, z, r), ko its curvature (float32). Returns (matched, rz residual,
+    |kx - ko|)."""
+    lib = _load()
+    H = _f32(np.asarray(H).ravel(), 12)
+    P0, P1 = _f32(P0, 4), _f32(P1, 4)
+    r = (C.c_float * 2)()
+    ok = lib.oracle_pixel_match(H.ctypes.data, P0.ctypes.data, P1.ctypes.data, float(np.float32(ko)),
+                                C.byref(_pcuts(pcuts)), r)
+    return bool(ok), np.float32(r[0]), np.float32(r[1])
 
 
 def t5_chi2(P, sigma):
@@ -199,6 +227,8 @@ class OracleResult:
     t5_sel: np.ndarray
     t5_chi2: np.ndarray
     t5_tc: np.ndarray
+    pix_tc: np.ndarray = None      # [n][3] (type 5/6/7/8, pLS index or -1, T5 / T3 index or -1)
+    pix_ties: int = 0
 
     @property
     def counts(self):
@@ -224,6 +254,18 @@ class OracleResult:
     def tc_hits(self):
         return self.t5_hits()[self.t5_tc.astype(bool)]
 
+    def pixel_tcs(self):
+        """Steps 5-8 as comparable tuples: (type, pLS index, the object's hit indices padded
+        with -1 to 10)."""
+        out = []
+        if self.pix_tc is None:
+            return out
+        t5h, t3h = self.t5_hits(), self.t3_hits()
+        for typ, p, o in self.pix_tc.tolist():
+            h = t5h[o].tolist() if typ in (5, 6) else t3h[o].tolist() if typ == 7 else []
+            out.append((typ, p, *(h + [-1] * (10 - len(h)))))
+        return out
+
 
 def _arr(ptr, n, dtype, shape=None):
     if n == 0:
@@ -234,8 +276,11 @@ def _arr(ptr, n, dtype, shape=None):
     return a.reshape((n,) + shape) if shape else a
 
 
-def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -> OracleResult:
-    """Run steps 1-4 and the score on one event (all arrays copied out)."""
+def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False, pls=None,
+              pcuts=None) -> OracleResult:
+    """Run steps 1-4 and the score on one event (all arrays copied out); with pixel seeds
+    (pls: float32 [n][4][3]) and their matching parameters also the track candidates of
+    steps 5-8."""
     lib = _load()
     layer = np.ascontiguousarray(geom.layer, np.int32)
     subdet = np.ascontiguousarray(geom.subdet, np.int32)
@@ -254,8 +299,14 @@ def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -
         m, keep = _mlp_struct(mlp_flat, n_hidden)
         mp = C.byref(m)
     res = _Result()
+    pk, npl, pcp = None, 0, None
+    if pls is not None:
+        pk = np.ascontiguousarray(pls, np.float32).reshape(-1, 12)
+        npl = pk.shape[0]
+        pcp = C.byref(_pcuts(pcuts))
     rc = lib.oracle_run(C.byref(g), x.ctypes.data, y.ctypes.data, z.ctypes.data, s.ctypes.data,
-                        x.shape[0], C.byref(_cuts(cuts)), mp, int(brute), C.byref(res))
+                        x.shape[0], C.byref(_cuts(cuts)), mp, int(brute),
+                        pk.ctypes.data if pk is not None else None, npl, pcp, C.byref(res))
     if rc != 0:
         raise ValueError("oracle: invalid hit (sensor id out of range or non-finite coordinate)")
     try:
@@ -271,7 +322,9 @@ def run_event(geom, event, cuts: dict, mlp_flat=None, n_hidden=2, brute=False) -
             t5_t3b=_arr(res.t5_t3b, n4, np.int32),
             t5_feat=_arr(res.t5_feat, n4, np.float64, (NFEAT,)),
             t5_score=_arr(res.t5_score, n4, np.float64), t5_sel=_arr(res.t5_sel, n4, np.uint8),
-            t5_chi2=_arr(res.t5_chi2, n4, np.float32), t5_tc=_arr(res.t5_tc, n4, np.uint8))
+            t5_chi2=_arr(res.t5_chi2, n4, np.float32), t5_tc=_arr(res.t5_tc, n4, np.uint8),
+            pix_tc=_arr(res.pix_tc, res.n_pix, np.int32, (3,)) if pls is not None else None,
+            pix_ties=int(res.pix_ties))
     finally:
         lib.oracle_free(C.byref(res))
     del keep

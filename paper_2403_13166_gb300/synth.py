@@ -507,6 +507,99 @@ def muon_event(g: Geometry, pts, etas, phis, qs, vertex=(0.0, 0.0, 0.0), sigma=0
 
 
 # --------------------------------------------------------------------------------------
+# pixel seeds (Table 1 step 0: track segments from the inner tracker)
+# --------------------------------------------------------------------------------------
+#: barrel pixel layers (cylinders) of the synthetic inner tracker
+PIXEL_R = (3.0, 6.8, 10.9, 16.0)
+PIXEL_ZMAX = 100.0
+PIXEL_SIGMA_RPHI = 0.001
+PIXEL_SIGMA_Z = 0.002
+
+
+@dataclass
+class PixelSeeds:
+    hits: np.ndarray     # float32 [n, 4, 3]: (x, y, z) on the four pixel layers, inner first
+    pid: np.ndarray      # int32 [n]: particle index, -1 for a fake seed
+
+    @property
+    def n(self) -> int:
+        return int(self.hits.shape[0])
+
+
+def _cylinder_crossing(C, R, q, phi0, rho):
+    """First crossing (smallest turning angle) of each transverse circle with the cylinder
+    of radius rho around the beamline: (x, y, psi, ok)."""
+    n = C.shape[0]
+    d = np.hypot(C[:, 0], C[:, 1])
+    ok = (np.abs(R - rho) <= d) & (d <= R + rho) & (d > 0)
+    dd = np.where(d > 0, d, 1.0)
+    a = (rho * rho - R * R + d * d) / (2.0 * dd)
+    h = np.sqrt(np.maximum(rho * rho - a * a, 0.0))
+    ux, uy = C[:, 0] / dd, C[:, 1] / dd
+    best_psi = np.full(n, np.inf)
+    best_x = np.zeros(n)
+    best_y = np.zeros(n)
+    for sgn in (-1.0, 1.0):
+        px = a * ux - sgn * h * uy
+        py = a * uy + sgn * h * ux
+        ph = np.arctan2(-(px - C[:, 0]) / (q * R), (py - C[:, 1]) / (q * R))
+        psi = _wrap2pi(q * (phi0 - ph))
+        better = psi < best_psi
+        best_psi = np.where(better, psi, best_psi)
+        best_x = np.where(better, px, best_x)
+        best_y = np.where(better, py, best_y)
+    return best_x, best_y, best_psi, ok & (best_psi <= np.pi)
+
+
+def pixel_seeds(ev: Event, fake_frac: float = 0.05, sigma_rphi: float = PIXEL_SIGMA_RPHI,
+                sigma_z: float = PIXEL_SIGMA_Z) -> PixelSeeds:
+    """Pixel seeds (pLS) of an event, standing in for the upstream iteration of the paper's
+    Section 1 that runs on the inner-tracker hits: every particle of the event whose helix
+    crosses all four pixel cylinders (PIXEL_R, |z| < PIXEL_ZMAX) before turning back gives
+    one seed of four hits, smeared by sigma_rphi along the cylinder and sigma_z in z. Fake
+    seeds (fake_frac of the real count) join the inner two hits of one seed to the outer
+    two of the seed nearest in azimuth at the third layer. Seeds come in random order. The
+    random stream is the event's own seed offset by 500000, so the hits are unchanged."""
+    P = ev.particles
+    rng = np.random.Generator(np.random.PCG64(int(ev.seed) + 500_000))
+    pt, eta, phi0, q = P["pt"], P["eta"], P["phi"], P["q"]
+    n = pt.shape[0]
+    R = pt / K_FIELD
+    C = np.stack([P["vx"] + q * R * np.sin(phi0), P["vy"] - q * R * np.cos(phi0)], axis=1)
+    sh = np.sinh(eta)
+    ok = np.ones(n, bool)
+    H = np.zeros((n, 4, 3))
+    for k, rho in enumerate(PIXEL_R):
+        x, y, psi, okk = _cylinder_crossing(C, R, q, phi0, rho)
+        z = P["vz"] + R * psi * sh
+        ok &= okk & (np.abs(z) < PIXEL_ZMAX)
+        H[:, k] = np.stack([x, y, z], axis=1)
+    sel = np.flatnonzero(ok)
+    H = H[sel]
+    r = np.hypot(H[..., 0], H[..., 1])
+    e1 = rng.normal(0.0, sigma_rphi, r.shape) if sigma_rphi > 0 else np.zeros(r.shape)
+    e2 = rng.normal(0.0, sigma_z, r.shape) if sigma_z > 0 else np.zeros(r.shape)
+    tx, ty = -H[..., 1] / r, H[..., 0] / r
+    H[..., 0] += tx * e1
+    H[..., 1] += ty * e1
+    H[..., 2] += e2
+    pid = sel.astype(np.int64)
+    nf = int(round(fake_frac * len(sel)))
+    if nf > 0 and len(sel) > 1:
+        ph3 = np.arctan2(H[:, 2, 1], H[:, 2, 0])
+        order = np.argsort(ph3, kind="stable")
+        pos = np.empty(len(sel), np.int64)
+        pos[order] = np.arange(len(sel))
+        a = rng.choice(len(sel), nf, replace=False)
+        b = order[(pos[a] + 1) % len(sel)]
+        F = np.concatenate([H[a, :2], H[b, 2:]], axis=1)
+        H = np.concatenate([H, F])
+        pid = np.concatenate([pid, np.full(nf, -1)])
+    perm = rng.permutation(H.shape[0])
+    return PixelSeeds(hits=H[perm].astype(np.float32), pid=pid[perm].astype(np.int32))
+
+
+# --------------------------------------------------------------------------------------
 # parameters passed to both implementations
 # --------------------------------------------------------------------------------------
 def default_cuts() -> dict:
@@ -530,6 +623,20 @@ def default_cuts() -> dict:
         k_field=np.float32(K_FIELD),
         wp=np.float32(0.5),
     )
+
+
+#: parameter order of the pixel-seed matching (lst_pixel_cuts)
+PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "cos_dphi", "dm_abs", "dm_rel")
+
+
+def default_pixel_cuts() -> dict:
+    """Matching of pixel seeds to T5s and T3s (float32 values): curvature consistency (the
+    relative and absolute tolerances, for the seed's own curvature and for the circle through
+    the seed's end hits and the object's first anchor), the rz interpolation tolerance at
+    the seed's outer hit, and the search window: azimuth between the seed's outer hit and
+    the object's first anchor (cosine) and r-z slope (absolute and relative)."""
+    return dict(kappa_rel=np.float32(0.2), kappa_abs=np.float32(0.0005), rz_tol=np.float32(0.05),
+                cos_dphi=np.float32(0.75), dm_abs=np.float32(0.05), dm_rel=np.float32(0.5))
 
 
 def open_cuts() -> dict:

@@ -1,9 +1,11 @@
-"""The threshold pins catch plausible mistakes in the oracle's cut code.
+"""The threshold pins catch plausible mistakes in the oracle's cut code, and the pixel-seed
+pins those in its pixel-seed steps.
 
 Each case edits one expression of a private copy of the oracle's C source (a dropped term,
-a removed branch, a loosened or mis-scaled tolerance, a wrong radius or sign), rebuilds it
-and runs `test_oracle_thresholds.py` against the copy: every edit must turn at least one of
-those tests red, and the unedited copy must stay green. The one edit that no test can
+a removed branch, a loosened or mis-scaled tolerance, a wrong radius, sign or order), rebuilds
+it and runs `test_oracle_thresholds.py` (cuts) or `test_oracle_pixel.py` (pixel seeds)
+against the copy: every edit must turn at least one of those tests red, and the unedited copy
+must stay green. The one edit that no test can
 catch, removing the barrel MD direction test, is left out on purpose: within the tracker
 (r <= 110 cm, 2.6 mm sensor gap) an upper hit on the beamline side of the lower hit always
 fails the MD bend or road test as well, so that branch changes no decision.
@@ -48,6 +50,23 @@ MUTANTS = {
     "T5 arc-length series dropped": ("float s = d * (1.0f + d * d * kbar * kbar / 24.0f);", "float s = d;"),
 }
 
+# edits of the pixel-seed steps, caught by test_oracle_pixel.py
+PIXEL_MUTANTS = {
+    "pixel azimuth window removed": ("if (!(H4[0] * P0[0] + H4[1] * P0[1] >= pc->cos_dphi * (r4 * P0[3]))) return 0;",
+                                     "if (0) return 0;"),
+    "pixel slope window removed": ("if (!(fabsf(mp - mo) <= pc->dm_abs + pc->dm_rel * fabsf(mo))) return 0;",
+                                   "if (0) return 0;"),
+    "pixel pT test removed": ("if (!pix_kappa_ok(kp, ko, pc)) return 0;", "if (0) return 0;"),
+    "pixel circle test removed": ("if (!pix_kappa_ok(kx, ko, pc)) return 0;", "if (0) return 0;"),
+    "pixel circle through H3": ("float kx = pix_curv3(H1, H4, P0);", "float kx = pix_curv3(H3, H4, P0);"),
+    "pixel rz tolerance x3": ("if (!(res <= pc->rz_tol)) return 0;", "if (!(res <= 3.0f * pc->rz_tol)) return 0;"),
+    "pixel greedy prefers the worse match": ("if (x->res != y->res) return x->res < y->res ? -1 : 1;",
+                                             "if (x->res != y->res) return x->res > y->res ? -1 : 1;"),
+    "pixel T3s of pT5s stay eligible": ("elig[u] = !(mdin[T3[u].md[0]] && mdin[T3[u].md[1]] && mdin[T3[u].md[2]]);",
+                                        "elig[u] = 1;"),
+    "pixel step 6 dropped": ("row[0] = t5p[t] >= 0 ? 5 : 6;", "if (t5p[t] < 0) { R.n--; continue; } row[0] = 5;"),
+}
+
 
 def _copy(dst):
     os.makedirs(dst)
@@ -55,11 +74,11 @@ def _copy(dst):
         shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d),
                         ignore=shutil.ignore_patterns("*.so", "_lib", "_tuned", "__pycache__", "weights", "csrc"))
     os.makedirs(os.path.join(dst, "tests"))
-    for f in ("conftest.py", "test_oracle_thresholds.py"):
+    for f in ("conftest.py", "test_oracle_thresholds.py", "test_oracle_pixel.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
 
 
-def _run(dst, edit):
+def _run(dst, edit, test_file):
     _copy(dst)
     if edit is not None:
         src = os.path.join(dst, "oracle", "lst_oracle.c")
@@ -68,15 +87,16 @@ def _run(dst, edit):
         assert text.count(a) == 1, a
         open(src, "w").write(text.replace(a, b))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_thresholds.py"], cwd=dst, capture_output=True, text=True,
-                       timeout=600)
+                        "tests/" + test_file], cwd=dst, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-400:]
 
 
-def test_every_mutant_is_caught(tmp_path):
-    jobs = {"unedited": None, **MUTANTS}
+@pytest.mark.parametrize("mutants,test_file", [(MUTANTS, "test_oracle_thresholds.py"),
+                                               (PIXEL_MUTANTS, "test_oracle_pixel.py")])
+def test_every_mutant_is_caught(tmp_path, mutants, test_file):
+    jobs = {"unedited": None, **mutants}
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        futs = {k: ex.submit(_run, str(tmp_path / f"m{i}"), v) for i, (k, v) in enumerate(jobs.items())}
+        futs = {k: ex.submit(_run, str(tmp_path / f"m{i}"), v, test_file) for i, (k, v) in enumerate(jobs.items())}
         res = {k: f.result() for k, f in futs.items()}
     rc, out = res.pop("unedited")
     assert rc == 0, out
