@@ -314,6 +314,26 @@ def run_gpu(args, rank, world, local_rank, pool):
                  "nodes_per_event": int(np.mean([s[0] for s in sizes])),
                  "edges_per_event": int(np.mean([s[1] for s in sizes]))}
 
+    # ---------------- pixel seeds (Table 1 steps 5-8): pT5 / T5 / pT3 / pLS track candidates
+    pixel = None
+    if not args.skip_plain:
+        pcuts = synth.default_pixel_cuts()
+        times, cnts = [], []
+        for i in range(min(5, B)):
+            # the seeds come from the event's particles (regenerated: the same seeded event)
+            full = synth.pileup_event(g, int(idx[i]), pileup=PILEUP, mean_per_vertex=PER_VERTEX, config=2)
+            seeds = torch.from_numpy(synth.pixel_seeds(full).hits).to(dev)
+            ev = ctx_p.run_event(*d_in[i], stream=stream)
+            sync_all()
+            t0 = time.perf_counter()
+            cnts.append(ev.match_pixel_seeds(seeds, pcuts))
+            times.append(time.perf_counter() - t0)
+            ev.release()
+        pixel = {"match_ms_per_event": round(1000 * float(np.median(times[1:] or times)), 4),
+                 "form": "one event per call, device seeds, synchronous (rounds of one-to-one matching)",
+                 "per_event_mean": {k: round(float(np.mean([c[k] for c in cnts])), 1)
+                                    for k in ("n_pt5", "n_t5", "n_pt3", "n_pls", "rounds_pt5", "rounds_pt3")}}
+
     # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
     h2d = int(sum(16 * n for n in n_hits))
@@ -393,6 +413,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         "plain": plain,
         "served": served,
         "ls_graph": graph,
+        "pixel_tc": pixel,
         "e2e": e2e,
         "roofline": roofline,
         "step_roofline": step,

@@ -326,6 +326,61 @@ lst_status lst_serve_free_result(lst_serve_result *r);
 lst_status lst_serve_stop(lst_server s);
 
 /* ---------------------------------------------------------------------------------
+ * Pixel seeds: Table 1 steps 0 and 5-8 (Section 1).
+ *
+ * Step 0 makes pixel seeds (pLSs) upstream from the inner tracker; each is four hits H1..H4
+ * (inner first). lst_match_pixel_seeds matches them to the outer-tracker objects of a
+ * finished event and forms the four mutually exclusive track-candidate types, longest
+ * first:
+ *   5 pT5: a track-candidate T5 (LST_TC) matched to a seed;
+ *   6 T5:  a track-candidate T5 matched to no seed;
+ *   7 pT3: a seed not in a pT5 matched to a T3 that is not in a pT5 (a T3 is in a pT5 when
+ *          each of its three MDs is an MD of a pT5's T5);
+ *   8 pLS: a seed in neither.
+ * A seed matches an object (the T5 by its first T3, or the T3) whose first anchors are P0,
+ * P1 and whose curvature is ko when (project specification, FP32):
+ *   azimuth window  H4 . P0 >= cos_dphi |H4|_T |P0|_T (transverse);
+ *   slope window    |m_p - m_o| <= dm_abs + dm_rel |m_o|, m_p = (z4 - z1) / (r4 - r1),
+ *                   m_o = (z(P1) - z(P0)) / (r(P1) - r(P0));
+ *   pT              |kp - ko| <= kappa_rel (|kp| + |ko|) / 2 + kappa_abs, kp the signed
+ *                   three-point curvature through H1, H3, H4;
+ *   circle          the same for kx, the curvature through H1, H4, P0;
+ *   rz              |z4 - zp| <= rz_tol, zp = z1 + (z(P0) - z1) s14 / (s14 + s40) with arc
+ *                   lengths s = d (1 + d^2 kbar^2 / 24) of the chords H1H4 and H4P0, kbar =
+ *                   (kx + ko) / 2.
+ * Matching is one-to-one: the matching pairs in ascending order of (the rz residual |z4 -
+ * zp|, |kx - ko|, seed index, the object's hit tuple), each taken when both are still free
+ * (first for the T5s, then for the T3s with the seeds left). */
+typedef struct lst_pixel_cuts {
+    float kappa_rel, kappa_abs, rz_tol, cos_dphi, dm_abs, dm_rel;
+} lst_pixel_cuts;
+
+typedef struct lst_pixel_counts {
+    int64_t n_rows;                 /* track candidates of steps 5-8 */
+    int64_t n_pt5, n_t5, n_pt3, n_pls;
+    int32_t rounds_pt5, rounds_pt3; /* matching rounds taken (the GPU's one-to-one passes) */
+} lst_pixel_counts;
+
+/*   ev        a finished event (lst_run_event or lst_run_batch) with status LST_OK;
+ *   seeds     float [n_seeds][4][3]: (x, y, z) of H1..H4 per seed, host or device, read
+ *             before the call returns;
+ *   pc        matching parameters (copied);
+ *   counts    host, may be NULL.
+ * Synchronous: returns when the track candidates are ready (lst_get_pixel_candidates); a
+ * later call on the same event replaces them. LST_ERR_CAPACITY if more than 8 objects tie
+ * at one seed in both ranking measures (the order would then rest on too long a list). */
+lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
+                                 lst_pixel_counts *counts);
+
+/* The track candidates of the event's last lst_match_pixel_seeds call, one row of three
+ * int32 each, in no particular order: (type 5..8, seed index or -1 for type 6, object
+ * index or -1 for type 8), the object index being the row of the T5 in
+ * lst_get_candidates(LST_T5) (types 5, 6) or of the T3 in lst_get_candidates(LST_T3)
+ * (type 7). rows host or device; n_out always set; LST_ERR_CAPACITY if capacity < n_out,
+ * LST_ERR_NOT_READY if the event was not matched. */
+lst_status lst_get_pixel_candidates(lst_event ev, int32_t *rows, int64_t capacity, int64_t *n_out);
+
+/* ---------------------------------------------------------------------------------
  * Mini-doublet finder that allocates nothing (the paper has no counterpart; it is a
  * deployment aid of this library).
  *

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblst.so")
-SOURCES = ["lst_kernels.cu", "lst_score.cu", "lst_mma.cu", "lst_tc.cu", "lst_api.cu", "lst_noalloc.cu"]
+SOURCES = ["lst_kernels.cu", "lst_score.cu", "lst_mma.cu", "lst_tc.cu", "lst_pixel.cu", "lst_api.cu",
+           "lst_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # IEEE FP32 everywhere: no contraction of a*b+c (explicit fmaf only), correctly rounded

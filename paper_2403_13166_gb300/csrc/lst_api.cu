@@ -47,6 +47,10 @@ cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, Dev
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
                                        const float *, int64_t, float *, int *, long long, bool split, int skip_mma);
 int score_bf16_blocks_per_sm(bool split);
+cudaError_t pix_launch_bin(PixDesc, int, cudaStream_t);
+cudaError_t pix_launch_round(const EvDesc *, PixDesc, int, lst_pixel_cuts, int, int, cudaStream_t);
+cudaError_t pix_launch_mark(const EvDesc *, PixDesc, int, cudaStream_t);
+cudaError_t pix_launch_rows(const EvDesc *, PixDesc, int, cudaStream_t);
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
 }  // namespace lstk
 
@@ -103,6 +107,10 @@ struct Slot {
   int md_cap = 0, ls_cap = 0, t3_cap = 0, t5_cap = 0;
   void *in_mem = nullptr;          // staging for host inputs
   int64_t in_cap = 0;
+  void *pix_mem = nullptr;         // pixel-seed matching (lst_match_pixel_seeds)
+  size_t pix_bytes = 0;
+  int64_t pix_rows = -1;           // its track candidates, -1 before a matching
+  const int32_t *pix_rows_ptr = nullptr;  // where they are (in pix_mem)
   bool busy = false;
   int lane = -1;                   // lane whose last batch holds this slot's counters
   int lane_pos = -1;
@@ -1071,6 +1079,111 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
   return LST_OK;
 }
 
+// ------------------------------------------------------------------ pixel seeds (steps 5-8)
+lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
+                                 lst_pixel_counts *counts) {
+  if (!ev || !pc) return fail(LST_ERR_ARG, "null event or parameters");
+  if (n_seeds < 0 || n_seeds > (int64_t)1 << 26) return fail(LST_ERR_ARG, "n_seeds outside 0..2^26");
+  if (n_seeds > 0 && !seeds) return fail(LST_ERR_ARG, "null seeds");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  lst_status s = wait_event(ev);
+  if (s != LST_OK) return s;
+  if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
+  Slot &S = c->slots[ev->slot];
+  S.pix_rows = -1;
+  const int np = (int)n_seeds, n5 = S.cnt[C_T5], n3 = S.cnt[C_T3], nmd = S.cnt[C_MD];
+  const size_t no = (size_t)n5 + n3, npl = std::max(np, 1);
+  size_t off = 0;
+  auto take = [&](size_t b) { size_t o = off; off = align_up(off + std::max<size_t>(b, 1), 256); return o; };
+  const size_t o_hits = take(48 * npl), o_cell = take(4 * npl), o_rank = take(4 * npl);
+  const size_t o_ccnt = take(4 * (size_t)PIX_NCELL), o_coff = take(4 * ((size_t)PIX_NCELL + 1));
+  const size_t o_sa = take(16 * npl), o_sb = take(16 * npl), o_sm = take(4 * npl), o_sidx = take(4 * npl);
+  const size_t o_pkey = take(8 * npl), o_pcnt = take(4 * npl), o_plist = take(4 * (size_t)PIX_TIES * npl);
+  const size_t o_pobj = take(4 * npl), o_pmatch = take(4 * npl);
+  const size_t o_okey = take(8 * no), o_op = take(4 * no), o_omatch = take(4 * no), o_md = take((size_t)nmd);
+  const size_t o_rows = take(12 * (no + npl)), o_ctr = take(32);
+  if (S.pix_bytes < off) {
+    CU(cudaDeviceSynchronize());
+    cudaFree(S.pix_mem);
+    S.pix_mem = nullptr;
+    S.pix_bytes = 0;
+    CU(cudaMalloc(&S.pix_mem, off));
+    S.pix_bytes = off;
+  }
+  char *b = (char *)S.pix_mem;
+  PixDesc P;
+  P.n_pls = np; P.n_t5 = n5; P.n_t3 = n3; P.n_md = nmd;
+  P.hits = (const float *)(b + o_hits);
+  P.cell = (int *)(b + o_cell); P.rank = (int *)(b + o_rank);
+  P.cell_cnt = (int *)(b + o_ccnt); P.cell_off = (int *)(b + o_coff);
+  P.sa = (float4 *)(b + o_sa); P.sb = (float4 *)(b + o_sb); P.sm = (float *)(b + o_sm); P.sidx = (int *)(b + o_sidx);
+  P.pkey = (unsigned long long *)(b + o_pkey); P.pcnt = (int *)(b + o_pcnt); P.plist = (int *)(b + o_plist);
+  P.pobj = (int *)(b + o_pobj); P.pmatch = (int *)(b + o_pmatch);
+  P.okey = (unsigned long long *)(b + o_okey); P.op = (int *)(b + o_op); P.omatch = (int *)(b + o_omatch);
+  P.mdflag = (uint8_t *)(b + o_md); P.rows = (int *)(b + o_rows); P.ctr = (int *)(b + o_ctr);
+  cudaStream_t st = c->aux;
+  CU(cudaMemsetAsync(P.cell_cnt, 0, 4 * (size_t)PIX_NCELL, st));
+  CU(cudaMemsetAsync(P.omatch, 0xff, 4 * std::max<size_t>(no, 1), st));
+  CU(cudaMemsetAsync(P.mdflag, 0, std::max(nmd, 1), st));
+  CU(cudaMemsetAsync(P.ctr, 0, 32, st));
+  if (np) CU(cudaMemcpyAsync(b + o_hits, seeds, 48 * (size_t)np, cudaMemcpyDefault, st));
+  EvDesc *dd;
+  s = slot_desc_device(c, ev->slot, &dd);
+  if (s != LST_OK) return s;
+  const int grid = 2 * c->n_sm;
+  CU(pix_launch_bin(P, grid, st));
+  // azimuth bins on either side of the object's bin: the window plus one bin for rounding
+  const double cd = std::min(1.0, std::max(-1.0, (double)pc->cos_dphi));
+  const int dphi_bins = (int)std::ceil(std::acos(cd) / (2.0 * M_PI / PIX_NPHI)) + 1;
+  int rounds[2] = {0, 0};
+  int h_ctr[8];
+  for (int k = 0; k < 2; k++) {
+    const int stage = k == 0 ? 5 : 7;
+    if (stage == 7) CU(pix_launch_mark(dd, P, grid, st));
+    if (np == 0 || (stage == 5 ? n5 : n3) == 0) continue;
+    for (;;) {
+      CU(cudaMemsetAsync(P.ctr, 0, 4, st));
+      CU(pix_launch_round(dd, P, stage, *pc, dphi_bins, grid, st));
+      CU(cudaMemcpyAsync(h_ctr, P.ctr, 32, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      rounds[k]++;
+      if (h_ctr[2]) return fail(LST_ERR_CAPACITY, "more than 8 objects tie at one seed in both ranking measures");
+      if (h_ctr[0] == 0) break;
+    }
+  }
+  CU(pix_launch_rows(dd, P, grid, st));
+  CU(cudaMemcpyAsync(h_ctr, P.ctr, 32, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  S.pix_rows = h_ctr[1];
+  S.pix_rows_ptr = P.rows;
+  if (counts) {
+    counts->n_rows = h_ctr[1];
+    counts->n_pt5 = h_ctr[4];
+    counts->n_t5 = h_ctr[5];
+    counts->n_pt3 = h_ctr[6];
+    counts->n_pls = h_ctr[7];
+    counts->rounds_pt5 = rounds[0];
+    counts->rounds_pt3 = rounds[1];
+  }
+  return LST_OK;
+}
+
+lst_status lst_get_pixel_candidates(lst_event ev, int32_t *rows, int64_t capacity, int64_t *n_out) {
+  if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
+  lst_ctx c = ev->ctx;
+  DeviceGuard gd(c->device);
+  const Slot &S = c->slots[ev->slot];
+  *n_out = S.pix_rows < 0 ? 0 : S.pix_rows;
+  if (S.pix_rows < 0) return fail(LST_ERR_NOT_READY, "no pixel-seed matching for this event");
+  if (capacity < S.pix_rows) return fail(LST_ERR_CAPACITY, "output capacity below the candidate count");
+  if (S.pix_rows == 0) return LST_OK;
+  if (!rows) return fail(LST_ERR_ARG, "rows is NULL");
+  CU(cudaMemcpyAsync(rows, S.pix_rows_ptr, 12 * (size_t)S.pix_rows, cudaMemcpyDefault, c->aux));
+  CU(cudaStreamSynchronize(c->aux));
+  return LST_OK;
+}
+
 lst_status lst_event_release(lst_event ev) {
   if (!ev) return fail(LST_ERR_ARG, "null event");
   lst_ctx c = ev->ctx;
@@ -1078,6 +1191,7 @@ lst_status lst_event_release(lst_event ev) {
   Slot &S = c->slots[ev->slot];
   if (!S.have_cnt && S.lane >= 0) lane_harvest(c, c->lanes[S.lane]);
   S.busy = false;
+  S.pix_rows = -1;
   delete ev;
   return LST_OK;
 }
@@ -1095,7 +1209,7 @@ lst_status lst_destroy(lst_ctx c) {
       for (auto &e : L.tev) if (e) cudaEventDestroy(e);
       if (L.cap_stream) cudaStreamDestroy(L.cap_stream);
     }
-    for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); }
+    for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); cudaFree(s.pix_mem); }
     cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt);
     cudaFree(c->d_ls_units);
     cudaFree(c->d_w); cudaFree(c->scratch); cudaFree(c->d_wpack); cudaFree(c->d_err);

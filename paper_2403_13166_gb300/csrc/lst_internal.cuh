@@ -80,6 +80,29 @@ struct EvDesc {
   int32_t *cnt;                // [C_NCOUNTERS]
 };
 
+// Device buffers of the pixel-seed matching of one event (lst_pixel.cu).
+struct PixDesc {
+  int n_pls, n_t5, n_t3, n_md;
+  const float *hits;              // [n_pls][12] seeds, input order
+  int *cell, *rank;               // [n_pls] bin and rank within it, input order
+  int *cell_cnt, *cell_off;       // [PIX_NCELL], [PIX_NCELL + 1]
+  float4 *sa, *sb;                // [n_pls] in bin order: (x1, y1, z1, kp), (x4, y4, z4, r4)
+  float *sm;                      // [n_pls] in bin order: r-z slope m_p
+  int *sidx;                      // [n_pls] in bin order: seed index
+  unsigned long long *pkey;       // [n_pls] the round's best (residual, difference) at the seed
+  int *pcnt, *plist;              // [n_pls], [n_pls][PIX_TIES] objects of that rank
+  int *pobj;                      // [n_pls] the round's chosen object
+  int *pmatch;                    // [n_pls] matched object (T5 index, or n_t5 + T3 index), -1
+  unsigned long long *okey;       // [n_t5 + n_t3] the round's best rank at the object
+  int *op;                        // [n_t5 + n_t3] and its seed
+  int *omatch;                    // [n_t5 + n_t3] matched seed, -1
+  uint8_t *mdflag;                // [n_md] MD of a pT5's T5
+  int *rows;                      // [n_t5 + n_t3 + n_pls][3] track candidates
+  int *ctr;                       // [8]: taken this round, rows, tie overflow, -, rows of type 5..8
+};
+constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
+constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)
+
 // ------------------------------------------------------------------ FP32 cut arithmetic
 // Step 1 (Section 1, Table 1): two hits of one pT-module, pT above 0.8 GeV and inside the
 // luminous-region road. L = lower-sensor hit, U = upper-sensor hit, both (x, y, z, r).

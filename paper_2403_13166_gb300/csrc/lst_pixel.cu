@@ -1,0 +1,329 @@
+// lst_pixel.cu -- pixel seeds on the GPU: Table 1 steps 0 and 5-8 (pT5, T5, pT3 and pLS
+// track candidates) for one finished event.
+//
+// A pixel seed (pLS) is four inner-tracker hits H1..H4 made upstream (step 0). It is matched
+// to an outer object -- a track-candidate T5 by its first T3, then a T3 -- whose first anchors
+// are P0, P1 and whose curvature is ko, when both lie on one helix (Section 1): the azimuth
+// and r-z slope windows, the seed's curvature against ko, the circle through H1, H4, P0
+// against ko, and H4's z against its interpolation between H1 and P0 along the arc (FP32,
+// the expression trees of the oracle). Matching is one-to-one with preference to the better
+// (rz residual, curvature difference): the edges in ascending (residual, difference, seed
+// index, object hit tuple) order, each taken when both ends are free. On the GPU that
+// greedy result is reached in rounds: every free object finds its best free seed, every free
+// seed its best free object, and the pairs that chose each other are taken (such an edge is
+// the minimum at both its ends, so the greedy pass takes it too); rounds repeat until none
+// is taken.
+//
+// Seeds are binned by the azimuth of H4 and their r-z slope; an object scans the bins of its
+// windows (one contiguous run of azimuth bins per slope row), so a pair that passes the
+// window test is always met.
+#include "lst_internal.cuh"
+
+namespace lstk {
+
+constexpr float PIX_MMAX = 6.0f;                // slope bins cover [-6, 6]; the end bins take the rest
+constexpr float PIX_PI = 3.14159265358979f;
+
+__device__ __forceinline__ float pix_curv3(float ax0, float ay0, float bx0, float by0, float cx0, float cy0) {
+  const float d01x = bx0 - ax0, d01y = by0 - ay0;
+  const float d12x = cx0 - bx0, d12y = cy0 - by0;
+  const float d02x = cx0 - ax0, d02y = cy0 - ay0;
+  const float a = sqrtf(d01x * d01x + d01y * d01y);
+  const float b = sqrtf(d12x * d12x + d12y * d12y);
+  const float c = sqrtf(d02x * d02x + d02y * d02y);
+  const float cr = d01x * d02y - d01y * d02x;
+  return 2.0f * cr / (a * b * c);
+}
+
+__device__ __forceinline__ bool pix_kappa_ok(float k1, float k2, const lst_pixel_cuts &pc) {
+  return fabsf(k1 - k2) <= pc.kappa_rel * 0.5f * (fabsf(k1) + fabsf(k2)) + pc.kappa_abs;
+}
+
+// The seed / object match: A = (x1, y1, z1, kp), B = (x4, y4, z4, r4), mp the seed's slope;
+// P0, P1 the object's first two anchors, mo = (P1.z - P0.z) / (P1.w - P0.w), ko its curvature.
+__device__ __forceinline__ bool pix_match(const float4 A, const float4 B, float mp, const float4 P0, float mo,
+                                          float ko, const lst_pixel_cuts &pc, float &res, float &dk) {
+  if (!(B.x * P0.x + B.y * P0.y >= pc.cos_dphi * (B.w * P0.w))) return false;      // azimuth
+  if (!(fabsf(mp - mo) <= pc.dm_abs + pc.dm_rel * fabsf(mo))) return false;          // slope
+  if (!pix_kappa_ok(A.w, ko, pc)) return false;                                     // pT
+  const float kx = pix_curv3(A.x, A.y, B.x, B.y, P0.x, P0.y);
+  if (!pix_kappa_ok(kx, ko, pc)) return false;                                      // circle
+  const float kbar = 0.5f * (kx + ko);
+  const float ax = B.x - A.x, ay = B.y - A.y, bx = P0.x - B.x, by = P0.y - B.y;
+  const float a = sqrtf(ax * ax + ay * ay), b = sqrtf(bx * bx + by * by);
+  const float s14 = a * (1.0f + a * a * kbar * kbar / 24.0f);
+  const float s40 = b * (1.0f + b * b * kbar * kbar / 24.0f);
+  const float zp = A.z + (P0.z - A.z) * s14 / (s14 + s40);
+  res = fabsf(B.z - zp);
+  if (!(res <= pc.rz_tol)) return false;                                            // rz
+  dk = fabsf(kx - ko);
+  return true;
+}
+
+__device__ __forceinline__ int pix_mbin(float m) {
+  const float v = fminf(fmaxf((m + PIX_MMAX) * (PIX_NM / (2.0f * PIX_MMAX)), 0.0f), (float)(PIX_NM - 1));
+  return (int)v;                     // NaN -> 0
+}
+__device__ __forceinline__ int pix_phibin(float y, float x) {
+  int b = (int)floorf((atan2f(y, x) + PIX_PI) * (PIX_NPHI / (2.0f * PIX_PI)));
+  return ((b % PIX_NPHI) + PIX_NPHI) % PIX_NPHI;
+}
+
+// the seed's derived values, the oracle's expressions: r1, r4, slope, curvature through H1, H3, H4
+__device__ __forceinline__ void pix_seed(const float *H, float4 &A, float4 &B, float &mp) {
+  const float r1 = sqrtf(H[0] * H[0] + H[1] * H[1]);
+  const float r4 = sqrtf(H[9] * H[9] + H[10] * H[10]);
+  mp = (H[11] - H[2]) / (r4 - r1);
+  A = make_float4(H[0], H[1], H[2], pix_curv3(H[0], H[1], H[6], H[7], H[9], H[10]));
+  B = make_float4(H[9], H[10], H[11], r4);
+}
+
+__global__ void k_pix_bin(PixDesc P) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    float4 A, B;
+    float mp;
+    pix_seed(P.hits + 12 * (size_t)p, A, B, mp);
+    const int c = pix_mbin(mp) * PIX_NPHI + pix_phibin(B.y, B.x);
+    P.cell[p] = c;
+    P.rank[p] = atomicAdd(P.cell_cnt + c, 1);
+    P.pkey[p] = ~0ull;
+    P.pcnt[p] = 0;
+    P.pobj[p] = -1;
+    P.pmatch[p] = -1;
+  }
+}
+
+__global__ void k_pix_scan(PixDesc P) {
+  block_exclusive_scan(P.cell_cnt, P.cell_off, PIX_NCELL);
+  if (threadIdx.x == 0) P.cell_off[PIX_NCELL] = P.n_pls;
+}
+
+__global__ void k_pix_scatter(PixDesc P) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    float4 A, B;
+    float mp;
+    pix_seed(P.hits + 12 * (size_t)p, A, B, mp);
+    const int q = P.cell_off[P.cell[p]] + P.rank[p];
+    P.sa[q] = A;
+    P.sb[q] = B;
+    P.sm[q] = mp;
+    P.sidx[q] = p;
+  }
+}
+
+// Object o of the stage: T5 (stage 5; only track-candidate T5s) or T3 (stage 7; not made of
+// MDs of pT5 quintuplets). Fills its first two anchors and curvature; false if it takes no part.
+__device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, int stage, int o, float4 &P0,
+                                           float4 &P1, float &ko) {
+  int m0, m1;
+  if (stage == 5) {
+    if (!ev.t5_tc[o]) return false;
+    const int4 a = ev.t5_a[o];
+    m0 = a.x;
+    m1 = a.y;
+    ko = ev.t3_kappa[ev.t5_b[o].y];
+  } else {
+    const int4 t = ev.t3_md[o];
+    if (P.mdflag[t.x] && P.mdflag[t.y] && P.mdflag[t.z]) return false;
+    m0 = t.x;
+    m1 = t.y;
+    ko = ev.t3_kappa[o];
+  }
+  P0 = ev.md_anchor[m0];
+  P1 = ev.md_anchor[m1];
+  return true;
+}
+
+// Visit every free seed in the object's windows that matches it: f(p, res, dk).
+template <typename F>
+__device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P0, const float4 P1, float ko,
+                                                const lst_pixel_cuts &pc, int dphi_bins, F f) {
+  const float mo = (P1.z - P0.z) / (P1.w - P0.w);
+  const float w = pc.dm_abs + pc.dm_rel * fabsf(mo);
+  const int m_lo = max(0, pix_mbin(mo - w) - 1), m_hi = min(PIX_NM - 1, pix_mbin(mo + w) + 1);
+  const bool all_m = !(w <= 1e30f);              // an infinite or NaN window: every row
+  const int r0 = all_m ? 0 : m_lo, r1 = all_m ? PIX_NM - 1 : m_hi;
+  const int c0 = pix_phibin(P0.y, P0.x);
+  const int span = min(2 * dphi_bins + 1, PIX_NPHI);
+  const int first = ((c0 - dphi_bins) % PIX_NPHI + PIX_NPHI) % PIX_NPHI;
+  for (int row = r0; row <= r1; row++) {
+    // the azimuth bins [first, first + span) modulo PIX_NPHI: one or two contiguous runs
+    const int runs = first + span > PIX_NPHI ? 2 : 1;
+    for (int k = 0; k < runs; k++) {
+      const int b0 = k == 0 ? first : 0;
+      const int b1 = k == 0 ? min(first + span, PIX_NPHI) : first + span - PIX_NPHI;
+      const int q0 = P.cell_off[row * PIX_NPHI + b0], q1 = P.cell_off[row * PIX_NPHI + b1];
+      for (int q = q0; q < q1; q++) {
+        const int p = P.sidx[q];
+        if (P.pmatch[p] >= 0) continue;
+        float res, dk;
+        if (pix_match(P.sa[q], P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk)) f(p, res, dk);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
+  return ((unsigned long long)__float_as_uint(res) << 32) | __float_as_uint(dk);
+}
+
+// Round, part 1: each free object's best free seed (rank, then seed index) and, at each seed,
+// the best rank over its free objects.
+__global__ void k_pix_propose(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc,
+                              int dphi_bins) {
+  const EvDesc &ev = *evp;
+  const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    unsigned long long best = ~0ull;
+    int bp = -1;
+    float4 P0, P1;
+    float ko;
+    if (P.omatch[base + o] < 0 && pix_object(ev, P, stage, o, P0, P1, ko))
+      pix_scan_object(P, P0, P1, ko, pc, dphi_bins, [&](int p, float res, float dk) {
+        const unsigned long long k = pix_key(res, dk);
+        atomicMin(P.pkey + p, k);
+        if (k < best || (k == best && p < bp)) { best = k; bp = p; }
+      });
+    P.okey[base + o] = best;
+    P.op[base + o] = bp;
+  }
+}
+
+// Round, part 2: the objects that reach a seed's best rank list themselves at that seed.
+__global__ void k_pix_ties(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc, int dphi_bins) {
+  const EvDesc &ev = *evp;
+  const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    if (P.okey[base + o] == ~0ull) continue;       // no free seed matches it
+    float4 P0, P1;
+    float ko;
+    if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
+    pix_scan_object(P, P0, P1, ko, pc, dphi_bins, [&](int p, float res, float dk) {
+      if (pix_key(res, dk) != P.pkey[p]) return;
+      const int s = atomicAdd(P.pcnt + p, 1);
+      if (s < PIX_TIES)
+        P.plist[PIX_TIES * (size_t)p + s] = o;
+      else
+        atomicOr(P.ctr + 2, 1);
+    });
+  }
+}
+
+// lexicographic comparison of two objects' hit tuples (original hit indices of their MDs)
+__device__ __forceinline__ bool pix_tuple_less(const EvDesc &ev, int stage, int a, int b) {
+  int ma[5], mb[5];
+  int nm;
+  if (stage == 5) {
+    const int4 a1 = ev.t5_a[a], b1 = ev.t5_a[b];
+    ma[0] = a1.x; ma[1] = a1.y; ma[2] = a1.z; ma[3] = a1.w; ma[4] = ev.t5_b[a].x;
+    mb[0] = b1.x; mb[1] = b1.y; mb[2] = b1.z; mb[3] = b1.w; mb[4] = ev.t5_b[b].x;
+    nm = 5;
+  } else {
+    const int4 a1 = ev.t3_md[a], b1 = ev.t3_md[b];
+    ma[0] = a1.x; ma[1] = a1.y; ma[2] = a1.z;
+    mb[0] = b1.x; mb[1] = b1.y; mb[2] = b1.z;
+    nm = 3;
+  }
+  for (int i = 0; i < nm; i++) {
+    const int2 ha = ev.md_hits[ma[i]], hb = ev.md_hits[mb[i]];
+    if (ha.x != hb.x) return ha.x < hb.x;
+    if (ha.y != hb.y) return ha.y < hb.y;
+  }
+  return false;
+}
+
+// Round, part 3: each seed's choice among the objects of its best rank: the smallest hit tuple.
+__global__ void k_pix_pick(const EvDesc *__restrict__ evp, PixDesc P, int stage) {
+  const EvDesc &ev = *evp;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    const int n = min(P.pcnt[p], PIX_TIES);
+    if (n == 0) continue;
+    int best = P.plist[PIX_TIES * (size_t)p];
+    for (int i = 1; i < n; i++) {
+      const int o = P.plist[PIX_TIES * (size_t)p + i];
+      if (pix_tuple_less(ev, stage, o, best)) best = o;
+    }
+    P.pobj[p] = best;
+  }
+}
+
+// Round, part 4: take the pairs that chose each other; clear the round's seed state.
+__global__ void k_pix_accept(PixDesc P, int stage) {
+  const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    const int p = P.op[base + o];
+    if (p >= 0 && P.pobj[p] == o) {
+      P.omatch[base + o] = p;
+      P.pmatch[p] = base + o;
+      atomicAdd(P.ctr, 1);
+    }
+  }
+}
+__global__ void k_pix_clear(PixDesc P) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    P.pkey[p] = ~0ull;
+    P.pcnt[p] = 0;
+    P.pobj[p] = -1;
+  }
+}
+
+// MDs of the pT5 quintuplets
+__global__ void k_pix_mark(const EvDesc *__restrict__ evp, PixDesc P) {
+  const EvDesc &ev = *evp;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.n_t5; o += gridDim.x * blockDim.x) {
+    if (P.omatch[o] < 0) continue;
+    const int4 a = ev.t5_a[o];
+    P.mdflag[a.x] = 1; P.mdflag[a.y] = 1; P.mdflag[a.z] = 1; P.mdflag[a.w] = 1;
+    P.mdflag[ev.t5_b[o].x] = 1;
+  }
+}
+
+// Track candidates as rows (type, seed, object): 5 pT5, 6 T5 without a seed, 7 pT3, 8 pLS.
+__global__ void k_pix_rows(const EvDesc *__restrict__ evp, PixDesc P) {
+  const EvDesc &ev = *evp;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  auto emit = [&](int t, int p, int o) {
+    const int r = atomicAdd(P.ctr + 1, 1);
+    atomicAdd(P.ctr + t - 1, 1);
+    P.rows[3 * (size_t)r] = t;
+    P.rows[3 * (size_t)r + 1] = p;
+    P.rows[3 * (size_t)r + 2] = o;
+  };
+  for (int o = tid; o < P.n_t5; o += st)
+    if (ev.t5_tc[o]) emit(P.omatch[o] >= 0 ? 5 : 6, P.omatch[o], o);
+  for (int u = tid; u < P.n_t3; u += st)
+    if (P.omatch[P.n_t5 + u] >= 0) emit(7, P.omatch[P.n_t5 + u], u);
+  for (int p = tid; p < P.n_pls; p += st)
+    if (P.pmatch[p] < 0) emit(8, p, -1);
+}
+
+// Host-side launch helpers (all on `st`); rounds are driven by the caller.
+cudaError_t pix_launch_bin(PixDesc P, int grid, cudaStream_t st) {
+  if (P.n_pls > 0) {
+    k_pix_bin<<<grid, 256, 0, st>>>(P);
+    k_pix_scan<<<1, 1024, 0, st>>>(P);
+    k_pix_scatter<<<grid, 256, 0, st>>>(P);
+  } else {
+    k_pix_scan<<<1, 1024, 0, st>>>(P);
+  }
+  return cudaGetLastError();
+}
+cudaError_t pix_launch_round(const EvDesc *dd, PixDesc P, int stage, lst_pixel_cuts pc, int dphi_bins, int grid,
+                             cudaStream_t st) {
+  k_pix_propose<<<grid, 128, 0, st>>>(dd, P, stage, pc, dphi_bins);
+  k_pix_ties<<<grid, 128, 0, st>>>(dd, P, stage, pc, dphi_bins);
+  k_pix_pick<<<grid, 256, 0, st>>>(dd, P, stage);
+  k_pix_accept<<<grid, 256, 0, st>>>(P, stage);
+  k_pix_clear<<<grid, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+cudaError_t pix_launch_mark(const EvDesc *dd, PixDesc P, int grid, cudaStream_t st) {
+  k_pix_mark<<<grid, 256, 0, st>>>(dd, P);
+  return cudaGetLastError();
+}
+cudaError_t pix_launch_rows(const EvDesc *dd, PixDesc P, int grid, cudaStream_t st) {
+  k_pix_rows<<<grid, 256, 0, st>>>(dd, P);
+  return cudaGetLastError();
+}
+
+}  // namespace lstk

@@ -58,6 +58,19 @@ class lst_launch(C.Structure):
                                           "t5_threads", "sc_threads", "t3_mds")]
 
 
+class lst_pixel_cuts(C.Structure):
+    _fields_ = [(f, C.c_float) for f in synth.PIXEL_CUT_FIELDS]
+
+
+class lst_pixel_counts(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_pt5", C.c_int64), ("n_t5", C.c_int64), ("n_pt3", C.c_int64),
+                ("n_pls", C.c_int64), ("rounds_pt5", C.c_int32), ("rounds_pt3", C.c_int32)]
+
+
+def pixel_cuts_struct(pc: dict) -> lst_pixel_cuts:
+    return lst_pixel_cuts(*[float(np.float32(pc[f])) for f in synth.PIXEL_CUT_FIELDS])
+
+
 class lst_counts(C.Structure):
     _fields_ = [("n_hits", C.c_int64), ("n_md", C.c_int64), ("n_ls", C.c_int64), ("n_t3", C.c_int64),
                 ("n_t5", C.c_int64), ("n_selected", C.c_int64), ("pairs", C.c_int64 * 4),
@@ -93,6 +106,8 @@ _SIGS = {
     "lst_device_errors": [C.c_void_p],
     "lst_test_skip_mma": [C.c_void_p, C.c_int32],
     "lst_test_fail_alloc": [C.c_void_p, C.c_int32],
+    "lst_match_pixel_seeds": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "lst_get_pixel_candidates": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
     "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_stage_times": [C.c_void_p, C.c_void_p, C.c_void_p],
@@ -253,6 +268,34 @@ class Event:
                                           C.byref(n)), "lst_get_candidates")
         if kind in (LST_T5, LST_TC):
             return out, score, selected
+        return out
+
+    def match_pixel_seeds(self, seeds, pcuts: dict) -> dict:
+        """Table 1 steps 5-8 for this event (lst_match_pixel_seeds): seeds float32 [n][4][3]
+        (numpy or a CUDA tensor). Returns the counts per track-candidate type."""
+        if hasattr(seeds, "data_ptr"):
+            n = int(seeds.shape[0])
+            assert seeds.dtype.itemsize == 4 and seeds.is_contiguous() and seeds.numel() == 12 * n
+            ptr = _ptr(seeds)
+        else:
+            seeds = np.ascontiguousarray(seeds, np.float32).reshape(-1, 12)
+            n = seeds.shape[0]
+            ptr = _ptr(seeds)
+        cnt = lst_pixel_counts()
+        pc = pixel_cuts_struct(pcuts)
+        _check(load_library().lst_match_pixel_seeds(self.h, ptr, n, C.byref(pc), C.byref(cnt)),
+               "lst_match_pixel_seeds")
+        return {f: getattr(cnt, f) for f, _ in lst_pixel_counts._fields_}
+
+    def pixel_candidates(self) -> np.ndarray:
+        """Rows (type 5..8, seed index or -1, T5 / T3 row or -1) of the last matching."""
+        lib = load_library()
+        n = C.c_int64(0)
+        _check(lib.lst_get_pixel_candidates(self.h, None, 0, C.byref(n)), "lst_get_pixel_candidates",
+               ok=(LST_OK, LST_ERR_CAPACITY))
+        out = np.zeros((n.value, 3), np.int32)
+        if n.value:
+            _check(lib.lst_get_pixel_candidates(self.h, _ptr(out), n.value, C.byref(n)), "lst_get_pixel_candidates")
         return out
 
     def features(self):

@@ -64,7 +64,8 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
     from paper_2403_13166_gb300 import lst
     structs = {"lst_module": lst.lst_module, "lst_cuts": lst.lst_cuts, "lst_mlp": lst.lst_mlp,
                "lst_config": lst.lst_config, "lst_counts": lst.lst_counts, "lst_launch": lst.lst_launch,
-               "lst_serve_config": lst.lst_serve_config, "lst_serve_result": lst.lst_serve_result}
+               "lst_serve_config": lst.lst_serve_config, "lst_serve_result": lst.lst_serve_result,
+               "lst_pixel_cuts": lst.lst_pixel_cuts, "lst_pixel_counts": lst.lst_pixel_counts}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lst.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
