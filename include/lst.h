@@ -339,7 +339,8 @@ lst_status lst_serve_stop(lst_server s);
  *   8 pLS: a seed in neither.
  * A seed matches an object (the T5 by its first T3, or the T3) whose first anchors are P0,
  * P1 and whose curvature is ko when (project specification, FP32):
- *   azimuth window  H4 . P0 >= cos_dphi |H4|_T |P0|_T (transverse);
+ *   azimuth window  H4 . P0 > 0 and |H4 x P0| <= (dphi0 + dphi_cm (r(P0) - r4)) r4 r(P0)
+ *                   (transverse; the sine of the turn of azimuth from H4 to P0);
  *   slope window    |m_p - m_o| <= dm_abs + dm_rel |m_o|, m_p = (z4 - z1) / (r4 - r1),
  *                   m_o = (z(P1) - z(P0)) / (r(P1) - r(P0));
  *   pT              |kp - ko| <= kappa_rel (|kp| + |ko|) / 2 + kappa_abs, kp the signed
@@ -352,7 +353,7 @@ lst_status lst_serve_stop(lst_server s);
  * zp|, |kx - ko|, seed index, the object's hit tuple), each taken when both are still free
  * (first for the T5s, then for the T3s with the seeds left). */
 typedef struct lst_pixel_cuts {
-    float kappa_rel, kappa_abs, rz_tol, cos_dphi, dm_abs, dm_rel;
+    float kappa_rel, kappa_abs, rz_tol, dphi0, dphi_cm, dm_abs, dm_rel;
 } lst_pixel_cuts;
 
 typedef struct lst_pixel_counts {
@@ -364,7 +365,7 @@ typedef struct lst_pixel_counts {
 /*   ev        a finished event (lst_run_event or lst_run_batch) with status LST_OK;
  *   seeds     float [n_seeds][4][3]: (x, y, z) of H1..H4 per seed, host or device, read
  *             before the call returns;
- *   pc        matching parameters (copied);
+ *   pc        matching parameters (copied; all non-negative, else LST_ERR_ARG);
  *   counts    host, may be NULL.
  * Synchronous: returns when the track candidates are ready (lst_get_pixel_candidates); a
  * later call on the same event replaces them. LST_ERR_CAPACITY if more than 8 objects tie

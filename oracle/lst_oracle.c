@@ -77,7 +77,7 @@ typedef struct {
 } oresult;
 
 typedef struct {
-    float kappa_rel, kappa_abs, rz_tol, cos_dphi, dm_abs, dm_rel;
+    float kappa_rel, kappa_abs, rz_tol, dphi0, dphi_cm, dm_abs, dm_rel;
 } opcuts;
 
 /* ------------------------------------------------------------------ growable arrays */
@@ -454,10 +454,11 @@ static void fill_md_anchor(const hit *H, float *a) { a[0] = H->x; a[1] = H->y; a
  * whose first anchors are P0, P1 and whose curvature is ko (the T3's three-point value) when
  * the two are consistent with one helix (Section 1). Project specification, FP32, only + - *
  * / sqrt, so that the GPU reaches the same decisions:
- *   window: the azimuth of P0 as seen from the beamline lies within acos(cos_dphi) of H4's,
- *     H4 . P0 >= cos_dphi |H4|_T |P0|_T, and the r-z slopes agree, |m_p - m_o| <=
- *     dm_abs + dm_rel |m_o| with m_p = (z4 - z1) / (r4 - r1) and m_o = (z1' - z0) /
- *     (r1' - r0) (P0 -> P1);
+ *   window: the azimuth of P0 seen from the beamline turns from H4's by less than the bend
+ *     of a track at the T3 pT limit allows over the radial distance, H4 . P0 > 0 and
+ *     |H4 x P0| <= (dphi0 + dphi_cm (|P0|_T - |H4|_T)) |H4|_T |P0|_T (sine of the turn),
+ *     and the r-z slopes agree, |m_p - m_o| <= dm_abs + dm_rel |m_o| with m_p = (z4 - z1) /
+ *     (r4 - r1) and m_o = (z1' - z0) / (r1' - r0) (P0 -> P1);
  *   pT: |kp - ko| <= rel (|kp| + |ko|) / 2 + abs, kp the seed's curvature through H1, H3, H4;
  *   circle: the same test for kx, the curvature through H1, H4 and P0 (the seed and the
  *     object on one circle);
@@ -492,7 +493,9 @@ int oracle_pixel_match(const float *H, const float *P0, const float *P1, float k
     const float *H1 = H, *H3 = H + 6, *H4 = H + 9;
     float r1 = sqrtf(H1[0] * H1[0] + H1[1] * H1[1]);
     float r4 = sqrtf(H4[0] * H4[0] + H4[1] * H4[1]);
-    if (!(H4[0] * P0[0] + H4[1] * P0[1] >= pc->cos_dphi * (r4 * P0[3]))) return 0;   /* azimuth */
+    if (!(H4[0] * P0[0] + H4[1] * P0[1] > 0.0f)) return 0;                        /* azimuth */
+    if (!(fabsf(H4[0] * P0[1] - H4[1] * P0[0]) <= (pc->dphi0 + pc->dphi_cm * (P0[3] - r4)) * (r4 * P0[3])))
+        return 0;
     float mp = (H4[2] - H1[2]) / (r4 - r1);
     float mo = (P1[2] - P0[2]) / (P1[3] - P0[3]);
     if (!(fabsf(mp - mo) <= pc->dm_abs + pc->dm_rel * fabsf(mo))) return 0;          /* slope */

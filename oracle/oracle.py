@@ -49,7 +49,7 @@ class _Result(C.Structure):
                 ("n_pix", C.c_int64), ("pix_tc", C.c_void_p), ("pix_ties", C.c_int64)]
 
 
-PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "cos_dphi", "dm_abs", "dm_rel")
+PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "dphi0", "dphi_cm", "dm_abs", "dm_rel")
 
 
 class _PCuts(C.Structure):

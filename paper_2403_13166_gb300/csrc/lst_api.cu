@@ -48,7 +48,7 @@ cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, con
                                        const float *, int64_t, float *, int *, long long, bool split, int skip_mma);
 int score_bf16_blocks_per_sm(bool split);
 cudaError_t pix_launch_bin(PixDesc, int, cudaStream_t);
-cudaError_t pix_launch_round(const EvDesc *, PixDesc, int, lst_pixel_cuts, int, int, cudaStream_t);
+cudaError_t pix_launch_round(const EvDesc *, PixDesc, int, lst_pixel_cuts, int, cudaStream_t);
 cudaError_t pix_launch_mark(const EvDesc *, PixDesc, int, cudaStream_t);
 cudaError_t pix_launch_rows(const EvDesc *, PixDesc, int, cudaStream_t);
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
@@ -1085,6 +1085,9 @@ lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_see
   if (!ev || !pc) return fail(LST_ERR_ARG, "null event or parameters");
   if (n_seeds < 0 || n_seeds > (int64_t)1 << 26) return fail(LST_ERR_ARG, "n_seeds outside 0..2^26");
   if (n_seeds > 0 && !seeds) return fail(LST_ERR_ARG, "null seeds");
+  const float pv[7] = {pc->kappa_rel, pc->kappa_abs, pc->rz_tol, pc->dphi0, pc->dphi_cm, pc->dm_abs, pc->dm_rel};
+  for (float v : pv)
+    if (!(v >= 0.0f)) return fail(LST_ERR_ARG, "pixel matching parameters must be non-negative numbers");
   lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
   lst_status s = wait_event(ev);
@@ -1127,15 +1130,13 @@ lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_see
   CU(cudaMemsetAsync(P.omatch, 0xff, 4 * std::max<size_t>(no, 1), st));
   CU(cudaMemsetAsync(P.mdflag, 0, std::max(nmd, 1), st));
   CU(cudaMemsetAsync(P.ctr, 0, 32, st));
+  CU(cudaMemsetAsync(P.ctr + 3, 0x7f, 4, st));            // smallest seed radius: +huge until binned
   if (np) CU(cudaMemcpyAsync(b + o_hits, seeds, 48 * (size_t)np, cudaMemcpyDefault, st));
   EvDesc *dd;
   s = slot_desc_device(c, ev->slot, &dd);
   if (s != LST_OK) return s;
   const int grid = 2 * c->n_sm;
   CU(pix_launch_bin(P, grid, st));
-  // azimuth bins on either side of the object's bin: the window plus one bin for rounding
-  const double cd = std::min(1.0, std::max(-1.0, (double)pc->cos_dphi));
-  const int dphi_bins = (int)std::ceil(std::acos(cd) / (2.0 * M_PI / PIX_NPHI)) + 1;
   int rounds[2] = {0, 0};
   int h_ctr[8];
   for (int k = 0; k < 2; k++) {
@@ -1144,7 +1145,7 @@ lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_see
     if (np == 0 || (stage == 5 ? n5 : n3) == 0) continue;
     for (;;) {
       CU(cudaMemsetAsync(P.ctr, 0, 4, st));
-      CU(pix_launch_round(dd, P, stage, *pc, dphi_bins, grid, st));
+      CU(pix_launch_round(dd, P, stage, *pc, grid, st));
       CU(cudaMemcpyAsync(h_ctr, P.ctr, 32, cudaMemcpyDeviceToHost, st));
       CU(cudaStreamSynchronize(st));
       rounds[k]++;

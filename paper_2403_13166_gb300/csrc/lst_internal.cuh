@@ -95,10 +95,11 @@ struct PixDesc {
   int *pmatch;                    // [n_pls] matched object (T5 index, or n_t5 + T3 index), -1
   unsigned long long *okey;       // [n_t5 + n_t3] the round's best rank at the object
   int *op;                        // [n_t5 + n_t3] and its seed
-  int *omatch;                    // [n_t5 + n_t3] matched seed, -1
+  int *omatch;                    // [n_t5 + n_t3] matched seed; -1 free, -2 out of the matching
   uint8_t *mdflag;                // [n_md] MD of a pT5's T5
   int *rows;                      // [n_t5 + n_t3 + n_pls][3] track candidates
-  int *ctr;                       // [8]: taken this round, rows, tie overflow, -, rows of type 5..8
+  int *ctr;                       // [8]: taken this round, rows, tie overflow, bits of the
+                                  // smallest seed radius, rows of type 5..8
 };
 constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
 constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)

@@ -14,9 +14,9 @@
 // the minimum at both its ends, so the greedy pass takes it too); rounds repeat until none
 // is taken.
 //
-// Seeds are binned by the azimuth of H4 and their r-z slope; an object scans the bins of its
-// windows (one contiguous run of azimuth bins per slope row), so a pair that passes the
-// window test is always met.
+// Seeds are binned by the azimuth of H4 and their r-z slope; a warp per object scans the bins
+// of its windows (one contiguous run of azimuth bins per slope row), so a pair that passes
+// the window test is always met.
 #include "lst_internal.cuh"
 
 namespace lstk {
@@ -43,7 +43,8 @@ __device__ __forceinline__ bool pix_kappa_ok(float k1, float k2, const lst_pixel
 // P0, P1 the object's first two anchors, mo = (P1.z - P0.z) / (P1.w - P0.w), ko its curvature.
 __device__ __forceinline__ bool pix_match(const float4 A, const float4 B, float mp, const float4 P0, float mo,
                                           float ko, const lst_pixel_cuts &pc, float &res, float &dk) {
-  if (!(B.x * P0.x + B.y * P0.y >= pc.cos_dphi * (B.w * P0.w))) return false;      // azimuth
+  if (!(B.x * P0.x + B.y * P0.y > 0.0f)) return false;                              // azimuth
+  if (!(fabsf(B.x * P0.y - B.y * P0.x) <= (pc.dphi0 + pc.dphi_cm * (P0.w - B.w)) * (B.w * P0.w))) return false;
   if (!(fabsf(mp - mo) <= pc.dm_abs + pc.dm_rel * fabsf(mo))) return false;          // slope
   if (!pix_kappa_ok(A.w, ko, pc)) return false;                                     // pT
   const float kx = pix_curv3(A.x, A.y, B.x, B.y, P0.x, P0.y);
@@ -84,6 +85,7 @@ __global__ void k_pix_bin(PixDesc P) {
     float mp;
     pix_seed(P.hits + 12 * (size_t)p, A, B, mp);
     const int c = pix_mbin(mp) * PIX_NPHI + pix_phibin(B.y, B.x);
+    if (B.w >= 0.0f) atomicMin(P.ctr + 3, __float_as_int(B.w));   // smallest r4 (non-negative: int order)
     P.cell[p] = c;
     P.rank[p] = atomicAdd(P.cell_cnt + c, 1);
     P.pkey[p] = ~0ull;
@@ -134,15 +136,22 @@ __device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, i
   return true;
 }
 
-// Visit every free seed in the object's windows that matches it: f(p, res, dk).
+// Visit every free seed in the object's windows that matches it, the lanes of a warp taking
+// the candidates in turn: f(p, res, dk) on the lane that tested the pair. The azimuth window
+// is the turn the cut allows at this radius from the smallest seed radius r4min (its sine
+// bound, arcsine, plus one bin for rounding); the slope window its rows plus one on each side.
 template <typename F>
 __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P0, const float4 P1, float ko,
-                                                const lst_pixel_cuts &pc, int dphi_bins, F f) {
+                                                const lst_pixel_cuts &pc, float r4min, F f) {
+  const int lane = threadIdx.x & 31;
   const float mo = (P1.z - P0.z) / (P1.w - P0.w);
   const float w = pc.dm_abs + pc.dm_rel * fabsf(mo);
   const int m_lo = max(0, pix_mbin(mo - w) - 1), m_hi = min(PIX_NM - 1, pix_mbin(mo + w) + 1);
   const bool all_m = !(w <= 1e30f);              // an infinite or NaN window: every row
   const int r0 = all_m ? 0 : m_lo, r1 = all_m ? PIX_NM - 1 : m_hi;
+  const float sb = pc.dphi0 + pc.dphi_cm * (P0.w - r4min);
+  const float turn = sb >= 1.0f || !(sb == sb) ? 0.5f * PIX_PI : asinf(fmaxf(sb, 0.0f));
+  const int dphi_bins = (int)(turn * (PIX_NPHI / (2.0f * PIX_PI))) + 2;
   const int c0 = pix_phibin(P0.y, P0.x);
   const int span = min(2 * dphi_bins + 1, PIX_NPHI);
   const int first = ((c0 - dphi_bins) % PIX_NPHI + PIX_NPHI) % PIX_NPHI;
@@ -153,7 +162,7 @@ __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P
       const int b0 = k == 0 ? first : 0;
       const int b1 = k == 0 ? min(first + span, PIX_NPHI) : first + span - PIX_NPHI;
       const int q0 = P.cell_off[row * PIX_NPHI + b0], q1 = P.cell_off[row * PIX_NPHI + b1];
-      for (int q = q0; q < q1; q++) {
+      for (int q = q0 + lane; q < q1; q += 32) {
         const int p = P.sidx[q];
         if (P.pmatch[p] >= 0) continue;
         float res, dk;
@@ -167,38 +176,53 @@ __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
   return ((unsigned long long)__float_as_uint(res) << 32) | __float_as_uint(dk);
 }
 
-// Round, part 1: each free object's best free seed (rank, then seed index) and, at each seed,
-// the best rank over its free objects.
-__global__ void k_pix_propose(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc,
-                              int dphi_bins) {
+// Round, part 1 (a warp per object): each free object's best free seed (rank, then seed
+// index) and, at each seed, the best rank over its free objects.
+__global__ void k_pix_propose(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = *evp;
+  const int lane = threadIdx.x & 31;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+  const float r4min = __int_as_float(P.ctr[3]);
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
     unsigned long long best = ~0ull;
-    int bp = -1;
+    int bp = 0x7fffffff;
     float4 P0, P1;
     float ko;
-    if (P.omatch[base + o] < 0 && pix_object(ev, P, stage, o, P0, P1, ko))
-      pix_scan_object(P, P0, P1, ko, pc, dphi_bins, [&](int p, float res, float dk) {
+    if (P.omatch[base + o] == -1 && pix_object(ev, P, stage, o, P0, P1, ko))
+      pix_scan_object(P, P0, P1, ko, pc, r4min, [&](int p, float res, float dk) {
         const unsigned long long k = pix_key(res, dk);
         atomicMin(P.pkey + p, k);
         if (k < best || (k == best && p < bp)) { best = k; bp = p; }
       });
-    P.okey[base + o] = best;
-    P.op[base + o] = bp;
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {                 // the warp's minimum of (rank, seed)
+      const unsigned long long ob = __shfl_xor_sync(FULL, best, s);
+      const int op = __shfl_xor_sync(FULL, bp, s);
+      if (ob < best || (ob == best && op < bp)) { best = ob; bp = op; }
+    }
+    if (lane == 0) {
+      P.okey[base + o] = best;
+      P.op[base + o] = best == ~0ull ? -1 : bp;
+      // no free seed matches it now, so none will later (seeds only leave): out for good
+      if (best == ~0ull && P.omatch[base + o] == -1) P.omatch[base + o] = -2;
+    }
   }
 }
 
-// Round, part 2: the objects that reach a seed's best rank list themselves at that seed.
-__global__ void k_pix_ties(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc, int dphi_bins) {
+// Round, part 2 (a warp per object): the objects that reach a seed's best rank list
+// themselves at that seed.
+__global__ void k_pix_ties(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = *evp;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
-    if (P.okey[base + o] == ~0ull) continue;       // no free seed matches it
+  const float r4min = __int_as_float(P.ctr[3]);
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
+    if (P.okey[base + o] == ~0ull) continue;       // no free seed matches it (warp-uniform)
     float4 P0, P1;
     float ko;
     if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
-    pix_scan_object(P, P0, P1, ko, pc, dphi_bins, [&](int p, float res, float dk) {
+    pix_scan_object(P, P0, P1, ko, pc, r4min, [&](int p, float res, float dk) {
       if (pix_key(res, dk) != P.pkey[p]) return;
       const int s = atomicAdd(P.pcnt + p, 1);
       if (s < PIX_TIES)
@@ -290,7 +314,7 @@ __global__ void k_pix_rows(const EvDesc *__restrict__ evp, PixDesc P) {
     P.rows[3 * (size_t)r + 2] = o;
   };
   for (int o = tid; o < P.n_t5; o += st)
-    if (ev.t5_tc[o]) emit(P.omatch[o] >= 0 ? 5 : 6, P.omatch[o], o);
+    if (ev.t5_tc[o]) emit(P.omatch[o] >= 0 ? 5 : 6, max(P.omatch[o], -1), o);
   for (int u = tid; u < P.n_t3; u += st)
     if (P.omatch[P.n_t5 + u] >= 0) emit(7, P.omatch[P.n_t5 + u], u);
   for (int p = tid; p < P.n_pls; p += st)
@@ -308,10 +332,9 @@ cudaError_t pix_launch_bin(PixDesc P, int grid, cudaStream_t st) {
   }
   return cudaGetLastError();
 }
-cudaError_t pix_launch_round(const EvDesc *dd, PixDesc P, int stage, lst_pixel_cuts pc, int dphi_bins, int grid,
-                             cudaStream_t st) {
-  k_pix_propose<<<grid, 128, 0, st>>>(dd, P, stage, pc, dphi_bins);
-  k_pix_ties<<<grid, 128, 0, st>>>(dd, P, stage, pc, dphi_bins);
+cudaError_t pix_launch_round(const EvDesc *dd, PixDesc P, int stage, lst_pixel_cuts pc, int grid, cudaStream_t st) {
+  k_pix_propose<<<4 * grid, 256, 0, st>>>(dd, P, stage, pc);
+  k_pix_ties<<<4 * grid, 256, 0, st>>>(dd, P, stage, pc);
   k_pix_pick<<<grid, 256, 0, st>>>(dd, P, stage);
   k_pix_accept<<<grid, 256, 0, st>>>(P, stage);
   k_pix_clear<<<grid, 256, 0, st>>>(P);

@@ -626,17 +626,20 @@ def default_cuts() -> dict:
 
 
 #: parameter order of the pixel-seed matching (lst_pixel_cuts)
-PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "cos_dphi", "dm_abs", "dm_rel")
+PIXEL_CUT_FIELDS = ("kappa_rel", "kappa_abs", "rz_tol", "dphi0", "dphi_cm", "dm_abs", "dm_rel")
 
 
 def default_pixel_cuts() -> dict:
     """Matching of pixel seeds to T5s and T3s (float32 values): curvature consistency (the
     relative and absolute tolerances, for the seed's own curvature and for the circle through
     the seed's end hits and the object's first anchor), the rz interpolation tolerance at
-    the seed's outer hit, and the search window: azimuth between the seed's outer hit and
-    the object's first anchor (cosine) and r-z slope (absolute and relative)."""
+    the seed's outer hit, and the search window: the turn of the azimuth from the seed's
+    outer hit to the object's first anchor (a constant plus a rate per cm of radius; 0.0125
+    per cm bounds the half-curvature of a T3 at its pT limit, 1.25 x 0.8 GeV / 0.64 GeV) and
+    the r-z slope (absolute and relative)."""
     return dict(kappa_rel=np.float32(0.2), kappa_abs=np.float32(0.0005), rz_tol=np.float32(0.05),
-                cos_dphi=np.float32(0.75), dm_abs=np.float32(0.05), dm_rel=np.float32(0.5))
+                dphi0=np.float32(0.05), dphi_cm=np.float32(0.0125), dm_abs=np.float32(0.05),
+                dm_rel=np.float32(0.5))
 
 
 def open_cuts() -> dict:

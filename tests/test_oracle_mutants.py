@@ -52,8 +52,10 @@ MUTANTS = {
 
 # edits of the pixel-seed steps, caught by test_oracle_pixel.py
 PIXEL_MUTANTS = {
-    "pixel azimuth window removed": ("if (!(H4[0] * P0[0] + H4[1] * P0[1] >= pc->cos_dphi * (r4 * P0[3]))) return 0;",
-                                     "if (0) return 0;"),
+    "pixel azimuth hemisphere test removed": ("if (!(H4[0] * P0[0] + H4[1] * P0[1] > 0.0f)) return 0;",
+                                              "if (0) return 0;"),
+    "pixel azimuth turn unbounded": ("(pc->dphi0 + pc->dphi_cm * (P0[3] - r4))", "(2.0f + pc->dphi_cm * (P0[3] - r4))"),
+    "pixel azimuth turn per cm dropped": ("(pc->dphi0 + pc->dphi_cm * (P0[3] - r4))", "(pc->dphi0)"),
     "pixel slope window removed": ("if (!(fabsf(mp - mo) <= pc->dm_abs + pc->dm_rel * fabsf(mo))) return 0;",
                                    "if (0) return 0;"),
     "pixel pT test removed": ("if (!pix_kappa_ok(kp, ko, pc)) return 0;", "if (0) return 0;"),

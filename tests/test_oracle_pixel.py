@@ -113,12 +113,23 @@ def _dphi(H4, P0):
 
 
 def test_azimuth_window_boundary():
+    """The sine of the azimuth turn from H4 to P0 is bounded by dphi0 + dphi_cm (r0 - r4):
+    each term alone is set just above or below the value this helix needs; a first anchor
+    on the far side of the beamline (same sine, negative cosine) is always rejected."""
     H, P0, P1, k = _helix_case(pt=0.85, eta=0.2)
-    dphi = _dphi(H[3], P0)
-    assert dphi > 0.02
-    for f, inside in ((1.02, True), (0.98, False)):      # window half-width dphi * f
-        pc = dict(PC, cos_dphi=np.float32(math.cos(dphi * f)))
-        assert oracle.pixel_match(H, P0, P1, k, pc)[0] == inside, f
+    sdphi = math.sin(_dphi(H[3], P0))
+    dr = float(P0[3]) - math.hypot(float(H[3, 0]), float(H[3, 1]))
+    assert sdphi > 0.02 and dr > 5.0
+    for f, inside in ((1.02, True), (0.98, False)):
+        pc = dict(PC, dphi0=np.float32(0.0), dphi_cm=np.float32(sdphi / dr * f))
+        assert oracle.pixel_match(H, P0, P1, k, pc)[0] == inside, ("per cm", f)
+        pc = dict(PC, dphi0=np.float32(sdphi * f), dphi_cm=np.float32(0.0))
+        assert oracle.pixel_match(H, P0, P1, k, pc)[0] == inside, ("constant", f)
+    Q = H.copy()
+    Q[:, :2] = -Q[:, :2]                   # the seed mirrored through the beamline
+    pc = dict(PC, dphi0=np.float32(1.0), kappa_rel=np.float32(10.0), kappa_abs=np.float32(1.0),
+              rz_tol=np.float32(100.0), dm_abs=np.float32(100.0))
+    assert oracle.pixel_match(H, P0, P1, k, pc)[0] and not oracle.pixel_match(Q, P0, P1, k, pc)[0]
 
 
 def test_slope_window_boundary():
