@@ -50,7 +50,11 @@ typedef enum lst_kind { LST_MD = 0, LST_LS = 1, LST_T3 = 2, LST_T5 = 3, LST_TC =
 /* Timed stages of one launch (lst_stage_times): hit grouping, step 1, step 2 (the LS
  * kernel, then the grouping of the LSs by inner MD), steps 3-4, score, track candidates. */
 #define LST_N_STAGES 8
-/* Arithmetic of the T5-DNN score (Section 2 network). LST_FP32: CUDA cores. LST_BF16:
+/* Arithmetic of the T5-DNN score (Section 2 network). LST_FP32: CUDA cores, FP32
+ * operations only, compensated: features in float-float (hi + lo pairs of floats) and
+ * every layer a compensated dot product with float-float activations, so that the score
+ * is within 1e-6 of an FP64 evaluation even for networks that amplify one FP32 rounding
+ * of an input beyond that (about 8x the FP32 operations of a plain evaluation). LST_BF16:
  * tensor cores, BF16 operands, FP32 accumulation. LST_BF16X3: tensor cores, each operand
  * split into BF16 hi + lo parts and hi*hi + lo*hi + hi*lo accumulated in FP32 (about 16
  * significant bits per operand; for networks whose score is sensitive to small input
@@ -203,11 +207,14 @@ lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float 
                             int64_t node_cap, int64_t edge_cap, int64_t *n_nodes, int64_t *n_edges);
 
 /* Copies the 38 T5-DNN input features of every T5 (Section 2 list) as float [n][38]
- * (HOST or DEVICE); same size protocol as lst_get_candidates. */
+ * (HOST or DEVICE); same size protocol as lst_get_candidates. These are the FP32 features
+ * the tensor-core precisions read (lst_score_t5 on them reproduces those scores); the
+ * LST_FP32 event path uses the float-float features. */
 lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out);
 
 /* Scores precomputed features with the loaded network (Section 2):
- *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores),
+ *   feat DEVICE float [n][38], score_out DEVICE float [n]; precision LST_FP32 (CUDA cores,
+ *   compensated network on the given FP32 features),
  *   LST_BF16 or LST_BF16X3 (tensor cores, see lst_precision). Asynchronous on
  *   cuda_stream; a tensor-core wait that ran out is reported by lst_device_errors. */
 lst_status lst_score_t5(lst_ctx ctx, const float *feat, int64_t n, int32_t precision,

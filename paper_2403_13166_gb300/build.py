@@ -55,7 +55,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=(), out_dir: s
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(lib):
+    if jobs or not _newer(lib, objs):          # also after a link that failed last time
         tmp = lib + f".{os.getpid()}.tmp"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"])
         os.replace(tmp, lib)

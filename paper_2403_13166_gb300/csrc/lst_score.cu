@@ -2,42 +2,61 @@
 // quintuplet and the 38 -> 32 -> ... -> 1 network (ReLU hidden layers, sigmoid output),
 // FP32 on the CUDA cores. Output candidates are exported as hit-index tuples here too.
 //
-// Features are FP32. Quantities that suffer cancellation in FP32 (three-point curvatures,
-// MD curvature estimates) use exact two-sum differences and FMA-compensated cross
-// products, so that every feature is within a few ulp of its exact value given the
-// FP32 hit coordinates; the network then keeps the score within 1e-6 of an FP64
-// evaluation.
+// The FP32 path keeps the score within 1e-6 of an FP64 evaluation for trained networks,
+// which move the score by ~1e-6 for a single FP32 rounding of one input or one hidden
+// activation: the features are computed in float-float (lst_ff.cuh) and every layer is a
+// compensated dot product of FP32 weights with float-float activations (Dot2: each
+// product split exactly by an FMA, the running sum's rounding errors collected and added
+// back), so that only the final sigmoid rounds to FP32.
 #include "lst_features.cuh"
 
 namespace lstk {
 
-// FP32 network with the weights in shared memory (flat layout of lst_mlp).
-__device__ __forceinline__ float mlp_fp32(const float *__restrict__ w, int n_hidden, const float *f) {
-  float h[NHID], t[NHID];
-#pragma unroll 4
-  for (int o = 0; o < NHID; o++) {
-    float s = w[NHID * NFEAT + o];
+// One neuron: bias + sum_i w[i] (xh[i] + xl[i]), compensated (Dot2 of Ogita, Rump and
+// Oishi with the activations' low parts folded into the error term).
+template <int N>
+__device__ __forceinline__ ff dot2(const float *__restrict__ w, float bias, const float *xh, const float *xl) {
+  float s = bias, c = 0.0f;
 #pragma unroll
-    for (int i = 0; i < NFEAT; i++) s = __fmaf_rn(w[o * NFEAT + i], f[i], s);
-    h[o] = fmaxf(s, 0.0f);
+  for (int i = 0; i < N; i++) {
+    const ff p = two_prod(w[i], xh[i]);
+    const ff q = two_sum(s, p.hi);
+    s = q.hi;
+    c = __fmaf_rn(w[i], xl[i], c + (q.lo + p.lo));
+  }
+  return two_sum(s, c);
+}
+
+// The network on float-float inputs with the weights in shared memory (flat layout of
+// lst_mlp); hidden activations stay float-float.
+__device__ __forceinline__ float mlp_ff(const float *__restrict__ w, int n_hidden, const float *fh, const float *fl) {
+  float hh[NHID], hl[NHID], th[NHID], tl[NHID];
+#pragma unroll 2
+  for (int o = 0; o < NHID; o++) {
+    const ff v = dot2<NFEAT>(w + o * NFEAT, w[NHID * NFEAT + o], fh, fl);
+    hh[o] = v.hi > 0.0f ? v.hi : 0.0f;
+    hl[o] = v.hi > 0.0f ? v.lo : 0.0f;
   }
   const float *p = w + NHID * NFEAT + NHID;
   for (int l = 1; l < n_hidden; l++) {
-#pragma unroll 4
+#pragma unroll 2
     for (int o = 0; o < NHID; o++) {
-      float s = p[NHID * NHID + o];
-#pragma unroll
-      for (int i = 0; i < NHID; i++) s = __fmaf_rn(p[o * NHID + i], h[i], s);
-      t[o] = fmaxf(s, 0.0f);
+      const ff v = dot2<NHID>(p + o * NHID, p[NHID * NHID + o], hh, hl);
+      th[o] = v.hi > 0.0f ? v.hi : 0.0f;
+      tl[o] = v.hi > 0.0f ? v.lo : 0.0f;
     }
 #pragma unroll
-    for (int o = 0; o < NHID; o++) h[o] = t[o];
+    for (int o = 0; o < NHID; o++) {
+      hh[o] = th[o];
+      hl[o] = tl[o];
+    }
     p += NHID * NHID + NHID;
   }
-  float s = p[NHID];
-#pragma unroll
-  for (int i = 0; i < NHID; i++) s = __fmaf_rn(p[i], h[i], s);
-  return 1.0f / (1.0f + expf(-s));
+  const ff v = dot2<NHID>(p, p[NHID], hh, hl);
+  // exp(-(hi + lo)) = exp(-hi) (1 - lo + ...), |lo| <= ulp(hi) / 2
+  const float E = expf(-v.hi);
+  const float Ec = E < 3.0e38f ? __fmaf_rn(-E, v.lo, E) : E;
+  return 1.0f / (1.0f + Ec);
 }
 
 __host__ __device__ constexpr int mlp_floats(int n_hidden) {
@@ -68,9 +87,9 @@ __global__ void __launch_bounds__(256) k_score_fp32(const EvDesc *__restrict__ e
       e = find_event(s_pref, n_events, u);
       const EvDesc &ev = evs[e];
       const int t = u - s_pref[e];
-      float f[NFEAT];
-      t5_features(ev, g, t, c.k_field, f);
-      const float s = mlp_fp32(s_w, n_hidden, f);
+      float fh[NFEAT], fl[NFEAT];
+      t5_features_ff(ev, g, t, c.k_field, fh, fl);
+      const float s = mlp_ff(s_w, n_hidden, fh, fl);
       sel = c.t5_chi2_max > 0.0f || s >= c.wp;     // pre-DNN mode: the chi2 cut selected it
       ev.t5_score[t] = s;
       ev.t5_sel[t] = sel ? 1 : 0;
@@ -85,7 +104,8 @@ __global__ void __launch_bounds__(256) k_score_fp32(const EvDesc *__restrict__ e
   }
 }
 
-// Feature export [n][38] of one event (lst_get_t5_features).
+// Feature export [n][38] of one event (lst_get_t5_features): the FP32 features the
+// tensor-core score paths read, so that lst_score_t5 on them reproduces those scores.
 __global__ void k_features(const EvDesc *__restrict__ ev_p, DevGeom g, float k_field, float *out, int n) {
   const EvDesc &ev = *ev_p;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -105,10 +125,13 @@ __global__ void __launch_bounds__(256) k_score_feat_fp32(const float *__restrict
   for (int i = threadIdx.x; i < nw; i += blockDim.x) s_w[i] = wts[i];
   __syncthreads();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    float f[NFEAT];
+    float f[NFEAT], fl[NFEAT];
 #pragma unroll
-    for (int i = 0; i < NFEAT; i++) f[i] = feat[t * NFEAT + i];
-    out[t] = mlp_fp32(s_w, n_hidden, f);
+    for (int i = 0; i < NFEAT; i++) {
+      f[i] = feat[t * NFEAT + i];
+      fl[i] = 0.0f;
+    }
+    out[t] = mlp_ff(s_w, n_hidden, f, fl);
   }
 }
 
