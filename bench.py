@@ -438,6 +438,32 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
     ctx.load_geometry(g, cuts, flat, nh)
     out = {"workload": "pu140_200_poisson", "pool_events": int(args.served_pool), "max_batch": args.served_max_batch,
            "lanes": 2, "score_precision": args.precision, "rates": []}
+    # the batched rate on the same pool (device inputs, batches of args.batch pool events, two
+    # in flight): what the served rates are compared with
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d_pool = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in e] for e in pinned]
+    batch_in = [d_pool[k % len(d_pool)] for k in range(args.batch)]
+
+    def step(prev):
+        hs = ctx.run_batch(batch_in, stream)
+        for h in prev or []:
+            h.release()
+        return hs
+    prev = None
+    for _ in range(3):
+        prev = step(prev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        prev = step(prev)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    for h in prev:
+        h.release()
+    out["batched_same_pool_per_s"] = round(10 * args.batch / (e0.elapsed_time(e1) / 1000.0), 1)
+    del d_pool, batch_in
     srv = lst.Server(ctx, max_batch=args.served_max_batch, lanes=2, mem_budget_bytes=int(args.served_mem_gb * 2**30),
                      copy_t5=True)
     # warm-up: one burst (captures the graphs for the batch sizes seen first)
@@ -446,7 +472,7 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
         srv.submit(*e, tag=k)
     got = 0
     while got < 2 * args.batch:
-        got += len(srv.poll(wait_ms=100))
+        got += len(srv.poll(wait_ms=100, keep_t5=False))
     tag = 10**6
     for rate in args.served_rates:
         n = max(50, int(rate * args.served_seconds))
@@ -461,16 +487,23 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
                     break
                 if arr[k] - now > 0.002:
                     time.sleep(0.0005)
-                res.extend(srv.poll())
+                res.extend(srv.poll(keep_t5=False))
             e = pinned[k % len(pinned)]
             srv.submit(*e, tag=tag + k, t_arrival=float(arr[k]))
         while len(res) < n:
-            res.extend(srv.poll(wait_ms=100))
+            res.extend(srv.poll(wait_ms=100, keep_t5=False))
         tag += n
         lat = np.array([r["t_done"] - r["t_arrival"] for r in res]) * 1000.0
         ok = all(r["status"] == lst.LST_OK for r in res)
         span = max(r["t_done"] for r in res) - arr[0]
+        # steady state: completions between the 10th and the 90th percentile of completion
+        # time over that interval (the fill at the start and the drain after the last
+        # arrival, ~one latency long, do not count)
+        td = np.sort([r["t_done"] for r in res])
+        k0, k1 = n // 10, n - 1 - n // 10
+        sustained = (k1 - k0) / max(td[k1] - td[k0], 1e-9)
         out["rates"].append({"offered_per_s": rate, "events": n, "achieved_per_s": round(n / span, 1),
+                             "sustained_per_s": round(float(sustained), 1),
                              "p50_ms": round(float(np.percentile(lat, 50)), 3),
                              "p99_ms": round(float(np.percentile(lat, 99)), 3), "all_ok": ok})
     srv.stop()
@@ -611,8 +644,8 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the launch-shape autotuner (default: tune once per GPU and workload)")
     ap.add_argument("--skip-served", action="store_true")
-    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 3500, 4000])
-    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 4000, 5000])
+    ap.add_argument("--served-seconds", type=float, default=3.0)
     ap.add_argument("--served-pool", type=int, default=48)
     ap.add_argument("--served-mem-gb", type=float, default=16.0)
     ap.add_argument("--served-max-batch", type=int, default=64, help="largest batch of one served launch")

@@ -284,22 +284,27 @@ lst_status lst_stage_times(lst_ctx ctx, float *ms, int64_t *n_launches);
 /* ---------------------------------------------------------------------------------
  * Serving: continuous batching of events that arrive one by one (Section 3 runs events
  * concurrently on CUDA streams; here events share batched launches instead).
- * A worker thread owns the context while the server runs (make no other call on it).
+ * Two worker threads own the context while the server runs (make no other call on it):
+ * one admits, stages and launches, the other completes batches and exports their results.
  * Requests are admitted in arrival order when an event slot is free and the estimated
  * object-buffer memory of all admitted events stays within mem_budget_bytes (a single
  * event is always admitted when nothing else is). Admitted events go to the GPU in
- * batches of up to max_batch (one launch per stage, CUDA graph) on `lanes` streams, so a
- * new batch starts while the previous one is still running.
+ * batches of up to max_batch (one launch per stage, CUDA graph, captured for every batch
+ * size when the server starts) on `lanes` streams, so a new batch starts while the
+ * previous one is still running.
  *   submit: x, y, z, sensor are HOST arrays that must stay valid until the request's
  *           result has been polled; t_arrival is the request time on lst_clock() (<= 0:
  *           now); the latency of a request is t_done - t_arrival, t_done being the time
  *           its results reached host memory (the library's pinned staging).
  *   poll:   returns up to `max` finished requests (waiting up to wait_ms for the first);
- *           each result owns host copies of its T5 tuples when copy_t5 is set, made by
- *           this call on the calling thread (lst_serve_free_result frees them). Until its
- *           results are polled, a finished batch keeps its pinned staging (about 45 bytes
- *           per T5); a caller that stops polling makes the library allocate more staging.
- *   stop:   finishes every submitted request, then joins the worker. */
+ *           when copy_t5 is set, a result's T5 arrays point into the pinned host staging
+ *           its batch was exported to (no copy is made) and stay valid until
+ *           lst_serve_free_result(result), which every polled result needs. A batch's
+ *           staging (about 45 bytes per T5) is reused once all its results are freed; a
+ *           caller that holds results or stops polling makes the library allocate more.
+ *   free_result: releases the result's hold on its staging; results may be freed after
+ *           lst_serve_stop (the last one frees the staging of a stopped server).
+ *   stop:   finishes every submitted request, then joins the workers. */
 typedef struct lst_serve_config {
     int32_t max_batch;          /* events per batched launch, 1..max_events */
     int32_t lanes;              /* batches in flight: 1 or 2 */
@@ -315,9 +320,10 @@ typedef struct lst_serve_result {
     lst_counts counts;
     double t_arrival, t_admit, t_launch, t_done;   /* lst_clock() seconds */
     int64_t n_t5;
-    int32_t *t5_hits;           /* HOST [n_t5][10] */
-    float *t5_score;            /* HOST [n_t5] */
-    uint8_t *t5_sel;            /* HOST [n_t5] */
+    int32_t *t5_hits;           /* HOST [n_t5][10], in the library's pinned staging */
+    float *t5_score;            /* HOST [n_t5], likewise */
+    uint8_t *t5_sel;            /* HOST [n_t5], likewise */
+    void *owner;                /* the staging the arrays belong to (library use) */
 } lst_serve_result;
 
 typedef struct lst_server_s *lst_server;

@@ -182,6 +182,9 @@ struct lst_ctx_s {
   cudaStream_t aux = nullptr;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  // event-slot buffers and input staging: stream-ordered allocations from a pool of the
+  // context that keeps its memory, so that a slot grows without waiting for the device
+  cudaMemPool_t pool = nullptr;
 };
 
 struct lst_event_s {
@@ -295,7 +298,11 @@ bool injected_alloc_failure(lst_ctx_s *c) {
   return false;
 }
 
-lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
+// (Re)size the buffers of slot s for an event of n_hits. The slot is idle: its last launch
+// was harvested when its event was released and every export synchronises before it
+// returns, so the old buffers can go back to the pool at once; the new ones are ready in
+// stream order on `st`, the stream of the slot's next launch.
+lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st) {
   int md, ls, t3, t5;
   caps_for(c, n_hits, md, ls, t3, t5);
   const int64_t hcap = std::max<int64_t>(n_hits, 1024);
@@ -307,13 +314,13 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits) {
   const SlotLayout L = slot_layout(H, (size_t)c->g.n_mod, md, ls, t3, t5);
   const size_t off = L.total;
   if (s.mem) {
-    CU(cudaDeviceSynchronize());
-    cudaFree(s.mem);
+    CU(cudaFreeAsync(s.mem, st));
     s.mem = nullptr;
+    s.hit_cap = 0; s.md_cap = 0; s.ls_cap = 0; s.t3_cap = 0; s.t5_cap = 0;
   }
   if (injected_alloc_failure(c))
     return fail(LST_ERR_NOMEM, "cudaMalloc(event buffers): injected failure (lst_test_fail_alloc)");
-  CU(cudaMalloc(&s.mem, off));
+  CU(cudaMallocFromPoolAsync(&s.mem, off, c->pool, st));
   s.bytes = off;
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
@@ -350,11 +357,11 @@ lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, co
     return LST_OK;
   }
   if (s.in_cap < n) {
-    if (s.in_mem) { CU(cudaDeviceSynchronize()); cudaFree(s.in_mem); s.in_mem = nullptr; s.in_cap = 0; }
+    if (s.in_mem) { CU(cudaFreeAsync(s.in_mem, st)); s.in_mem = nullptr; s.in_cap = 0; }
     if (injected_alloc_failure(c))
       return fail(LST_ERR_NOMEM, "cudaMalloc(input staging): injected failure (lst_test_fail_alloc)");
     const int64_t cap = (int64_t)(n * 1.1) + 1024;
-    CU(cudaMalloc(&s.in_mem, (size_t)cap * 16));
+    CU(cudaMallocFromPoolAsync(&s.in_mem, (size_t)cap * 16, c->pool, st));
     s.in_cap = cap;
   }
   float *b = (float *)s.in_mem;
@@ -605,6 +612,19 @@ lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out) {
     if (s != LST_OK) { lst_destroy(x); return s; }
   }
   cudaStreamCreateWithFlags(&x->aux, cudaStreamNonBlocking);
+  {
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = cuda_device;
+    if (cudaMemPoolCreate(&x->pool, &pp) != cudaSuccess) {
+      x->pool = nullptr;
+      lst_destroy(x);
+      return fail(LST_ERR_CUDA, "memory pool creation");
+    }
+    uint64_t keep = ~0ull;     // freed blocks stay in the pool for the next slot growth
+    cudaMemPoolSetAttribute(x->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (cudaMalloc(&x->d_err, sizeof(int)) != cudaSuccess || cudaMemset(x->d_err, 0, sizeof(int)) != cudaSuccess) {
     lst_destroy(x);
     return fail(LST_ERR_NOMEM, "device error word");
@@ -695,6 +715,29 @@ lst_status lst_load_geometry(lst_ctx c, const lst_module *mods, int32_t n_mod, c
   return LST_OK;
 }
 
+// The lane's graph of the whole pipeline for n events (captured on first use): the kernels
+// read the events' descriptors from the lane's device array, so one graph serves every
+// batch of n events.
+static lst_status lane_graph(lst_ctx c, Lane &L, int n, bool timed, cudaGraphExec_t *out) {
+  const long long key = (long long)n * 16 + c->cfg.precision * 2 + (timed ? 1 : 0);
+  auto it = L.graphs.find(key);
+  if (it == L.graphs.end()) {
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(L.cap_stream, cudaStreamCaptureModeThreadLocal));
+    lst_status s = enqueue_pipeline(c, L, n, L.cap_stream, timed, true);
+    cudaError_t e = cudaStreamEndCapture(L.cap_stream, &graph);
+    if (s != LST_OK) return s;
+    if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    it = L.graphs.emplace(key, exec).first;
+  }
+  *out = it->second;
+  return LST_OK;
+}
+
 static lst_status run_lane(lst_ctx c, Lane &L, int n, const int *slot_ids, cudaStream_t st, bool allow_graph,
                            bool timed) {
   L.gen++;
@@ -711,22 +754,10 @@ static lst_status run_lane(lst_ctx c, Lane &L, int n, const int *slot_ids, cudaS
   }
   CU(cudaMemcpyAsync(L.d_desc, L.h_desc, sizeof(EvDesc) * n, cudaMemcpyHostToDevice, st));
   if (allow_graph && c->cfg.use_graphs) {
-    const long long key = (long long)n * 16 + c->cfg.precision * 2 + (timed ? 1 : 0);
-    auto it = L.graphs.find(key);
-    if (it == L.graphs.end()) {
-      cudaGraph_t graph;
-      CU(cudaStreamBeginCapture(L.cap_stream, cudaStreamCaptureModeThreadLocal));
-      lst_status s = enqueue_pipeline(c, L, n, L.cap_stream, timed, true);
-      cudaError_t e = cudaStreamEndCapture(L.cap_stream, &graph);
-      if (s != LST_OK) return s;
-      if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      cudaGraphExec_t exec;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return fail(LST_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-      it = L.graphs.emplace(key, exec).first;
-    }
-    CU(cudaGraphLaunch(it->second, st));
+    cudaGraphExec_t exec = nullptr;
+    lst_status s = lane_graph(c, L, n, timed, &exec);
+    if (s != LST_OK) return s;
+    CU(cudaGraphLaunch(exec, st));
   } else {
     lst_status s = enqueue_pipeline(c, L, n, st, timed, false);
     if (s != LST_OK) return s;
@@ -753,7 +784,7 @@ lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float 
   if (si < 0) return fail(LST_ERR_NOT_READY, "no free event slot (release events)");
   Slot &S = c->slots[si];
   for (int attempt = 0; attempt < 6; attempt++) {
-    s = slot_alloc(c, S, n_hits);
+    s = slot_alloc(c, S, n_hits, st);
     if (s != LST_OK) return s;
     s = slot_inputs(c, S, x, y, z, sensor, n_hits, st);
     if (s != LST_OK) return s;
@@ -803,7 +834,7 @@ lst_status lst_run_batch(lst_ctx c, int32_t n, const float *const *x, const floa
   for (int i = 0; i < n; i++) {
     Slot &S = c->slots[ids[i]];
     if (S.lane >= 0 && S.lane != li) { s = lane_harvest(c, c->lanes[S.lane]); if (s != LST_OK) return s; }
-    s = slot_alloc(c, S, n_hits[i]);
+    s = slot_alloc(c, S, n_hits[i], st);
     if (s != LST_OK) return s;
     s = slot_inputs(c, S, x[i], y[i], z[i], sensor[i], n_hits[i], st);
     if (s != LST_OK) return s;
@@ -1215,6 +1246,8 @@ lst_status lst_destroy(lst_ctx c) {
     cudaFree(c->d_ls_units);
     cudaFree(c->d_w); cudaFree(c->scratch); cudaFree(c->d_wpack); cudaFree(c->d_err);
     if (c->aux) cudaStreamDestroy(c->aux);
+    cudaDeviceSynchronize();
+    if (c->pool) cudaMemPoolDestroy(c->pool);
   }
   delete c;
   return LST_OK;
@@ -1331,12 +1364,15 @@ void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 }  // namespace lstk
 
 // ================================================================ serving (continuous batching)
-// A worker thread owns the context while the server runs. Requests (host hit arrays) are
-// admitted in arrival order while an event slot is free and the estimated object-buffer
-// memory of the admitted events stays within the budget; admitted events go out in
-// batches (one launch per stage over the batch, CUDA graph) on two lanes with their own
-// streams, so a batch can start while the previous one is still on the device. Requests
-// that arrive meanwhile wait only for a slot and memory, not for the running batch.
+// Two worker threads own the context while the server runs. The launcher admits requests
+// (host hit arrays) in arrival order while an event slot is free and the estimated
+// object-buffer memory of the admitted events stays within the budget, stages their inputs
+// and sends them out in batches (one launch per stage over the batch, a CUDA graph captured
+// for every batch size when the server starts) on two lanes with their own streams, so a
+// batch can start while the previous one is still on the device. The completer waits for
+// each launched batch, reads its counters, exports its T5 results to the host and releases
+// its slots, so that this host work overlaps the launcher's. Requests that arrive
+// meanwhile wait only for a slot and memory, not for the running batch.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -1372,15 +1408,37 @@ size_t est_bytes(const lst_ctx_s *c, int64_t n) {
 }  // namespace
 
 // Pinned host staging of one finished lane batch's T5 results (one batched export). The
-// results of the batch point into it until lst_serve_poll copies them out on the polling
-// thread; it returns to the pool when the last of them has been copied.
+// polled results of the batch point into it (no copy) and it returns to the server's pool
+// when the last of them has been freed (lst_serve_free_result). A stage whose results
+// outlive the server is freed by the last of them.
 struct ServeStage {
   int32_t *hits = nullptr;
   float *score = nullptr;
   uint8_t *sel = nullptr;
   int64_t cap = 0;
-  int pending = 0;                      // guarded by the server's mu
+  std::mutex m;
+  int pending = 0;                      // results referring to the stage; guarded by m
+  bool orphan = false;                  // the server has stopped; guarded by m
 };
+
+namespace {
+void stage_free(ServeStage *g) {
+  cudaFreeHost(g->hits);
+  cudaFreeHost(g->score);
+  cudaFreeHost(g->sel);
+  delete g;
+}
+// One result referring to g is gone; frees g if it was the last one of a stopped server.
+void stage_release(ServeStage *g) {
+  bool last = false;
+  {
+    std::lock_guard<std::mutex> lk(g->m);
+    g->pending--;
+    last = g->orphan && g->pending == 0;
+  }
+  if (last) stage_free(g);
+}
+}  // namespace
 
 // A finished request: its result, and where its T5 rows sit in a stage (if anywhere).
 struct ServeDone {
@@ -1392,7 +1450,7 @@ struct ServeDone {
 struct lst_server_s {
   lst_ctx c = nullptr;
   lst_serve_config cfg{};
-  std::thread th;
+  std::thread th, th_done;              // launcher, completer
   std::mutex mu;
   std::condition_variable cv;
   std::deque<ServeReq> submitted;       // guarded by mu
@@ -1400,10 +1458,15 @@ struct lst_server_s {
   std::vector<ServeStage *> stages;     // every stage; guarded by mu
   bool stop = false;                    // guarded by mu
   std::string error;                    // guarded by mu
-  // worker-only state
+  // state of the two workers, guarded by wm: the queues, the lanes' batches, the slots'
+  // busy flags, the memory in use and the context's capacity ratios
+  std::mutex wm;
+  std::condition_variable wcv;
   std::deque<ServeReq> waiting;         // not yet given a slot
   std::deque<ServeReq> ready;           // holds a slot, not launched
-  std::vector<ServeReq> inflight[2];
+  std::vector<ServeReq> inflight[2];    // a lane's batch, from its launch until completed
+  std::deque<int> launched;             // lanes in launch order, for the completer
+  bool launcher_done = false;
   cudaStream_t st[2] = {nullptr, nullptr};
   size_t mem_in_use = 0;
 };
@@ -1436,8 +1499,12 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   d.stage = stage;
   d.row = row;
   d.n5 = n5;
-  c->slots[r.slot].busy = false;
-  S->mem_in_use -= std::min(S->mem_in_use, r.est);
+  {
+    std::lock_guard<std::mutex> wl(S->wm);
+    c->slots[r.slot].busy = false;
+    S->mem_in_use -= std::min(S->mem_in_use, r.est);
+  }
+  S->wcv.notify_all();
   std::lock_guard<std::mutex> lk(S->mu);
   S->done.push_back(d);
   S->cv.notify_all();
@@ -1449,6 +1516,7 @@ ServeStage *serve_stage(lst_server_s *S, int64_t n) {
   {
     std::lock_guard<std::mutex> lk(S->mu);
     for (ServeStage *g : S->stages) {
+      std::lock_guard<std::mutex> gl(g->m);
       if (g->pending) continue;
       if (g->cap >= n) return g;
       free_small = g;
@@ -1501,7 +1569,7 @@ void serve_finish_batch(lst_server_s *S, std::vector<ServeReq> &done, const std:
                                       offs.data())
            : LST_ERR_CUDA;
     if (xs == LST_OK) {
-      std::lock_guard<std::mutex> lk(S->mu);
+      std::lock_guard<std::mutex> gl(g->m);
       g->pending += (int)which.size();
     }
   }
@@ -1520,99 +1588,147 @@ void serve_finish_batch(lst_server_s *S, std::vector<ServeReq> &done, const std:
   }
 }
 
+// Launcher: admission, input staging and launches. It holds wm while it changes the shared
+// state and launches (all asynchronous with pinned inputs); it never waits for the device.
 void serve_loop(lst_server_s *S) {
   lst_ctx_s *c = S->c;
   cudaSetDevice(c->device);
   const int nl = std::max(1, std::min(2, S->cfg.lanes));
   for (;;) {
-    bool progress = false;
+    bool progress = false, stop = false;
+    std::vector<ServeReq> incoming, failed;
+    std::vector<lst_status> failed_st;
     {
-      std::unique_lock<std::mutex> lk(S->mu);
+      std::lock_guard<std::mutex> lk(S->mu);
       while (!S->submitted.empty()) {
-        S->waiting.push_back(S->submitted.front());
+        incoming.push_back(S->submitted.front());
         S->submitted.pop_front();
+      }
+      stop = S->stop;
+    }
+    {
+      std::unique_lock<std::mutex> wl(S->wm);
+      for (auto &r : incoming) S->waiting.push_back(r);
+      progress = !incoming.empty();
+      const bool idle = S->waiting.empty() && S->ready.empty() && S->inflight[0].empty() && S->inflight[1].empty();
+      if (stop && idle) {
+        S->launcher_done = true;
+        wl.unlock();
+        S->wcv.notify_all();
+        break;
+      }
+      if (idle) {
+        wl.unlock();
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->submitted.empty() && !S->stop) S->cv.wait_for(lk, std::chrono::microseconds(200));
+        continue;
+      }
+      // admission: a free slot and room in the memory budget, in arrival order
+      while (!S->waiting.empty()) {
+        ServeReq &r = S->waiting.front();
+        const size_t est = est_bytes(c, r.n);
+        const bool fits = S->mem_in_use == 0 || S->mem_in_use + est <= (size_t)S->cfg.mem_budget_bytes;
+        const int si = fits ? find_free_slot(c) : -1;
+        if (si < 0) break;
+        c->slots[si].busy = true;
+        r.slot = si;
+        r.est = est;
+        r.t_admit = now_s();
+        S->mem_in_use += est;
+        S->ready.push_back(r);
+        S->waiting.pop_front();
         progress = true;
       }
-      const bool idle = S->waiting.empty() && S->ready.empty() && S->inflight[0].empty() && S->inflight[1].empty();
-      if (S->stop && idle) break;
-      if (idle) {
-        S->cv.wait_for(lk, std::chrono::microseconds(200));
-        continue;
-      }
-    }
-    // admission: a free slot and room in the memory budget, in arrival order
-    while (!S->waiting.empty()) {
-      ServeReq &r = S->waiting.front();
-      const size_t est = est_bytes(c, r.n);
-      const bool fits = S->mem_in_use == 0 || S->mem_in_use + est <= (size_t)S->cfg.mem_budget_bytes;
-      const int si = fits ? find_free_slot(c) : -1;
-      if (si < 0) break;
-      c->slots[si].busy = true;
-      r.slot = si;
-      r.est = est;
-      r.t_admit = now_s();
-      S->mem_in_use += est;
-      S->ready.push_back(r);
-      S->waiting.pop_front();
-      progress = true;
-    }
-    // launch: every free lane takes up to max_batch ready events
-    for (int li = 0; li < nl && !S->ready.empty(); li++) {
-      if (!S->inflight[li].empty()) continue;
-      Lane &L = c->lanes[1 + li];
-      std::vector<int> ids;
-      std::vector<ServeReq> batch;
-      while (!S->ready.empty() && (int)batch.size() < S->cfg.max_batch) {
-        batch.push_back(S->ready.front());
-        S->ready.pop_front();
-      }
-      lst_status st = LST_OK;
-      for (auto &r : batch) {
-        Slot &sl = c->slots[r.slot];
-        if (st == LST_OK) st = slot_alloc(c, sl, r.n);
-        if (st == LST_OK) st = slot_inputs(c, sl, r.x, r.y, r.z, r.sensor, r.n, S->st[li]);
-        ids.push_back(r.slot);
-      }
-      const double tl = now_s();
-      for (auto &r : batch) r.t_launch = tl;
-      if (st == LST_OK) st = run_lane(c, L, (int)batch.size(), ids.data(), S->st[li], true, false);
-      if (st != LST_OK) {
-        for (auto &r : batch) serve_finish(S, r, st, nullptr, nullptr, 0, 0);
-        continue;
-      }
-      S->inflight[li] = std::move(batch);
-      progress = true;
-    }
-    // completion
-    for (int li = 0; li < nl; li++) {
-      if (S->inflight[li].empty()) continue;
-      Lane &L = c->lanes[1 + li];
-      const cudaError_t q = cudaEventQuery(L.done);
-      if (q == cudaErrorNotReady) continue;
-      lst_status st = q == cudaSuccess ? lane_harvest(c, L) : LST_ERR_CUDA;
-      std::vector<ServeReq> fin;
-      std::vector<lst_status> fst;
-      for (auto &r : S->inflight[li]) {
-        Slot &sl = c->slots[r.slot];
-        const lst_status es = st != LST_OK ? st : status_of(sl.cnt);
-        if (es == LST_ERR_CAPACITY && r.retries < 4) {
-          grow_ratios(c, sl, sl.cnt);       // run again with larger buffers
-          r.retries++;
-          S->ready.push_front(r);
+      // launch: every free lane takes up to max_batch ready events
+      for (int li = 0; li < nl && !S->ready.empty(); li++) {
+        if (!S->inflight[li].empty()) continue;
+        Lane &L = c->lanes[1 + li];
+        std::vector<int> ids;
+        std::vector<ServeReq> batch;
+        while (!S->ready.empty() && (int)batch.size() < S->cfg.max_batch) {
+          batch.push_back(S->ready.front());
+          S->ready.pop_front();
+        }
+        lst_status st = LST_OK;
+        for (auto &r : batch) {
+          Slot &sl = c->slots[r.slot];
+          if (st == LST_OK) st = slot_alloc(c, sl, r.n, S->st[li]);
+          if (st == LST_OK) st = slot_inputs(c, sl, r.x, r.y, r.z, r.sensor, r.n, S->st[li]);
+          ids.push_back(r.slot);
+        }
+        const double tl = now_s();
+        for (auto &r : batch) r.t_launch = tl;
+        if (st == LST_OK) st = run_lane(c, L, (int)batch.size(), ids.data(), S->st[li], true, false);
+        if (st != LST_OK) {
+          for (auto &r : batch) {
+            failed.push_back(r);
+            failed_st.push_back(st);
+          }
           continue;
         }
-        fin.push_back(r);
-        fst.push_back(es);
+        S->inflight[li] = std::move(batch);
+        S->launched.push_back(li);
+        progress = true;
       }
-      if (st != LST_OK) {
-        for (auto &r : fin) serve_finish(S, r, st, nullptr, nullptr, 0, 0);
-      } else {
-        serve_finish_batch(S, fin, fst);
-      }
-      S->inflight[li].clear();
-      progress = true;
     }
-    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (progress) S->wcv.notify_all();
+    for (size_t k = 0; k < failed.size(); k++) serve_finish(S, failed[k], failed_st[k], nullptr, nullptr, 0, 0);
+    if (!progress && failed.empty()) {
+      // nothing to do until a request arrives or the completer frees a lane, a slot or memory
+      std::unique_lock<std::mutex> wl(S->wm);
+      S->wcv.wait_for(wl, std::chrono::microseconds(100));
+    }
+  }
+}
+
+// Completer: waits for the launched batches in launch order, reads their counters, exports
+// their T5 results and releases their slots; events whose object buffers overflowed go back
+// to the front of the ready queue with larger buffers.
+void serve_complete_loop(lst_server_s *S) {
+  lst_ctx_s *c = S->c;
+  cudaSetDevice(c->device);
+  for (;;) {
+    int li;
+    std::vector<ServeReq> batch;
+    {
+      std::unique_lock<std::mutex> wl(S->wm);
+      S->wcv.wait(wl, [&] { return !S->launched.empty() || S->launcher_done; });
+      if (S->launched.empty()) break;
+      li = S->launched.front();
+      batch = S->inflight[li];
+    }
+    Lane &L = c->lanes[1 + li];
+    const cudaError_t q = cudaEventSynchronize(L.done);
+    const lst_status st = q == cudaSuccess ? lane_harvest(c, L) : LST_ERR_CUDA;
+    std::vector<ServeReq> fin, retry;
+    std::vector<lst_status> fst;
+    for (auto &r : batch) {
+      Slot &sl = c->slots[r.slot];
+      const lst_status es = st != LST_OK ? st : status_of(sl.cnt);
+      if (es == LST_ERR_CAPACITY && r.retries < 4) {
+        {
+          std::lock_guard<std::mutex> wl(S->wm);
+          grow_ratios(c, sl, sl.cnt);       // run again with larger buffers
+        }
+        r.retries++;
+        retry.push_back(r);
+        continue;
+      }
+      fin.push_back(r);
+      fst.push_back(es);
+    }
+    if (st != LST_OK) {
+      for (auto &r : fin) serve_finish(S, r, st, nullptr, nullptr, 0, 0);
+    } else {
+      serve_finish_batch(S, fin, fst);
+    }
+    {
+      std::lock_guard<std::mutex> wl(S->wm);
+      for (auto it = retry.rbegin(); it != retry.rend(); ++it) S->ready.push_front(*it);
+      S->inflight[li].clear();
+      S->launched.pop_front();
+    }
+    S->wcv.notify_all();
   }
 }
 
@@ -1641,11 +1757,27 @@ lst_status lst_serve_start(lst_ctx c, const lst_serve_config *cfg, lst_server *o
   S->cfg = *cfg;
   for (auto &s : S->st) {
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto &t : S->st) if (t) cudaStreamDestroy(t);
       delete S;
       return fail(LST_ERR_CUDA, "stream creation");
     }
   }
+  // every batch size's graph on every lane now, so that no capture delays a request later
+  if (c->cfg.use_graphs) {
+    const int nl = std::max(1, std::min(2, cfg->lanes));
+    for (int li = 0; li < nl; li++)
+      for (int n = 1; n <= cfg->max_batch; n++) {
+        cudaGraphExec_t exec;
+        const lst_status gs = lane_graph(c, c->lanes[1 + li], n, false, &exec);
+        if (gs != LST_OK) {
+          for (auto &t : S->st) cudaStreamDestroy(t);
+          delete S;
+          return gs;
+        }
+      }
+  }
   S->th = std::thread(serve_loop, S);
+  S->th_done = std::thread(serve_complete_loop, S);
   *out = S;
   return LST_OK;
 }
@@ -1679,31 +1811,18 @@ lst_status lst_serve_poll(lst_server S, lst_serve_result *out, int32_t max, int3
       S->done.pop_front();
     }
   }
-  // copies out of the stages on this (the polling) thread, then the stages are released
+  // the results point into their batch's stage; lst_serve_free_result releases it
   for (size_t i = 0; i < got.size(); i++) {
     ServeDone &d = got[i];
     lst_serve_result &res = d.res;
-    if (d.stage && d.n5 > 0) {
-      const int64_t n5 = d.n5;
-      res.t5_hits = (int32_t *)std::malloc((size_t)n5 * 10 * 4);
-      res.t5_score = (float *)std::malloc((size_t)n5 * 4);
-      res.t5_sel = (uint8_t *)std::malloc((size_t)n5);
-      if (!res.t5_hits || !res.t5_score || !res.t5_sel) {
-        lst_serve_free_result(&res);
-        res.status = LST_ERR_CUDA;
-      } else {
-        std::memcpy(res.t5_hits, d.stage->hits + d.row * 10, (size_t)n5 * 10 * 4);
-        std::memcpy(res.t5_score, d.stage->score + d.row, (size_t)n5 * 4);
-        std::memcpy(res.t5_sel, d.stage->sel + d.row, (size_t)n5);
-        res.n_t5 = n5;
-      }
+    if (d.stage) {
+      res.t5_hits = d.stage->hits + d.row * 10;
+      res.t5_score = d.stage->score + d.row;
+      res.t5_sel = d.stage->sel + d.row;
+      res.n_t5 = d.n5;
+      res.owner = d.stage;
     }
     out[i] = res;
-  }
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    for (auto &d : got)
-      if (d.stage) d.stage->pending--;
   }
   *n_out = (int32_t)got.size();
   return LST_OK;
@@ -1711,10 +1830,10 @@ lst_status lst_serve_poll(lst_server S, lst_serve_result *out, int32_t max, int3
 
 lst_status lst_serve_free_result(lst_serve_result *r) {
   if (!r) return fail(LST_ERR_ARG, "null result");
-  std::free(r->t5_hits);
-  std::free(r->t5_score);
-  std::free(r->t5_sel);
+  if (r->owner) stage_release((ServeStage *)r->owner);
+  r->owner = nullptr;
   r->t5_hits = nullptr; r->t5_score = nullptr; r->t5_sel = nullptr;
+  r->n_t5 = 0;
   return LST_OK;
 }
 
@@ -1726,12 +1845,21 @@ lst_status lst_serve_stop(lst_server S) {
     S->cv.notify_all();
   }
   if (S->th.joinable()) S->th.join();
+  if (S->th_done.joinable()) S->th_done.join();
   for (auto &s : S->st) if (s) cudaStreamDestroy(s);
+  // results never polled release their stages now; stages with results still held by
+  // the caller are freed by the last lst_serve_free_result
+  for (ServeDone &d : S->done)
+    if (d.stage) stage_release(d.stage);
+  S->done.clear();
   for (ServeStage *g : S->stages) {
-    cudaFreeHost(g->hits);
-    cudaFreeHost(g->score);
-    cudaFreeHost(g->sel);
-    delete g;
+    bool now = false;
+    {
+      std::lock_guard<std::mutex> lk(g->m);
+      g->orphan = true;
+      now = g->pending == 0;
+    }
+    if (now) stage_free(g);
   }
   delete S;
   return LST_OK;

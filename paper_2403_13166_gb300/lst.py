@@ -546,7 +546,7 @@ class lst_serve_result(C.Structure):
     _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32), ("counts", lst_counts),
                 ("t_arrival", C.c_double), ("t_admit", C.c_double), ("t_launch", C.c_double),
                 ("t_done", C.c_double), ("n_t5", C.c_int64), ("t5_hits", C.c_void_p),
-                ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p)]
+                ("t5_score", C.c_void_p), ("t5_sel", C.c_void_p), ("owner", C.c_void_p)]
 
 
 def _serve_sigs(lib):
@@ -590,7 +590,10 @@ class Server:
         _check(load_library().lst_serve_submit(self.h, *[_ptr(a) for a in arrs], int(arrs[0].shape[0]), int(tag),
                                                float(t_arrival)), "lst_serve_submit")
 
-    def poll(self, wait_ms: int = 0, max_results: int = 256):
+    def poll(self, wait_ms: int = 0, max_results: int = 256, keep_t5: bool = True):
+        """Finished requests as dicts. With keep_t5 the T5 tuples, scores and selection flags
+        are copied out of the library's pinned staging into numpy arrays; without, only the
+        counts and times are kept. Either way the staging is released before returning."""
         lib = load_library()
         n = C.c_int32(0)
         _check(lib.lst_serve_poll(self.h, self._buf, min(max_results, 256), C.byref(n), int(wait_ms)),
@@ -601,7 +604,7 @@ class Server:
             d = dict(tag=r.tag, status=r.status, t_arrival=r.t_arrival, t_admit=r.t_admit, t_launch=r.t_launch,
                      t_done=r.t_done, n_t5=r.n_t5, t5=r.counts.n_t5, md=r.counts.n_md, ls=r.counts.n_ls,
                      t3=r.counts.n_t3, selected=r.counts.n_selected, tc=r.counts.n_tc)
-            if r.t5_hits and r.n_t5:
+            if keep_t5 and r.t5_hits and r.n_t5:
                 n5 = r.n_t5
                 d["t5_hits"] = np.ctypeslib.as_array((C.c_int32 * (n5 * 10)).from_address(r.t5_hits)).reshape(n5, 10).copy()
                 d["t5_score"] = np.ctypeslib.as_array((C.c_float * n5).from_address(r.t5_score)).copy()

@@ -92,3 +92,63 @@ def test_serve_rejects_bad_config(geom_full, cuts):
     with pytest.raises(lst.LstError):
         lst.Server(ctx, max_batch=5)          # more than the context's event slots
     ctx.close()
+
+
+def test_results_point_into_staging_and_outlive_the_server(geom_full, cuts):
+    """Polled results refer to the server's pinned staging (no copy): they hold the same T5
+    tuples as the event alone, stay readable after lst_serve_stop until freed, and freeing
+    them afterwards (the last one frees the staging) is clean; the staging of freed results
+    is reused, so many more batches than stages go through."""
+    import ctypes as C
+    w = synth.mlp_flat(synth.xavier_mlp())
+    events = [synth.pileup_event(geom_full, 40 + i, pileup=pu, mean_per_vertex=96, config=5)
+              for i, pu in enumerate((60, 20, 90))]
+    alone = lst.Context(0, max_events=2, precision=lst.LST_BF16X3)
+    alone.load_geometry(geom_full, cuts, w, 2)
+    ref = []
+    for e in events:
+        ev = alone.run_event(e.x, e.y, e.z, e.sensor)
+        h = ev.candidates(lst.LST_T5)[0]
+        ref.append(h[np.lexsort(h.T[::-1])])
+        ev.release()
+    alone.close()
+
+    ctx = lst.Context(0, max_events=4, precision=lst.LST_BF16X3)
+    ctx.load_geometry(geom_full, cuts, w, 2)
+    srv = lst.Server(ctx, max_batch=2, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True)
+    lib = lst.load_library()
+    # many batches through, results freed as they come (the staging is reused)
+    for k in range(24):
+        e = events[k % 3]
+        srv.submit(e.x, e.y, e.z, e.sensor, tag=k)
+    got = []
+    deadline = time.time() + 60
+    while len(got) < 24 and time.time() < deadline:
+        got.extend(srv.poll(wait_ms=50))
+    assert len(got) == 24 and all(r["status"] == lst.LST_OK for r in got)
+    for r in got:
+        h = r["t5_hits"]
+        assert np.array_equal(h[np.lexsort(h.T[::-1])], ref[r["tag"] % 3])
+    # raw results kept past stop
+    for k, e in enumerate(events):
+        srv.submit(e.x, e.y, e.z, e.sensor, tag=100 + k)
+    buf = (lst.lst_serve_result * 8)()
+    held = []
+    deadline = time.time() + 60
+    while len(held) < 3 and time.time() < deadline:
+        n = C.c_int32(0)
+        assert lib.lst_serve_poll(srv.h, buf, 8, C.byref(n), 50) == lst.LST_OK
+        for i in range(n.value):
+            r = lst.lst_serve_result()
+            C.memmove(C.byref(r), C.byref(buf[i]), C.sizeof(r))
+            held.append(r)
+    srv.stop()
+    ctx.close()
+    assert len(held) == 3
+    for r in held:
+        assert r.status == lst.LST_OK and r.owner
+        n5 = r.n_t5
+        h = np.ctypeslib.as_array((C.c_int32 * (n5 * 10)).from_address(r.t5_hits)).reshape(n5, 10).copy()
+        assert np.array_equal(h[np.lexsort(h.T[::-1])], ref[r.tag - 100])
+        assert lib.lst_serve_free_result(C.byref(r)) == lst.LST_OK
+        assert not r.owner and not r.t5_hits
