@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lst_internal.cuh"
 
 namespace lstk {
@@ -73,6 +75,38 @@ lst_status fail(lst_status s, const std::string &msg) {
                   std::string(#call) + ": " + cudaGetErrorString(_e));                     \
     }                                                                                     \
   } while (0)
+
+// NVTX ranges (domain "lst") around the public calls and, while a launch sequence is
+// enqueued, around each stage's launches, so that a profiler attributes kernels to steps
+// (ncu --nvtx --nvtx-include). Without a tool attached the NVTX calls return at once.
+nvtxDomainHandle_t nvtx_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("lst");
+  return d;
+}
+void nvtx_push(const char *name) {
+  nvtxEventAttributes_t a{};
+  a.version = NVTX_VERSION;
+  a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  a.message.ascii = name;
+  nvtxDomainRangePushEx(nvtx_domain(), &a);
+}
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtx_push(name); }
+  ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+};
+// consecutive stage ranges of one launch sequence; the open one closes on scope exit
+struct NvtxStages {
+  bool open = false;
+  void next(const char *name) {
+    if (open) nvtxDomainRangePop(nvtx_domain());
+    open = name != nullptr;
+    if (open) nvtx_push(name);
+  }
+  ~NvtxStages() { next(nullptr); }
+};
+const char *const STAGE_NAMES[LST_N_STAGES] = {"hit grouping", "step 1: MD", "step 2: LS", "LS grouping",
+                                               "step 3: T3", "step 4: T5", "T5-DNN score", "track candidates"};
 
 struct DeviceGuard {
   int prev = -1;
@@ -414,7 +448,9 @@ lst_status lane_harvest(lst_ctx_s *c, Lane &L) {
 lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool timed, bool capturing) {
   const DevGeom g = c->g;
   // stage boundary events; inside a capture they become event-record nodes of the graph
+  NvtxStages ranges;
   auto mark = [&](int i) {
+    ranges.next(i < LST_N_STAGES ? STAGE_NAMES[i] : nullptr);
     if (timed) cudaEventRecordWithFlags(L.tev[i], st, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   };
   mark(0);
@@ -770,6 +806,7 @@ static lst_status run_lane(lst_ctx c, Lane &L, int n, const int *slot_ids, cudaS
 
 lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float *z, const int32_t *sensor,
                          int64_t n_hits, void *cuda_stream, lst_event *out) {
+  NvtxRange nvtx_range("lst_run_event");
   if (!c || !out) return fail(LST_ERR_ARG, "null ctx/out");
   *out = nullptr;
   if (n_hits < 0 || n_hits > (int64_t)1 << 30) return fail(LST_ERR_ARG, "n_hits out of range");
@@ -813,6 +850,7 @@ lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float 
 lst_status lst_run_batch(lst_ctx c, int32_t n, const float *const *x, const float *const *y,
                          const float *const *z, const int32_t *const *sensor, const int64_t *n_hits,
                          void *cuda_stream, lst_event *out) {
+  NvtxRange nvtx_range("lst_run_batch");
   if (!c || !out || !x || !y || !z || !sensor || !n_hits) return fail(LST_ERR_ARG, "null argument");
   if (n < 1 || n > (int32_t)c->slots.size()) return fail(LST_ERR_ARG, "batch size outside 1..max_events");
   if (!c->have_geom) return fail(LST_ERR_NOT_READY, "no geometry loaded");
@@ -894,6 +932,7 @@ static lst_status slot_desc_device(lst_ctx c, int si, EvDesc **dptr) {
 
 lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, float *score, uint8_t *selected,
                               int64_t capacity, int64_t *n_out) {
+  NvtxRange nvtx_range("lst_get_candidates");
   if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
   if (kind < LST_MD || kind > LST_TC) return fail(LST_ERR_ARG, "bad kind");
   lst_ctx c = ev->ctx;
@@ -940,6 +979,7 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
 
 lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kind, int32_t *hit_idx, float *score,
                                     uint8_t *selected, int64_t capacity, int64_t *offsets) {
+  NvtxRange nvtx_range("lst_get_candidates_batch");
   if (!evs || n < 1 || !offsets) return fail(LST_ERR_ARG, "null argument or n < 1");
   if (kind < LST_MD || kind > LST_TC) return fail(LST_ERR_ARG, "bad kind");
   lst_ctx c = evs[0] ? evs[0]->ctx : nullptr;
@@ -1008,6 +1048,7 @@ lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kin
 
 lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float *node_feat, float *edge_feat,
                            int64_t node_cap, int64_t edge_cap, int64_t *n_nodes, int64_t *n_edges) {
+  NvtxRange nvtx_range("lst_get_ls_graph");
   if (!ev || !n_nodes || !n_edges) return fail(LST_ERR_ARG, "null argument");
   lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
@@ -1055,6 +1096,7 @@ lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float 
 }
 
 lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int64_t *n_out) {
+  NvtxRange nvtx_range("lst_get_t5_features");
   if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
   lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
@@ -1088,6 +1130,7 @@ lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int6
 
 lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precision, float *score_out,
                         void *cuda_stream) {
+  NvtxRange nvtx_range("lst_score_t5");
   if (!c) return fail(LST_ERR_ARG, "null ctx");
   if (n < 0) return fail(LST_ERR_ARG, "n < 0");
   if (precision != LST_FP32 && precision != LST_BF16 && precision != LST_BF16X3)
@@ -1113,6 +1156,7 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
 // ------------------------------------------------------------------ pixel seeds (steps 5-8)
 lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
                                  lst_pixel_counts *counts) {
+  NvtxRange nvtx_range("lst_match_pixel_seeds");
   if (!ev || !pc) return fail(LST_ERR_ARG, "null event or parameters");
   if (n_seeds < 0 || n_seeds > (int64_t)1 << 26) return fail(LST_ERR_ARG, "n_seeds outside 0..2^26");
   if (n_seeds > 0 && !seeds) return fail(LST_ERR_ARG, "null seeds");
@@ -1202,6 +1246,7 @@ lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_see
 }
 
 lst_status lst_get_pixel_candidates(lst_event ev, int32_t *rows, int64_t capacity, int64_t *n_out) {
+  NvtxRange nvtx_range("lst_get_pixel_candidates");
   if (!ev || !n_out) return fail(LST_ERR_ARG, "null argument");
   lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
@@ -1642,6 +1687,7 @@ void serve_loop(lst_server_s *S) {
       // launch: every free lane takes up to max_batch ready events
       for (int li = 0; li < nl && !S->ready.empty(); li++) {
         if (!S->inflight[li].empty()) continue;
+        NvtxRange nvtx_range("serve: stage inputs and launch");
         Lane &L = c->lanes[1 + li];
         std::vector<int> ids;
         std::vector<ServeReq> batch;
@@ -1698,6 +1744,7 @@ void serve_complete_loop(lst_server_s *S) {
       batch = S->inflight[li];
     }
     Lane &L = c->lanes[1 + li];
+    NvtxRange nvtx_range("serve: complete batch");
     const cudaError_t q = cudaEventSynchronize(L.done);
     const lst_status st = q == cudaSuccess ? lane_harvest(c, L) : LST_ERR_CUDA;
     std::vector<ServeReq> fin, retry;
