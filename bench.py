@@ -68,9 +68,10 @@ def _oracle_time(args):
     return dt, r.counts["t5"]
 
 
-# kernels of one launch sequence: reset, 3 grouping, 3 MD, 3 LS, 3 T3, T5, score, 4 track
+# kernels of one launch sequence: reset, 3 grouping, 4 MD (grouping and order), 3 LS, 3 T3, T5,
+# score, 4 track
 # candidate, counter collection
-KERNELS_PER_LAUNCH = 20
+KERNELS_PER_LAUNCH = 21
 
 # score arithmetic of the batched and served forms (the plain form is always FP32)
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
@@ -644,7 +645,7 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the launch-shape autotuner (default: tune once per GPU and workload)")
     ap.add_argument("--skip-served", action="store_true")
-    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 4000, 5000])
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 4000, 5000, 6000])
     ap.add_argument("--served-seconds", type=float, default=3.0)
     ap.add_argument("--served-pool", type=int, default=48)
     ap.add_argument("--served-mem-gb", type=float, default=16.0)

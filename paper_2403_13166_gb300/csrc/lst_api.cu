@@ -25,6 +25,7 @@ __global__ void k_bin_scatter(const EvDesc *, int, DevGeom);
 __global__ void k_md(const EvDesc *, int, DevGeom, lst_cuts);
 __global__ void k_md_scan(const EvDesc *, DevGeom);
 __global__ void k_md_scatter(const EvDesc *, int);
+__global__ void k_md_sort(const EvDesc *, int);
 __global__ void k_ls(const EvDesc *, int, DevGeom, lst_cuts, int *, const int32_t *, int, int);
 __global__ void k_ls_scan(const EvDesc *);
 __global__ void k_ls_scatter(const EvDesc *, int);
@@ -207,7 +208,8 @@ struct lst_ctx_s {
   int grid_md = 0, grid_ls = 0, grid_t3 = 0, grid_t5 = 0, grid_sc = 0;
   // grids of the 256-thread grid-stride kernels: as many CTAs as are resident at once (an
   // event-major loop must not leave a second wave of CTAs to redo every event)
-  int grid_bin_count = 0, grid_bin_scatter = 0, grid_md_scatter = 0, grid_ls_scatter = 0, grid_t3_scatter = 0;
+  int grid_bin_count = 0, grid_bin_scatter = 0, grid_md_scatter = 0, grid_md_sort = 0, grid_ls_scatter = 0,
+      grid_t3_scatter = 0;
   int grid_tc_count = 0, grid_tc_scatter = 0, grid_tc_decide = 0;
   // per-stage device times accumulated over timed launches
   bool timing = false;
@@ -229,7 +231,7 @@ struct lst_event_s {
 
 namespace {
 
-constexpr int LS_WARP_BYTES = 4688;     // sizeof(LsWarp): each warp's targets, inner MDs and pair queue
+constexpr int LS_WARP_BYTES = 4944;     // sizeof(LsWarp): each warp's targets, inner MDs and pair queue
 constexpr int LS_SMALL_TB = 8;          // target modules per step-2 unit in small launches
 size_t ls_smem(const lst_ctx_s *c) { return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES; }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
@@ -275,6 +277,7 @@ lst_status compute_grids(lst_ctx_s *c) {
   CU(resident((const void *)k_bin_count, c->grid_bin_count));
   CU(resident((const void *)k_bin_scatter, c->grid_bin_scatter));
   CU(resident((const void *)k_md_scatter, c->grid_md_scatter));
+  CU(resident((const void *)k_md_sort, c->grid_md_sort));
   CU(resident((const void *)k_ls_scatter, c->grid_ls_scatter));
   CU(resident((const void *)k_t3_scatter, c->grid_t3_scatter));
   CU(resident((const void *)k_tc_count, c->grid_tc_count));
@@ -297,7 +300,7 @@ void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5)
 // Byte offsets of one event's buffers in its slot allocation (H hits, nm modules, md/ls/t3/t5
 // object capacities); `total` is the allocation size.
 struct SlotLayout {
-  size_t hit, orig, hmod, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank;
+  size_t hit, orig, hmod, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank, mperm, mq;
   size_t lin, lout, lst, lcn, lost, locn, lsu, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl,
       tcf, cnt;
   size_t total;
@@ -312,7 +315,7 @@ SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, si
   L.manc = take(16 * md); L.mk = take(8 * md); L.mmod = take(4 * md); L.mh = take(8 * md);
   L.mst = take(4 * nm); L.mcn = take(4 * nm);
   L.uanc = take(16 * md); L.uk = take(8 * md); L.umod = take(4 * md); L.uh = take(8 * md);
-  L.urank = take(4 * md);
+  L.urank = take(4 * md); L.mperm = take(4 * md); L.mq = take(4 * md);
   L.lin = take(4 * ls); L.lout = take(4 * ls);
   L.lst = take(4 * md); L.lcn = take(4 * md); L.lost = take(4 * md); L.locn = take(4 * md); L.lsu = take(16 * ls);
   L.t3 = take(16 * t3); L.t3k = take(4 * t3); L.t3s = take(4 * md); L.t3c = take(4 * md);
@@ -365,6 +368,7 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st) {
   d.md_hits = (int2 *)(b + L.mh); d.md_start = (int32_t *)(b + L.mst); d.md_cnt = (int32_t *)(b + L.mcn);
   d.mdu_anchor = (float4 *)(b + L.uanc); d.mdu_kappa = (float2 *)(b + L.uk);
   d.mdu_mod = (int32_t *)(b + L.umod); d.mdu_hits = (int2 *)(b + L.uh); d.mdu_rank = (int32_t *)(b + L.urank);
+  d.md_perm = (int32_t *)(b + L.mperm); d.md_q = (float *)(b + L.mq);
   d.ls_to = (int32_t *)(b + L.lin); d.ls_from = (int32_t *)(b + L.lout);
   d.ls_start = (int32_t *)(b + L.lst); d.ls_cnt = (int32_t *)(b + L.lcn);
   d.lso_start = (int32_t *)(b + L.lost); d.lso_cnt = (int32_t *)(b + L.locn);
@@ -463,6 +467,7 @@ lst_status enqueue_pipeline(lst_ctx_s *c, Lane &L, int n, cudaStream_t st, bool 
   k_md<<<c->grid_md, c->md_threads, md_smem(c), st>>>(L.d_desc, n, g, c->cuts);
   k_md_scan<<<n, 1024, 0, st>>>(L.d_desc, g);
   k_md_scatter<<<c->grid_md_scatter, 256, 0, st>>>(L.d_desc, n);
+  k_md_sort<<<c->grid_md_sort, 256, 0, st>>>(L.d_desc, n);
   mark(2);
   {
     // few events: units of LS_SMALL_TB target modules, so that dense modules spread over

@@ -54,10 +54,13 @@ struct EvDesc {
   int32_t *mdu_mod;
   int2 *mdu_hits;
   int32_t *mdu_rank;           // [md_cap] rank of each MD within its module
-  float4 *md_anchor;           // [md_cap] MDs grouped by module: lower-sensor hit (anchor) x, y, z, r
+  float4 *md_anchor;           // [md_cap] MDs grouped by module, within a module in ascending
+                               // md_key: lower-sensor hit (anchor) x, y, z, r
   float2 *md_kappa;            // [md_cap] (cut curvature, feature curvature); 0 for endcap
   int32_t *md_mod;             // [md_cap] module
   int2 *md_hits;               // [md_cap] original (lower, upper) hit indices
+  int32_t *md_perm;            // [md_cap] grouped by module before the order within modules:
+  float *md_q;                 //   the MD (index as found) at each position and its key
   int32_t *md_start, *md_cnt;  // [n_mod] MDs of each module: contiguous range
   int4 *lsu;                   // [ls_cap] LSs as found, any order: (inner MD, outer MD, rank
                                // within the inner MD's LSs, rank within the outer MD's LSs)
@@ -400,6 +403,10 @@ __device__ __forceinline__ bool t5_cut(const float4 *P, float ka, float kb, cons
     if (!(fabsf(P[j].z - (z0 + (z4 - z0) * S[j] / S[4])) <= c.t5_rz_tol)) return false;  // rz
   return true;
 }
+
+// Sort key of an MD within its module, q = z / r of its anchor (approximate quotient, a few
+// ulp; the same function wherever the order is relied on).
+__device__ __forceinline__ float md_key(const float4 A) { return __fdividef(A.z, A.w); }
 
 // Ranking value of a T5 among duplicates: the chi2, with NaN and +inf both +inf.
 __device__ __forceinline__ float tc_rank(float chi2) { return chi2 <= 3.40282347e38f ? chi2 : __int_as_float(0x7f800000); }

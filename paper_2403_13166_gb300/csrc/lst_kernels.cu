@@ -284,8 +284,8 @@ __global__ void k_md_scan(const EvDesc *__restrict__ evs, DevGeom g) {
   }
 }
 
-// ... then a scatter into module order: each MD to its module's start plus the rank the
-// producer drew when it counted the MD.
+// ... then a scatter into module order: each MD's index (as found) and key to its module's
+// start plus the rank the producer drew when it counted the MD ...
 __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ evs, int n_events) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   for (int e0 = 0; e0 < n_events; e0 += GROUP_EV) {
@@ -311,11 +311,60 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
       for (int k = 0; k < GROUP_EV; k++) {
         const EvDesc &ev = evs[e0 + k];
         if (o >= n[k] || !chk(ev, pos[k], ev.md_cap, 14)) continue;
-        ev.md_anchor[pos[k]] = ev.mdu_anchor[o];
-        ev.md_kappa[pos[k]] = ev.mdu_kappa[o];
+        ev.md_perm[pos[k]] = o;
+        ev.md_q[pos[k]] = md_key(ev.mdu_anchor[o]);
         ev.md_mod[pos[k]] = m[k];
-        ev.md_hits[pos[k]] = ev.mdu_hits[o];
       }
+    }
+  }
+}
+
+// ... and within each module the MDs in ascending md_key (ties: lower, then upper hit
+// index, so the order is reproducible), moved into place. Step 2 relies on that order: its
+// cut's luminous-region road, divided by rA rB, bounds |qA - qB|, so for a group of
+// targets the inner MDs that can pass form one run of a module's list. A CTA takes a tile
+// of MD_SORT_TILE consecutive positions of one event with their keys in shared memory;
+// each thread ranks its MDs by counting the smaller keys of their module's range (keys of a
+// module that crosses the tile's edge come from global memory).
+constexpr int MD_SORT_TILE = 1024;
+__global__ void __launch_bounds__(256) k_md_sort(const EvDesc *__restrict__ evs, int n_events) {
+  __shared__ int s_pref[MAX_EVENTS + 1];
+  __shared__ float s_q[MD_SORT_TILE];
+  block_event_prefix(n_events, [&](int e) {
+    const EvDesc &ev = evs[e];
+    return ev_void(ev) ? 0 : (clamp_count(ev.cnt[C_MD], ev.md_cap) + MD_SORT_TILE - 1) / MD_SORT_TILE;
+  }, s_pref);
+  const int total = s_pref[n_events];
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int e = find_event(s_pref, n_events, u);
+    const EvDesc &ev = evs[e];
+    const int n = clamp_count(ev.cnt[C_MD], ev.md_cap);
+    const int p0 = (u - s_pref[e]) * MD_SORT_TILE, p1 = min(n, p0 + MD_SORT_TILE);
+    __syncthreads();                                   // the previous tile's readers are done
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) s_q[p - p0] = ev.md_q[p];
+    __syncthreads();
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const int m = ev.md_mod[p];
+      const int s0 = ev.md_start[m], cn = ev.md_cnt[m];
+      const int op = ev.md_perm[p];
+      if (!chk(ev, op, ev.md_cap, 16) || !chk(ev, (long long)s0 + cn - 1, ev.md_cap, 15)) continue;
+      const float kp = s_q[p - p0];
+      const int2 hp = ev.mdu_hits[op];
+      int r = 0;
+      for (int j = s0; j < s0 + cn; j++) {
+        const float kj = (j >= p0 && j < p1) ? s_q[j - p0] : ev.md_q[j];
+        if (kj < kp) {
+          r++;
+        } else if (kj == kp && j != p) {
+          const int oj = ev.md_perm[j];
+          const int2 hj = chk(ev, oj, ev.md_cap, 17) ? ev.mdu_hits[oj] : hp;
+          r += (hj.x < hp.x || (hj.x == hp.x && hj.y < hp.y)) ? 1 : 0;
+        }
+      }
+      const int d = s0 + r;
+      ev.md_anchor[d] = ev.mdu_anchor[op];
+      ev.md_kappa[d] = ev.mdu_kappa[op];
+      ev.md_hits[d] = hp;
     }
   }
 }
@@ -324,14 +373,18 @@ __global__ void __launch_bounds__(256) k_md_scatter(const EvDesc *__restrict__ e
 // One warp per (event, module m); the warps of a CTA never wait for one another. The
 // targets (all MDs of the modules linked to m by the module map) are spread over the lanes
 // 32 at a time and held in registers; the inner MDs of m sit in the warp's shared memory
-// in chunks of LS_IN_CHUNK and are read as broadcasts. Every (inner, target) pair goes
-// through the division-free necessary test; the survivors (~9%) are queued and, 32 at a time,
+// in chunks of LS_IN_CHUNK and are read as broadcasts. MDs are sorted by q = z / r within
+// their module (k_md_sort), so for each group of 32 targets only a run of the chunk can pass
+// the luminous-region road (a window on q);
+// every (inner, target) pair of that run goes through the division-free necessary test;
+// the survivors (~9% of all pairs) are queued and, 32 at a time,
 // through the necessary curvature-consistency test (~1.8% of all pairs pass), whose survivors
 // wait in a second queue that lives for the whole unit and run through the exact FP32 cut
 // 32 at a time. LSs go out in any order, each with its ranks among the LSs of its inner and
 // of its outer MD (the values of the counting atomicAdds); k_ls_scan / k_ls_scatter then
 // list every LS by inner MD (its outer MD) and by outer MD (its inner MD).
 constexpr int LS_IN_CHUNK = 64;
+constexpr int LS_WINDOW_MIN = 8;         // chunks of more inner MDs than this are windowed
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
   float4 in[LS_IN_CHUNK];                  // inner anchors
@@ -340,6 +393,7 @@ struct LsWarp {
   int2 q2[64];                             // pairs past the curvature test: inner MD, target MD
                                            // (bit 31: target in the barrel), global indices
   float ink[LS_IN_CHUNK];                  // inner MD curvatures (cut values)
+  float inq[LS_IN_CHUNK];                  // inner keys q = z / r (ascending: MDs are sorted by q)
   float kB[32];
   int md[32];
   int tpref[LS_TB + 4];                    // MD-count prefix over the target modules
@@ -348,7 +402,7 @@ struct LsWarp {
   unsigned char bB[32];
   unsigned char tbar[LS_TB];
 };
-static_assert(sizeof(LsWarp) == 4688, "the host sizes k_ls shared memory with 4688 bytes per warp");
+static_assert(sizeof(LsWarp) == 4944, "the host sizes k_ls shared memory with 4944 bytes per warp");
 
 // Units: with unit_off == nullptr one unit per module (all its targets); otherwise
 // unit_off[m] .. unit_off[m + 1] are the units of module m, unit b taking the target
@@ -443,19 +497,30 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
         __syncwarp();                                  // the previous chunk's readers are done
         // padded to a multiple of 4 with NaN anchors, which fail every comparison of the test
         const int nc4 = (nc + 3) & ~3;
+        float rmin = 3.0e38f, rmax = 0.0f;
         for (int t = lane; t < nc4; t += 32) {
           if (t < nc) {
             const float4 A = ev.md_anchor[in0 + c0 + t];
             w.in[t] = A;
             w.inx[t] = make_float2(A.w * A.w, c.hit_err * A.w + 0.05f);
             w.ink[t] = ev.md_kappa[in0 + c0 + t].x;
+            w.inq[t] = md_key(A);
+            rmin = fminf(rmin, A.w);
+            rmax = fmaxf(rmax, A.w);
           } else {
             const float nan = __int_as_float(0x7fc00000);
             w.in[t] = make_float4(nan, nan, nan, nan);
             w.inx[t] = make_float2(nan, nan);
             w.ink[t] = 0.0f;
+            w.inq[t] = nan;
           }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          rmin = fminf(rmin, __shfl_xor_sync(FULL, rmin, o));
+          rmax = fmaxf(rmax, __shfl_xor_sync(FULL, rmax, o));
+        }
+        const float irmin = __fdividef(1.0f, rmin), irmax = __fdividef(1.0f, rmax);
         __syncwarp();
         for (int j0 = 0; j0 < S; j0 += 32) {
           const int j = j0 + lane;
@@ -506,12 +571,48 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               q2n -= 32;
             }
           };
-          // each lane tests its target against the inner MDs 32 at a time, collecting the
-          // survivors as a bit mask (no warp-wide step in the loop), then the masks are drained
-          // into the queue, one pair per lane and round
+          // The luminous-region road of ls_cut, |A.z rB - rA B.z| <= c1 |rB - rA| + e rA (the
+          // cut's left side equals A.z rB - rA B.z in real arithmetic), divided by rA rB > 0
+          // reads |qA - qB| <= c1 |1/rA - 1/rB| + e / rB with q = z / r, and |1/rA - 1/rB| is
+          // largest at an end of the chunk's [rmin, rmax]. So only inner MDs whose key lies
+          // in the union of the group's windows qB -+ wB can pass, one run [ilo, ihi) of the
+          // sorted chunk. Slack: 0.05 / (rA rB) covers the cut's FP32 rounding of either side
+          // (below 0.02: every product is below 3.2e4 in magnitude), 1e-3 wB + 1e-5 (1 + |qB|)
+          // the rounding of q and of the window (approximate reciprocals and quotients, a
+          // few ulp). Small chunks are taken whole.
+          int ilo = 0, ihi = nc;
+          if (nc > LS_WINDOW_MIN) {
+            float qlo = 3.0e38f, qhi = -3.0e38f;
+            if (valid) {
+              const float ib = __fdividef(1.0f, B.w);
+              const float qB = B.z * ib;
+              const float wB = c1 * fmaxf(fabsf(irmin - ib), fabsf(irmax - ib)) + c.hit_err * ib;
+              const float sl = 1e-3f * wB + 0.05f * irmin * ib + 1e-5f * (1.0f + fabsf(qB));
+              qlo = qB - wB - sl;
+              qhi = qB + wB + sl;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              qlo = fminf(qlo, __shfl_xor_sync(FULL, qlo, o));
+              qhi = fmaxf(qhi, __shfl_xor_sync(FULL, qhi, o));
+            }
+            // positions in the sorted chunk: keys below qlo, keys up to qhi
+            const float a0 = w.inq[lane];
+            ilo = __popc(__ballot_sync(FULL, lane < nc && a0 < qlo));
+            ihi = __popc(__ballot_sync(FULL, lane < nc && a0 <= qhi));
+            if (nc > 32) {
+              const float a1 = w.inq[lane + 32];
+              ilo += __popc(__ballot_sync(FULL, lane + 32 < nc && a1 < qlo));
+              ihi += __popc(__ballot_sync(FULL, lane + 32 < nc && a1 <= qhi));
+            }
+          }
+          const int ib4 = ilo & ~3, ie4 = ihi > ilo ? min(nc4, (ihi + 3) & ~3) : ib4;
+          // each lane tests its target against the inner MDs of the run 32 at a time,
+          // collecting the survivors as a bit mask (no warp-wide step in the loop), then the
+          // masks are drained into the queue, one pair per lane and round
           int qn = 0;
-          for (int i0 = 0; i0 < nc; i0 += 32) {
-            const int n4 = min(32, nc4 - i0);
+          for (int i0 = ib4; i0 < ie4; i0 += 32) {
+            const int n4 = min(32, ie4 - i0);
             unsigned mask = 0;
             if (valid) {
               for (int i = 0; i < n4; i += 4) {

@@ -181,3 +181,68 @@ def test_t3_prefilter_keeps_every_triplet(event, cuts):
     for rel in APPROX:
         ok = t3_prefilter(P[0], P[1], P[2], cuts, rel)
         assert ok.all(), int((~ok).sum())
+
+
+def q_window(zB, rB, rmin, rmax, c, rel=1.0):
+    """The window of k_ls on an inner key for target anchor (zB, rB) and a chunk of inner MDs
+    with radii in [rmin, rmax], float32 (no contraction); the approximate reciprocals
+    (__fdividef, within 2 ulp) are scaled by `rel`."""
+    e = f32(c["hit_err"])
+    c1 = f32(f32(c["z_lum"]) + e)
+    rel = f32(rel)
+    ib = (f32(1.0) / rB) * rel
+    irmin, irmax = (f32(1.0) / rmin) * rel, (f32(1.0) / rmax) * rel
+    qB = zB * ib
+    wB = c1 * np.maximum(np.abs(irmin - ib), np.abs(irmax - ib)) + e * ib
+    sl = f32(1e-3) * wB + f32(0.05) * irmin * ib + f32(1e-5) * (f32(1.0) + np.abs(qB))
+    return (qB - wB) - sl, (qB + wB) + sl
+
+
+def test_ls_q_window_keeps_every_line_segment(event, geom_full, cuts):
+    """Every LS the oracle accepts has its inner MD's key q = z / r inside the window k_ls
+    computes for its target. The window only widens when the chunk's radius range [rmin,
+    rmax] grows, so the check takes the narrowest case, a chunk holding the inner MD alone
+    (rmin = rmax = its own radius): then it holds for every chunk the MD can sit in, and
+    skipping the inner MDs outside the union of a group's windows drops no LS."""
+    e, r, H = event
+    x, y, z, rr = H
+    q = z[r.md_lo] * (f32(1.0) / rr[r.md_lo])
+    i, j = r.ls_in, r.ls_out
+    ra = rr[r.md_lo[i]]
+    assert len(i) > 1_000_000
+    for rel in (1.0 - 3e-7, 1.0, 1.0 + 3e-7):
+        lo, hi = q_window(z[r.md_lo[j]], rr[r.md_lo[j]], ra, ra, cuts, rel)
+        qi = q[i] * f32(rel)
+        inside = (qi >= lo) & (qi <= hi)
+        assert inside.all(), (rel, int((~inside).sum()))
+
+
+def test_ls_q_window_prunes(event, geom_full, cuts):
+    """Over 300 modules, with groups of 32 consecutive targets and chunks of 64 inner MDs (in
+    the order the MDs were found): the inner MDs inside the union of a group's windows make
+    well under the full count of lane steps."""
+    e, r, H = event
+    g = geom_full
+    x, y, z, rr = H
+    q = z[r.md_lo] * (f32(1.0) / rr[r.md_lo])
+    order = np.argsort(r.md_mod, kind="stable")
+    cnt = np.bincount(r.md_mod, minlength=g.n_mod)
+    start = np.concatenate([[0], np.cumsum(cnt)])
+    full_steps = run_steps = 0
+    mods = np.flatnonzero(cnt)
+    for m in mods[::max(1, len(mods) // 300)]:
+        ia = order[start[m]:start[m + 1]]
+        tg = g.map_tgt[g.map_off[m]:g.map_off[m + 1]]
+        T = np.concatenate([order[start[t]:start[t + 1]] for t in tg]) if len(tg) else np.zeros(0, int)
+        if len(T) == 0:
+            continue
+        for c0 in range(0, len(ia), 64):
+            ch = ia[c0:c0 + 64]
+            qa, ra = q[ch], rr[r.md_lo[ch]]
+            lo, hi = q_window(z[r.md_lo[T]], rr[r.md_lo[T]], ra.min(), ra.max(), cuts)
+            n4 = (len(ch) + 3) // 4 * 4
+            for j0 in range(0, len(T), 32):
+                k = int(((qa >= lo[j0:j0 + 32].min()) & (qa <= hi[j0:j0 + 32].max())).sum())
+                full_steps += 32 * n4
+                run_steps += 32 * (n4 if len(ch) <= 8 else (k + 3) // 4 * 4)
+    assert full_steps > 1_000_000 and run_steps < 0.75 * full_steps, run_steps / full_steps
