@@ -142,6 +142,7 @@ struct Slot {
   int md_cap = 0, ls_cap = 0, t3_cap = 0, t5_cap = 0;
   void *in_mem = nullptr;          // staging for host inputs
   int64_t in_cap = 0;
+  bool mem_pooled = false, in_pooled = false;  // mem / in_mem came from the context's pool
   void *pix_mem = nullptr;         // pixel-seed matching (lst_match_pixel_seeds)
   size_t pix_bytes = 0;
   int64_t pix_rows = -1;           // its track candidates, -1 before a matching
@@ -218,8 +219,9 @@ struct lst_ctx_s {
   cudaStream_t aux = nullptr;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
-  // event-slot buffers and input staging: stream-ordered allocations from a pool of the
-  // context that keeps its memory, so that a slot grows without waiting for the device
+  // event-slot buffers and input staging of the serving workers: stream-ordered allocations
+  // from a pool of the context that keeps its memory, so that a slot grows without waiting
+  // for the device
   cudaMemPool_t pool = nullptr;
 };
 
@@ -335,11 +337,26 @@ bool injected_alloc_failure(lst_ctx_s *c) {
   return false;
 }
 
-// (Re)size the buffers of slot s for an event of n_hits. The slot is idle: its last launch
-// was harvested when its event was released and every export synchronises before it
-// returns, so the old buffers can go back to the pool at once; the new ones are ready in
-// stream order on `st`, the stream of the slot's next launch.
-lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st) {
+// Device buffers of a slot. The serving workers take them from the context's stream-ordered
+// pool (pooled): the slot is idle when it grows (its last launch was harvested when its
+// event was released and every export synchronises before it returns), so the old buffers
+// go back to the pool at once and the new ones are ready in stream order on `st`, the
+// stream of the slot's next launch, without waiting for the device. The other callers use
+// plain allocations, after a device synchronisation when a buffer is replaced (a profiler
+// replaying kernels saves and restores those, which it may not do for pool memory).
+cudaError_t slot_buf_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st, bool pooled) {
+  return pooled ? cudaMallocFromPoolAsync(p, bytes, c->pool, st) : cudaMalloc(p, bytes);
+}
+cudaError_t slot_buf_free(void *p, cudaStream_t st, bool pooled) {
+  if (!p) return cudaSuccess;
+  if (pooled) return cudaFreeAsync(p, st);
+  const cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(p);
+  return e;
+}
+
+// (Re)size the buffers of slot s for an event of n_hits.
+lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st, bool pooled) {
   int md, ls, t3, t5;
   caps_for(c, n_hits, md, ls, t3, t5);
   const int64_t hcap = std::max<int64_t>(n_hits, 1024);
@@ -351,13 +368,14 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st) {
   const SlotLayout L = slot_layout(H, (size_t)c->g.n_mod, md, ls, t3, t5);
   const size_t off = L.total;
   if (s.mem) {
-    CU(cudaFreeAsync(s.mem, st));
+    CU(slot_buf_free(s.mem, st, s.mem_pooled));
     s.mem = nullptr;
     s.hit_cap = 0; s.md_cap = 0; s.ls_cap = 0; s.t3_cap = 0; s.t5_cap = 0;
   }
   if (injected_alloc_failure(c))
     return fail(LST_ERR_NOMEM, "cudaMalloc(event buffers): injected failure (lst_test_fail_alloc)");
-  CU(cudaMallocFromPoolAsync(&s.mem, off, c->pool, st));
+  CU(slot_buf_alloc(c, &s.mem, off, st, pooled));
+  s.mem_pooled = pooled;
   s.bytes = off;
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
@@ -386,7 +404,7 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st) {
 
 // stage host inputs into the slot's own device buffer (copies on `st`)
 lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, const float *z,
-                       const int32_t *sensor, int64_t n, cudaStream_t st) {
+                       const int32_t *sensor, int64_t n, cudaStream_t st, bool pooled) {
   s.d.n_hits = (int32_t)n;
   s.n_hits = n;
   const bool dev = n == 0 || is_device_ptr(x);
@@ -395,11 +413,12 @@ lst_status slot_inputs(lst_ctx_s *c, Slot &s, const float *x, const float *y, co
     return LST_OK;
   }
   if (s.in_cap < n) {
-    if (s.in_mem) { CU(cudaFreeAsync(s.in_mem, st)); s.in_mem = nullptr; s.in_cap = 0; }
+    if (s.in_mem) { CU(slot_buf_free(s.in_mem, st, s.in_pooled)); s.in_mem = nullptr; s.in_cap = 0; }
     if (injected_alloc_failure(c))
       return fail(LST_ERR_NOMEM, "cudaMalloc(input staging): injected failure (lst_test_fail_alloc)");
     const int64_t cap = (int64_t)(n * 1.1) + 1024;
-    CU(cudaMallocFromPoolAsync(&s.in_mem, (size_t)cap * 16, c->pool, st));
+    CU(slot_buf_alloc(c, &s.in_mem, (size_t)cap * 16, st, pooled));
+    s.in_pooled = pooled;
     s.in_cap = cap;
   }
   float *b = (float *)s.in_mem;
@@ -826,9 +845,9 @@ lst_status lst_run_event(lst_ctx c, const float *x, const float *y, const float 
   if (si < 0) return fail(LST_ERR_NOT_READY, "no free event slot (release events)");
   Slot &S = c->slots[si];
   for (int attempt = 0; attempt < 6; attempt++) {
-    s = slot_alloc(c, S, n_hits, st);
+    s = slot_alloc(c, S, n_hits, st, false);
     if (s != LST_OK) return s;
-    s = slot_inputs(c, S, x, y, z, sensor, n_hits, st);
+    s = slot_inputs(c, S, x, y, z, sensor, n_hits, st, false);
     if (s != LST_OK) return s;
     s = run_lane(c, L, 1, &si, st, false, c->timing);
     if (s != LST_OK) return s;
@@ -877,9 +896,9 @@ lst_status lst_run_batch(lst_ctx c, int32_t n, const float *const *x, const floa
   for (int i = 0; i < n; i++) {
     Slot &S = c->slots[ids[i]];
     if (S.lane >= 0 && S.lane != li) { s = lane_harvest(c, c->lanes[S.lane]); if (s != LST_OK) return s; }
-    s = slot_alloc(c, S, n_hits[i], st);
+    s = slot_alloc(c, S, n_hits[i], st, false);
     if (s != LST_OK) return s;
-    s = slot_inputs(c, S, x[i], y[i], z[i], sensor[i], n_hits[i], st);
+    s = slot_inputs(c, S, x[i], y[i], z[i], sensor[i], n_hits[i], st, false);
     if (s != LST_OK) return s;
   }
   s = run_lane(c, L, n, ids.data(), st, true, c->timing);
@@ -1291,7 +1310,11 @@ lst_status lst_destroy(lst_ctx c) {
       for (auto &e : L.tev) if (e) cudaEventDestroy(e);
       if (L.cap_stream) cudaStreamDestroy(L.cap_stream);
     }
-    for (auto &s : c->slots) { cudaFree(s.mem); cudaFree(s.in_mem); cudaFree(s.pix_mem); }
+    for (auto &s : c->slots) {
+      slot_buf_free(s.mem, 0, s.mem_pooled);
+      slot_buf_free(s.in_mem, 0, s.in_pooled);
+      cudaFree(s.pix_mem);
+    }
     cudaFree(c->d_subdet); cudaFree(c->d_layer); cudaFree(c->d_map_off); cudaFree(c->d_map_tgt);
     cudaFree(c->d_ls_units);
     cudaFree(c->d_w); cudaFree(c->scratch); cudaFree(c->d_wpack); cudaFree(c->d_err);
@@ -1703,8 +1726,8 @@ void serve_loop(lst_server_s *S) {
         lst_status st = LST_OK;
         for (auto &r : batch) {
           Slot &sl = c->slots[r.slot];
-          if (st == LST_OK) st = slot_alloc(c, sl, r.n, S->st[li]);
-          if (st == LST_OK) st = slot_inputs(c, sl, r.x, r.y, r.z, r.sensor, r.n, S->st[li]);
+          if (st == LST_OK) st = slot_alloc(c, sl, r.n, S->st[li], true);
+          if (st == LST_OK) st = slot_inputs(c, sl, r.x, r.y, r.z, r.sensor, r.n, S->st[li], true);
           ids.push_back(r.slot);
         }
         const double tl = now_s();
