@@ -27,24 +27,47 @@ __device__ __forceinline__ ff dot2(const float *__restrict__ w, float bias, cons
   return two_sum(s, c);
 }
 
+// Four neurons o0..o0+3 of one layer at once (rows of N weights, biases b), ReLU: each
+// input is read once for the four, and the four compensated sums are independent.
+template <int N>
+__device__ __forceinline__ void dot2x4_relu(const float *__restrict__ w, const float *__restrict__ b, int o0,
+                                            const float *xh, const float *xl, float *oh, float *ol) {
+  float s[4], c[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    s[k] = b[o0 + k];
+    c[k] = 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    const float xhi = xh[i], xlo = xl[i];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float wk = w[(o0 + k) * N + i];
+      const ff p = two_prod(wk, xhi);
+      const ff q = two_sum(s[k], p.hi);
+      s[k] = q.hi;
+      c[k] = __fmaf_rn(wk, xlo, c[k] + (q.lo + p.lo));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const ff v = two_sum(s[k], c[k]);
+    oh[o0 + k] = v.hi > 0.0f ? v.hi : 0.0f;
+    ol[o0 + k] = v.hi > 0.0f ? v.lo : 0.0f;
+  }
+}
+
 // The network on float-float inputs with the weights in shared memory (flat layout of
 // lst_mlp); hidden activations stay float-float.
 __device__ __forceinline__ float mlp_ff(const float *__restrict__ w, int n_hidden, const float *fh, const float *fl) {
   float hh[NHID], hl[NHID], th[NHID], tl[NHID];
-#pragma unroll 2
-  for (int o = 0; o < NHID; o++) {
-    const ff v = dot2<NFEAT>(w + o * NFEAT, w[NHID * NFEAT + o], fh, fl);
-    hh[o] = v.hi > 0.0f ? v.hi : 0.0f;
-    hl[o] = v.hi > 0.0f ? v.lo : 0.0f;
-  }
+#pragma unroll 1
+  for (int o = 0; o < NHID; o += 4) dot2x4_relu<NFEAT>(w, w + NHID * NFEAT, o, fh, fl, hh, hl);
   const float *p = w + NHID * NFEAT + NHID;
   for (int l = 1; l < n_hidden; l++) {
-#pragma unroll 2
-    for (int o = 0; o < NHID; o++) {
-      const ff v = dot2<NHID>(p + o * NHID, p[NHID * NHID + o], hh, hl);
-      th[o] = v.hi > 0.0f ? v.hi : 0.0f;
-      tl[o] = v.hi > 0.0f ? v.lo : 0.0f;
-    }
+#pragma unroll 1
+    for (int o = 0; o < NHID; o += 4) dot2x4_relu<NHID>(p, p + NHID * NHID, o, hh, hl, th, tl);
 #pragma unroll
     for (int o = 0; o < NHID; o++) {
       hh[o] = th[o];
