@@ -36,11 +36,13 @@ L2_BYTES = 129 * 2 ** 20
 
 # ------------------------------------------------------------------ host-side workers (spawn)
 def _gen_event(args):
-    index, pileup, per_vertex, config = args
+    """(index, x, y, z, sensor, pixel seeds or None) of one synthetic event."""
+    index, pileup, per_vertex, config = args[:4]
+    with_seeds = len(args) > 4 and args[4]
     from paper_2403_13166_gb300 import synth
     g = _geom()
     e = synth.pileup_event(g, index, pileup=pileup, mean_per_vertex=per_vertex, config=config)
-    return index, e.x, e.y, e.z, e.sensor
+    return index, e.x, e.y, e.z, e.sensor, (synth.pixel_seeds(e).hits if with_seeds else None)
 
 
 _GEOM = None
@@ -208,7 +210,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     B = args.batch
     # events of this rank (distinct seeds per rank)
     idx = rank_event_indices(rank, B)
-    evs = pool.map(_gen_event, [(i, PILEUP, PER_VERTEX, 2) for i in idx])
+    evs = pool.map(_gen_event, [(i, PILEUP, PER_VERTEX, 2, not args.skip_plain) for i in idx])
     n_hits = np.array([len(e[1]) for e in evs])
     g = _geom()
     flat, nh, wp, wname = _weights()
@@ -221,7 +223,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     # the plain form: one launch sequence per event, FP32 score
     ctx_p = lst.Context(local_rank, max_events=2, precision=lst.LST_FP32, use_graphs=0)
     ctx_p.load_geometry(g, cuts, flat, nh)
-    d_in = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in e[1:]] for e in evs]
+    d_in = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in e[1:5]] for e in evs]
     stream = torch.cuda.current_stream(dev)
     tuned = None
     if args.tune:   # launch shapes from the project's autotuner (tuned once per GPU and workload)
@@ -316,27 +318,35 @@ def run_gpu(args, rank, world, local_rank, pool):
                  "edges_per_event": int(np.mean([s[1] for s in sizes]))}
 
     # ---------------- pixel seeds (Table 1 steps 5-8): pT5 / T5 / pT3 / pLS track candidates
+    # (seeds from each event's particles, made with the event); all events of the batch in
+    # one call, and one event per call for comparison
     pixel = None
     if not args.skip_plain:
         pcuts = synth.default_pixel_cuts()
-        times, cnts = [], []
+        seeds = [torch.from_numpy(e[5]).to(dev) for e in evs]
+        hs = ctx.run_batch(d_in, stream)
+        for h in hs:
+            h.counts()
+        ctx.match_pixel_seeds_batch(hs, seeds, pcuts)          # buffers sized once
+        sync_all()
+        t0 = time.perf_counter()
+        cnts = ctx.match_pixel_seeds_batch(hs, seeds, pcuts)
+        t_batch = time.perf_counter() - t0
+        single = []
         for i in range(min(5, B)):
-            # the seeds come from the event's particles (regenerated: the same seeded event)
-            full = synth.pileup_event(g, int(idx[i]), pileup=PILEUP, mean_per_vertex=PER_VERTEX, config=2)
-            seeds = torch.from_numpy(synth.pixel_seeds(full).hits).to(dev)
-            ev = ctx_p.run_event(*d_in[i], stream=stream)
-            sync_all()
             t0 = time.perf_counter()
-            cnts.append(ev.match_pixel_seeds(seeds, pcuts))
-            times.append(time.perf_counter() - t0)
-            ev.release()
-        pixel = {"match_ms_per_event": round(1000 * float(np.median(times[1:] or times)), 4),
-                 "form": "one event per call, device seeds, synchronous (rounds of one-to-one matching)",
+            hs[i].match_pixel_seeds(seeds[i], pcuts)
+            single.append(time.perf_counter() - t0)
+        for h in hs:
+            h.release()
+        pixel = {"match_ms_per_event": round(1000 * t_batch / B, 4),
+                 "form": f"all {B} events in one call (lst_match_pixel_seeds_batch), device seeds, synchronous",
+                 "match_ms_per_event_single_call": round(1000 * float(np.median(single)), 4),
                  "per_event_mean": {k: round(float(np.mean([c[k] for c in cnts])), 1)
                                     for k in ("n_pt5", "n_t5", "n_pt3", "n_pls", "rounds_pt5", "rounds_pt3")}}
 
     # ---------------- e2e: host pinned inputs -> C-ABI -> host outputs (T5 tuples + scores)
-    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:]] for e in evs]
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in e[1:5]] for e in evs]
     h2d = int(sum(16 * n for n in n_hits))
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     # pinned result buffers for the whole batch (one export call per step)
@@ -434,7 +444,7 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
     rng = np.random.default_rng(5)
     pus = rng.integers(140, 201, args.served_pool)
     evs = pool.map(_gen_event, [(500_000 + i, int(pu), PER_VERTEX, 5) for i, pu in enumerate(pus)])
-    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in e[1:]] for e in evs]
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in e[1:5]] for e in evs]
     ctx = lst.Context(local_rank, max_events=2 * args.batch, precision=PRECISIONS[args.precision], use_graphs=1)
     ctx.load_geometry(g, cuts, flat, nh)
     out = {"workload": "pu140_200_poisson", "pool_events": int(args.served_pool), "max_batch": args.served_max_batch,

@@ -386,6 +386,15 @@ typedef struct lst_pixel_counts {
 lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
                                  lst_pixel_counts *counts);
 
+/* The same for n events of one context at once (distinct events; the results are those of
+ * n single calls): seeds[i], n_seeds[i] belong to evs[i]; counts, if not NULL, has n
+ * entries. One launch per kernel and round covers all n events, and the host waits once
+ * per round for the whole batch (an event whose round took no pair is done with the
+ * stage). n within 1..max_events, else LST_ERR_ARG. */
+lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const float *const *seeds,
+                                       const int64_t *n_seeds, const lst_pixel_cuts *pc,
+                                       lst_pixel_counts *counts);
+
 /* The track candidates of the event's last lst_match_pixel_seeds call, one row of three
  * int32 each, in no particular order: (type 5..8, seed index or -1 for type 6, object
  * index or -1 for type 8), the object index being the row of the T5 in

@@ -50,10 +50,11 @@ cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, Dev
 cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, const uint16_t *, const float *, int,
                                        const float *, int64_t, float *, int *, long long, bool split, int skip_mma);
 int score_bf16_blocks_per_sm(bool split);
-cudaError_t pix_launch_bin(PixDesc, int, cudaStream_t);
-cudaError_t pix_launch_round(const EvDesc *, PixDesc, int, lst_pixel_cuts, int, cudaStream_t);
-cudaError_t pix_launch_mark(const EvDesc *, PixDesc, int, cudaStream_t);
-cudaError_t pix_launch_rows(const EvDesc *, PixDesc, int, cudaStream_t);
+cudaError_t pix_launch_bin(const PixDesc *, int, bool, int, cudaStream_t);
+cudaError_t pix_launch_stage_begin(const PixDesc *, int, int, cudaStream_t);
+cudaError_t pix_launch_round(const EvDesc *, const PixDesc *, int, int, lst_pixel_cuts, int, int *, cudaStream_t);
+cudaError_t pix_launch_mark(const EvDesc *, const PixDesc *, int, int, cudaStream_t);
+cudaError_t pix_launch_rows(const EvDesc *, const PixDesc *, int, int, cudaStream_t);
 void pack_weights_bf16(const float *wflat, int n_hidden, uint16_t *out);
 }  // namespace lstk
 
@@ -1178,95 +1179,138 @@ lst_status lst_score_t5(lst_ctx c, const float *feat, int64_t n, int32_t precisi
 }
 
 // ------------------------------------------------------------------ pixel seeds (steps 5-8)
-lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
-                                 lst_pixel_counts *counts) {
-  NvtxRange nvtx_range("lst_match_pixel_seeds");
-  if (!ev || !pc) return fail(LST_ERR_ARG, "null event or parameters");
-  if (n_seeds < 0 || n_seeds > (int64_t)1 << 26) return fail(LST_ERR_ARG, "n_seeds outside 0..2^26");
-  if (n_seeds > 0 && !seeds) return fail(LST_ERR_ARG, "null seeds");
+lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const float *const *seeds,
+                                       const int64_t *n_seeds, const lst_pixel_cuts *pc, lst_pixel_counts *counts) {
+  NvtxRange nvtx_range("lst_match_pixel_seeds_batch");
+  if (!evs || !seeds || !n_seeds || !pc || n < 1) return fail(LST_ERR_ARG, "null argument or n < 1");
+  lst_ctx c = evs[0] ? evs[0]->ctx : nullptr;
+  if (!c) return fail(LST_ERR_ARG, "null event");
+  if (n > (int32_t)c->slots.size()) return fail(LST_ERR_ARG, "more events than the context's slots");
+  for (int i = 0; i < n; i++) {
+    if (!evs[i] || evs[i]->ctx != c) return fail(LST_ERR_ARG, "events of one context expected");
+    for (int j = 0; j < i; j++)
+      if (evs[j]->slot == evs[i]->slot) return fail(LST_ERR_ARG, "an event appears twice");
+    if (n_seeds[i] < 0 || n_seeds[i] > (int64_t)1 << 26) return fail(LST_ERR_ARG, "n_seeds outside 0..2^26");
+    if (n_seeds[i] > 0 && !seeds[i]) return fail(LST_ERR_ARG, "null seeds");
+  }
   const float pv[7] = {pc->kappa_rel, pc->kappa_abs, pc->rz_tol, pc->dphi0, pc->dphi_cm, pc->dm_abs, pc->dm_rel};
   for (float v : pv)
     if (!(v >= 0.0f)) return fail(LST_ERR_ARG, "pixel matching parameters must be non-negative numbers");
-  lst_ctx c = ev->ctx;
   DeviceGuard gd(c->device);
-  lst_status s = wait_event(ev);
-  if (s != LST_OK) return s;
-  if (ev->status != LST_OK) return fail((lst_status)ev->status, "event has no valid results");
-  Slot &S = c->slots[ev->slot];
-  S.pix_rows = -1;
-  const int np = (int)n_seeds, n5 = S.cnt[C_T5], n3 = S.cnt[C_T3], nmd = S.cnt[C_MD];
-  const size_t no = (size_t)n5 + n3, npl = std::max(np, 1);
-  size_t off = 0;
-  auto take = [&](size_t b) { size_t o = off; off = align_up(off + std::max<size_t>(b, 1), 256); return o; };
-  const size_t o_hits = take(48 * npl), o_cell = take(4 * npl), o_rank = take(4 * npl);
-  const size_t o_ccnt = take(4 * (size_t)PIX_NCELL), o_coff = take(4 * ((size_t)PIX_NCELL + 1));
-  const size_t o_sa = take(16 * npl), o_sb = take(16 * npl), o_sm = take(4 * npl), o_sidx = take(4 * npl);
-  const size_t o_pkey = take(8 * npl), o_pcnt = take(4 * npl), o_plist = take(4 * (size_t)PIX_TIES * npl);
-  const size_t o_pobj = take(4 * npl), o_pmatch = take(4 * npl);
-  const size_t o_okey = take(8 * no), o_op = take(4 * no), o_omatch = take(4 * no), o_md = take((size_t)nmd);
-  const size_t o_rows = take(12 * (no + npl)), o_ctr = take(32);
-  if (S.pix_bytes < off) {
-    CU(cudaDeviceSynchronize());
-    cudaFree(S.pix_mem);
-    S.pix_mem = nullptr;
-    S.pix_bytes = 0;
-    CU(cudaMalloc(&S.pix_mem, off));
-    S.pix_bytes = off;
+  for (int i = 0; i < n; i++) {
+    lst_status s = wait_event(evs[i]);
+    if (s != LST_OK) return s;
+    if (evs[i]->status != LST_OK) return fail((lst_status)evs[i]->status, "event has no valid results");
   }
-  char *b = (char *)S.pix_mem;
-  PixDesc P;
-  P.n_pls = np; P.n_t5 = n5; P.n_t3 = n3; P.n_md = nmd;
-  P.hits = (const float *)(b + o_hits);
-  P.cell = (int *)(b + o_cell); P.rank = (int *)(b + o_rank);
-  P.cell_cnt = (int *)(b + o_ccnt); P.cell_off = (int *)(b + o_coff);
-  P.sa = (float4 *)(b + o_sa); P.sb = (float4 *)(b + o_sb); P.sm = (float *)(b + o_sm); P.sidx = (int *)(b + o_sidx);
-  P.pkey = (unsigned long long *)(b + o_pkey); P.pcnt = (int *)(b + o_pcnt); P.plist = (int *)(b + o_plist);
-  P.pobj = (int *)(b + o_pobj); P.pmatch = (int *)(b + o_pmatch);
-  P.okey = (unsigned long long *)(b + o_okey); P.op = (int *)(b + o_op); P.omatch = (int *)(b + o_omatch);
-  P.mdflag = (uint8_t *)(b + o_md); P.rows = (int *)(b + o_rows); P.ctr = (int *)(b + o_ctr);
   cudaStream_t st = c->aux;
-  CU(cudaMemsetAsync(P.cell_cnt, 0, 4 * (size_t)PIX_NCELL, st));
-  CU(cudaMemsetAsync(P.omatch, 0xff, 4 * std::max<size_t>(no, 1), st));
-  CU(cudaMemsetAsync(P.mdflag, 0, std::max(nmd, 1), st));
-  CU(cudaMemsetAsync(P.ctr, 0, 32, st));
-  CU(cudaMemsetAsync(P.ctr + 3, 0x7f, 4, st));            // smallest seed radius: +huge until binned
-  if (np) CU(cudaMemcpyAsync(b + o_hits, seeds, 48 * (size_t)np, cudaMemcpyDefault, st));
-  EvDesc *dd;
-  s = slot_desc_device(c, ev->slot, &dd);
-  if (s != LST_OK) return s;
-  const int grid = 2 * c->n_sm;
-  CU(pix_launch_bin(P, grid, st));
-  int rounds[2] = {0, 0};
-  int h_ctr[8];
-  for (int k = 0; k < 2; k++) {
-    const int stage = k == 0 ? 5 : 7;
-    if (stage == 7) CU(pix_launch_mark(dd, P, grid, st));
-    if (np == 0 || (stage == 5 ? n5 : n3) == 0) continue;
-    for (;;) {
-      CU(cudaMemsetAsync(P.ctr, 0, 4, st));
-      CU(pix_launch_round(dd, P, stage, *pc, grid, st));
-      CU(cudaMemcpyAsync(h_ctr, P.ctr, 32, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      rounds[k]++;
-      if (h_ctr[2]) return fail(LST_ERR_CAPACITY, "more than 8 objects tie at one seed in both ranking measures");
-      if (h_ctr[0] == 0) break;
+  std::vector<PixDesc> P(n);
+  std::vector<EvDesc> D(n);
+  bool any_seeds = false;
+  for (int i = 0; i < n; i++) {
+    Slot &S = c->slots[evs[i]->slot];
+    S.pix_rows = -1;
+    const int np = (int)n_seeds[i], n5 = S.cnt[C_T5], n3 = S.cnt[C_T3], nmd = S.cnt[C_MD];
+    const size_t no = (size_t)n5 + n3, npl = std::max(np, 1);
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + std::max<size_t>(b, 1), 256); return o; };
+    const size_t o_hits = take(48 * npl), o_cell = take(4 * npl), o_rank = take(4 * npl);
+    const size_t o_ccnt = take(4 * (size_t)PIX_NCELL), o_coff = take(4 * ((size_t)PIX_NCELL + 1));
+    const size_t o_sa = take(16 * npl), o_sb = take(16 * npl), o_sm = take(4 * npl), o_sidx = take(4 * npl);
+    const size_t o_pkey = take(8 * npl), o_pcnt = take(4 * npl), o_plist = take(4 * (size_t)PIX_TIES * npl);
+    const size_t o_pobj = take(4 * npl), o_pmatch = take(4 * npl);
+    const size_t o_okey = take(8 * no), o_op = take(4 * no), o_omatch = take(4 * no), o_md = take((size_t)nmd);
+    const size_t o_rows = take(12 * (no + npl)), o_ctr = take(4 * PIX_NCTR);
+    if (S.pix_bytes < off) {
+      CU(cudaDeviceSynchronize());
+      cudaFree(S.pix_mem);
+      S.pix_mem = nullptr;
+      S.pix_bytes = 0;
+      CU(cudaMalloc(&S.pix_mem, off));
+      S.pix_bytes = off;
+    }
+    char *b = (char *)S.pix_mem;
+    PixDesc &Q = P[i];
+    Q.n_pls = np; Q.n_t5 = n5; Q.n_t3 = n3; Q.n_md = nmd;
+    Q.hits = (const float *)(b + o_hits);
+    Q.cell = (int *)(b + o_cell); Q.rank = (int *)(b + o_rank);
+    Q.cell_cnt = (int *)(b + o_ccnt); Q.cell_off = (int *)(b + o_coff);
+    Q.sa = (float4 *)(b + o_sa); Q.sb = (float4 *)(b + o_sb); Q.sm = (float *)(b + o_sm); Q.sidx = (int *)(b + o_sidx);
+    Q.pkey = (unsigned long long *)(b + o_pkey); Q.pcnt = (int *)(b + o_pcnt); Q.plist = (int *)(b + o_plist);
+    Q.pobj = (int *)(b + o_pobj); Q.pmatch = (int *)(b + o_pmatch);
+    Q.okey = (unsigned long long *)(b + o_okey); Q.op = (int *)(b + o_op); Q.omatch = (int *)(b + o_omatch);
+    Q.mdflag = (uint8_t *)(b + o_md); Q.rows = (int *)(b + o_rows); Q.ctr = (int *)(b + o_ctr);
+    CU(cudaMemsetAsync(Q.cell_cnt, 0, 4 * (size_t)PIX_NCELL, st));
+    CU(cudaMemsetAsync(Q.omatch, 0xff, 4 * std::max<size_t>(no, 1), st));
+    CU(cudaMemsetAsync(Q.mdflag, 0, std::max(nmd, 1), st));
+    CU(cudaMemsetAsync(Q.ctr, 0, 4 * PIX_NCTR, st));
+    CU(cudaMemsetAsync(Q.ctr + 3, 0x7f, 4, st));          // smallest seed radius: +huge until binned
+    if (np) CU(cudaMemcpyAsync(b + o_hits, seeds[i], 48 * (size_t)np, cudaMemcpyDefault, st));
+    any_seeds = any_seeds || np > 0;
+    D[i] = S.d;
+  }
+  // device copies of the descriptors and the per-event flags of the rounds
+  const size_t b_p = align_up(sizeof(PixDesc) * (size_t)n, 256), b_d = align_up(sizeof(EvDesc) * (size_t)n, 256);
+  void *tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, b_p + b_d + 4 * (size_t)n, st));
+  PixDesc *dP = (PixDesc *)tmp;
+  EvDesc *dD = (EvDesc *)((char *)tmp + b_p);
+  int *dflags = (int *)((char *)tmp + b_p + b_d);
+  CU(cudaMemcpyAsync(dP, P.data(), sizeof(PixDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(dD, D.data(), sizeof(EvDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
+  const int grid = std::max(1, 2 * c->n_sm / n);
+  lst_status res = LST_OK;
+  std::vector<int> hflags(n);
+  auto run = [&]() -> lst_status {
+    CU(pix_launch_bin(dP, n, any_seeds, grid, st));
+    for (int stage : {5, 7}) {
+      if (stage == 7) CU(pix_launch_mark(dD, dP, n, grid, st));
+      CU(pix_launch_stage_begin(dP, n, stage, st));
+      for (int round = 0; round < 1 << 20; round++) {
+        CU(pix_launch_round(dD, dP, n, stage, *pc, grid, dflags, st));
+        CU(cudaMemcpyAsync(hflags.data(), dflags, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int f : hflags) {
+          if (f & 2) return fail(LST_ERR_CAPACITY, "more than 8 objects tie at one seed in both ranking measures");
+          all = all && (f & 1);
+        }
+        if (all) break;
+      }
+    }
+    CU(pix_launch_rows(dD, dP, n, grid, st));
+    return LST_OK;
+  };
+  res = run();
+  std::vector<int> hctr((size_t)n * PIX_NCTR);
+  if (res == LST_OK) {
+    for (int i = 0; i < n; i++)
+      CU(cudaMemcpyAsync(hctr.data() + (size_t)i * PIX_NCTR, P[i].ctr, 4 * PIX_NCTR, cudaMemcpyDeviceToHost, st));
+  }
+  cudaFreeAsync(tmp, st);
+  CU(cudaStreamSynchronize(st));
+  if (res != LST_OK) return res;
+  for (int i = 0; i < n; i++) {
+    const int *h = hctr.data() + (size_t)i * PIX_NCTR;
+    Slot &S = c->slots[evs[i]->slot];
+    S.pix_rows = h[1];
+    S.pix_rows_ptr = P[i].rows;
+    if (counts) {
+      counts[i].n_rows = h[1];
+      counts[i].n_pt5 = h[4];
+      counts[i].n_t5 = h[5];
+      counts[i].n_pt3 = h[6];
+      counts[i].n_pls = h[7];
+      counts[i].rounds_pt5 = h[PIX_ROUNDS5];
+      counts[i].rounds_pt3 = h[PIX_ROUNDS7];
     }
   }
-  CU(pix_launch_rows(dd, P, grid, st));
-  CU(cudaMemcpyAsync(h_ctr, P.ctr, 32, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  S.pix_rows = h_ctr[1];
-  S.pix_rows_ptr = P.rows;
-  if (counts) {
-    counts->n_rows = h_ctr[1];
-    counts->n_pt5 = h_ctr[4];
-    counts->n_t5 = h_ctr[5];
-    counts->n_pt3 = h_ctr[6];
-    counts->n_pls = h_ctr[7];
-    counts->rounds_pt5 = rounds[0];
-    counts->rounds_pt3 = rounds[1];
-  }
   return LST_OK;
+}
+
+lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_seeds, const lst_pixel_cuts *pc,
+                                 lst_pixel_counts *counts) {
+  if (!ev || !pc) return fail(LST_ERR_ARG, "null event or parameters");
+  return lst_match_pixel_seeds_batch(&ev, 1, &seeds, &n_seeds, pc, counts);
 }
 
 lst_status lst_get_pixel_candidates(lst_event ev, int32_t *rows, int64_t capacity, int64_t *n_out) {

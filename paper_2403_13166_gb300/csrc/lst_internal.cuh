@@ -101,9 +101,11 @@ struct PixDesc {
   int *omatch;                    // [n_t5 + n_t3] matched seed; -1 free, -2 out of the matching
   uint8_t *mdflag;                // [n_md] MD of a pT5's T5
   int *rows;                      // [n_t5 + n_t3 + n_pls][3] track candidates
-  int *ctr;                       // [8]: taken this round, rows, tie overflow, bits of the
-                                  // smallest seed radius, rows of type 5..8
+  int *ctr;                       // [16]: taken this round, rows, tie overflow, bits of the
+                                  // smallest seed radius, rows of type 5..8; PIX_DONE: done
+                                  // with the current stage; rounds of stages 5 and 7
 };
+constexpr int PIX_DONE = 8, PIX_ROUNDS5 = 9, PIX_ROUNDS7 = 10, PIX_NCTR = 16;
 constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
 constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)
 

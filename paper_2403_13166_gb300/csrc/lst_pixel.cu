@@ -79,7 +79,8 @@ __device__ __forceinline__ void pix_seed(const float *H, float4 &A, float4 &B, f
   B = make_float4(H[9], H[10], H[11], r4);
 }
 
-__global__ void k_pix_bin(PixDesc P) {
+__global__ void k_pix_bin(const PixDesc *Ps) {
+  const PixDesc &P = Ps[blockIdx.y];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
     float4 A, B;
     float mp;
@@ -95,12 +96,14 @@ __global__ void k_pix_bin(PixDesc P) {
   }
 }
 
-__global__ void k_pix_scan(PixDesc P) {
+__global__ void k_pix_scan(const PixDesc *Ps) {
+  const PixDesc &P = Ps[blockIdx.y];
   block_exclusive_scan(P.cell_cnt, P.cell_off, PIX_NCELL);
   if (threadIdx.x == 0) P.cell_off[PIX_NCELL] = P.n_pls;
 }
 
-__global__ void k_pix_scatter(PixDesc P) {
+__global__ void k_pix_scatter(const PixDesc *Ps) {
+  const PixDesc &P = Ps[blockIdx.y];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
     float4 A, B;
     float mp;
@@ -178,8 +181,10 @@ __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
 
 // Round, part 1 (a warp per object): each free object's best free seed (rank, then seed
 // index) and, at each seed, the best rank over its free objects.
-__global__ void k_pix_propose(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc) {
-  const EvDesc &ev = *evp;
+__global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const PixDesc &P = Ps[blockIdx.y];
+  if (P.ctr[PIX_DONE]) return;
   const int lane = threadIdx.x & 31;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   const float r4min = __int_as_float(P.ctr[3]);
@@ -212,8 +217,10 @@ __global__ void k_pix_propose(const EvDesc *__restrict__ evp, PixDesc P, int sta
 
 // Round, part 2 (a warp per object): the objects that reach a seed's best rank list
 // themselves at that seed.
-__global__ void k_pix_ties(const EvDesc *__restrict__ evp, PixDesc P, int stage, lst_pixel_cuts pc) {
-  const EvDesc &ev = *evp;
+__global__ void k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const PixDesc &P = Ps[blockIdx.y];
+  if (P.ctr[PIX_DONE]) return;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   const float r4min = __int_as_float(P.ctr[3]);
   const int W = (gridDim.x * blockDim.x) >> 5;
@@ -257,8 +264,10 @@ __device__ __forceinline__ bool pix_tuple_less(const EvDesc &ev, int stage, int 
 }
 
 // Round, part 3: each seed's choice among the objects of its best rank: the smallest hit tuple.
-__global__ void k_pix_pick(const EvDesc *__restrict__ evp, PixDesc P, int stage) {
-  const EvDesc &ev = *evp;
+__global__ void k_pix_pick(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const PixDesc &P = Ps[blockIdx.y];
+  if (P.ctr[PIX_DONE]) return;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
     const int n = min(P.pcnt[p], PIX_TIES);
     if (n == 0) continue;
@@ -272,7 +281,9 @@ __global__ void k_pix_pick(const EvDesc *__restrict__ evp, PixDesc P, int stage)
 }
 
 // Round, part 4: take the pairs that chose each other; clear the round's seed state.
-__global__ void k_pix_accept(PixDesc P, int stage) {
+__global__ void k_pix_accept(const PixDesc *Ps, int stage) {
+  const PixDesc &P = Ps[blockIdx.y];
+  if (P.ctr[PIX_DONE]) return;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
     const int p = P.op[base + o];
@@ -283,7 +294,9 @@ __global__ void k_pix_accept(PixDesc P, int stage) {
     }
   }
 }
-__global__ void k_pix_clear(PixDesc P) {
+__global__ void k_pix_clear(const PixDesc *Ps) {
+  const PixDesc &P = Ps[blockIdx.y];
+  if (P.ctr[PIX_DONE]) return;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
     P.pkey[p] = ~0ull;
     P.pcnt[p] = 0;
@@ -292,8 +305,9 @@ __global__ void k_pix_clear(PixDesc P) {
 }
 
 // MDs of the pT5 quintuplets
-__global__ void k_pix_mark(const EvDesc *__restrict__ evp, PixDesc P) {
-  const EvDesc &ev = *evp;
+__global__ void k_pix_mark(const EvDesc *__restrict__ evs, const PixDesc *Ps) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const PixDesc &P = Ps[blockIdx.y];
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.n_t5; o += gridDim.x * blockDim.x) {
     if (P.omatch[o] < 0) continue;
     const int4 a = ev.t5_a[o];
@@ -303,8 +317,9 @@ __global__ void k_pix_mark(const EvDesc *__restrict__ evp, PixDesc P) {
 }
 
 // Track candidates as rows (type, seed, object): 5 pT5, 6 T5 without a seed, 7 pT3, 8 pLS.
-__global__ void k_pix_rows(const EvDesc *__restrict__ evp, PixDesc P) {
-  const EvDesc &ev = *evp;
+__global__ void k_pix_rows(const EvDesc *__restrict__ evs, const PixDesc *Ps) {
+  const EvDesc &ev = evs[blockIdx.y];
+  const PixDesc &P = Ps[blockIdx.y];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
   auto emit = [&](int t, int p, int o) {
     const int r = atomicAdd(P.ctr + 1, 1);
@@ -321,31 +336,57 @@ __global__ void k_pix_rows(const EvDesc *__restrict__ evp, PixDesc P) {
     if (P.pmatch[p] < 0) emit(8, p, -1);
 }
 
-// Host-side launch helpers (all on `st`); rounds are driven by the caller.
-cudaError_t pix_launch_bin(PixDesc P, int grid, cudaStream_t st) {
-  if (P.n_pls > 0) {
-    k_pix_bin<<<grid, 256, 0, st>>>(P);
-    k_pix_scan<<<1, 1024, 0, st>>>(P);
-    k_pix_scatter<<<grid, 256, 0, st>>>(P);
-  } else {
-    k_pix_scan<<<1, 1024, 0, st>>>(P);
+// Stage bookkeeping per event (a thread per event): at the start of a stage an event takes
+// part unless it has no seeds or no objects of the stage; after each round an event whose
+// round took no pair is done with the stage (a further round would find the same), and
+// flags[e] reports done (1) and a tie-list overflow (2) to the host.
+__global__ void k_pix_stage_begin(const PixDesc *Ps, int n_events, int stage) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_events; e += gridDim.x * blockDim.x) {
+    const PixDesc &P = Ps[e];
+    P.ctr[0] = 0;
+    P.ctr[PIX_DONE] = P.n_pls == 0 || (stage == 5 ? P.n_t5 : P.n_t3) == 0;
   }
+}
+__global__ void k_pix_round_end(const PixDesc *Ps, int n_events, int stage, int *flags) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_events; e += gridDim.x * blockDim.x) {
+    const PixDesc &P = Ps[e];
+    if (!P.ctr[PIX_DONE]) {
+      P.ctr[stage == 5 ? PIX_ROUNDS5 : PIX_ROUNDS7]++;
+      if (P.ctr[0] == 0) P.ctr[PIX_DONE] = 1;
+      P.ctr[0] = 0;
+    }
+    flags[e] = (P.ctr[PIX_DONE] ? 1 : 0) | (P.ctr[2] ? 2 : 0);
+  }
+}
+
+// Host-side launch helpers for n events (all on `st`, grid x `grid` per event); rounds are
+// driven by the caller.
+cudaError_t pix_launch_bin(const PixDesc *Ps, int n, bool any_seeds, int grid, cudaStream_t st) {
+  if (any_seeds) k_pix_bin<<<dim3(grid, n), 256, 0, st>>>(Ps);
+  k_pix_scan<<<dim3(1, n), 1024, 0, st>>>(Ps);
+  if (any_seeds) k_pix_scatter<<<dim3(grid, n), 256, 0, st>>>(Ps);
   return cudaGetLastError();
 }
-cudaError_t pix_launch_round(const EvDesc *dd, PixDesc P, int stage, lst_pixel_cuts pc, int grid, cudaStream_t st) {
-  k_pix_propose<<<4 * grid, 256, 0, st>>>(dd, P, stage, pc);
-  k_pix_ties<<<4 * grid, 256, 0, st>>>(dd, P, stage, pc);
-  k_pix_pick<<<grid, 256, 0, st>>>(dd, P, stage);
-  k_pix_accept<<<grid, 256, 0, st>>>(P, stage);
-  k_pix_clear<<<grid, 256, 0, st>>>(P);
+cudaError_t pix_launch_stage_begin(const PixDesc *Ps, int n, int stage, cudaStream_t st) {
+  k_pix_stage_begin<<<(n + 255) / 256, 256, 0, st>>>(Ps, n, stage);
   return cudaGetLastError();
 }
-cudaError_t pix_launch_mark(const EvDesc *dd, PixDesc P, int grid, cudaStream_t st) {
-  k_pix_mark<<<grid, 256, 0, st>>>(dd, P);
+cudaError_t pix_launch_round(const EvDesc *dd, const PixDesc *Ps, int n, int stage, lst_pixel_cuts pc, int grid,
+                             int *flags, cudaStream_t st) {
+  k_pix_propose<<<dim3(4 * grid, n), 256, 0, st>>>(dd, Ps, stage, pc);
+  k_pix_ties<<<dim3(4 * grid, n), 256, 0, st>>>(dd, Ps, stage, pc);
+  k_pix_pick<<<dim3(grid, n), 256, 0, st>>>(dd, Ps, stage);
+  k_pix_accept<<<dim3(grid, n), 256, 0, st>>>(Ps, stage);
+  k_pix_clear<<<dim3(grid, n), 256, 0, st>>>(Ps);
+  k_pix_round_end<<<(n + 255) / 256, 256, 0, st>>>(Ps, n, stage, flags);
   return cudaGetLastError();
 }
-cudaError_t pix_launch_rows(const EvDesc *dd, PixDesc P, int grid, cudaStream_t st) {
-  k_pix_rows<<<grid, 256, 0, st>>>(dd, P);
+cudaError_t pix_launch_mark(const EvDesc *dd, const PixDesc *Ps, int n, int grid, cudaStream_t st) {
+  k_pix_mark<<<dim3(grid, n), 256, 0, st>>>(dd, Ps);
+  return cudaGetLastError();
+}
+cudaError_t pix_launch_rows(const EvDesc *dd, const PixDesc *Ps, int n, int grid, cudaStream_t st) {
+  k_pix_rows<<<dim3(grid, n), 256, 0, st>>>(dd, Ps);
   return cudaGetLastError();
 }
 

@@ -107,6 +107,7 @@ _SIGS = {
     "lst_test_skip_mma": [C.c_void_p, C.c_int32],
     "lst_test_fail_alloc": [C.c_void_p, C.c_int32],
     "lst_match_pixel_seeds": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "lst_match_pixel_seeds_batch": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "lst_get_pixel_candidates": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
     "lst_get_launch": [C.c_void_p, C.POINTER(lst_launch)],
     "lst_set_launch": [C.c_void_p, C.POINTER(lst_launch)],
@@ -398,6 +399,29 @@ class Context:
         _check(lib.lst_run_batch(self.h, n, xs, ys, zs, ss, nh, _stream_handle(stream), out),
                "lst_run_batch")
         return [Event(self, C.c_void_p(out[i]), LST_ERR_NOT_READY) for i in range(n)]
+
+    def match_pixel_seeds_batch(self, events, seeds, pcuts: dict) -> list:
+        """lst_match_pixel_seeds_batch: seeds[i] (float32 [n][4][3], numpy or a CUDA tensor)
+        for events[i]; returns the counts per event. Each event's rows are then read with
+        its pixel_candidates()."""
+        n = len(events)
+        keep, ptrs = [], (C.c_void_p * n)()
+        ns = (C.c_int64 * n)()
+        for i, sd in enumerate(seeds):
+            if hasattr(sd, "data_ptr"):
+                assert sd.dtype.itemsize == 4 and sd.is_contiguous() and sd.numel() % 12 == 0
+                ns[i] = int(sd.numel()) // 12
+            else:
+                sd = np.ascontiguousarray(sd, np.float32).reshape(-1, 12)
+                ns[i] = sd.shape[0]
+            keep.append(sd)
+            ptrs[i] = _ptr(sd) if ns[i] else None
+        evs = (C.c_void_p * n)(*[e.h for e in events])
+        cnt = (lst_pixel_counts * n)()
+        pc = pixel_cuts_struct(pcuts)
+        _check(load_library().lst_match_pixel_seeds_batch(evs, n, ptrs, ns, C.byref(pc), cnt),
+               "lst_match_pixel_seeds_batch")
+        return [{f: getattr(c, f) for f, _ in lst_pixel_counts._fields_} for c in cnt]
 
     def candidates_batch(self, events, kind: int, out=None, score=None, selected=None):
         """Objects of several events in one call (lst_get_candidates_batch): returns (hits,

@@ -83,3 +83,30 @@ def test_pixel_without_seeds_and_after_a_batch(ctx, geom_full):
         ev.pixel_candidates()
     assert ei.value.status == lst.LST_ERR_NOT_READY
     ev.release()
+
+
+def test_pixel_batch_equals_the_oracle(ctx, geom_full):
+    """lst_match_pixel_seeds_batch over a batch of events of uneven size (one without seeds)
+    gives each event the oracle's track candidates, as a single call would; counts per event."""
+    ev_in = [synth.pileup_event(geom_full, 20 + k, pileup=pu, mean_per_vertex=96) for k, pu in enumerate((60, 10, 120))]
+    seeds = [synth.pixel_seeds(e) for e in ev_in]
+    hs = ctx.run_batch([_dev(e) for e in ev_in])
+    assert all(h.counts()["status"] == lst.LST_OK for h in hs)
+    seed_arrays = [seeds[0].hits, np.zeros((0, 4, 3), np.float32), torch.from_numpy(seeds[2].hits).cuda()]
+    cnts = ctx.match_pixel_seeds_batch(hs, seed_arrays, PC)
+    for k, (e, h, cnt) in enumerate(zip(ev_in, hs, cnts)):
+        sd = seeds[k].hits if k != 1 else np.zeros((0, 4, 3), np.float32)
+        ref = oracle.run_event(geom_full, e, _cuts(), synth.mlp_flat(synth.xavier_mlp()), 2, pls=sd, pcuts=PC)
+        got = _gpu_tuples(h, h.pixel_candidates())
+        assert got == sorted(ref.pixel_tcs())
+        assert cnt["n_rows"] == len(got)
+        if k == 1:
+            assert cnt["n_pt5"] == cnt["n_pt3"] == cnt["n_pls"] == 0 and cnt["rounds_pt5"] == 0
+        else:
+            assert cnt["n_pt5"] > 0 and cnt["rounds_pt5"] >= 2
+    # the same event twice is an argument error
+    with pytest.raises(lst.LstError) as ei:
+        ctx.match_pixel_seeds_batch([hs[0], hs[0]], [seeds[0].hits, seeds[0].hits], PC)
+    assert ei.value.status == lst.LST_ERR_ARG
+    for h in hs:
+        h.release()
