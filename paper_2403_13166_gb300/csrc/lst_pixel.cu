@@ -166,10 +166,13 @@ __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P
       const int b1 = k == 0 ? min(first + span, PIX_NPHI) : first + span - PIX_NPHI;
       const int q0 = P.cell_off[row * PIX_NPHI + b0], q1 = P.cell_off[row * PIX_NPHI + b1];
       for (int q = q0 + lane; q < q1; q += 32) {
+        // the seed's curvature first: the pT test rejects most seeds of a window, from one load
+        const float4 A = P.sa[q];
+        if (!pix_kappa_ok(A.w, ko, pc)) continue;
         const int p = P.sidx[q];
         if (P.pmatch[p] >= 0) continue;
         float res, dk;
-        if (pix_match(P.sa[q], P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk)) f(p, res, dk);
+        if (pix_match(A, P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk)) f(p, res, dk);
       }
     }
   }

@@ -246,3 +246,4 @@ def test_ls_q_window_prunes(event, geom_full, cuts):
                 full_steps += 32 * n4
                 run_steps += 32 * (n4 if len(ch) <= 8 else (k + 3) // 4 * 4)
     assert full_steps > 1_000_000 and run_steps < 0.75 * full_steps, run_steps / full_steps
+
