@@ -1219,6 +1219,7 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
     const size_t o_pkey = take(8 * npl), o_pcnt = take(4 * npl), o_plist = take(4 * (size_t)PIX_TIES * npl);
     const size_t o_pobj = take(4 * npl), o_pmatch = take(4 * npl);
     const size_t o_okey = take(8 * no), o_op = take(4 * no), o_omatch = take(4 * no), o_md = take((size_t)nmd);
+    const size_t o_ocnt = take(4 * no), o_oseed = take(4 * (size_t)PIX_OCAP * no), o_okeys = take(8 * (size_t)PIX_OCAP * no);
     const size_t o_rows = take(12 * (no + npl)), o_ctr = take(4 * PIX_NCTR);
     if (S.pix_bytes < off) {
       CU(cudaDeviceSynchronize());
@@ -1239,8 +1240,10 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
     Q.pobj = (int *)(b + o_pobj); Q.pmatch = (int *)(b + o_pmatch);
     Q.okey = (unsigned long long *)(b + o_okey); Q.op = (int *)(b + o_op); Q.omatch = (int *)(b + o_omatch);
     Q.mdflag = (uint8_t *)(b + o_md); Q.rows = (int *)(b + o_rows); Q.ctr = (int *)(b + o_ctr);
+    Q.ocnt = (int *)(b + o_ocnt); Q.oseed = (int *)(b + o_oseed); Q.okeys = (unsigned long long *)(b + o_okeys);
     CU(cudaMemsetAsync(Q.cell_cnt, 0, 4 * (size_t)PIX_NCELL, st));
     CU(cudaMemsetAsync(Q.omatch, 0xff, 4 * std::max<size_t>(no, 1), st));
+    CU(cudaMemsetAsync(Q.ocnt, 0xff, 4 * std::max<size_t>(no, 1), st));
     CU(cudaMemsetAsync(Q.mdflag, 0, std::max(nmd, 1), st));
     CU(cudaMemsetAsync(Q.ctr, 0, 4 * PIX_NCTR, st));
     CU(cudaMemsetAsync(Q.ctr + 3, 0x7f, 4, st));          // smallest seed radius: +huge until binned

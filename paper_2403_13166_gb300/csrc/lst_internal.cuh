@@ -99,6 +99,9 @@ struct PixDesc {
   unsigned long long *okey;       // [n_t5 + n_t3] the round's best rank at the object
   int *op;                        // [n_t5 + n_t3] and its seed
   int *omatch;                    // [n_t5 + n_t3] matched seed; -1 free, -2 out of the matching
+  int *ocnt;                      // [n_t5 + n_t3] the object's cached candidates: -1 none yet,
+  int *oseed;                     //   PIX_OCAP + 1 too many (scan the windows), else their number;
+  unsigned long long *okeys;      //   [n_t5 + n_t3][PIX_OCAP] their seeds and ranks
   uint8_t *mdflag;                // [n_md] MD of a pT5's T5
   int *rows;                      // [n_t5 + n_t3 + n_pls][3] track candidates
   int *ctr;                       // [16]: taken this round, rows, tie overflow, bits of the
@@ -108,6 +111,7 @@ struct PixDesc {
 constexpr int PIX_DONE = 8, PIX_ROUNDS5 = 9, PIX_ROUNDS7 = 10, PIX_NCTR = 16;
 constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
 constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)
+constexpr int PIX_OCAP = 8;                     // candidate seeds cached per object
 
 // ------------------------------------------------------------------ FP32 cut arithmetic
 // Step 1 (Section 1, Table 1): two hits of one pT-module, pT above 0.8 GeV and inside the

@@ -140,7 +140,8 @@ __device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, i
 }
 
 // Visit every free seed in the object's windows that matches it, the lanes of a warp taking
-// the candidates in turn: f(p, res, dk) on the lane that tested the pair. The azimuth window
+// the candidates 32 at a time: f(hit, p, res, dk) on every lane at every step (warp-uniform,
+// so f may vote), hit telling whether the lane's seed matched. The azimuth window
 // is the turn the cut allows at this radius from the smallest seed radius r4min (its sine
 // bound, arcsine, plus one bin for rounding); the slope window its rows plus one on each side.
 template <typename F>
@@ -165,14 +166,20 @@ __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P
       const int b0 = k == 0 ? first : 0;
       const int b1 = k == 0 ? min(first + span, PIX_NPHI) : first + span - PIX_NPHI;
       const int q0 = P.cell_off[row * PIX_NPHI + b0], q1 = P.cell_off[row * PIX_NPHI + b1];
-      for (int q = q0 + lane; q < q1; q += 32) {
-        // the seed's curvature first: the pT test rejects most seeds of a window, from one load
-        const float4 A = P.sa[q];
-        if (!pix_kappa_ok(A.w, ko, pc)) continue;
-        const int p = P.sidx[q];
-        if (P.pmatch[p] >= 0) continue;
-        float res, dk;
-        if (pix_match(A, P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk)) f(p, res, dk);
+      for (int qb = q0; qb < q1; qb += 32) {
+        const int q = qb + lane;
+        bool hit = false;
+        int p = -1;
+        float res = 0.0f, dk = 0.0f;
+        if (q < q1) {
+          // the seed's curvature first: the pT test rejects most seeds of a window, from one load
+          const float4 A = P.sa[q];
+          if (pix_kappa_ok(A.w, ko, pc)) {
+            p = P.sidx[q];
+            hit = P.pmatch[p] < 0 && pix_match(A, P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk);
+          }
+        }
+        f(hit, p, res, dk);
       }
     }
   }
@@ -183,7 +190,11 @@ __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
 }
 
 // Round, part 1 (a warp per object): each free object's best free seed (rank, then seed
-// index) and, at each seed, the best rank over its free objects.
+// index) and, at each seed, the best rank over its free objects. The first round of a stage
+// scans the object's windows and caches its candidates (PIX_OCAP at most; an object with
+// more keeps scanning); later rounds and part 2 read the cache, dropping seeds taken since
+// (seeds only leave the free pool and the match of a pair does not change, so the
+// candidates are the same as a scan's).
 __global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
@@ -193,16 +204,42 @@ __global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps,
   const float r4min = __int_as_float(P.ctr[3]);
   const int W = (gridDim.x * blockDim.x) >> 5;
   for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
+    const int g = base + o;
+    if (P.omatch[g] != -1) continue;               // taken or out (warp-uniform)
     unsigned long long best = ~0ull;
     int bp = 0x7fffffff;
-    float4 P0, P1;
-    float ko;
-    if (P.omatch[base + o] == -1 && pix_object(ev, P, stage, o, P0, P1, ko))
-      pix_scan_object(P, P0, P1, ko, pc, r4min, [&](int p, float res, float dk) {
-        const unsigned long long k = pix_key(res, dk);
-        atomicMin(P.pkey + p, k);
-        if (k < best || (k == best && p < bp)) { best = k; bp = p; }
-      });
+    auto consider = [&](int p, unsigned long long k) {
+      atomicMin(P.pkey + p, k);
+      if (k < best || (k == best && p < bp)) { best = k; bp = p; }
+    };
+    const int cached = P.ocnt[g];
+    if (cached >= 0 && cached <= PIX_OCAP) {
+      for (int j = lane; j < cached; j += 32) {
+        const int p = P.oseed[(size_t)g * PIX_OCAP + j];
+        if (P.pmatch[p] < 0) consider(p, P.okeys[(size_t)g * PIX_OCAP + j]);
+      }
+    } else {
+      float4 P0, P1;
+      float ko;
+      if (pix_object(ev, P, stage, o, P0, P1, ko)) {
+        const bool build = cached == -1;
+        int cnt = 0;
+        pix_scan_object(P, P0, P1, ko, pc, r4min, [&](bool hit, int p, float res, float dk) {
+          const unsigned long long k = pix_key(res, dk);
+          if (hit) consider(p, k);
+          if (build) {
+            const unsigned m = __ballot_sync(FULL, hit);
+            const int at = cnt + __popc(m & lanemask_lt());
+            if (hit && at < PIX_OCAP) {
+              P.oseed[(size_t)g * PIX_OCAP + at] = p;
+              P.okeys[(size_t)g * PIX_OCAP + at] = k;
+            }
+            cnt += __popc(m);
+          }
+        });
+        if (build && lane == 0) P.ocnt[g] = min(cnt, PIX_OCAP + 1);
+      }
+    }
 #pragma unroll
     for (int s = 16; s; s >>= 1) {                 // the warp's minimum of (rank, seed)
       const unsigned long long ob = __shfl_xor_sync(FULL, best, s);
@@ -210,10 +247,10 @@ __global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps,
       if (ob < best || (ob == best && op < bp)) { best = ob; bp = op; }
     }
     if (lane == 0) {
-      P.okey[base + o] = best;
-      P.op[base + o] = best == ~0ull ? -1 : bp;
+      P.okey[g] = best;
+      P.op[g] = best == ~0ull ? -1 : bp;
       // no free seed matches it now, so none will later (seeds only leave): out for good
-      if (best == ~0ull && P.omatch[base + o] == -1) P.omatch[base + o] = -2;
+      if (best == ~0ull) P.omatch[g] = -2;
     }
   }
 }
@@ -224,22 +261,35 @@ __global__ void k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, in
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
   if (P.ctr[PIX_DONE]) return;
+  const int lane = threadIdx.x & 31;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   const float r4min = __int_as_float(P.ctr[3]);
   const int W = (gridDim.x * blockDim.x) >> 5;
   for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
-    if (P.okey[base + o] == ~0ull) continue;       // no free seed matches it (warp-uniform)
-    float4 P0, P1;
-    float ko;
-    if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
-    pix_scan_object(P, P0, P1, ko, pc, r4min, [&](int p, float res, float dk) {
-      if (pix_key(res, dk) != P.pkey[p]) return;
+    const int g = base + o;
+    if (P.okey[g] == ~0ull || P.omatch[g] != -1) continue;   // no free seed matches it (warp-uniform)
+    auto list_at = [&](int p, unsigned long long k) {
+      if (k != P.pkey[p]) return;
       const int s = atomicAdd(P.pcnt + p, 1);
       if (s < PIX_TIES)
         P.plist[PIX_TIES * (size_t)p + s] = o;
       else
         atomicOr(P.ctr + 2, 1);
-    });
+    };
+    const int cached = P.ocnt[g];
+    if (cached >= 0 && cached <= PIX_OCAP) {
+      for (int j = lane; j < cached; j += 32) {
+        const int p = P.oseed[(size_t)g * PIX_OCAP + j];
+        if (P.pmatch[p] < 0) list_at(p, P.okeys[(size_t)g * PIX_OCAP + j]);
+      }
+    } else {
+      float4 P0, P1;
+      float ko;
+      if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
+      pix_scan_object(P, P0, P1, ko, pc, r4min, [&](bool hit, int p, float res, float dk) {
+        if (hit) list_at(p, pix_key(res, dk));
+      });
+    }
   }
 }
 
