@@ -475,8 +475,9 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
         h.release()
     out["batched_same_pool_per_s"] = round(10 * args.batch / (e0.elapsed_time(e1) / 1000.0), 1)
     del d_pool, batch_in
+    slot_hits = int(1.2 * max(len(e[0]) for e in pinned))     # every slot sized for the pool's events
     srv = lst.Server(ctx, max_batch=args.served_max_batch, lanes=2, mem_budget_bytes=int(args.served_mem_gb * 2**30),
-                     copy_t5=True)
+                     copy_t5=True, slot_hits=slot_hits)
     # warm-up: one burst (captures the graphs for the batch sizes seen first)
     for k in range(2 * args.batch):
         e = pinned[k % len(pinned)]
@@ -485,7 +486,12 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
     while got < 2 * args.batch:
         got += len(srv.poll(wait_ms=100, keep_t5=False))
     tag = 10**6
+    import gc
     for rate in args.served_rates:
+        # no garbage-collection pause of this client inside a rate's window (arrival times are
+        # the scheduled ones, so a stalled client would show as server latency)
+        gc.collect()
+        gc.disable()
         n = max(50, int(rate * args.served_seconds))
         gaps = rng.exponential(1.0 / rate, n)
         t0 = lst.clock() + 0.01
@@ -503,6 +509,7 @@ def run_served(args, pool, g, cuts, flat, nh, local_rank):
             srv.submit(*e, tag=tag + k, t_arrival=float(arr[k]))
         while len(res) < n:
             res.extend(srv.poll(wait_ms=100, keep_t5=False))
+        gc.enable()
         tag += n
         lat = np.array([r["t_done"] - r["t_arrival"] for r in res]) * 1000.0
         ok = all(r["status"] == lst.LST_OK for r in res)

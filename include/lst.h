@@ -310,7 +310,9 @@ typedef struct lst_serve_config {
     int32_t lanes;              /* batches in flight: 1 or 2 */
     int64_t mem_budget_bytes;   /* admission budget (estimated device bytes of admitted events) */
     int32_t copy_t5;            /* 1: results carry the T5 hit tuples, scores, selection */
-    int32_t reserved;
+    int32_t slot_hits;          /* > 0: every event slot is sized at start for this many hits
+                                   (growing a slot while serving can pause the workers for
+                                   the memory mapping); 0: slots are sized as events need */
 } lst_serve_config;
 
 typedef struct lst_serve_result {

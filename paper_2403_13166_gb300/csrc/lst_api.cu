@@ -1630,33 +1630,38 @@ void serve_finish(lst_server_s *S, ServeReq &r, lst_status status, const int32_t
   S->cv.notify_all();
 }
 
-// A stage with room for n T5 rows and no pending results (grown or added if none).
+// A pinned stage of cap T5 rows (nullptr if the host memory is not available).
+ServeStage *stage_new(int64_t cap) {
+  ServeStage *g = new ServeStage();
+  if (cudaMallocHost(&g->hits, (size_t)cap * 10 * 4) == cudaSuccess &&
+      cudaMallocHost(&g->score, (size_t)cap * 4) == cudaSuccess && cudaMallocHost(&g->sel, (size_t)cap) == cudaSuccess) {
+    g->cap = cap;
+    return g;
+  }
+  stage_free(g);
+  return nullptr;
+}
+
+// A stage with room for n T5 rows and no pending results. The server starts with stages
+// for full batches; should none fit, a larger one is added (with headroom) and kept: pinned
+// allocations are slow and freeing pinned memory waits for the device, so neither happens
+// on this path once the stages cover the batches seen.
 ServeStage *serve_stage(lst_server_s *S, int64_t n) {
-  ServeStage *free_small = nullptr;
   {
     std::lock_guard<std::mutex> lk(S->mu);
+    ServeStage *fit = nullptr;
     for (ServeStage *g : S->stages) {
       std::lock_guard<std::mutex> gl(g->m);
-      if (g->pending) continue;
-      if (g->cap >= n) return g;
-      free_small = g;
+      if (g->pending || g->cap < n) continue;
+      if (!fit || g->cap < fit->cap) fit = g;           // the smallest that fits
     }
+    if (fit) return fit;
   }
-  ServeStage *g = free_small;
-  if (!g) {
-    g = new ServeStage();
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->stages.push_back(g);
-  }
-  cudaFreeHost(g->hits);
-  cudaFreeHost(g->score);
-  cudaFreeHost(g->sel);
-  g->hits = nullptr; g->score = nullptr; g->sel = nullptr; g->cap = 0;
-  const int64_t cap = n + n / 4 + 1024;
-  if (cudaMallocHost(&g->hits, (size_t)cap * 10 * 4) == cudaSuccess &&
-      cudaMallocHost(&g->score, (size_t)cap * 4) == cudaSuccess && cudaMallocHost(&g->sel, (size_t)cap) == cudaSuccess)
-    g->cap = cap;
-  return g->cap >= n ? g : nullptr;
+  ServeStage *g = stage_new(n + n / 2 + 1024);
+  if (!g) return nullptr;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->stages.push_back(g);
+  return g;
 }
 
 // Finish the requests of one lane batch: the T5 results of every successful event are
@@ -1867,6 +1872,7 @@ lst_status lst_serve_start(lst_ctx c, const lst_serve_config *cfg, lst_server *o
   if (cfg->max_batch < 1 || cfg->max_batch > (int)c->slots.size())
     return fail(LST_ERR_ARG, "max_batch outside 1..max_events");
   if (cfg->mem_budget_bytes <= 0) return fail(LST_ERR_ARG, "mem_budget_bytes <= 0");
+  if (cfg->slot_hits < 0 || cfg->slot_hits > 1 << 30) return fail(LST_ERR_ARG, "slot_hits outside 0..2^30");
   DeviceGuard gd(c->device);
   for (auto &L : c->lanes) {
     lst_status s = lane_harvest(c, L);
@@ -1874,6 +1880,37 @@ lst_status lst_serve_start(lst_ctx c, const lst_serve_config *cfg, lst_server *o
   }
   for (auto &sl : c->slots)
     if (sl.busy) return fail(LST_ERR_NOT_READY, "release every event before serving");
+  // slot buffers of earlier plain allocations go now (freeing them waits for the device),
+  // so that served slots grow within the pool only
+  for (auto &sl : c->slots) {
+    if (sl.mem && !sl.mem_pooled) {
+      CU(slot_buf_free(sl.mem, 0, false));
+      sl.mem = nullptr;
+      sl.bytes = 0;
+      sl.hit_cap = 0; sl.md_cap = sl.ls_cap = sl.t3_cap = sl.t5_cap = 0;
+    }
+    if (sl.in_mem && !sl.in_pooled) {
+      CU(slot_buf_free(sl.in_mem, 0, false));
+      sl.in_mem = nullptr;
+      sl.in_cap = 0;
+    }
+  }
+  if (cfg->slot_hits > 0) {
+    for (auto &sl : c->slots) {
+      lst_status as = slot_alloc(c, sl, cfg->slot_hits, 0, true);
+      if (as != LST_OK) return as;
+      if (sl.in_cap < cfg->slot_hits) {
+        if (sl.in_mem) CU(slot_buf_free(sl.in_mem, 0, sl.in_pooled));
+        sl.in_mem = nullptr;
+        sl.in_cap = 0;
+        const int64_t cap = (int64_t)(cfg->slot_hits * 1.1) + 1024;
+        CU(slot_buf_alloc(c, &sl.in_mem, (size_t)cap * 16, 0, true));
+        sl.in_cap = cap;
+        sl.in_pooled = true;
+      }
+    }
+    CU(cudaStreamSynchronize(0));
+  }
   lst_server_s *S = new lst_server_s();
   S->c = c;
   S->cfg = *cfg;
@@ -1897,6 +1934,16 @@ lst_status lst_serve_start(lst_ctx c, const lst_serve_config *cfg, lst_server *o
           return gs;
         }
       }
+  }
+  // pinned staging for the results of full batches, two per lane (batches in flight and
+  // results not yet freed by the caller), sized from the PU200-like T5 count per event
+  if (cfg->copy_t5) {
+    const int nl = std::max(1, std::min(2, cfg->lanes));
+    for (int k = 0; k < 2 * nl; k++) {
+      ServeStage *g = stage_new((int64_t)cfg->max_batch * 50000);
+      if (!g) break;                                   // added later as batches need them
+      S->stages.push_back(g);
+    }
   }
   S->th = std::thread(serve_loop, S);
   S->th_done = std::thread(serve_complete_loop, S);

@@ -563,7 +563,7 @@ def header_symbols(header_path: str):
 # ------------------------------------------------------------------ serving
 class lst_serve_config(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("lanes", C.c_int32), ("mem_budget_bytes", C.c_int64),
-                ("copy_t5", C.c_int32), ("reserved", C.c_int32)]
+                ("copy_t5", C.c_int32), ("slot_hits", C.c_int32)]
 
 
 class lst_serve_result(C.Structure):
@@ -598,9 +598,9 @@ def clock() -> float:
 class Server:
     """lst_serve_*: continuous batching of events submitted one at a time (host arrays)."""
 
-    def __init__(self, ctx: Context, max_batch=32, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True):
+    def __init__(self, ctx: Context, max_batch=32, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True, slot_hits=0):
         lib = _serve_sigs(load_library())
-        cfg = lst_serve_config(int(max_batch), int(lanes), int(mem_budget_bytes), int(bool(copy_t5)), 0)
+        cfg = lst_serve_config(int(max_batch), int(lanes), int(mem_budget_bytes), int(bool(copy_t5)), int(slot_hits))
         h = C.c_void_p()
         _check(lib.lst_serve_start(ctx.h, C.byref(cfg), C.byref(h)), "lst_serve_start")
         self.h = h

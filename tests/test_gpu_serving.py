@@ -115,7 +115,9 @@ def test_results_point_into_staging_and_outlive_the_server(geom_full, cuts):
 
     ctx = lst.Context(0, max_events=4, precision=lst.LST_BF16X3)
     ctx.load_geometry(geom_full, cuts, w, 2)
-    srv = lst.Server(ctx, max_batch=2, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True)
+    # every slot sized at start (slot_hits), as a latency-sensitive server would
+    srv = lst.Server(ctx, max_batch=2, lanes=2, mem_budget_bytes=8 << 30, copy_t5=True,
+                     slot_hits=int(1.2 * max(len(e.x) for e in events)))
     lib = lst.load_library()
     # many batches through, results freed as they come (the staging is reused)
     for k in range(24):
