@@ -234,7 +234,7 @@ struct lst_event_s {
 
 namespace {
 
-constexpr int LS_WARP_BYTES = 4944;     // sizeof(LsWarp): each warp's targets, inner MDs and pair queue
+constexpr int LS_WARP_BYTES = 5456;     // sizeof(LsWarp): each warp's targets, inner MDs and pair queue
 constexpr int LS_SMALL_TB = 8;          // target modules per step-2 unit in small launches
 size_t ls_smem(const lst_ctx_s *c) { return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES; }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }

@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(256) k_md_sort(const EvDesc *__restrict__ evs,
 // of its outer MD (the values of the counting atomicAdds); k_ls_scan / k_ls_scatter then
 // list every LS by inner MD (its outer MD) and by outer MD (its inner MD).
 constexpr int LS_IN_CHUNK = 64;
+constexpr int LS_QCAP = 320;             // pairs the first queue holds (a sub-chunk's survivors at once)
 constexpr int LS_WINDOW_MIN = 8;         // chunks of more inner MDs than this are windowed
 constexpr int LS_TB = 160;                 // target modules per batch of the warp's table
 struct LsWarp {
@@ -398,11 +399,11 @@ struct LsWarp {
   int md[32];
   int tpref[LS_TB + 4];                    // MD-count prefix over the target modules
   int tstart[LS_TB];
-  unsigned short q[64];                    // queued pairs: inner index << 5 | target lane
+  unsigned short q[LS_QCAP];               // queued pairs: inner index << 5 | target lane
   unsigned char bB[32];
   unsigned char tbar[LS_TB];
 };
-static_assert(sizeof(LsWarp) == 4944, "the host sizes k_ls shared memory with 4944 bytes per warp");
+static_assert(sizeof(LsWarp) == 5456, "the host sizes k_ls shared memory with 5456 bytes per warp");
 
 // Units: with unit_off == nullptr one unit per module (all its targets); otherwise
 // unit_off[m] .. unit_off[m + 1] are the units of module m, unit b taking the target
@@ -549,11 +550,11 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           w.bB[lane] = bB ? 1 : 0;
           __syncwarp();
           // curvature test of the first n queued pairs; survivors join the second queue
-          auto run_kappa = [&](int n) {
+          auto run_kappa = [&](int off, int n) {       // the queued pairs [off, off + n)
             bool pass = false;
             int2 ent = make_int2(0, 0);
             if (lane < n) {
-              const int qe = w.q[lane];
+              const int qe = w.q[off + lane];
               const int ie = qe >> 5, le = qe & 31;
               const bool b2 = w.bB[le] != 0;
               pass = ls_kappa_prefilter(w.in[ie], w.B[le], w.ink[ie], w.kB[le], bA, b2, Gp, ce);
@@ -623,28 +624,56 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
                 mask |= bits << i;
               }
             }
-            for (;;) {
-              const unsigned act = __ballot_sync(FULL, mask != 0);
-              if (act == 0) break;
-              if (mask != 0) {
+            // the sub-chunk's survivors into the queue at once: each lane writes its own after
+            // the warp's prefix of the counts; then the curvature test on full runs of 32
+            const int cntl = __popc(mask);
+            const int incl = warp_incl_scan(cntl);
+            const int T = __shfl_sync(FULL, incl, 31);
+            if (qn + T <= LS_QCAP) {
+              int pos = qn + incl - cntl;
+              while (mask != 0) {
                 const int i = __ffs(mask) - 1;
                 mask &= mask - 1;
-                w.q[qn + __popc(act & lanemask_lt())] = (unsigned short)(((i0 + i) << 5) | lane);
+                w.q[pos++] = (unsigned short)(((i0 + i) << 5) | lane);
               }
-              qn += __popc(act);
-              if (qn >= 32) {
+              qn += T;
+              __syncwarp();
+              int off = 0;
+              for (; qn - off >= 32; off += 32) {
+                run_kappa(off, 32);
                 __syncwarp();
-                run_kappa(32);
+              }
+              if (off > 0) {                           // the rest (< 32) to the front
+                const unsigned short v = lane < qn - off ? w.q[off + lane] : 0;
                 __syncwarp();
-                if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
+                if (lane < qn - off) w.q[lane] = v;
                 __syncwarp();
-                qn -= 32;
+                qn -= off;
+              }
+            } else {                                   // too many at once: one per lane and round
+              for (;;) {
+                const unsigned act = __ballot_sync(FULL, mask != 0);
+                if (act == 0) break;
+                if (mask != 0) {
+                  const int i = __ffs(mask) - 1;
+                  mask &= mask - 1;
+                  w.q[qn + __popc(act & lanemask_lt())] = (unsigned short)(((i0 + i) << 5) | lane);
+                }
+                qn += __popc(act);
+                if (qn >= 32) {
+                  __syncwarp();
+                  run_kappa(0, 32);
+                  __syncwarp();
+                  if (lane + 32 < qn) w.q[lane] = w.q[lane + 32];
+                  __syncwarp();
+                  qn -= 32;
+                }
               }
             }
           }
           if (qn > 0) {
             __syncwarp();
-            run_kappa(qn);
+            run_kappa(0, qn);
           }
         }
       }
