@@ -51,6 +51,7 @@ cudaError_t launch_score_bf16_features(int, cudaStream_t, DevGeom, lst_cuts, con
                                        const float *, int64_t, float *, int *, long long, bool split, int skip_mma);
 int score_bf16_blocks_per_sm(bool split);
 cudaError_t pix_launch_bin(const PixDesc *, int, bool, int, cudaStream_t);
+cudaError_t pix_launch_rebin(const PixDesc *, int, bool, int, cudaStream_t);
 cudaError_t pix_launch_stage_begin(const PixDesc *, int, int, cudaStream_t);
 cudaError_t pix_launch_round(const EvDesc *, const PixDesc *, int, int, lst_pixel_cuts, int, int *, cudaStream_t);
 cudaError_t pix_launch_mark(const EvDesc *, const PixDesc *, int, int, cudaStream_t);
@@ -1215,7 +1216,7 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + std::max<size_t>(b, 1), 256); return o; };
     const size_t o_hits = take(48 * npl), o_cell = take(4 * npl), o_rank = take(4 * npl);
     const size_t o_ccnt = take(4 * (size_t)PIX_NCELL), o_coff = take(4 * ((size_t)PIX_NCELL + 1));
-    const size_t o_sa = take(16 * npl), o_sb = take(16 * npl), o_sm = take(4 * npl), o_sidx = take(4 * npl);
+    const size_t o_sa = take(16 * npl), o_sb = take(16 * npl), o_sm = take(4 * npl), o_sk = take(4 * npl), o_sidx = take(4 * npl);
     const size_t o_pkey = take(8 * npl), o_pcnt = take(4 * npl), o_plist = take(4 * (size_t)PIX_TIES * npl);
     const size_t o_pobj = take(4 * npl), o_pmatch = take(4 * npl);
     const size_t o_okey = take(8 * no), o_op = take(4 * no), o_omatch = take(4 * no), o_md = take((size_t)nmd);
@@ -1235,7 +1236,7 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
     Q.hits = (const float *)(b + o_hits);
     Q.cell = (int *)(b + o_cell); Q.rank = (int *)(b + o_rank);
     Q.cell_cnt = (int *)(b + o_ccnt); Q.cell_off = (int *)(b + o_coff);
-    Q.sa = (float4 *)(b + o_sa); Q.sb = (float4 *)(b + o_sb); Q.sm = (float *)(b + o_sm); Q.sidx = (int *)(b + o_sidx);
+    Q.sa = (float4 *)(b + o_sa); Q.sb = (float4 *)(b + o_sb); Q.sm = (float *)(b + o_sm); Q.sk = (float *)(b + o_sk); Q.sidx = (int *)(b + o_sidx);
     Q.pkey = (unsigned long long *)(b + o_pkey); Q.pcnt = (int *)(b + o_pcnt); Q.plist = (int *)(b + o_plist);
     Q.pobj = (int *)(b + o_pobj); Q.pmatch = (int *)(b + o_pmatch);
     Q.okey = (unsigned long long *)(b + o_okey); Q.op = (int *)(b + o_op); Q.omatch = (int *)(b + o_omatch);
@@ -1266,7 +1267,10 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
   auto run = [&]() -> lst_status {
     CU(pix_launch_bin(dP, n, any_seeds, grid, st));
     for (int stage : {5, 7}) {
-      if (stage == 7) CU(pix_launch_mark(dD, dP, n, grid, st));
+      if (stage == 7) {
+        CU(pix_launch_mark(dD, dP, n, grid, st));
+        CU(pix_launch_rebin(dP, n, any_seeds, grid, st));
+      }
       CU(pix_launch_stage_begin(dP, n, stage, st));
       for (int round = 0; round < 1 << 20; round++) {
         CU(pix_launch_round(dD, dP, n, stage, *pc, grid, dflags, st));

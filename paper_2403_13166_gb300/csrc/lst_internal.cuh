@@ -91,6 +91,7 @@ struct PixDesc {
   int *cell_cnt, *cell_off;       // [PIX_NCELL], [PIX_NCELL + 1]
   float4 *sa, *sb;                // [n_pls] in bin order: (x1, y1, z1, kp), (x4, y4, z4, r4)
   float *sm;                      // [n_pls] in bin order: r-z slope m_p
+  float *sk;                      // [n_pls] in bin order: the seed's curvature kp (sa's w, packed)
   int *sidx;                      // [n_pls] in bin order: seed index
   unsigned long long *pkey;       // [n_pls] the round's best (residual, difference) at the seed
   int *pcnt, *plist;              // [n_pls], [n_pls][PIX_TIES] objects of that rank
@@ -112,6 +113,8 @@ constexpr int PIX_DONE = 8, PIX_ROUNDS5 = 9, PIX_ROUNDS7 = 10, PIX_NCTR = 16;
 constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
 constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)
 constexpr int PIX_OCAP = 8;                     // candidate seeds cached per object
+constexpr int PIX_QCAP = 160;                   // a warp's queue of seeds past the curvature test
+constexpr int PIX_SCAN_THREADS = 256;           // CTA size of the two window-scan kernels
 
 // ------------------------------------------------------------------ FP32 cut arithmetic
 // Step 1 (Section 1, Table 1): two hits of one pT-module, pT above 0.8 GeV and inside the

@@ -79,9 +79,17 @@ __device__ __forceinline__ void pix_seed(const float *H, float4 &A, float4 &B, f
   B = make_float4(H[9], H[10], H[11], r4);
 }
 
-__global__ void k_pix_bin(const PixDesc *Ps) {
+// Seeds into their (slope row, azimuth bin) cells: counts and ranks. With rebin (between the
+// stages) only the seeds still free are binned again: the seeds the pT5s took leave the scans
+// of stage 7, the per-seed state and the smallest seed radius stay as they are (the windows
+// drawn from the smaller radius of all seeds stay wide enough).
+__global__ void k_pix_bin(const PixDesc *Ps, int rebin) {
   const PixDesc &P = Ps[blockIdx.y];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    if (rebin) {
+      if (P.pmatch[p] < 0) P.rank[p] = atomicAdd(P.cell_cnt + P.cell[p], 1);
+      continue;
+    }
     float4 A, B;
     float mp;
     pix_seed(P.hits + 12 * (size_t)p, A, B, mp);
@@ -96,15 +104,22 @@ __global__ void k_pix_bin(const PixDesc *Ps) {
   }
 }
 
+__global__ void k_pix_rebin_clear(const PixDesc *Ps) {
+  const PixDesc &P = Ps[blockIdx.y];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < PIX_NCELL; c += gridDim.x * blockDim.x) P.cell_cnt[c] = 0;
+}
+
 __global__ void k_pix_scan(const PixDesc *Ps) {
   const PixDesc &P = Ps[blockIdx.y];
   block_exclusive_scan(P.cell_cnt, P.cell_off, PIX_NCELL);
-  if (threadIdx.x == 0) P.cell_off[PIX_NCELL] = P.n_pls;
+  __syncthreads();
+  if (threadIdx.x == 0) P.cell_off[PIX_NCELL] = P.cell_off[PIX_NCELL - 1] + P.cell_cnt[PIX_NCELL - 1];
 }
 
-__global__ void k_pix_scatter(const PixDesc *Ps) {
+__global__ void k_pix_scatter(const PixDesc *Ps, int rebin) {
   const PixDesc &P = Ps[blockIdx.y];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_pls; p += gridDim.x * blockDim.x) {
+    if (rebin && P.pmatch[p] >= 0) continue;
     float4 A, B;
     float mp;
     pix_seed(P.hits + 12 * (size_t)p, A, B, mp);
@@ -112,6 +127,7 @@ __global__ void k_pix_scatter(const PixDesc *Ps) {
     P.sa[q] = A;
     P.sb[q] = B;
     P.sm[q] = mp;
+    P.sk[q] = A.w;
     P.sidx[q] = p;
   }
 }
@@ -139,14 +155,18 @@ __device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, i
   return true;
 }
 
-// Visit every free seed in the object's windows that matches it, the lanes of a warp taking
-// the candidates 32 at a time: f(hit, p, res, dk) on every lane at every step (warp-uniform,
-// so f may vote), hit telling whether the lane's seed matched. The azimuth window
-// is the turn the cut allows at this radius from the smallest seed radius r4min (its sine
-// bound, arcsine, plus one bin for rounding); the slope window its rows plus one on each side.
+// Visit every free seed in the object's windows that matches it: f(hit, p, res, dk) is called
+// on every lane of the warp (warp-uniform, so f may vote), hit telling whether the lane's seed
+// p matched. The azimuth window is the turn the cut allows at this radius from the smallest
+// seed radius r4min (its sine bound, arcsine, plus one bin for rounding); the slope window its
+// rows plus one on each side. The scan runs in two passes: the seeds of each run are tested
+// 128 at a time (four per lane) on the packed curvatures alone -- the pT test, which rejects
+// about 85% of a window -- and the survivors go into the warp's queue (PIX_QCAP seed positions
+// in shared memory), from which the full match runs on full warps, 32 seeds at a time. The
+// run bounds of 32 slope rows are loaded at once, a lane per row.
 template <typename F>
 __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P0, const float4 P1, float ko,
-                                                const lst_pixel_cuts &pc, float r4min, F f) {
+                                                const lst_pixel_cuts &pc, float r4min, int *queue, F f) {
   const int lane = threadIdx.x & 31;
   const float mo = (P1.z - P0.z) / (P1.w - P0.w);
   const float w = pc.dm_abs + pc.dm_rel * fabsf(mo);
@@ -159,30 +179,76 @@ __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P
   const int c0 = pix_phibin(P0.y, P0.x);
   const int span = min(2 * dphi_bins + 1, PIX_NPHI);
   const int first = ((c0 - dphi_bins) % PIX_NPHI + PIX_NPHI) % PIX_NPHI;
-  for (int row = r0; row <= r1; row++) {
-    // the azimuth bins [first, first + span) modulo PIX_NPHI: one or two contiguous runs
-    const int runs = first + span > PIX_NPHI ? 2 : 1;
-    for (int k = 0; k < runs; k++) {
-      const int b0 = k == 0 ? first : 0;
-      const int b1 = k == 0 ? min(first + span, PIX_NPHI) : first + span - PIX_NPHI;
-      const int q0 = P.cell_off[row * PIX_NPHI + b0], q1 = P.cell_off[row * PIX_NPHI + b1];
-      for (int qb = q0; qb < q1; qb += 32) {
-        const int q = qb + lane;
-        bool hit = false;
-        int p = -1;
-        float res = 0.0f, dk = 0.0f;
-        if (q < q1) {
-          // the seed's curvature first: the pT test rejects most seeds of a window, from one load
-          const float4 A = P.sa[q];
-          if (pix_kappa_ok(A.w, ko, pc)) {
-            p = P.sidx[q];
-            hit = P.pmatch[p] < 0 && pix_match(A, P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk);
-          }
-        }
-        f(hit, p, res, dk);
+  // the azimuth bins [first, first + span) modulo PIX_NPHI: [first, e0), and [0, e1) if it wraps
+  const bool wrap = first + span > PIX_NPHI;
+  const int e0 = min(first + span, PIX_NPHI), e1 = first + span - PIX_NPHI;
+  int qn = 0;                                    // seed positions in the queue (warp-uniform)
+  // the full match on queue entries [j, j + 32); lanes at or past `upto` take no seed
+  auto match = [&](int j, int upto) {
+    const int t = j + lane;
+    bool hit = false;
+    int p = -1;
+    float res = 0.0f, dk = 0.0f;
+    if (t < upto) {
+      const int q = queue[t];
+      p = P.sidx[q];
+      hit = P.pmatch[p] < 0 && pix_match(P.sa[q], P.sb[q], P.sm[q], P0, mo, ko, pc, res, dk);
+    }
+    f(hit, p, res, dk);
+  };
+  auto scan_run = [&](int q0, int q1) {
+    for (int qb = q0; qb < q1; qb += 128) {
+      float kv[4];
+#pragma unroll
+      for (int s = 0; s < 4; s++) kv[s] = P.sk[min(qb + 32 * s + lane, q1 - 1)];   // in range: q1 > qb
+      unsigned m = 0;
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+        if (qb + 32 * s + lane < q1 && pix_kappa_ok(kv[s], ko, pc)) m |= 1u << s;
+      const int c = __popc(m);
+      int x = c;                                 // inclusive prefix of the survivor counts
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+      }
+      int at = qn + x - c;
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+        if (m >> s & 1u) queue[at++] = qb + 32 * s + lane;
+      qn += __shfl_sync(FULL, x, 31);
+      __syncwarp();
+      if (qn >= 32) {
+        int j = 0;
+        for (; j + 32 <= qn; j += 32) match(j, qn);
+        const int rem = qn - j;                  // below 32: to the front of the queue
+        const int v = lane < rem ? queue[j + lane] : 0;
+        __syncwarp();
+        if (lane < rem) queue[lane] = v;
+        __syncwarp();
+        qn = rem;
       }
     }
+  };
+  for (int rb = r0; rb <= r1; rb += 32) {
+    const int row = rb + lane;
+    int a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    if (row <= r1) {
+      const int *co = P.cell_off + row * PIX_NPHI;
+      a0 = co[first];
+      a1 = co[e0];
+      if (wrap) {
+        b0 = co[0];
+        b1 = co[e1];
+      }
+    }
+    const int nr = min(32, r1 - rb + 1);
+    for (int k = 0; k < nr; k++) {
+      scan_run(__shfl_sync(FULL, a0, k), __shfl_sync(FULL, a1, k));
+      if (wrap) scan_run(__shfl_sync(FULL, b0, k), __shfl_sync(FULL, b1, k));
+    }
   }
+  if (qn > 0) match(0, qn);
 }
 
 __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
@@ -195,13 +261,15 @@ __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
 // more keeps scanning); later rounds and part 2 read the cache, dropping seeds taken since
 // (seeds only leave the free pool and the match of a pair does not change, so the
 // candidates are the same as a scan's).
-__global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
+__global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
   if (P.ctr[PIX_DONE]) return;
   const int lane = threadIdx.x & 31;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   const float r4min = __int_as_float(P.ctr[3]);
+  __shared__ int s_queue[(PIX_SCAN_THREADS / 32) * PIX_QCAP];
+  int *queue = s_queue + (threadIdx.x >> 5) * PIX_QCAP;
   const int W = (gridDim.x * blockDim.x) >> 5;
   for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
     const int g = base + o;
@@ -224,7 +292,7 @@ __global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps,
       if (pix_object(ev, P, stage, o, P0, P1, ko)) {
         const bool build = cached == -1;
         int cnt = 0;
-        pix_scan_object(P, P0, P1, ko, pc, r4min, [&](bool hit, int p, float res, float dk) {
+        pix_scan_object(P, P0, P1, ko, pc, r4min, queue, [&](bool hit, int p, float res, float dk) {
           const unsigned long long k = pix_key(res, dk);
           if (hit) consider(p, k);
           if (build) {
@@ -257,13 +325,15 @@ __global__ void k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps,
 
 // Round, part 2 (a warp per object): the objects that reach a seed's best rank list
 // themselves at that seed.
-__global__ void k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
+__global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
   if (P.ctr[PIX_DONE]) return;
   const int lane = threadIdx.x & 31;
   const int n = stage == 5 ? P.n_t5 : P.n_t3, base = stage == 5 ? 0 : P.n_t5;
   const float r4min = __int_as_float(P.ctr[3]);
+  __shared__ int s_queue[(PIX_SCAN_THREADS / 32) * PIX_QCAP];
+  int *queue = s_queue + (threadIdx.x >> 5) * PIX_QCAP;
   const int W = (gridDim.x * blockDim.x) >> 5;
   for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
     const int g = base + o;
@@ -286,7 +356,7 @@ __global__ void k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, in
       float4 P0, P1;
       float ko;
       if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
-      pix_scan_object(P, P0, P1, ko, pc, r4min, [&](bool hit, int p, float res, float dk) {
+      pix_scan_object(P, P0, P1, ko, pc, r4min, queue, [&](bool hit, int p, float res, float dk) {
         if (hit) list_at(p, pix_key(res, dk));
       });
     }
@@ -415,9 +485,17 @@ __global__ void k_pix_round_end(const PixDesc *Ps, int n_events, int stage, int 
 // Host-side launch helpers for n events (all on `st`, grid x `grid` per event); rounds are
 // driven by the caller.
 cudaError_t pix_launch_bin(const PixDesc *Ps, int n, bool any_seeds, int grid, cudaStream_t st) {
-  if (any_seeds) k_pix_bin<<<dim3(grid, n), 256, 0, st>>>(Ps);
+  if (any_seeds) k_pix_bin<<<dim3(grid, n), 256, 0, st>>>(Ps, 0);
   k_pix_scan<<<dim3(1, n), 1024, 0, st>>>(Ps);
-  if (any_seeds) k_pix_scatter<<<dim3(grid, n), 256, 0, st>>>(Ps);
+  if (any_seeds) k_pix_scatter<<<dim3(grid, n), 256, 0, st>>>(Ps, 0);
+  return cudaGetLastError();
+}
+cudaError_t pix_launch_rebin(const PixDesc *Ps, int n, bool any_seeds, int grid, cudaStream_t st) {
+  if (!any_seeds) return cudaSuccess;
+  k_pix_rebin_clear<<<dim3(grid, n), 256, 0, st>>>(Ps);
+  k_pix_bin<<<dim3(grid, n), 256, 0, st>>>(Ps, 1);
+  k_pix_scan<<<dim3(1, n), 1024, 0, st>>>(Ps);
+  k_pix_scatter<<<dim3(grid, n), 256, 0, st>>>(Ps, 1);
   return cudaGetLastError();
 }
 cudaError_t pix_launch_stage_begin(const PixDesc *Ps, int n, int stage, cudaStream_t st) {
@@ -426,8 +504,8 @@ cudaError_t pix_launch_stage_begin(const PixDesc *Ps, int n, int stage, cudaStre
 }
 cudaError_t pix_launch_round(const EvDesc *dd, const PixDesc *Ps, int n, int stage, lst_pixel_cuts pc, int grid,
                              int *flags, cudaStream_t st) {
-  k_pix_propose<<<dim3(4 * grid, n), 256, 0, st>>>(dd, Ps, stage, pc);
-  k_pix_ties<<<dim3(4 * grid, n), 256, 0, st>>>(dd, Ps, stage, pc);
+  k_pix_propose<<<dim3(4 * grid, n), PIX_SCAN_THREADS, 0, st>>>(dd, Ps, stage, pc);
+  k_pix_ties<<<dim3(4 * grid, n), PIX_SCAN_THREADS, 0, st>>>(dd, Ps, stage, pc);
   k_pix_pick<<<dim3(grid, n), 256, 0, st>>>(dd, Ps, stage);
   k_pix_accept<<<dim3(grid, n), 256, 0, st>>>(Ps, stage);
   k_pix_clear<<<dim3(grid, n), 256, 0, st>>>(Ps);
