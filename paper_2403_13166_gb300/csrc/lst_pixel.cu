@@ -159,11 +159,13 @@ __device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, i
 // on every lane of the warp (warp-uniform, so f may vote), hit telling whether the lane's seed
 // p matched. The azimuth window is the turn the cut allows at this radius from the smallest
 // seed radius r4min (its sine bound, arcsine, plus one bin for rounding); the slope window its
-// rows plus one on each side. The scan runs in two passes: the seeds of each run are tested
-// 128 at a time (four per lane) on the packed curvatures alone -- the pT test, which rejects
-// about 85% of a window -- and the survivors go into the warp's queue (PIX_QCAP seed positions
-// in shared memory), from which the full match runs on full warps, 32 seeds at a time. The
-// run bounds of 32 slope rows are loaded at once, a lane per row.
+// rows plus one on each side. The scan runs in two passes: the seeds of the window are tested
+// on the packed curvatures alone -- the pT test, which rejects about 85% of a window -- and
+// the survivors go into the warp's queue (PIX_QCAP seed positions in shared memory), from
+// which the full match runs on full warps, 32 seeds at a time. The run bounds of 32 slope rows
+// are loaded at once, a lane per row; then either the warp walks the non-empty runs one after
+// another, 128 seeds at a time, or (sparse windows: cheaper when the longest run is short)
+// every lane walks its own row's runs, four seeds a step.
 template <typename F>
 __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P0, const float4 P1, float ko,
                                                 const lst_pixel_cuts &pc, float r4min, int *queue, F f) {
@@ -196,56 +198,89 @@ __device__ __forceinline__ void pix_scan_object(const PixDesc &P, const float4 P
     }
     f(hit, p, res, dk);
   };
-  auto scan_run = [&](int q0, int q1) {
-    for (int qb = q0; qb < q1; qb += 128) {
-      float kv[4];
+  // append the lane's survivors (bit s of m: position qs[s]) to the queue; match full warps of it
+  auto enqueue = [&](unsigned m, const int (&qs)[4]) {
+    const int c = __popc(m);
+    int x = c;                                   // inclusive prefix of the survivor counts
 #pragma unroll
-      for (int s = 0; s < 4; s++) kv[s] = P.sk[min(qb + 32 * s + lane, q1 - 1)];   // in range: q1 > qb
-      unsigned m = 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, d);
+      if (lane >= d) x += y;
+    }
+    int at = qn + x - c;
 #pragma unroll
-      for (int s = 0; s < 4; s++)
-        if (qb + 32 * s + lane < q1 && pix_kappa_ok(kv[s], ko, pc)) m |= 1u << s;
-      const int c = __popc(m);
-      int x = c;                                 // inclusive prefix of the survivor counts
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, d);
-        if (lane >= d) x += y;
-      }
-      int at = qn + x - c;
-#pragma unroll
-      for (int s = 0; s < 4; s++)
-        if (m >> s & 1u) queue[at++] = qb + 32 * s + lane;
-      qn += __shfl_sync(FULL, x, 31);
+    for (int s = 0; s < 4; s++)
+      if (m >> s & 1u) queue[at++] = qs[s];
+    qn += __shfl_sync(FULL, x, 31);
+    __syncwarp();
+    if (qn >= 32) {
+      int j = 0;
+      for (; j + 32 <= qn; j += 32) match(j, qn);
+      const int rem = qn - j;                    // below 32: to the front of the queue
+      const int v = lane < rem ? queue[j + lane] : 0;
       __syncwarp();
-      if (qn >= 32) {
-        int j = 0;
-        for (; j + 32 <= qn; j += 32) match(j, qn);
-        const int rem = qn - j;                  // below 32: to the front of the queue
-        const int v = lane < rem ? queue[j + lane] : 0;
-        __syncwarp();
-        if (lane < rem) queue[lane] = v;
-        __syncwarp();
-        qn = rem;
-      }
+      if (lane < rem) queue[lane] = v;
+      __syncwarp();
+      qn = rem;
     }
   };
   for (int rb = r0; rb <= r1; rb += 32) {
     const int row = rb + lane;
-    int a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    int a0 = 0, la = 0, b0 = 0, lb = 0;
     if (row <= r1) {
       const int *co = P.cell_off + row * PIX_NPHI;
       a0 = co[first];
-      a1 = co[e0];
+      la = co[e0] - a0;
       if (wrap) {
         b0 = co[0];
-        b1 = co[e1];
+        lb = co[e1] - b0;
       }
     }
-    const int nr = min(32, r1 - rb + 1);
-    for (int k = 0; k < nr; k++) {
-      scan_run(__shfl_sync(FULL, a0, k), __shfl_sync(FULL, a1, k));
-      if (wrap) scan_run(__shfl_sync(FULL, b0, k), __shfl_sync(FULL, b1, k));
+    const int len = la + lb;
+    const int maxlen = __reduce_max_sync(FULL, (unsigned)len);
+    // steps of the two walks: the longest run's, four seeds a step; the non-empty runs' one by one
+    const int n_runs = __popc(__ballot_sync(FULL, la > 0)) + __popc(__ballot_sync(FULL, lb > 0));
+    const int total = __reduce_add_sync(FULL, (unsigned)len);
+    if ((maxlen + 3) / 4 <= n_runs + total / 128) {
+      for (int t = 0; t < maxlen; t += 4) {
+        int qs[4];
+        float kv[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+          const int u = t + s;
+          qs[s] = u < la ? a0 + u : b0 + (u - la);
+          kv[s] = u < len ? P.sk[qs[s]] : 0.0f;
+        }
+        unsigned m = 0;
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+          if (t + s < len && pix_kappa_ok(kv[s], ko, pc)) m |= 1u << s;
+        enqueue(m, qs);
+      }
+    } else {
+      for (int k = 0; k < 2; k++) {
+        unsigned nonempty = __ballot_sync(FULL, (k == 0 ? la : lb) > 0);
+        while (nonempty) {
+          const int src = __ffs(nonempty) - 1;
+          nonempty &= nonempty - 1;
+          const int q0 = __shfl_sync(FULL, k == 0 ? a0 : b0, src);
+          const int q1 = q0 + __shfl_sync(FULL, k == 0 ? la : lb, src);
+          for (int qb = q0; qb < q1; qb += 128) {
+            int qs[4];
+            float kv[4];
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+              qs[s] = qb + 32 * s + lane;
+              kv[s] = P.sk[min(qs[s], q1 - 1)];  // in range: q1 > qb
+            }
+            unsigned m = 0;
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+              if (qs[s] < q1 && pix_kappa_ok(kv[s], ko, pc)) m |= 1u << s;
+            enqueue(m, qs);
+          }
+        }
+      }
     }
   }
   if (qn > 0) match(0, qn);
@@ -255,12 +290,13 @@ __device__ __forceinline__ unsigned long long pix_key(float res, float dk) {
   return ((unsigned long long)__float_as_uint(res) << 32) | __float_as_uint(dk);
 }
 
-// Round, part 1 (a warp per object): each free object's best free seed (rank, then seed
-// index) and, at each seed, the best rank over its free objects. The first round of a stage
-// scans the object's windows and caches its candidates (PIX_OCAP at most; an object with
-// more keeps scanning); later rounds and part 2 read the cache, dropping seeds taken since
-// (seeds only leave the free pool and the match of a pair does not change, so the
-// candidates are the same as a scan's).
+// Round, part 1: each free object's best free seed (rank, then seed index) and, at each seed,
+// the best rank over its free objects. A warp takes G consecutive objects at a time (32, or
+// fewer when the objects would not give every warp that many). The first round of a stage
+// scans each object's windows (the whole warp, one object after another) and caches its
+// candidates (PIX_OCAP at most; an object with more keeps scanning); later rounds and part 2
+// read the cache, a lane per object, dropping seeds taken since (seeds only leave the free
+// pool and the match of a pair does not change, so the candidates are the same as a scan's).
 __global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_propose(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
@@ -271,60 +307,74 @@ __global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_propose(const EvDes
   __shared__ int s_queue[(PIX_SCAN_THREADS / 32) * PIX_QCAP];
   int *queue = s_queue + (threadIdx.x >> 5) * PIX_QCAP;
   const int W = (gridDim.x * blockDim.x) >> 5;
-  for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
-    const int g = base + o;
-    if (P.omatch[g] != -1) continue;               // taken or out (warp-uniform)
-    unsigned long long best = ~0ull;
-    int bp = 0x7fffffff;
-    auto consider = [&](int p, unsigned long long k) {
-      atomicMin(P.pkey + p, k);
-      if (k < best || (k == best && p < bp)) { best = k; bp = p; }
-    };
-    const int cached = P.ocnt[g];
-    if (cached >= 0 && cached <= PIX_OCAP) {
-      for (int j = lane; j < cached; j += 32) {
+  const int G = min(32, max(1, n / W));           // objects per warp and step (W warps: balance)
+  for (int ob = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; ob < n; ob += G * W) {
+    const int o = ob + lane, g = base + o;
+    const bool active = lane < G && o < n && P.omatch[g] == -1;   // not taken, not out
+    const int cached = active ? P.ocnt[g] : 0;
+    const bool from_cache = active && cached >= 0 && cached <= PIX_OCAP;
+    if (from_cache) {
+      unsigned long long best = ~0ull;
+      int bp = 0x7fffffff;
+      for (int j = 0; j < cached; j++) {
         const int p = P.oseed[(size_t)g * PIX_OCAP + j];
-        if (P.pmatch[p] < 0) consider(p, P.okeys[(size_t)g * PIX_OCAP + j]);
+        if (P.pmatch[p] >= 0) continue;
+        const unsigned long long k = P.okeys[(size_t)g * PIX_OCAP + j];
+        atomicMin(P.pkey + p, k);
+        if (k < best || (k == best && p < bp)) { best = k; bp = p; }
       }
-    } else {
-      float4 P0, P1;
-      float ko;
-      if (pix_object(ev, P, stage, o, P0, P1, ko)) {
-        const bool build = cached == -1;
-        int cnt = 0;
-        pix_scan_object(P, P0, P1, ko, pc, r4min, queue, [&](bool hit, int p, float res, float dk) {
-          const unsigned long long k = pix_key(res, dk);
-          if (hit) consider(p, k);
-          if (build) {
-            const unsigned m = __ballot_sync(FULL, hit);
-            const int at = cnt + __popc(m & lanemask_lt());
-            if (hit && at < PIX_OCAP) {
-              P.oseed[(size_t)g * PIX_OCAP + at] = p;
-              P.okeys[(size_t)g * PIX_OCAP + at] = k;
-            }
-            cnt += __popc(m);
-          }
-        });
-        if (build && lane == 0) P.ocnt[g] = min(cnt, PIX_OCAP + 1);
-      }
-    }
-#pragma unroll
-    for (int s = 16; s; s >>= 1) {                 // the warp's minimum of (rank, seed)
-      const unsigned long long ob = __shfl_xor_sync(FULL, best, s);
-      const int op = __shfl_xor_sync(FULL, bp, s);
-      if (ob < best || (ob == best && op < bp)) { best = ob; bp = op; }
-    }
-    if (lane == 0) {
       P.okey[g] = best;
       P.op[g] = best == ~0ull ? -1 : bp;
       // no free seed matches it now, so none will later (seeds only leave): out for good
       if (best == ~0ull) P.omatch[g] = -2;
     }
+    unsigned to_scan = __ballot_sync(FULL, active && !from_cache);
+    while (to_scan) {
+      const int src = __ffs(to_scan) - 1;
+      to_scan &= to_scan - 1;
+      const int so = ob + src, sg = base + so;
+      const bool build = __shfl_sync(FULL, cached, src) == -1;
+      unsigned long long best = ~0ull;
+      int bp = 0x7fffffff;
+      float4 P0, P1;
+      float ko;
+      if (pix_object(ev, P, stage, so, P0, P1, ko)) {
+        int cnt = 0;
+        pix_scan_object(P, P0, P1, ko, pc, r4min, queue, [&](bool hit, int p, float res, float dk) {
+          const unsigned long long k = pix_key(res, dk);
+          if (hit) {
+            atomicMin(P.pkey + p, k);
+            if (k < best || (k == best && p < bp)) { best = k; bp = p; }
+          }
+          if (build) {
+            const unsigned m = __ballot_sync(FULL, hit);
+            const int at = cnt + __popc(m & lanemask_lt());
+            if (hit && at < PIX_OCAP) {
+              P.oseed[(size_t)sg * PIX_OCAP + at] = p;
+              P.okeys[(size_t)sg * PIX_OCAP + at] = k;
+            }
+            cnt += __popc(m);
+          }
+        });
+        if (build && lane == 0) P.ocnt[sg] = min(cnt, PIX_OCAP + 1);
+      }
+#pragma unroll
+      for (int s = 16; s; s >>= 1) {               // the warp's minimum of (rank, seed)
+        const unsigned long long ob2 = __shfl_xor_sync(FULL, best, s);
+        const int op2 = __shfl_xor_sync(FULL, bp, s);
+        if (ob2 < best || (ob2 == best && op2 < bp)) { best = ob2; bp = op2; }
+      }
+      if (lane == 0) {
+        P.okey[sg] = best;
+        P.op[sg] = best == ~0ull ? -1 : bp;
+        if (best == ~0ull) P.omatch[sg] = -2;
+      }
+    }
   }
 }
 
-// Round, part 2 (a warp per object): the objects that reach a seed's best rank list
-// themselves at that seed.
+// Round, part 2: the objects that reach a seed's best rank list themselves at that seed; as
+// in part 1, a lane per cached object and the whole warp for an object that scans.
 __global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_ties(const EvDesc *__restrict__ evs, const PixDesc *Ps, int stage, lst_pixel_cuts pc) {
   const EvDesc &ev = evs[blockIdx.y];
   const PixDesc &P = Ps[blockIdx.y];
@@ -335,29 +385,37 @@ __global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_ties(const EvDesc *
   __shared__ int s_queue[(PIX_SCAN_THREADS / 32) * PIX_QCAP];
   int *queue = s_queue + (threadIdx.x >> 5) * PIX_QCAP;
   const int W = (gridDim.x * blockDim.x) >> 5;
-  for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += W) {
-    const int g = base + o;
-    if (P.okey[g] == ~0ull || P.omatch[g] != -1) continue;   // no free seed matches it (warp-uniform)
-    auto list_at = [&](int p, unsigned long long k) {
-      if (k != P.pkey[p]) return;
-      const int s = atomicAdd(P.pcnt + p, 1);
-      if (s < PIX_TIES)
-        P.plist[PIX_TIES * (size_t)p + s] = o;
-      else
-        atomicOr(P.ctr + 2, 1);
-    };
-    const int cached = P.ocnt[g];
-    if (cached >= 0 && cached <= PIX_OCAP) {
-      for (int j = lane; j < cached; j += 32) {
+  auto list_at = [&](int o, int p, unsigned long long k) {
+    if (k != P.pkey[p]) return;
+    const int s = atomicAdd(P.pcnt + p, 1);
+    if (s < PIX_TIES)
+      P.plist[PIX_TIES * (size_t)p + s] = o;
+    else
+      atomicOr(P.ctr + 2, 1);
+  };
+  const int G = min(32, max(1, n / W));           // objects per warp and step (W warps: balance)
+  for (int ob = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; ob < n; ob += G * W) {
+    const int o = ob + lane, g = base + o;
+    // a free seed matches it (okey set by part 1) and it is still free
+    const bool active = lane < G && o < n && P.okey[g] != ~0ull && P.omatch[g] == -1;
+    const int cached = active ? P.ocnt[g] : 0;
+    const bool from_cache = active && cached >= 0 && cached <= PIX_OCAP;
+    if (from_cache) {
+      for (int j = 0; j < cached; j++) {
         const int p = P.oseed[(size_t)g * PIX_OCAP + j];
-        if (P.pmatch[p] < 0) list_at(p, P.okeys[(size_t)g * PIX_OCAP + j]);
+        if (P.pmatch[p] < 0) list_at(o, p, P.okeys[(size_t)g * PIX_OCAP + j]);
       }
-    } else {
+    }
+    unsigned to_scan = __ballot_sync(FULL, active && !from_cache);
+    while (to_scan) {
+      const int src = __ffs(to_scan) - 1;
+      to_scan &= to_scan - 1;
+      const int so = ob + src;
       float4 P0, P1;
       float ko;
-      if (!pix_object(ev, P, stage, o, P0, P1, ko)) continue;
+      if (!pix_object(ev, P, stage, so, P0, P1, ko)) continue;
       pix_scan_object(P, P0, P1, ko, pc, r4min, queue, [&](bool hit, int p, float res, float dk) {
-        if (hit) list_at(p, pix_key(res, dk));
+        if (hit) list_at(so, p, pix_key(res, dk));
       });
     }
   }
