@@ -404,6 +404,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     roofline["stage_ms_per_launch"] = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
     step = step_roofline(mean_counts, pairs, float(np.mean(n_hits)), float(np.mean(np.diff(g.map_off))),
                          value, clk.summary(), torch.cuda.get_device_properties(dev).multi_processor_count)
+    score_rf = score_roofline(float(stage_ms[names.index("score")]), B, mean_counts, precision)
     if graph is not None:   # the graph build inside the batched launch: grouping, MD and LS stages
         graph["build_ms_per_event_batched"] = round(float(sum(stage_ms[:4])) / B, 4)
     roofline["launches_timed"] = int(n_launch)
@@ -428,6 +429,7 @@ def run_gpu(args, rank, world, local_rank, pool):
         "e2e": e2e,
         "roofline": roofline,
         "step_roofline": step,
+        "score_roofline": score_rf,
         "clocks": clk.summary(),
         "gpu_launches": KERNELS_PER_LAUNCH * args.steps,
     }
@@ -616,6 +618,38 @@ def step_roofline(counts, pairs, hits, fan, events_per_s, clocks, n_sm):
             "alu_issue_frac": round(2 * tops / alu, 4),
             "note": "mean module-map fan-out %.1f; FP32 ops per candidate pair MD/LS/T3/T5 = %s" % (
                 fan, "/".join(map(str, STEP_OPS_PER_PAIR)))}
+
+
+def score_roofline(ms, B, counts, precision):
+    """The T5-DNN stage against the tensor peak (the network's 4544 flop per T5; the split
+    form issues three MMAs per K-step) and against HBM (what the feature gather reads)."""
+    from paper_2403_13166_gb300 import lst
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    t5 = B * counts["t5"]
+    sec = ms / 1000.0
+    flop = t5 * MLP_FLOP_PER_T5
+    by = t5 * (32 + 5 * (16 + 8 + 4) + 5)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"stage_ms_per_launch": round(ms, 4), "t5_per_launch": int(t5),
+           "hbm_achieved_GBs": round(by / sec / 1e9, 1), "hbm_frac": round(by / sec / 1e9 / hbm, 4)}
+    if precision == lst.LST_FP32:
+        out.update({"kernel": "k_score_fp32", "bound": "alu", "achieved": round(flop / sec / 1e12, 3),
+                    "unit": "TFLOP/s", "note": "compensated FP32 (float-float) layers on the CUDA cores"})
+        return out
+    mma = 3 if precision == lst.LST_BF16X3 else 1
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = flop / sec / 1e12
+    out.update({"kernel": "k_score_bf16", "bound": "tensor", "achieved": round(achieved, 3), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "mma_per_kstep": mma,
+                "issued_frac": round(mma * achieved / peak, 5),
+                "peak_note": ("measured sustained bf16 (cuBLAS)" if peaks else "fallback"),
+                "note": "the stage gathers each T5's features from five MD anchors; the tensor pipe "
+                        "is idle most of the time (feature gathering bounds it)"})
+    return out
 
 
 # ------------------------------------------------------------------ reference arm: the oracle

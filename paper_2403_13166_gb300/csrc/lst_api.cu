@@ -1272,8 +1272,10 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
         CU(pix_launch_rebin(dP, n, any_seeds, grid, st));
       }
       CU(pix_launch_stage_begin(dP, n, stage, st));
-      for (int round = 0; round < 1 << 20; round++) {
-        CU(pix_launch_round(dD, dP, n, stage, *pc, grid, dflags, st));
+      // rounds go out PIX_ROUNDS_PER_WAIT at a time between host waits (a stage takes about
+      // three; the kernels of an event that is done return at once)
+      for (int round = 0; round < 1 << 20; round += PIX_ROUNDS_PER_WAIT) {
+        for (int r = 0; r < PIX_ROUNDS_PER_WAIT; r++) CU(pix_launch_round(dD, dP, n, stage, *pc, grid, dflags, st));
         CU(cudaMemcpyAsync(hflags.data(), dflags, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         bool all = true;

@@ -113,6 +113,7 @@ constexpr int PIX_DONE = 8, PIX_ROUNDS5 = 9, PIX_ROUNDS7 = 10, PIX_NCTR = 16;
 constexpr int PIX_NPHI = 256, PIX_NM = 64, PIX_NCELL = PIX_NPHI * PIX_NM;
 constexpr int PIX_TIES = 8;                     // objects equal in rank at one seed (more: error)
 constexpr int PIX_OCAP = 8;                     // candidate seeds cached per object
+constexpr int PIX_ROUNDS_PER_WAIT = 3;           // matching rounds launched per host wait
 constexpr int PIX_QCAP = 160;                   // a warp's queue of seeds past the curvature test
 constexpr int PIX_SCAN_THREADS = 256;           // CTA size of the two window-scan kernels
 
