@@ -155,6 +155,13 @@ __device__ __forceinline__ bool pix_object(const EvDesc &ev, const PixDesc &P, i
   return true;
 }
 
+// Whether object o takes part in the stage at all (what pix_object decides first).
+__device__ __forceinline__ bool pix_eligible(const EvDesc &ev, const PixDesc &P, int stage, int o) {
+  if (stage == 5) return ev.t5_tc[o] != 0;
+  const int4 t = ev.t3_md[o];
+  return !(P.mdflag[t.x] && P.mdflag[t.y] && P.mdflag[t.z]);
+}
+
 // Visit every free seed in the object's windows that matches it: f(hit, p, res, dk) is called
 // on every lane of the warp (warp-uniform, so f may vote), hit telling whether the lane's seed
 // p matched. The azimuth window is the turn the cut allows at this radius from the smallest
@@ -310,8 +317,14 @@ __global__ void __launch_bounds__(PIX_SCAN_THREADS, 4) k_pix_propose(const EvDes
   const int G = min(32, max(1, n / W));           // objects per warp and step (W warps: balance)
   for (int ob = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; ob < n; ob += G * W) {
     const int o = ob + lane, g = base + o;
-    const bool active = lane < G && o < n && P.omatch[g] == -1;   // not taken, not out
+    bool active = lane < G && o < n && P.omatch[g] == -1;   // not taken, not out
     const int cached = active ? P.ocnt[g] : 0;
+    if (active && cached == -1 && !pix_eligible(ev, P, stage, o)) {   // first round: out for good
+      P.okey[g] = ~0ull;
+      P.op[g] = -1;
+      P.omatch[g] = -2;
+      active = false;
+    }
     const bool from_cache = active && cached >= 0 && cached <= PIX_OCAP;
     if (from_cache) {
       unsigned long long best = ~0ull;
