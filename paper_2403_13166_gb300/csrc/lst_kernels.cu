@@ -97,7 +97,7 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
       const int pos = ev.sens_off[key] + ev.hit_rank[i];
       ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
       ev.hit_orig[pos] = i;
-      ev.hit_mod[pos] = s >> 1;
+      if (!(s & 1)) ev.hit_mod[pos] = s >> 1;         // read for lower-sensor hits only (k_md)
     }
   }
 }
