@@ -304,7 +304,7 @@ void caps_for(const lst_ctx_s *c, int64_t n, int &md, int &ls, int &t3, int &t5)
 // Byte offsets of one event's buffers in its slot allocation (H hits, nm modules, md/ls/t3/t5
 // object capacities); `total` is the allocation size.
 struct SlotLayout {
-  size_t hit, orig, hmod, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank, mperm, mq;
+  size_t hit, om, hrank, scnt, soff, manc, mk, mmod, mh, mst, mcn, uanc, uk, umod, uh, urank, mperm, mq;
   size_t lin, lout, lst, lcn, lost, locn, lsu, t3, t3k, t3s, t3c, t3u, t3uk, t5a, t5b, t5s, t5e, tcc, tcp, tcl,
       tcf, cnt;
   size_t total;
@@ -313,7 +313,7 @@ SlotLayout slot_layout(int64_t H, size_t nm, size_t md, size_t ls, size_t t3, si
   SlotLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-  L.hit = take(16 * (size_t)H); L.orig = take(4 * (size_t)H); L.hmod = take(4 * (size_t)H);
+  L.hit = take(16 * (size_t)H); L.om = take(8 * (size_t)H);
   L.hrank = take(4 * (size_t)H);
   L.scnt = take(4 * 2 * nm); L.soff = take(4 * (2 * nm + 1));
   L.manc = take(16 * md); L.mk = take(8 * md); L.mmod = take(4 * md); L.mh = take(8 * md);
@@ -381,7 +381,7 @@ lst_status slot_alloc(lst_ctx_s *c, Slot &s, int64_t n_hits, cudaStream_t st, bo
   s.bytes = off;
   char *b = (char *)s.mem;
   EvDesc &d = s.d;
-  d.hit = (float4 *)(b + L.hit); d.hit_orig = (int32_t *)(b + L.orig); d.hit_mod = (int32_t *)(b + L.hmod);
+  d.hit = (float4 *)(b + L.hit); d.hit_om = (int2 *)(b + L.om);
   d.hit_rank = (int32_t *)(b + L.hrank);
   d.sens_cnt = (int32_t *)(b + L.scnt); d.sens_off = (int32_t *)(b + L.soff);
   d.md_anchor = (float4 *)(b + L.manc); d.md_kappa = (float2 *)(b + L.mk); d.md_mod = (int32_t *)(b + L.mmod);

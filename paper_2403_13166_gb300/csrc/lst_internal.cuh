@@ -43,8 +43,8 @@ struct EvDesc {
   int32_t md_cap, ls_cap, t3_cap, t5_cap;
   int32_t pad;
   float4 *hit;                 // [n_hits] hits grouped by sensor: x, y, z, r
-  int32_t *hit_orig;           // [n_hits] original index of each grouped hit
-  int32_t *hit_mod;            // [n_hits] module of each grouped hit (lower-sensor hits only)
+  int2 *hit_om;                // [n_hits] per grouped hit: original index, module (the module
+                               // for lower-sensor hits only, the ones step 1 reads it for)
   int32_t *sens_cnt;           // [2 n_mod] histogram by key
   int32_t *hit_rank;           // [n_hits] rank of each input hit within its key (input order)
   int32_t *sens_off;           // [2 n_mod + 1] key k < n_mod: lower sensor of module k,

@@ -96,8 +96,10 @@ __global__ void k_bin_scatter(const EvDesc *__restrict__ evs, int n_events, DevG
       const int key = (s & 1) * g.n_mod + (s >> 1);
       const int pos = ev.sens_off[key] + ev.hit_rank[i];
       ev.hit[pos] = make_float4(x, y, z, sqrtf(x * x + y * y));
-      ev.hit_orig[pos] = i;
-      if (!(s & 1)) ev.hit_mod[pos] = s >> 1;         // read for lower-sensor hits only (k_md)
+      if (s & 1)
+        ev.hit_om[pos].x = i;
+      else
+        ev.hit_om[pos] = make_int2(i, s >> 1);         // one store: index and module
     }
   }
 }
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
     float4 L = make_float4(0.f, 0.f, 0.f, 1.f);
     MdLow q{};
     if (h < ev.sens_off[nm]) {
-      const int m = ev.hit_mod[h];
+      const int m = ev.hit_om[h].y;
       up0 = ev.sens_off[nm + m];
       nup = ev.sens_off[nm + m + 1] - up0;
       endcap = g.subdet[m] != 0;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256) k_md(const EvDesc *__restrict__ evs, int 
             ev.mdu_anchor[o] = w.L[x];
             ev.mdu_kappa[o] = make_float2(kc, kf);
             ev.mdu_mod[o] = w.mod[x];
-            ev.mdu_hits[o] = make_int2(ev.hit_orig[w.lo[x]], ev.hit_orig[uh]);
+            ev.mdu_hits[o] = make_int2(ev.hit_om[w.lo[x]].x, ev.hit_om[uh].x);
             ev.mdu_rank[o] = atomicAdd(ev.md_cnt + w.mod[x], 1);
           }
         }
