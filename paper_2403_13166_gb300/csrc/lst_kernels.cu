@@ -372,6 +372,19 @@ __global__ void __launch_bounds__(256) k_md_sort(const EvDesc *__restrict__ evs,
 }
 
 // ===================================================================== step 2: line segments
+// Warp minimum / maximum of finite floats in one redux each: the map from a float's bits to
+// a signed integer that flips the magnitude bits of negative values preserves their order.
+__device__ __forceinline__ int float_order_key(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float warp_min_float(float f) {
+  return __int_as_float(float_order_key(__int_as_float(__reduce_min_sync(FULL, float_order_key(f)))));
+}
+__device__ __forceinline__ float warp_max_float(float f) {
+  return __int_as_float(float_order_key(__int_as_float(__reduce_max_sync(FULL, float_order_key(f)))));
+}
+
 // One warp per (event, module m); the warps of a CTA never wait for one another. The
 // targets (all MDs of the modules linked to m by the module map) are spread over the lanes
 // 32 at a time and held in registers; the inner MDs of m sit in the warp's shared memory
@@ -518,13 +531,11 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
             w.inq[t] = nan;
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          rmin = fminf(rmin, __shfl_xor_sync(FULL, rmin, o));
-          rmax = fmaxf(rmax, __shfl_xor_sync(FULL, rmax, o));
-        }
+        rmin = warp_min_float(rmin);
+        rmax = warp_max_float(rmax);
         const float irmin = __fdividef(1.0f, rmin), irmax = __fdividef(1.0f, rmax);
         __syncwarp();
+        int tg = 0;                                    // target module of the group's first target
         for (int j0 = 0; j0 < S; j0 += 32) {
           const int j = j0 + lane;
           bool valid = j < S;
@@ -532,8 +543,10 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
           float kB = 0.0f, k1 = 0.0f;
           bool bB = false;
           int md = 0;
+          while (w.tpref[tg + 1] <= j0) tg++;          // warp-uniform; tpref[nb] = S > j0
           if (valid) {
-            const int t = find_event(w.tpref, nb + 1, j);
+            int t = tg;                                // the last t with tpref[t] <= j: a group
+            while (w.tpref[t + 1] <= j) t++;           // spans a few target modules
             md = w.tstart[t] + (j - w.tpref[t]);
             if (chk(ev, md, ev.md_cap, 21)) {
               B = ev.md_anchor[md];
@@ -594,11 +607,8 @@ __global__ void __launch_bounds__(256) k_ls(const EvDesc *__restrict__ evs, int 
               qlo = qB - wB - sl;
               qhi = qB + wB + sl;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              qlo = fminf(qlo, __shfl_xor_sync(FULL, qlo, o));
-              qhi = fmaxf(qhi, __shfl_xor_sync(FULL, qhi, o));
-            }
+            qlo = warp_min_float(qlo);
+            qhi = warp_max_float(qhi);
             // positions in the sorted chunk: keys below qlo, keys up to qhi
             const float a0 = w.inq[lane];
             ilo = __popc(__ballot_sync(FULL, lane < nc && a0 < qlo));
