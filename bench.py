@@ -218,7 +218,7 @@ def run_gpu(args, rank, world, local_rank, pool):
     if wp is not None:
         cuts["wp"] = np.float32(wp)
     precision = PRECISIONS[args.precision]
-    ctx = lst.Context(local_rank, max_events=2 * B, precision=precision, use_graphs=1)
+    ctx = lst.Context(local_rank, max_events=3 * B, precision=precision, use_graphs=1)
     ctx.load_geometry(g, cuts, flat, nh)
     # the plain form: one launch sequence per event, FP32 score
     ctx_p = lst.Context(local_rank, max_events=2, precision=lst.LST_FP32, use_graphs=0)
@@ -236,21 +236,25 @@ def run_gpu(args, rank, world, local_rank, pool):
             import torch.distributed as dist
             dist.barrier()
 
-    def batched_step(inputs, prev):
-        hs = ctx.run_batch(inputs, stream)
-        if prev is not None:
-            for h in prev:
+    # three batches in flight: each step enqueues one and then takes the results of the one
+    # launched two steps before, so a late host leaves the GPU a whole batch of work
+    def batched_step(inputs, pending):
+        pending = (pending or []) + [ctx.run_batch(inputs, stream)]
+        if len(pending) > 2:
+            for h in pending.pop(0):
                 c = h.counts()
                 if c["status"] != lst.LST_OK:
                     raise RuntimeError(f"event status {c['status']}")
                 h.release()
-        return hs
+        return pending
 
-    def drain(prev):
+    def drain(pending):
         out = []
-        for h in prev or []:
-            out.append(h.counts())
-            h.release()
+        for hs in pending or []:
+            out = []
+            for h in hs:
+                out.append(h.counts())
+                h.release()
         return out
 
     # ---------------- batched (graph) path; warm-up captures the same (timed) graph

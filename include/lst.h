@@ -154,7 +154,10 @@ lst_status lst_run_event(lst_ctx ctx, const float *x, const float *y, const floa
  * HOST) go through one persistent launch per stage; with cfg.use_graphs the launch
  * sequence is a CUDA graph captured once. Asynchronous: returns once the work is
  * enqueued. lst_event_counts / lst_get_candidates wait for it. An event whose buffers
- * overflowed reports LST_ERR_CAPACITY (and grows its slot for the next run). */
+ * overflowed reports LST_ERR_CAPACITY (and grows its slot for the next run). Up to three
+ * batches are in flight: consecutive calls take three lanes in turn, and a call first
+ * waits for the batch that last ran on its lane (the context needs max_events slots for
+ * all events in flight). */
 lst_status lst_run_batch(lst_ctx ctx, int32_t n_events, const float *const *x,
                          const float *const *y, const float *const *z,
                          const int32_t *const *sensor, const int64_t *n_hits,

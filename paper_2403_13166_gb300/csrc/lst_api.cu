@@ -158,6 +158,11 @@ struct Slot {
   int64_t n_hits = 0;
 };
 
+// Batches of lst_run_batch in flight at once: the lanes are taken round robin and a launch
+// on a lane first waits for that lane's previous batch, so a caller that keeps two earlier
+// batches pending while the third runs leaves the GPU a full batch of slack.
+constexpr int BATCH_LANES = 3;
+
 struct Lane {
   EvDesc *d_desc = nullptr;        // [MAX_EVENTS]
   EvDesc *h_desc = nullptr;        // pinned
@@ -668,7 +673,7 @@ lst_status lst_create(int cuda_device, const lst_config *cfg, lst_ctx *out) {
   if (cudaGetDeviceProperties(&p, cuda_device) != cudaSuccess) { delete x; return fail(LST_ERR_CUDA, "device properties"); }
   x->n_sm = p.multiProcessorCount;
   x->slots.resize(c.max_events);
-  x->lanes.resize(1 + 2);
+  x->lanes.resize(1 + BATCH_LANES);
   for (auto &L : x->lanes) {
     lst_status s = lane_init(L);
     if (s != LST_OK) { lst_destroy(x); return s; }

@@ -199,6 +199,25 @@ def test_list_overflow_paths(geom_full, cuts, model):
     c.close()
 
 
+def test_batches_in_flight(geom_full, cuts, model):
+    """Four batches launched without reading anything in between: three lanes hold the first
+    three, the fourth waits for the first lane's batch and reuses that lane; every event of
+    every batch equals the oracle."""
+    c = lst.Context(0, max_events=16)
+    c.load_geometry(geom_full, cuts, *model)
+    evs = [synth.pileup_event(geom_full, 80 + i, pileup=pu, mean_per_vertex=96)
+           for i, pu in enumerate((20, 3, 30, 10, 25, 5, 15, 35))]
+    refs = [oracle.run_event(geom_full, e, cuts, *model) for e in evs]
+    inputs = [dev(e) for e in evs]
+    batches = [c.run_batch(inputs[2 * b:2 * b + 2]) for b in range(4)]
+    for b, hs in enumerate(batches):
+        for k, h in enumerate(hs):
+            assert h.counts()["status"] == lst.LST_OK
+            compare(h, refs[2 * b + k], float(cuts["wp"]))
+            h.release()
+    c.close()
+
+
 def test_batch_equals_single_and_graph_replay(ctx_full, geom_full, cuts, model):
     evs = [synth.pileup_event(geom_full, i, pileup=pu, mean_per_vertex=96, config=4)
            for i, pu in enumerate((50, 250, 120, 7, 180, 90))]
