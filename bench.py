@@ -544,10 +544,10 @@ STRICT_OPS = {"ls": (12, 35)}
 
 
 # DRAM bytes (read + write) per event of a kernel, from one ncu capture of a 16-event
-# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 66.57 +
-# 247.52 MB for k_ls); the traffic is the per-event LS output plus MD reads, so it scales
+# launch of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum = 65.38 +
+# 244.44 MB for k_ls); the traffic is the per-event LS output plus MD reads, so it scales
 # with the events.
-TRAFFIC_PER_EVENT = {"ls": 314.09e6 / 16}
+TRAFFIC_PER_EVENT = {"ls": 309.82e6 / 16}
 
 
 def traffic_per_launch(stage, events):
