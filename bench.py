@@ -365,21 +365,23 @@ def run_gpu(args, rank, world, local_rank, pool):
             h.release()
         return int(offs[-1]) * (40 + 4 + 1) + 8 * (B + 1)
 
-    # two streams in turn, so that batch k+1's host-to-device copies overlap batch k's kernels
-    e2e_streams = [stream, torch.cuda.Stream(dev)]
+    # three streams in turn, so that the host-to-device copies of the next batches overlap
+    # the kernels of the current one
+    e2e_streams = [stream, torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
 
     def e2e_run(steps):
-        # batch k+1 is enqueued (H2D + kernels) before batch k's results are read back
-        prev, d2h = None, 0
+        # batches k+1 and k+2 are enqueued (H2D + kernels) before batch k's results are read
+        # back (three batches in flight, as in the device-resident loop)
+        pending, d2h = [], 0
         for k in range(steps):
-            hs = ctx.run_batch(pinned, e2e_streams[k % 2])
-            if prev is not None:
-                d2h += export(prev)
-            prev = hs
-        d2h += export(prev)
+            pending.append(ctx.run_batch(pinned, e2e_streams[k % 3]))
+            if len(pending) > 2:
+                d2h += export(pending.pop(0))
+        for hs in pending:
+            d2h += export(hs)
         return d2h
 
-    e2e_run(2)
+    e2e_run(3)
     sync_all()
     t0 = time.perf_counter()
     d2h = e2e_run(e2e_steps)
