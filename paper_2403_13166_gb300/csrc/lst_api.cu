@@ -245,7 +245,7 @@ constexpr int LS_SMALL_TB = 8;          // target modules per step-2 unit in sma
 size_t ls_smem(const lst_ctx_s *c) { return (size_t)(c->ls_threads / 32) * LS_WARP_BYTES; }
 size_t md_smem(const lst_ctx_s *c) { return (size_t)(c->md_threads / 32) * (512 + 3 * 128 + 2 * 256); }
 size_t t3_smem(const lst_ctx_s *c) { return (size_t)(c->t3_threads / 32) * 6288; }   // sizeof(T3Warp)
-size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512 + 128); }
+size_t t5_smem(const lst_ctx_s *c) { return (size_t)(c->t5_threads / 32) * (4 * 128 + 3 * 512); }
 int mlp_floats_host(int nh) { return NHID * NFEAT + NHID + (nh - 1) * (NHID * NHID + NHID) + NHID + 1; }
 
 lst_status compute_grids(lst_ctx_s *c) {

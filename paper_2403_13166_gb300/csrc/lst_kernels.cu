@@ -1026,8 +1026,8 @@ struct T5Warp {
   int incl[32], st2[32], ta[32];
   float ka[32];
   float4 P0[32], P1[32], P2[32];
-  int md1[32];
 };
+static_assert(sizeof(T5Warp) == 2048, "the host sizes k_t5 shared memory with 2048 bytes per warp");
 
 __global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int n_events, lst_cuts c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1055,13 +1055,14 @@ __global__ void __launch_bounds__(256) k_t5(const EvDesc *__restrict__ evs, int 
     if (ta < nt3) {
       const int4 A3 = ev.t3_md[ta];
       deg = ev.t3_cnt[A3.z];
-      w.st2[lane] = ev.t3_pos[A3.z];
-      w.ta[lane] = ta;
-      w.ka[lane] = ev.t3_kappa[ta];
-      w.md1[lane] = A3.y;
-      w.P0[lane] = ev.md_anchor[A3.x];
-      w.P1[lane] = ev.md_anchor[A3.y];
-      w.P2[lane] = ev.md_anchor[A3.z];
+      if (deg > 0) {                               // most T3s start no T5: skip their anchors
+        w.st2[lane] = ev.t3_pos[A3.z];
+        w.ta[lane] = ta;
+        w.ka[lane] = ev.t3_kappa[ta];
+        w.P0[lane] = ev.md_anchor[A3.x];
+        w.P1[lane] = ev.md_anchor[A3.y];
+        w.P2[lane] = ev.md_anchor[A3.z];
+      }
     }
     const int inc = warp_incl_scan(deg);
     w.incl[lane] = inc;
