@@ -351,6 +351,13 @@ bool injected_alloc_failure(lst_ctx_s *c) {
 // stream of the slot's next launch, without waiting for the device. The other callers use
 // plain allocations, after a device synchronisation when a buffer is replaced (a profiler
 // replaying kernels saves and restores those, which it may not do for pool memory).
+// Short-lived device staging of the exports and the pixel matching, from the context's own
+// pool: its freed blocks stay reserved (release threshold: never), so a call does not map
+// new memory each time (the device's default pool hands freed memory back at every
+// synchronisation, and the next call maps it again while the driver holds its locks).
+cudaError_t tmp_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+}
 cudaError_t slot_buf_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st, bool pooled) {
   return pooled ? cudaMallocFromPoolAsync(p, bytes, c->pool, st) : cudaMalloc(p, bytes);
 }
@@ -597,7 +604,7 @@ lst_status gather_tc(lst_ctx_s *c, const EvDesc *dd, int n_t5, int64_t n, int32_
   const bool dev_out = is_device_ptr(hit_idx);
   const size_t bytes = 256 + (dev_out ? 0 : (size_t)n * 40 + (size_t)n * 4 + (size_t)n);
   void *tmp = nullptr;
-  CU(cudaMallocAsync(&tmp, bytes, c->aux));
+  CU(tmp_alloc(c, &tmp, bytes, c->aux));
   int *d_counter = (int *)tmp;
   int32_t *d_idx = dev_out ? hit_idx : (int32_t *)((char *)tmp + 256);
   float *d_sc = dev_out ? score : (float *)(d_idx + (size_t)n * 10);
@@ -994,7 +1001,7 @@ lst_status lst_get_candidates(lst_event ev, int32_t kind, int32_t *hit_idx, floa
   }
   const size_t bytes = (size_t)n * width * 4 + (size_t)n * 4 + (size_t)n + 1024;
   void *tmp = nullptr;
-  CU(cudaMallocAsync(&tmp, bytes, c->aux));
+  CU(tmp_alloc(c, &tmp, bytes, c->aux));
   int32_t *d_idx = (int32_t *)tmp;
   float *d_sc = (float *)(d_idx + (size_t)n * width);
   uint8_t *d_sel = (uint8_t *)(d_sc + n);
@@ -1042,7 +1049,7 @@ lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kin
   const size_t b_sc = dev_out ? 0 : align_up((size_t)total * 4, 256);
   const size_t b_sel = dev_out ? 0 : align_up((size_t)total, 256);
   void *tmp = nullptr;
-  CU(cudaMallocAsync(&tmp, b_desc + b_cnt + b_idx + b_sc + b_sel, c->aux));
+  CU(tmp_alloc(c, &tmp, b_desc + b_cnt + b_idx + b_sc + b_sel, c->aux));
   char *p = (char *)tmp;
   EvDesc *d_desc = (EvDesc *)p;
   int *d_cnt = (int *)(p + b_desc);
@@ -1102,7 +1109,7 @@ lst_status lst_get_ls_graph(lst_event ev, int32_t *row_off, int32_t *col, float 
   int32_t *d_row = row_off, *d_col = col;
   float *d_nf = node_feat, *d_ef = edge_feat;
   if (!dev_out) {
-    CU(cudaMallocAsync(&tmp, b_row + b_col + b_nf + b_ef + 1024, c->aux));
+    CU(tmp_alloc(c, &tmp, b_row + b_col + b_nf + b_ef + 1024, c->aux));
     char *p = (char *)tmp;
     d_row = (int32_t *)p; p += align_up(b_row, 256);
     d_col = (int32_t *)p; p += align_up(b_col, 256);
@@ -1150,7 +1157,7 @@ lst_status lst_get_t5_features(lst_event ev, float *feat, int64_t capacity, int6
     return LST_OK;
   }
   void *tmp = nullptr;
-  CU(cudaMallocAsync(&tmp, (size_t)n * NFEAT * 4, c->aux));
+  CU(tmp_alloc(c, &tmp, (size_t)n * NFEAT * 4, c->aux));
   k_features<<<grid, 128, 0, c->aux>>>(dd, c->g, c->cuts.k_field, (float *)tmp, (int)n);
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(feat, tmp, (size_t)n * NFEAT * 4, cudaMemcpyDeviceToHost, c->aux));
@@ -1260,7 +1267,7 @@ lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const fl
   // device copies of the descriptors and the per-event flags of the rounds
   const size_t b_p = align_up(sizeof(PixDesc) * (size_t)n, 256), b_d = align_up(sizeof(EvDesc) * (size_t)n, 256);
   void *tmp = nullptr;
-  CU(cudaMallocAsync(&tmp, b_p + b_d + 4 * (size_t)n, st));
+  CU(tmp_alloc(c, &tmp, b_p + b_d + 4 * (size_t)n, st));
   PixDesc *dP = (PixDesc *)tmp;
   EvDesc *dD = (EvDesc *)((char *)tmp + b_p);
   int *dflags = (int *)((char *)tmp + b_p + b_d);
