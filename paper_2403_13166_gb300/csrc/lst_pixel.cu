@@ -14,9 +14,10 @@
 // the minimum at both its ends, so the greedy pass takes it too); rounds repeat until none
 // is taken.
 //
-// Seeds are binned by the azimuth of H4 and their r-z slope; a warp per object scans the bins
-// of its windows (one contiguous run of azimuth bins per slope row), so a pair that passes
-// the window test is always met.
+// Seeds are binned by the azimuth of H4 and their r-z slope; a warp scans the bins of an
+// object's windows (one contiguous run of azimuth bins per slope row), so a pair that passes
+// the window test is always met. The seeds that the pT5s took are binned out before the T3
+// stage (they can match nothing there), which shrinks its windows about fivefold.
 #include "lst_internal.cuh"
 
 namespace lstk {
