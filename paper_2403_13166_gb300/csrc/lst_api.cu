@@ -42,7 +42,7 @@ __global__ void k_tc_count(const EvDesc *, int);
 __global__ void k_tc_scan(const EvDesc *);
 __global__ void k_tc_scatter(const EvDesc *, int);
 __global__ void k_tc_decide(const EvDesc *, int);
-__global__ void k_gather_tc(const EvDesc *, int, int *, int32_t *, float *, uint8_t *);
+__global__ void k_gather_tc(const EvDesc *, int, int *, int32_t *, float *, uint8_t *, int64_t);
 __global__ void k_graph_rows(const EvDesc *, int, int32_t *);
 __global__ void k_graph_fill(const EvDesc *, DevGeom, int, const int32_t *, int32_t *, float *, float *);
 cudaError_t launch_score_bf16_events(int, cudaStream_t, const EvDesc *, int, DevGeom, lst_cuts, const uint16_t *,
@@ -611,7 +611,7 @@ lst_status gather_tc(lst_ctx_s *c, const EvDesc *dd, int n_t5, int64_t n, int32_
   uint8_t *d_sel = dev_out ? selected : (uint8_t *)(d_sc + n);
   CU(cudaMemsetAsync(d_counter, 0, sizeof(int), c->aux));
   const int grid = (int)std::min<int64_t>((n_t5 + 255) / 256, 4 * c->n_sm);
-  if (grid > 0) k_gather_tc<<<grid, 256, 0, c->aux>>>(dd, n_t5, d_counter, d_idx, d_sc, d_sel);
+  if (grid > 0) k_gather_tc<<<grid, 256, 0, c->aux>>>(dd, n_t5, d_counter, d_idx, d_sc, d_sel, n);
   CU(cudaGetLastError());
   if (!dev_out) {
     CU(cudaMemcpyAsync(hit_idx, d_idx, (size_t)n * 40, cudaMemcpyDeviceToHost, c->aux));
@@ -1067,7 +1067,7 @@ lst_status lst_get_candidates_batch(const lst_event *evs, int32_t n, int32_t kin
     if (kind == LST_TC) {
       const int n5 = c->slots[evs[i]->slot].cnt[C_T5];
       const int grid = (int)std::min<int64_t>((n5 + 255) / 256, 4 * c->n_sm);
-      k_gather_tc<<<std::max(grid, 1), 256, 0, c->aux>>>(d_desc + i, n5, d_cnt + i, o, sc, se);
+      k_gather_tc<<<std::max(grid, 1), 256, 0, c->aux>>>(d_desc + i, n5, d_cnt + i, o, sc, se, k);
     } else {
       const int grid = (int)std::min<int64_t>((k + 255) / 256, 4 * c->n_sm);
       k_gather<<<grid, 256, 0, c->aux>>>(d_desc + i, kind, (int)k, o, sc, se);

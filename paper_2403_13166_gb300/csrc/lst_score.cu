@@ -194,9 +194,11 @@ __global__ void k_gather(const EvDesc *__restrict__ ev_p, int kind, int n, int32
 }
 
 // Hit-index tuples, scores and selection flags of the track candidates of one event, in
-// no particular order (counter: one int on the device, zeroed by the caller).
+// no particular order (counter: one int on the device, zeroed by the caller; cap: the rows
+// the output holds, the event's candidate count: a row past it is not written, so a counter
+// that did not start at zero can never send a write out of the buffer).
 __global__ void k_gather_tc(const EvDesc *__restrict__ ev_p, int n_t5, int *counter, int32_t *out, float *score,
-                            uint8_t *sel) {
+                            uint8_t *sel, int64_t cap) {
   const EvDesc &ev = *ev_p;
   const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_t5; base += gridDim.x * blockDim.x) {
@@ -206,8 +208,8 @@ __global__ void k_gather_tc(const EvDesc *__restrict__ ev_p, int n_t5, int *coun
     int o0 = 0;
     if (lane == 0 && bal) o0 = atomicAdd(counter, __popc(bal));
     o0 = __shfl_sync(FULL, o0, 0);
-    if (keep) {
-      const int o = o0 + __popc(bal & lanemask_lt());
+    const int o = o0 + __popc(bal & lanemask_lt());
+    if (keep && o >= 0 && o < cap) {
       const int4 a = ev.t5_a[t], b = ev.t5_b[t];
       const int md[5] = {a.x, a.y, a.z, a.w, b.x};
 #pragma unroll
