@@ -393,9 +393,10 @@ lst_status lst_match_pixel_seeds(lst_event ev, const float *seeds, int64_t n_see
 
 /* The same for n events of one context at once (distinct events; the results are those of
  * n single calls): seeds[i], n_seeds[i] belong to evs[i]; counts, if not NULL, has n
- * entries. One launch per kernel and round covers all n events, and the host waits once
- * per round for the whole batch (an event whose round took no pair is done with the
- * stage). n within 1..max_events, else LST_ERR_ARG. */
+ * entries. One launch per kernel and round covers all n events; rounds go out three at a
+ * time and the host then waits once for the whole batch (an event whose round took no pair
+ * is done with the stage, and its later rounds return at once). n within 1..max_events,
+ * else LST_ERR_ARG. */
 lst_status lst_match_pixel_seeds_batch(const lst_event *evs, int32_t n, const float *const *seeds,
                                        const int64_t *n_seeds, const lst_pixel_cuts *pc,
                                        lst_pixel_counts *counts);
