@@ -344,6 +344,16 @@ bool injected_alloc_failure(lst_ctx_s *c) {
   return false;
 }
 
+// Short-lived device staging of the exports and the pixel matching, from the context's own
+// pool: its freed blocks stay reserved (release threshold: never), so a call does not map
+// new memory each time (the device's default pool hands freed memory back at every
+// synchronisation, and the next call maps it again while the driver holds its locks).
+// Every kernel that writes such staging either writes the same values on every run or
+// bounds its writes (a profiler replay may not restore pool memory between its passes).
+cudaError_t tmp_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+}
+
 // Device buffers of a slot. The serving workers take them from the context's stream-ordered
 // pool (pooled): the slot is idle when it grows (its last launch was harvested when its
 // event was released and every export synchronises before it returns), so the old buffers
@@ -351,13 +361,6 @@ bool injected_alloc_failure(lst_ctx_s *c) {
 // stream of the slot's next launch, without waiting for the device. The other callers use
 // plain allocations, after a device synchronisation when a buffer is replaced (a profiler
 // replaying kernels saves and restores those, which it may not do for pool memory).
-// Short-lived device staging of the exports and the pixel matching, from the context's own
-// pool: its freed blocks stay reserved (release threshold: never), so a call does not map
-// new memory each time (the device's default pool hands freed memory back at every
-// synchronisation, and the next call maps it again while the driver holds its locks).
-cudaError_t tmp_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st) {
-  return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
-}
 cudaError_t slot_buf_alloc(lst_ctx_s *c, void **p, size_t bytes, cudaStream_t st, bool pooled) {
   return pooled ? cudaMallocFromPoolAsync(p, bytes, c->pool, st) : cudaMalloc(p, bytes);
 }
