@@ -702,7 +702,7 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the launch-shape autotuner (default: tune once per GPU and workload)")
     ap.add_argument("--skip-served", action="store_true")
-    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 4000, 5000, 6000])
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[100, 500, 1000, 2000, 3000, 4000, 5000, 6000, 7000])
     ap.add_argument("--served-seconds", type=float, default=3.0)
     ap.add_argument("--served-pool", type=int, default=48)
     ap.add_argument("--served-mem-gb", type=float, default=16.0)
