@@ -876,16 +876,16 @@ __global__ void __launch_bounds__(256, 4) k_t3(const EvDesc *__restrict__ evs, i
     const int m0 = (u - s_pref[e]) * mdu;
     const int m = m0 + lane;
     int nI = 0, nO = 0, sI = 0, sO = 0;
-    if (lane < mdu && m < nmd) {
+    float4 P1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < mdu && m < nmd) {                 // the anchor with the counts: one round trip
       nI = ev.lso_cnt[m];
       nO = ev.ls_cnt[m];
       sI = ev.lso_start[m];
       sO = ev.ls_start[m];
+      P1 = ev.md_anchor[m];
     }
     const int np = nI * nO;
     if (np == 0) nI = nO = 0;
-    float4 P1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (np) P1 = ev.md_anchor[m];
     const int incI = warp_incl_scan(nI), incO = warp_incl_scan(nO), incP = warp_incl_scan(np);
     __syncwarp();                                  // the previous unit's table readers are done
     w.ioff[lane] = incI - nI;
